@@ -1,0 +1,196 @@
+/*
+ * pinnlbm.h - C ABI of the GB300 (sm_103a) PINN-LBM droplet hot path.
+ *
+ * Method: arXiv 2504.10539, "Physics-Informed Neural Networks for Enhanced
+ * Interface Preservation in Lattice Boltzmann Multiphase Simulations".
+ *   - lattice update: Sec. II-A, Eq. 1 (D2Q9 pseudopotential lattice,
+ *     psi = rho0 (1 - exp(-rho/rho0)), Shan-Chen force, force-shifted
+ *     equilibrium, BGK collision, periodic streaming);
+ *   - network N(x, y) -> (rho, u_x, u_y): Sec. II-B Eq. 2, architecture Sec. III-B;
+ *   - coupling / correction: Sec. II-C (correct "with emphasis on interface
+ *     regions", at an adaptive, not per-step, frequency);
+ *   - metrics: Sec. II-D Eqs. 9-13, discretised in Sec. IV-E Eqs. 14-16;
+ *   - droplet set-up: Sec. III-A.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: PL_OK (0) or a negative PL_ERR_*.
+ *     No C++ exception crosses this boundary.  A call that fails with
+ *     PL_ERR_INVALID_ARG or PL_ERR_STATE has changed nothing.
+ *   - The CALLER owns all device memory.  pl_lattice_bytes() says how many
+ *     bytes a lattice needs; the caller allocates them (e.g. a torch uint8
+ *     tensor on the GPU) and passes the pointer to pl_lattice_create(), which
+ *     carves it up and never allocates device memory itself.  The pointer must
+ *     be 256-byte aligned and stay valid until pl_destroy().
+ *   - The CALLER owns the stream (a cudaStream_t passed as void*; NULL = the
+ *     legacy default stream).  All work is enqueued on it asynchronously,
+ *     except the calls documented as synchronising (pl_metrics, pl_get_*,
+ *     pl_lattice_status), which wait for that stream.
+ *   - Host pointers passed in are only read during the call; the library keeps
+ *     its own copies where it needs the data later.
+ *   - The library owns the opaque handle (host memory), freed by pl_destroy().
+ *   - Population exchange format (pl_get_state / pl_set_state): FP64, layout
+ *     f[i][y][x] (i = 0..8 direction-major, x fastest), with the D2Q9 order
+ *     c_0=(0,0), c_1..4=(1,0),(0,1),(-1,0),(0,-1), c_5..8=(1,1),(-1,1),(-1,-1),(1,-1).
+ */
+#ifndef PINNLBM_H
+#define PINNLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PL_API __attribute__((visibility("default")))
+#else
+#define PL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PL_OK 0
+#define PL_ERR_INVALID_ARG (-1) /* bad pointer, size, enum or value                 */
+#define PL_ERR_CUDA (-2)        /* a CUDA runtime call failed; see pl_last_cuda_error */
+#define PL_ERR_BUDGET (-3)      /* not enough caller memory / device budget           */
+#define PL_ERR_NONPHYSICAL (-4) /* correction would give rho <= 0 or non-finite state */
+#define PL_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up                 */
+#define PL_ERR_STATE (-6)       /* call not valid in the handle's current state       */
+
+/* Population storage (bytes per population: 8, 4, 2). */
+#define PL_F64 0        /* FP64 storage, FP64 arithmetic                          */
+#define PL_F32 1        /* FP32 storage, FP32 arithmetic                          */
+#define PL_F16_OFFSET 2 /* FP16 storage of f_i - w_i*rho_ref, FP32 arithmetic     */
+
+/* Network arithmetic for the correction. */
+#define PL_MLP_F64 0  /* FP64 on CUDA cores                                        */
+#define PL_MLP_F32 1  /* FP32 on CUDA cores                                        */
+#define PL_MLP_BF16 2 /* BF16 operands on tcgen05 tensor cores, FP32 accumulation  */
+
+#define PL_MAX_DROPLETS 4096
+
+/* Lattice parameters.  G, tau, rho0: Sec. II-A / Sec. III-A (the paper's g and tau);
+ * rho_ref: reference density of the FP16-offset storage (ignored otherwise);
+ * beta_rho, beta_u: gains of the interface correction; threshold: the
+ * |grad rho| threshold of the interface width W (Eq. 9; the paper uses 0.01). */
+typedef struct pl_params {
+    int32_t nx, ny;   /* lattice size, each >= 1, nx*ny < 2^31                  */
+    int32_t storage;  /* PL_F64 / PL_F32 / PL_F16_OFFSET                        */
+    int32_t mlp;      /* PL_MLP_*                                               */
+    double G;         /* interaction strength (< 0 attracts); the paper: -5.5   */
+    double tau;       /* BGK relaxation time, > 0.5; the paper: 1.0             */
+    double rho0;      /* pseudopotential scale, > 0                             */
+    double rho_ref;   /* FP16-offset reference density                          */
+    double beta_rho;  /* correction gain on density  (default 0.1)              */
+    double beta_u;    /* correction gain on momentum (default 0.01)             */
+    double threshold; /* Eq. 9 gradient threshold    (default 0.01)             */
+} pl_params;
+
+/* One droplet of the initial state: centre (cx, cy) in lattice units, radius r. */
+typedef struct pl_droplet {
+    double cx, cy, r;
+} pl_droplet;
+
+/* Metric record (FP64).  Eqs. 9-15 plus the mass and the Laplace measurement
+ * about the droplet's centre (NaN unless the lattice was initialised from
+ * exactly one droplet). */
+typedef struct pl_metric_record {
+    double mass;      /* sum of rho over the lattice                         */
+    double W;         /* Eq. 9:  fraction of cells with |grad rho| > threshold */
+    double G_max;     /* Eq. 10: max |grad rho|                               */
+    double delta_rho; /* Eq. 11: rho_max - rho_min                            */
+    double W_eff;     /* Eq. 12/14: sum|grad rho| / (G_max * N); 0 if G_max=0 */
+    double E_int;     /* Eq. 13/15: sum |grad rho|^2 (dx = dy = 1)            */
+    double rho_max, rho_min, sum_g, sum_g2;
+    int64_t count;    /* cells with |grad rho| > threshold                    */
+    double R_eq, rho_in, rho_out, p_in, p_out, dP; /* Laplace measurement      */
+    double mass0;     /* reference mass M0 of the correction's projection     */
+    int64_t step;     /* time steps taken since initialisation                */
+    int32_t status;   /* PL_OK, or the lattice's sticky error (e.g. NONPHYSICAL) */
+    int32_t corrections; /* corrections applied so far                        */
+} pl_metric_record;
+
+typedef struct pl_lattice pl_lattice;
+
+/* Status text (static string, never NULL). */
+PL_API const char* pl_status_string(int status);
+/* cudaError_t value of the most recent failing CUDA call in this thread (0 if none). */
+PL_API int pl_last_cuda_error(void);
+/* Number of CUDA kernels this library has launched in this process (a graph
+ * replay counts each of its kernel nodes), for launch accounting. */
+PL_API int pl_kernel_launches(int64_t* out);
+/* Fill p with the defaults: storage F32, mlp BF16, G=-5.5, tau=1, rho0=1,
+ * rho_ref=1.075, beta_rho=0.1, beta_u=0.01, threshold=0.01, size nx x ny. */
+PL_API int pl_params_default(pl_params* p, int32_t nx, int32_t ny);
+
+/* Bytes of caller device memory one lattice with these parameters needs. */
+PL_API int pl_lattice_bytes(const pl_params* p, size_t* bytes_out);
+
+/* Create a lattice over caller memory dev_mem[0, bytes) (>= pl_lattice_bytes,
+ * 256-byte aligned) that enqueues on `stream`.  No device work is done. */
+PL_API int pl_lattice_create(const pl_params* p, void* dev_mem, size_t bytes, void* stream, pl_lattice** out);
+
+/* Initial state (Sec. III-A): rho = rho_out + (rho_in - rho_out) * max_k 1/2 (1 - tanh((d_k - r_k)/width))
+ * + noise_amp * (2 U - 1), d_k the periodic minimum-image distance from cell (x, y)
+ * to droplet k, U = SplitMix64 uniform of output index y*nx + x for `seed`;
+ * u = 0, f_i = w_i rho.  n in [0, PL_MAX_DROPLETS].  Resets the step count, the
+ * correction count and the status, and records M0 = mass of the stored state. */
+PL_API int pl_lattice_init_droplets(pl_lattice* lat, const pl_droplet* droplets, int n, double rho_in,
+                             double rho_out, double width, double noise_amp, uint64_t seed);
+
+/* Initial state from a host density field rho[y][x] (FP64, nx*ny values): f_i = w_i rho. */
+PL_API int pl_lattice_init_rho(pl_lattice* lat, const double* host_rho);
+
+/* Network weights (Sec. III-B, 2 -> 64 -> 128 -> 128 -> 64 -> 3, tanh hidden, linear output):
+ * FP32 blob W1[64x2] b1[64] W2[128x64] b2[128] W3[128x128] b3[128] W4[64x128] b4[64] W5[3x64] b5[3],
+ * row-major W[out][in]; n must equal pl_mlp_blob_size().  Copied to the device
+ * (and converted to the tensor-core operand layout) on the lattice's stream. */
+PL_API int pl_mlp_blob_size(void);
+PL_API int pl_set_mlp_weights(pl_lattice* lat, const float* host_blob, size_t n);
+
+/* n >= 0 time steps of Eq. 1 on the device (no host synchronisation). */
+PL_API int pl_step(pl_lattice* lat, int32_t n);
+
+/* One interface correction (Sec. II-C step 3), all on the device:
+ *   g = |grad rho| (Eq. 16), m = g / max g, (rho^, u^) = N(x^, y^) at the cell
+ *   centre mapped to [-1, 1]; drho = beta_rho m (rho^ - rho) projected so that
+ *   the total mass returns to M0; dj = beta_u m (rho' u^ - j) projected to keep
+ *   the total momentum; f_i += f_i^eq(rho', u') - f_i^eq(rho, u) where m > 0.
+ * If any corrected density would be <= 0 or non-finite, the state is left
+ * unchanged and the lattice's status becomes PL_ERR_NONPHYSICAL (read it with
+ * pl_lattice_status or pl_metrics).  Requires weights (PL_ERR_STATE otherwise). */
+PL_API int pl_apply_correction(pl_lattice* lat);
+
+/* Coupled run (Sec. II-C): nsteps time steps; after every step whose count
+ * (since initialisation) is a multiple of K (K > 0) a correction is applied.
+ * K = 0 runs pure LBM.  The step/correction sequence is captured once in a
+ * CUDA graph per (K, buffer parity) and replayed. */
+PL_API int pl_run(pl_lattice* lat, int32_t nsteps, int32_t K);
+
+/* Metrics of the current state (Eqs. 9-16, mass, Laplace).  Synchronises the stream. */
+PL_API int pl_metrics(pl_lattice* lat, pl_metric_record* out);
+
+/* Density field rho[y][x] (FP64, nx*ny values) of the current state.  Synchronises. */
+PL_API int pl_get_rho(pl_lattice* lat, double* host_rho);
+
+/* Network field N(x^, y^) at every cell centre (the tensor used by the correction):
+ * host_out3[3][ny][nx] = (rho^, u^_x, u^_y), FP64.  Requires weights.  Synchronises. */
+PL_API int pl_get_mlp_field(pl_lattice* lat, double* host_out3);
+
+/* Checkpoint: the current populations in the exchange format (9*nx*ny FP64) and
+ * the step count.  pl_get_state synchronises; pl_set_state encodes into the
+ * lattice's storage type (rounding for F32/F16) and sets the step count. */
+PL_API int pl_get_state(pl_lattice* lat, double* host_f, int64_t* step);
+PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
+
+/* Sticky lattice status (PL_OK or the first device-detected error).  Synchronises. */
+PL_API int pl_lattice_status(pl_lattice* lat);
+
+/* Free the handle; the caller's device memory is not touched. */
+PL_API int pl_destroy(pl_lattice* lat);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PINNLBM_H */

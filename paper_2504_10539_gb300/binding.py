@@ -1,0 +1,312 @@
+"""ctypes binding of ``libpinnlbm.so`` (C ABI in include/pinnlbm.h).
+
+Argument marshalling only: each ``pl_*`` function here calls the C function of
+the same name and raises :class:`PLError` on a non-zero status.  Every step of
+the hot path runs in the library's CUDA kernels; if the library has not been
+built this module raises instead of computing anything another way.
+
+``Lattice`` is a convenience owner: it allocates the caller-side device buffer
+with torch (device memory and streams are the only things torch provides) and
+keeps the handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpinnlbm.so")
+
+PL_OK = 0
+PL_ERR_INVALID_ARG = -1
+PL_ERR_CUDA = -2
+PL_ERR_BUDGET = -3
+PL_ERR_NONPHYSICAL = -4
+PL_ERR_TIMEOUT = -5
+PL_ERR_STATE = -6
+
+PL_F64, PL_F32, PL_F16_OFFSET = 0, 1, 2
+PL_MLP_F64, PL_MLP_F32, PL_MLP_BF16 = 0, 1, 2
+PL_MAX_DROPLETS = 4096
+
+
+class pl_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("mlp", ctypes.c_int32), ("G", ctypes.c_double), ("tau", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("rho_ref", ctypes.c_double), ("beta_rho", ctypes.c_double),
+                ("beta_u", ctypes.c_double), ("threshold", ctypes.c_double)]
+
+
+class pl_droplet(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("r", ctypes.c_double)]
+
+
+class pl_metric_record(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("W", ctypes.c_double), ("G_max", ctypes.c_double),
+                ("delta_rho", ctypes.c_double), ("W_eff", ctypes.c_double), ("E_int", ctypes.c_double),
+                ("rho_max", ctypes.c_double), ("rho_min", ctypes.c_double), ("sum_g", ctypes.c_double),
+                ("sum_g2", ctypes.c_double), ("count", ctypes.c_int64), ("R_eq", ctypes.c_double),
+                ("rho_in", ctypes.c_double), ("rho_out", ctypes.c_double), ("p_in", ctypes.c_double),
+                ("p_out", ctypes.c_double), ("dP", ctypes.c_double), ("mass0", ctypes.c_double),
+                ("step", ctypes.c_int64), ("status", ctypes.c_int32), ("corrections", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PLError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        msg = "%s failed: %s (%d)" % (fn, pl_status_string(status), status)
+        if status == PL_ERR_CUDA:
+            msg += ", cudaError %d" % _L().pl_last_cuda_error()
+        super().__init__(msg)
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpinnlbm.so is not built (expected at %s); run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u64, d, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                    ctypes.c_double, ctypes.c_size_t)
+        P = ctypes.POINTER
+        sigs = {
+            "pl_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "pl_last_cuda_error": (ctypes.c_int, []),
+            "pl_kernel_launches": (ctypes.c_int, [P(i64)]),
+            "pl_params_default": (ctypes.c_int, [P(pl_params), i32, i32]),
+            "pl_lattice_bytes": (ctypes.c_int, [P(pl_params), P(sz)]),
+            "pl_lattice_create": (ctypes.c_int, [P(pl_params), vp, sz, vp, P(vp)]),
+            "pl_lattice_init_droplets": (ctypes.c_int, [vp, P(pl_droplet), ctypes.c_int, d, d, d, d, u64]),
+            "pl_lattice_init_rho": (ctypes.c_int, [vp, P(d)]),
+            "pl_mlp_blob_size": (ctypes.c_int, []),
+            "pl_set_mlp_weights": (ctypes.c_int, [vp, P(ctypes.c_float), sz]),
+            "pl_step": (ctypes.c_int, [vp, i32]),
+            "pl_apply_correction": (ctypes.c_int, [vp]),
+            "pl_run": (ctypes.c_int, [vp, i32, i32]),
+            "pl_metrics": (ctypes.c_int, [vp, P(pl_metric_record)]),
+            "pl_get_rho": (ctypes.c_int, [vp, P(d)]),
+            "pl_get_mlp_field": (ctypes.c_int, [vp, P(d)]),
+            "pl_get_state": (ctypes.c_int, [vp, P(d), P(i64)]),
+            "pl_set_state": (ctypes.c_int, [vp, P(d), i64]),
+            "pl_lattice_status": (ctypes.c_int, [vp]),
+            "pl_destroy": (ctypes.c_int, [vp]),
+        }
+        for name, (res, args) in sigs.items():
+            if hasattr(L, name):
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def lib():
+    return _L()
+
+
+def _chk(fn, st):
+    if st != PL_OK:
+        raise PLError(fn, st)
+    return st
+
+
+def _dptr(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ----------------------------------------------------------------------------- C ABI, one wrapper per call
+
+def pl_status_string(status: int) -> str:
+    return _L().pl_status_string(status).decode()
+
+
+def pl_last_cuda_error() -> int:
+    return _L().pl_last_cuda_error()
+
+
+def pl_kernel_launches() -> int:
+    n = ctypes.c_int64()
+    _chk("pl_kernel_launches", _L().pl_kernel_launches(ctypes.byref(n)))
+    return n.value
+
+
+def pl_params_default(nx: int, ny: int, **kw) -> pl_params:
+    p = pl_params()
+    _chk("pl_params_default", _L().pl_params_default(ctypes.byref(p), nx, ny))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def pl_lattice_bytes(p: pl_params) -> int:
+    n = ctypes.c_size_t()
+    _chk("pl_lattice_bytes", _L().pl_lattice_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def pl_lattice_create(p: pl_params, dev_ptr: int, nbytes: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _chk("pl_lattice_create", _L().pl_lattice_create(ctypes.byref(p), ctypes.c_void_p(dev_ptr), nbytes,
+                                                      ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def pl_lattice_init_droplets(h, droplets: Sequence, rho_in, rho_out, width, noise_amp, seed):
+    n = len(droplets)
+    arr = (pl_droplet * max(n, 1))(*[pl_droplet(*map(float, d)) for d in droplets])
+    return _chk("pl_lattice_init_droplets", _L().pl_lattice_init_droplets(
+        ctypes.c_void_p(h), arr, n, rho_in, rho_out, width, noise_amp, seed & (2 ** 64 - 1)))
+
+
+def pl_lattice_init_rho(h, rho: np.ndarray):
+    r = np.ascontiguousarray(rho, dtype=np.float64)
+    return _chk("pl_lattice_init_rho", _L().pl_lattice_init_rho(ctypes.c_void_p(h), _dptr(r)))
+
+
+def pl_mlp_blob_size() -> int:
+    return _L().pl_mlp_blob_size()
+
+
+def pl_set_mlp_weights(h, blob: np.ndarray):
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    return _chk("pl_set_mlp_weights", _L().pl_set_mlp_weights(
+        ctypes.c_void_p(h), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+
+
+def pl_step(h, n: int):
+    return _chk("pl_step", _L().pl_step(ctypes.c_void_p(h), n))
+
+
+def pl_apply_correction(h):
+    return _chk("pl_apply_correction", _L().pl_apply_correction(ctypes.c_void_p(h)))
+
+
+def pl_run(h, nsteps: int, K: int):
+    return _chk("pl_run", _L().pl_run(ctypes.c_void_p(h), nsteps, K))
+
+
+def pl_metrics(h) -> dict:
+    m = pl_metric_record()
+    _chk("pl_metrics", _L().pl_metrics(ctypes.c_void_p(h), ctypes.byref(m)))
+    return m.as_dict()
+
+
+def pl_get_rho(h, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((ny, nx), dtype=np.float64)
+    _chk("pl_get_rho", _L().pl_get_rho(ctypes.c_void_p(h), _dptr(out)))
+    return out
+
+
+def pl_get_mlp_field(h, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((3, ny, nx), dtype=np.float64)
+    _chk("pl_get_mlp_field", _L().pl_get_mlp_field(ctypes.c_void_p(h), _dptr(out)))
+    return out
+
+
+def pl_get_state(h, nx: int, ny: int):
+    out = np.empty((9, ny, nx), dtype=np.float64)
+    step = ctypes.c_int64()
+    _chk("pl_get_state", _L().pl_get_state(ctypes.c_void_p(h), _dptr(out), ctypes.byref(step)))
+    return out, step.value
+
+
+def pl_set_state(h, f: np.ndarray, step: int = 0):
+    a = np.ascontiguousarray(f, dtype=np.float64)
+    return _chk("pl_set_state", _L().pl_set_state(ctypes.c_void_p(h), _dptr(a), step))
+
+
+def pl_lattice_status(h) -> int:
+    return _L().pl_lattice_status(ctypes.c_void_p(h))
+
+
+def pl_destroy(h):
+    return _chk("pl_destroy", _L().pl_destroy(ctypes.c_void_p(h)))
+
+
+# ----------------------------------------------------------------------------- owner of one lattice
+
+class Lattice:
+    """One lattice over a torch-allocated device buffer, enqueuing on a torch stream."""
+
+    def __init__(self, params: pl_params, device: str = "cuda", stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.nbytes = pl_lattice_bytes(params)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+        # a stream of its own (capturable into CUDA graphs, unlike the legacy default stream);
+        # the buffer's allocation is ordered before any work on it
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.mem.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.mem.device))
+        self.h = pl_lattice_create(params, self.mem.data_ptr(), self.nbytes, self.stream.cuda_stream)
+
+    @classmethod
+    def from_workload(cls, job, device="cuda", stream=None):
+        """Build, initialise and load weights for a ``workloads.Lattice`` description."""
+        p = pl_params_default(job.nx, job.ny, storage=job.storage, mlp=job.mlp, G=job.G, tau=job.tau,
+                              rho0=job.rho0, rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u)
+        lat = cls(p, device=device, stream=stream)
+        lat.init_droplets(job.droplets, job.rho_in, job.rho_out, job.width, job.noise_amp, job.seed)
+        if job.K > 0:
+            lat.set_weights(job.weights())
+        return lat
+
+    def init_droplets(self, droplets, rho_in, rho_out, width, noise_amp, seed):
+        pl_lattice_init_droplets(self.h, droplets, rho_in, rho_out, width, noise_amp, seed)
+
+    def init_rho(self, rho):
+        pl_lattice_init_rho(self.h, rho)
+
+    def set_weights(self, blob):
+        pl_set_mlp_weights(self.h, blob)
+
+    def step(self, n):
+        pl_step(self.h, n)
+
+    def correct(self):
+        pl_apply_correction(self.h)
+
+    def run(self, nsteps, K):
+        pl_run(self.h, nsteps, K)
+
+    def metrics(self):
+        return pl_metrics(self.h)
+
+    def rho(self):
+        return pl_get_rho(self.h, self.nx, self.ny)
+
+    def mlp_field(self):
+        return pl_get_mlp_field(self.h, self.nx, self.ny)
+
+    def state(self):
+        return pl_get_state(self.h, self.nx, self.ny)
+
+    def set_state(self, f, step=0):
+        pl_set_state(self.h, f, step)
+
+    def status(self):
+        return pl_lattice_status(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,110 @@
+// Correction network on CUDA cores (FP64 or FP32), arXiv 2504.10539 Sec. II-B
+// Eq. 2 and Sec. III-B: N(x, y) = (rho^, u^_x, u^_y), 2 -> 64 -> 128 -> 128 -> 64 -> 3,
+// tanh on the hidden layers, linear output.  Input: the cell centre mapped to
+// [-1, 1] (x^ = 2 (x + 0.5) / nx - 1).
+//
+// One thread per cell.  Activations live in shared memory, feature-major
+// ([feature][thread]) so that a warp's accesses are consecutive; each thread
+// accumulates 16 outputs at a time in registers while the weights (the same
+// for every thread) are broadcast from the read-only cache.
+#include "pl_device.cuh"
+#include "pl_kernels.h"
+
+namespace pl {
+
+constexpr int MLP_THREADS = 64;
+constexpr int MLP_CHUNK = 16;
+
+template <typename R>
+__device__ __forceinline__ R act_tanh(R z);
+template <>
+__device__ __forceinline__ float act_tanh<float>(float z) { return tanhf(z); }
+template <>
+__device__ __forceinline__ double act_tanh<double>(double z) { return tanh(z); }
+
+// One dense layer in -> out for this thread's cell: dst[o] = act(sum_k W[o][k] src[k] + b[o]).
+template <typename R, bool TANH>
+__device__ __forceinline__ void dense(const float* __restrict__ W, const float* __restrict__ b, int nin, int nout,
+                                      const R* src, R* dst, int t) {
+    for (int o0 = 0; o0 < nout; o0 += MLP_CHUNK) {
+        R acc[MLP_CHUNK];
+#pragma unroll
+        for (int j = 0; j < MLP_CHUNK; ++j) acc[j] = (o0 + j < nout) ? R(__ldg(b + o0 + j)) : R(0);
+        for (int k = 0; k < nin; ++k) {
+            const R a = src[k * MLP_THREADS + t];
+#pragma unroll
+            for (int j = 0; j < MLP_CHUNK; ++j)
+                if (o0 + j < nout) acc[j] += R(__ldg(W + (o0 + j) * nin + k)) * a;
+        }
+#pragma unroll
+        for (int j = 0; j < MLP_CHUNK; ++j)
+            if (o0 + j < nout) dst[(o0 + j) * MLP_THREADS + t] = TANH ? act_tanh<R>(acc[j]) : acc[j];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restrict__ w, int nx, int ny,
+                                                          R* __restrict__ out3) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* bufA = reinterpret_cast<R*>(smem_raw);     // [128][MLP_THREADS]
+    R* bufB = bufA + 128 * MLP_THREADS;            // [128][MLP_THREADS]
+    const long long N = (long long)nx * ny;
+    const int t = threadIdx.x;
+    // blob offsets
+    const float* W1 = w;
+    const float* b1 = W1 + 64 * 2;
+    const float* W2 = b1 + 64;
+    const float* b2 = W2 + 128 * 64;
+    const float* W3 = b2 + 128;
+    const float* b3 = W3 + 128 * 128;
+    const float* W4 = b3 + 128;
+    const float* b4 = W4 + 64 * 128;
+    const float* W5 = b4 + 64;
+    const float* b5 = W5 + 3 * 64;
+    for (long long base = (long long)blockIdx.x * MLP_THREADS; base < N; base += (long long)gridDim.x * MLP_THREADS) {
+        const long long c = base + t;
+        const long long cc = c < N ? c : N - 1;
+        const int x = (int)(cc % nx), y = (int)(cc / nx);
+        bufA[0 * MLP_THREADS + t] = R(2) * (R(x) + R(0.5)) / R(nx) - R(1);
+        bufA[1 * MLP_THREADS + t] = R(2) * (R(y) + R(0.5)) / R(ny) - R(1);
+        dense<R, true>(W1, b1, 2, 64, bufA, bufB, t);
+        dense<R, true>(W2, b2, 64, 128, bufB, bufA, t);
+        dense<R, true>(W3, b3, 128, 128, bufA, bufB, t);
+        dense<R, true>(W4, b4, 128, 64, bufB, bufA, t);
+        dense<R, false>(W5, b5, 64, 3, bufA, bufB, t);
+        if (c < N) {
+            out3[c] = bufB[0 * MLP_THREADS + t];
+            out3[N + c] = bufB[1 * MLP_THREADS + t];
+            out3[2 * N + c] = bufB[2 * MLP_THREADS + t];
+        }
+    }
+}
+
+template <typename R>
+static cudaError_t mlp_simt_t(const LatticeView& v, cudaStream_t s) {
+    const size_t smem = 2 * 128 * MLP_THREADS * sizeof(R);
+    static bool attr_set = false;  // per-process, per-instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long N = (long long)v.nx * v.ny;
+    long long blocks = (N + MLP_THREADS - 1) / MLP_THREADS;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_mlp_simt<R><<<(int)blocks, MLP_THREADS, smem, s>>>(v.w32, v.nx, v.ny, static_cast<R*>(v.out3));
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_simt(const LatticeView& v, int mlp_mode, cudaStream_t s) {
+    // The output element type follows the lattice's scratch type.
+    if (v.storage == PL_F64) {
+        if (mlp_mode != PL_MLP_F64) return cudaErrorInvalidValue;
+        return mlp_simt_t<double>(v, s);
+    }
+    if (mlp_mode != PL_MLP_F32) return cudaErrorInvalidValue;
+    return mlp_simt_t<float>(v, s);
+}
+
+}  // namespace pl

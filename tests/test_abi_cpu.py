@@ -1,0 +1,100 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function the
+header declares, and the host-only calls behave as documented."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import build as pkg_build
+from paper_2504_10539_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return B.lib()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^PL_API\s+[\w\s\*]+?\b(pl_\w+)\s*\(", src, flags=re.M))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("pl_lattice_bytes", "pl_lattice_create", "pl_lattice_init_droplets", "pl_step",
+                 "pl_apply_correction", "pl_metrics", "pl_destroy", "pl_run", "pl_set_mlp_weights"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for st in (B.PL_OK, B.PL_ERR_INVALID_ARG, B.PL_ERR_CUDA, B.PL_ERR_BUDGET, B.PL_ERR_NONPHYSICAL,
+               B.PL_ERR_TIMEOUT, B.PL_ERR_STATE):
+        assert B.pl_status_string(st) != "unknown status"
+    assert B.pl_status_string(12345) == "unknown status"
+
+
+def test_blob_size_agrees_everywhere(lib):
+    assert B.pl_mlp_blob_size() == wl.mlp_blob_size() == O.mlp_blob_size() == 33475
+
+
+def test_params_default_and_bytes(lib):
+    p = B.pl_params_default(64, 48)
+    assert (p.nx, p.ny, p.storage, p.mlp) == (64, 48, B.PL_F32, B.PL_MLP_BF16)
+    assert p.G == -5.5 and p.tau == 1.0 and p.threshold == 0.01
+    n32 = B.pl_lattice_bytes(p)
+    assert n32 >= 2 * 9 * 64 * 48 * 4
+    p.storage = B.PL_F16_OFFSET
+    n16 = B.pl_lattice_bytes(p)
+    assert 2 * 9 * 64 * 48 * 2 <= n16 < n32
+    p.storage, p.mlp = B.PL_F64, B.PL_MLP_F64
+    assert B.pl_lattice_bytes(p) > n32
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("ny", -3), ("tau", 0.5), ("tau", float("nan")),
+                                         ("rho0", 0.0), ("storage", 7), ("mlp", 9), ("G", float("inf"))])
+def test_invalid_params_rejected(lib, field, value):
+    p = B.pl_params_default(16, 16)
+    setattr(p, field, value)
+    n = ctypes.c_size_t()
+    assert lib.pl_lattice_bytes(ctypes.byref(p), ctypes.byref(n)) == B.PL_ERR_INVALID_ARG
+
+
+def test_f64_storage_needs_f64_network(lib):
+    p = B.pl_params_default(16, 16, storage=B.PL_F64)   # mlp stays BF16
+    n = ctypes.c_size_t()
+    assert lib.pl_lattice_bytes(ctypes.byref(p), ctypes.byref(n)) == B.PL_ERR_INVALID_ARG
+
+
+def test_create_rejects_bad_buffers_without_touching_the_device(lib):
+    p = B.pl_params_default(16, 16)
+    need = B.pl_lattice_bytes(p)
+    h = ctypes.c_void_p()
+    # NULL buffer, misaligned buffer, too small buffer
+    assert lib.pl_lattice_create(ctypes.byref(p), None, need, None, ctypes.byref(h)) == B.PL_ERR_INVALID_ARG
+    assert lib.pl_lattice_create(ctypes.byref(p), ctypes.c_void_p(0x1000 + 8), need, None,
+                                 ctypes.byref(h)) == B.PL_ERR_INVALID_ARG
+    assert lib.pl_lattice_create(ctypes.byref(p), ctypes.c_void_p(0x1000), need - 1, None,
+                                 ctypes.byref(h)) == B.PL_ERR_BUDGET
+
+
+def test_null_handle_rejected(lib):
+    for name in ("pl_step", "pl_apply_correction", "pl_lattice_status", "pl_destroy"):
+        fn = getattr(lib, name)
+        args = [None] + ([1] if name == "pl_step" else [])
+        assert fn(*args) == B.PL_ERR_INVALID_ARG

@@ -1,0 +1,247 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several CTA strips (126 owned columns each) and row blocks (32 rows)
+with ragged tails, plus degenerate lattices (1x1, 2x3, 1xN).  Tolerances:
+FP64 storage ~ 1e-12 relative (operation order only); FP32 storage 1e-4
+relative L-infinity on rho (the target for FP32 storage); FP16-offset storage
+bounded by the FP16 rounding of the stored offsets.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+F64, F32, F16 = B.PL_F64, B.PL_F32, B.PL_F16_OFFSET
+SIZES = [(1, 1), (2, 3), (1, 9), (5, 7), (67, 35), (130, 70), (300, 33)]
+RHO_REF = 1.075
+
+
+def lattice(nx, ny, storage, mlp=None, **kw):
+    if mlp is None:
+        mlp = B.PL_MLP_F64 if storage == F64 else B.PL_MLP_F32
+    p = B.pl_params_default(nx, ny, storage=storage, mlp=mlp, rho_ref=RHO_REF, **kw)
+    return B.Lattice(p)
+
+
+def stored(f, storage):
+    """The FP64 values a storage type actually holds for populations f."""
+    if storage == F64:
+        return f.copy()
+    if storage == F32:
+        return f.astype(np.float32).astype(np.float64)
+    _, _, w = O.lattice_tables()
+    off = (w * RHO_REF).astype(np.float32)[:, None, None]
+    h = (f.astype(np.float32) - off).astype(np.float16)        # encode: rn_half(float(f) - off)
+    return (h.astype(np.float32) + off).astype(np.float64)     # decode: float(h) + off
+
+
+def rel_linf(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+# ----------------------------------------------------------------------------- initial state
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("nx,ny", SIZES)
+def test_init_droplets_matches_oracle(storage, nx, ny):
+    drops = [(nx / 2, ny / 2, min(nx, ny) / 4), (0.3 * nx, 0.8 * ny, 2.5)]
+    lat = lattice(nx, ny, storage)
+    lat.init_droplets(drops, 2.0, 0.15, 2.0, 0.01, 7)
+    f, step = lat.state()
+    fo = O.init_equilibrium(O.init_rho(nx, ny, drops, 2.0, 0.15, 2.0, 0.01, 7))
+    assert step == 0
+    tol = {F64: 2e-15, F32: 1e-7, F16: 3e-4}[storage]
+    assert np.abs(f - fo).max() <= tol
+    if storage == F32:
+        assert np.array_equal(f, stored(fo, F32))
+
+
+# ----------------------------------------------------------------------------- one step
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+@pytest.mark.parametrize("nx,ny", SIZES)
+@pytest.mark.parametrize("tau", [1.0, 0.8])
+def test_step_matches_oracle(storage, nx, ny, tau):
+    f0 = stored(wl.random_populations(nx, ny, seed=nx * 1000 + ny, lo=0.02, hi=0.3), storage)
+    lat = lattice(nx, ny, storage, tau=tau, G=-5.5)
+    lat.set_state(f0, 0)
+    assert np.array_equal(lat.state()[0], f0)
+    lat.step(3)
+    f, step = lat.state()
+    fo = f0.copy()
+    O.step(fo, 3, -5.5, tau)
+    assert step == 3
+    tol = {F64: 1e-13, F32: 2e-6, F16: 2e-3}[storage]
+    assert np.abs(f - fo).max() <= tol * np.abs(fo).max()
+
+
+# ----------------------------------------------------------------------------- coupled droplet runs
+
+def test_single_64_fp64_coupled_run_matches_oracle():
+    """64x64 FP64 droplet, 2000 steps, FP64 network correction every 50 steps."""
+    job = wl.single_64()
+    lat = B.Lattice.from_workload(job)
+    lat.run(job.steps, job.K)
+    m = lat.metrics()
+    f_gpu, step = lat.state()
+    fo = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
+                                       job.noise_amp, job.seed))
+    M0 = O.mass(fo)
+    assert O.run(fo, job.steps, job.G, job.tau, K=job.K, blob=job.weights(), mode=O.MLP_F64,
+                 beta_rho=job.beta_rho, beta_u=job.beta_u, M0=M0) == 0
+    ro = O.density(fo)
+    assert step == 2000 and m["corrections"] == 40 and m["status"] == 0
+    assert rel_linf(O.density(f_gpu), ro) < 1e-11
+    mo = O.metrics_rho(ro)
+    lo = O.laplace(ro, 32.0, 32.0, job.width, job.G)
+    assert abs(m["mass"] - M0) < 1e-12 * M0 and abs(mo["mass"] - M0) < 1e-12 * M0
+    assert m["count"] == mo["count"]
+    for k in ("G_max", "W_eff", "E_int", "delta_rho"):
+        assert abs(m[k] - mo[k]) <= 1e-10 * abs(mo[k]), k
+    for k in ("R_eq", "rho_in", "rho_out", "p_in", "p_out", "dP"):
+        assert abs(m[k] - lo[k]) <= 1e-9 * abs(lo[k]), k
+
+
+def test_fp32_droplet_with_fp32_network_matches_oracle():
+    n = 128
+    job = wl.Lattice(n, n, storage=F32, droplets=[(64.0, 64.0, 20.0)], seed=5, steps=600, K=100,
+                     mlp=wl.MLP_F32, weight_seed=15)
+    lat = B.Lattice.from_workload(job)
+    lat.run(job.steps, job.K)
+    m = lat.metrics()
+    f_gpu, _ = lat.state()
+    fo = O.init_equilibrium(O.init_rho(n, n, job.droplets, 2.0, 0.15, 2.0, 0.01, 5))
+    M0 = O.mass(fo)
+    assert O.run(fo, job.steps, job.G, job.tau, K=job.K, blob=job.weights(), mode=O.MLP_F64, M0=M0) == 0
+    assert rel_linf(O.density(f_gpu), O.density(fo)) < 1e-4
+    assert abs(m["mass"] - M0) < 1e-6 * M0
+    mo = O.metrics_rho(O.density(fo))
+    assert abs(m["W"] - mo["W"]) <= 0.02 * mo["W"]
+
+
+# ----------------------------------------------------------------------------- metrics, network, correction
+
+@pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (300, 33)])
+def test_metrics_match_oracle_on_same_state(nx, ny):
+    drops = [(nx / 2, ny / 2, min(nx, ny) / 4)]
+    lat = lattice(nx, ny, F64)
+    lat.init_droplets(drops, 2.0, 0.15, 2.0, 0.01, 3)
+    lat.step(50)
+    m = lat.metrics()
+    f, _ = lat.state()
+    r = O.density(f)
+    mo = O.metrics_rho(r)
+    lo = O.laplace(r, nx / 2, ny / 2, 2.0, -5.5)
+    assert m["count"] == mo["count"]
+    for k in ("mass", "G_max", "W", "W_eff", "E_int", "delta_rho", "rho_max", "rho_min"):
+        assert abs(m[k] - mo[k]) <= 1e-12 * max(abs(mo[k]), 1e-300), k
+    for k in ("R_eq", "rho_in", "rho_out", "p_in", "p_out"):
+        assert abs(m[k] - lo[k]) <= 1e-12 * abs(lo[k]), k
+    # same state; the GPU sums the 9 populations pairwise, the oracle in order
+    assert np.abs(lat.rho() - r).max() <= 4e-16 * np.abs(r).max() * 9
+
+
+@pytest.mark.parametrize("storage,mode,tol", [(F64, B.PL_MLP_F64, 1e-13), (F32, B.PL_MLP_F32, 2e-5)])
+@pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35)])
+def test_network_field_matches_oracle(storage, mode, tol, nx, ny):
+    blob = wl.mlp_weights(41)
+    lat = lattice(nx, ny, storage, mlp=mode)
+    lat.init_droplets([], 1.0, 1.0, 2.0, 0.0, 1)
+    lat.set_weights(blob)
+    out = lat.mlp_field()
+    ref = O.mlp_field(blob, nx, ny, O.MLP_F64)
+    assert np.abs(out - ref).max() <= tol
+
+
+@pytest.mark.parametrize("storage,tol", [(F64, 1e-13), (F32, 2e-5)])
+def test_single_correction_matches_oracle(storage, tol):
+    n = 48
+    lat = lattice(n, n, storage, beta_rho=0.3, beta_u=0.05)
+    lat.init_droplets([(24.0, 24.0, 10.0)], 2.0, 0.15, 2.0, 0.01, 9)
+    lat.step(40)
+    f0, _ = lat.state()
+    m0 = lat.metrics()
+    blob = wl.mlp_weights(42)
+    lat.set_weights(blob)
+    lat.correct()
+    f1, _ = lat.state()
+    fo = f0.copy()
+    assert O.correct(fo, blob, 0.3, 0.05, m0["mass0"], O.MLP_F64) == 0
+    assert np.abs(f1 - fo).max() <= tol * np.abs(fo).max()
+    m1 = lat.metrics()
+    assert m1["corrections"] == 1 and m1["status"] == 0
+    assert abs(m1["mass"] - m0["mass0"]) <= (1e-12 if storage == F64 else 1e-6) * m0["mass0"]
+
+
+def test_nonphysical_correction_leaves_state_and_sets_status():
+    n = 32
+    lat = lattice(n, n, F64, beta_rho=1.0, beta_u=0.0)
+    lat.init_droplets([(16.0, 16.0, 6.0)], 2.0, 0.15, 2.0, 0.01, 1)
+    lat.step(20)
+    f0, _ = lat.state()
+    blob = np.zeros(wl.mlp_blob_size(), dtype=np.float32)
+    offs, o = [], 0
+    dims = wl.MLP_DIMS
+    for l in range(5):
+        offs.append(o)
+        o += dims[l + 1] * dims[l] + dims[l + 1]
+    for l, w in enumerate([2.0, 1.0, 1.0, 1.0, 200.0]):
+        blob[offs[l]] = w
+    lat.set_weights(blob)
+    lat.correct()
+    assert lat.status() == B.PL_ERR_NONPHYSICAL
+    assert np.array_equal(lat.state()[0], f0)
+    fo = f0.copy()
+    assert O.correct(fo, blob, 1.0, 0.0, O.mass(f0)) == -4
+
+
+# ----------------------------------------------------------------------------- determinism, checkpoint
+
+@pytest.mark.parametrize("storage", [F32, F16])
+def test_repeat_runs_are_bit_identical(storage):
+    job = wl.Lattice(96, 80, storage=storage, droplets=[(40.0, 40.0, 15.0)], seed=2, K=25, mlp=wl.MLP_F32)
+    outs = []
+    for _ in range(2):
+        lat = B.Lattice.from_workload(job)
+        lat.run(120, 25)
+        outs.append((lat.state()[0], lat.metrics()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("storage", [F64, F32])
+def test_checkpoint_resume_is_exact(storage):
+    job = wl.Lattice(70, 40, storage=storage, droplets=[(30.0, 20.0, 9.0)], seed=4, K=10,
+                     mlp=wl.MLP_F64 if storage == F64 else wl.MLP_F32)
+    a = B.Lattice.from_workload(job)
+    a.run(30, 10)
+    a.run(30, 10)
+    b = B.Lattice.from_workload(job)
+    b.run(30, 10)
+    f_mid, step = b.state()
+    c = B.Lattice.from_workload(job)   # fresh lattice, weights loaded, state overwritten
+    c.set_state(f_mid, step)
+    c.run(30, 10)
+    assert np.array_equal(a.state()[0], c.state()[0])
+    assert c.state()[1] == 60
+
+
+def test_run_schedule_equals_explicit_steps_and_corrections():
+    job = wl.Lattice(40, 40, storage=F64, droplets=[(20.0, 20.0, 8.0)], seed=6, K=7, mlp=wl.MLP_F64)
+    a = B.Lattice.from_workload(job)
+    a.run(23, 7)
+    b = B.Lattice.from_workload(job)
+    for s in range(1, 24):
+        b.step(1)
+        if s % 7 == 0:
+            b.correct()
+    assert np.array_equal(a.state()[0], b.state()[0])
+    assert a.metrics()["corrections"] == 3
