@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--storage", default="f16", choices=["f16", "f32"],
+                    help="storage of the timed workload (profiling aid; the headline is f16)")
     return ap.parse_args()
 
 
@@ -222,7 +224,7 @@ def run_gb300(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    mlp = {"auto": wl.MLP_F32, "bf16": wl.MLP_BF16, "f32": wl.MLP_F32}[args.mlp]
+    mlp = {"auto": wl.MLP_BF16, "bf16": wl.MLP_BF16, "f32": wl.MLP_F32}[args.mlp]
 
     def build(storage):
         job = wl.field_4096(storage=storage, seed=3 + rank, side=args.side)
@@ -264,8 +266,16 @@ def run_gb300(args):
                "metrics": m}
         return res, lat
 
-    storage = wl.F16_OFFSET
+    storage = wl.F16_OFFSET if args.storage == "f16" else wl.F32
     main, lat = time_workload(storage, args.steps, args.warmup, True)
+    # mass drift after the timed region: one more interval, read before and after its correction
+    lat.step(main["job"].K)
+    pre = lat.metrics()
+    lat.correct()
+    post = lat.metrics()
+    M0 = post["mass0"]
+    drift = {"pre_correction": abs(pre["mass"] - M0) / M0, "post_correction": abs(post["mass"] - M0) / M0,
+             "after_steps": post["step"]}
     job = main["job"]
     K = job.K
     cells = job.cells
@@ -331,7 +341,8 @@ def run_gb300(args):
                        "step": "K lattice steps + correction + metrics",
                        "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (cells * 18 / 1e6),
                        "parallelism": "replicas x%d" % world},
-            "roofline": {"bound": "hbm", "kernel": "k_step<f16_offset>", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "hbm", "kernel": "k_step<%s>" % STORAGE_NAME[storage], "achieved": achieved,
+                         "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[storage],
                          "step_kernel_ms": main["step_kernel_ms"]},
@@ -342,6 +353,7 @@ def run_gb300(args):
             "fp32_plain": fp32,
             "cpu_baseline": cpu,
             "final_metrics": {k: main["metrics"][k] for k in ("mass", "mass0", "W", "G_max", "W_eff", "E_int")},
+            "mass_drift": drift,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -58,6 +58,10 @@ inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 size_t storage_bytes(int storage) { return storage == PL_F64 ? 8 : (storage == PL_F32 ? 4 : 2); }
 size_t scratch_elem_bytes(int storage) { return storage == PL_F64 ? 8 : 4; }
+// Stored rows are padded to a multiple of 8 populations so that every row, and
+// every even column pair, is aligned for vector access.
+int row_pitch(int nx) { return (nx + 7) / 8 * 8; }
+size_t plane_elems(const pl_params* p) { return (size_t)row_pitch(p->nx) * p->ny; }
 
 constexpr int MLP_BLOB = 64 * 2 + 64 + 128 * 64 + 128 + 128 * 128 + 128 + 64 * 128 + 64 + 3 * 64 + 3;
 constexpr int MAX_RED_BLOCKS = 1024;
@@ -86,7 +90,7 @@ Layout layout_for(const pl_params* p) {
     size_t o = 0;
     for (int b = 0; b < 2; ++b) {
         L.pops[b] = o;
-        o = align_up(o + 9 * N * storage_bytes(p->storage));
+        o = align_up(o + 9 * plane_elems(p) * storage_bytes(p->storage));
     }
     L.scratch = o;  // rho, jx, jy, g, out3[3]: 7 fields (also >= 8N bytes for FP64 staging)
     o = align_up(o + 7 * N * scratch_elem_bytes(p->storage));
@@ -213,7 +217,8 @@ int pl_lattice_create(const pl_params* p, void* dev_mem, size_t bytes, void* str
     v.nx = p->nx;
     v.ny = p->ny;
     v.storage = p->storage;
-    v.plane = (long long)N;
+    v.pitch = row_pitch(p->nx);
+    v.plane = (long long)plane_elems(p);
     v.pops[0] = L->base + Ly.pops[0];
     v.pops[1] = L->base + Ly.pops[1];
     char* sc = L->base + Ly.scratch;

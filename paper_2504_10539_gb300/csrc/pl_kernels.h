@@ -18,7 +18,8 @@ long long launches_total();
 struct LatticeView {
     int nx, ny;
     int storage;
-    long long plane;   // elements per population plane (nx*ny)
+    int pitch;         // elements per stored row (nx rounded up to a multiple of 8)
+    long long plane;   // elements per population plane (pitch*ny)
     void* pops[2];     // two-lattice population buffers, 9 planes each
     // scratch fields, element type = double for F64 storage, float otherwise
     void* rho;

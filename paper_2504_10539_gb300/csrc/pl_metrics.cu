@@ -25,14 +25,15 @@ int reduction_blocks(const LatticeView& v) {
 
 // rho = sum_i f_i and j = sum_i f_i c_i per cell, from the decoded stored state.
 template <int MODE>
-__global__ void k_moments(const typename Traits<MODE>::S* __restrict__ f, long long N, long long plane,
-                          typename Traits<MODE>::R rho_ref, typename Traits<MODE>::R* __restrict__ rho,
+__global__ void k_moments(const typename Traits<MODE>::S* __restrict__ f, int nx, int pitch, long long N,
+                          long long plane, typename Traits<MODE>::R rho_ref, typename Traits<MODE>::R* __restrict__ rho,
                           typename Traits<MODE>::R* __restrict__ jx, typename Traits<MODE>::R* __restrict__ jy) {
     using R = typename Traits<MODE>::R;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const long long o = (c / nx) * pitch + c % nx;
         R P[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + c], wq<R>(i) * rho_ref);
+        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
         rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
         jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
         jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
@@ -163,8 +164,8 @@ static cudaError_t metrics_t(const LatticeView& v, const PhysParams& p, int cur,
     const long long N = (long long)v.nx * v.ny;
     const int nb = reduction_blocks(v);
     R* rho = static_cast<R*>(v.rho);
-    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), N, v.plane, R(p.rho_ref), rho,
-                                              static_cast<R*>(v.jx), static_cast<R*>(v.jy));
+    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), v.nx, v.pitch, N, v.plane,
+                                              R(p.rho_ref), rho, static_cast<R*>(v.jx), static_cast<R*>(v.jy));
     k_grad_reduce<R><<<nb, RB_THREADS, 0, s>>>(rho, v.nx, v.ny, static_cast<R*>(v.g), p.threshold, v.partials);
     k_final_metrics<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec, set_mass0);
     if (has_centre) {
@@ -306,7 +307,7 @@ __device__ __forceinline__ void feq9(double rho, double ux, double uy, double (&
 }
 
 template <int MODE>
-__global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, long long plane,
+__global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, int nx, int pitch, long long plane,
                              const typename Traits<MODE>::R* __restrict__ rho, const typename Traits<MODE>::R* __restrict__ jx,
                              const typename Traits<MODE>::R* __restrict__ jy, const typename Traits<MODE>::R* __restrict__ g,
                              const typename Traits<MODE>::R* __restrict__ out3, long long N, double beta_rho,
@@ -322,11 +323,28 @@ __global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, long long
         double fn[9], fo[9];
         feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
         feq9<R>(r, jxc / r, jyc / r, fo);
+        const long long o = (c / nx) * pitch + c % nx;
+        if constexpr (MODE == PL_F16_OFFSET) {
+            // stored offsets h_i + (f_i^eq' - f_i^eq), with the rest population absorbing the
+            // FP16 rounding residual of the other eight (one rounding per cell's mass)
+            float hn[9];
+            float res = 0.0f;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const R off = R(wq<double>(i) * rho_ref);
-            const double fi = (double)decode<MODE>(f[i * plane + c], off);
-            f[i * plane + c] = encode<MODE>(R(fi + (fn[i] - fo[i])), off);
+            for (int i = 0; i < 9; ++i) hn[i] = __half2float(f[i * plane + o]) + (float)(fn[i] - fo[i]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const __half q = __float2half_rn(hn[i]);
+                res += __half2float(q) - hn[i];
+                f[i * plane + o] = q;
+            }
+            f[o] = __float2half_rn(hn[0] - res);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const R off = R(wq<double>(i) * rho_ref);
+                const double fi = (double)decode<MODE>(f[i * plane + o], off);
+                f[i * plane + o] = encode<MODE>(R(fi + (fn[i] - fo[i])), off);
+            }
         }
     }
 }
@@ -344,7 +362,8 @@ static cudaError_t correction_t(const LatticeView& v, const PhysParams& p, int c
     R* out3 = static_cast<R*>(v.out3);
     cudaError_t e = launch_mlp_field(v, mlp_mode, s);
     if (e != cudaSuccess) return e;
-    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), N, v.plane, R(p.rho_ref), rho, jx, jy);
+    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), v.nx, v.pitch, N, v.plane, R(p.rho_ref),
+                                              rho, jx, jy);
     k_grad_reduce<R><<<nb, RB_THREADS, 0, s>>>(rho, v.nx, v.ny, g, p.threshold, v.partials);
     k_final_metrics<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec, 0);
     k_corr_sums1<R><<<nb, RB_THREADS, 0, s>>>(rho, g, out3, N, p.beta_rho, v.rec, v.partials);
@@ -353,7 +372,7 @@ static cudaError_t correction_t(const LatticeView& v, const PhysParams& p, int c
     k_corr_final2<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec);
     long long blocks = (N + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    k_corr_apply<MODE><<<(int)blocks, 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.plane, rho, jx, jy, g, out3, N,
+    k_corr_apply<MODE><<<(int)blocks, 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.pitch, v.plane, rho, jx, jy, g, out3, N,
                                                    p.beta_rho, p.beta_u, p.rho_ref, v.rec);
     note_launches(8);
     return cudaGetLastError();

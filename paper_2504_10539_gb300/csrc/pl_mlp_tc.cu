@@ -1,5 +1,28 @@
-// Correction network on tcgen05 tensor cores (BF16 operands, FP32 accumulation
-// in tensor memory).  Work in progress: only the weight conversion exists yet.
+// Correction network on tcgen05 tensor cores (sm_103a): BF16 operands in shared
+// memory, FP32 accumulators in tensor memory (TMEM).
+//
+// N(x, y) -> (rho^, u^_x, u^_y) (arXiv 2504.10539 Sec. II-B Eq. 2, Sec. III-B):
+// 2 -> 64 -> 128 -> 128 -> 64 -> 3, tanh on the hidden layers, linear output.
+//   layer 1 (2 -> 64)     : FP32 FMA per cell, tanh, rounded to BF16 (A operand of layer 2)
+//   layers 2, 3, 4        : tcgen05.mma kind::f16, M = 128 cells, N = 128/128/64, K = 64/128/128,
+//                           D in TMEM; epilogue tcgen05.ld -> + bias -> tanh -> BF16 -> smem
+//   layer 5 (64 -> 3)     : FP32 FMA on the FP32 tanh outputs of layer 4
+//
+// CTA = 2 warpgroups; each warpgroup runs its own 128-cell tile pipeline with its
+// own A buffers, TMEM columns and mbarrier, so one warpgroup's tanh epilogue
+// overlaps the other's MMAs.  Thread t of a warpgroup owns cell row t of the tile
+// (TMEM lane t: warp w of the group reads lanes 32*(w%4)..+31).  The weights are
+// loaded once per CTA by bulk async copies (the grid is persistent, one CTA per SM).
+//
+// Operand layout (no swizzle, K-major): 8x8 BF16 "core matrices" of 128 contiguous
+// bytes (8 rows of 16 bytes).  An R x K operand is stored core-matrix (kb, rb) at
+// byte ((kb * R/8) + rb) * 128, so core matrices adjacent in R are 128 B apart
+// (stride byte offset) and those adjacent in K are R/8 * 128 B apart (leading
+// byte offset).  One MMA consumes K = 16, i.e. two core matrices along K.
+//
+// Every wait on an mbarrier is bounded by %globaltimer; on expiry the warpgroup
+// records an error, stops issuing work, waits (bounded) for its MMAs in flight,
+// and the CTA frees its TMEM before returning.
 #include <cuda_bf16.h>
 
 #include "pl_device.cuh"
@@ -7,20 +30,173 @@
 
 namespace pl {
 
-size_t bf16_weight_elems() { return 128 * 64 + 128 * 128 + 64 * 128; }
+namespace tc {
 
-__global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* __restrict__ wb) {
-    // W2 [128x64], W3 [128x128], W4 [64x128] copied in blob order, rounded to nearest even.
-    const int off_w2 = 64 * 2 + 64;
-    const int off_w3 = off_w2 + 128 * 64 + 128;
-    const int off_w4 = off_w3 + 128 * 128 + 128;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 32768; k += gridDim.x * blockDim.x) {
-        float v;
-        if (k < 8192) v = w32[off_w2 + k];
-        else if (k < 8192 + 16384) v = w32[off_w3 + (k - 8192)];
-        else v = w32[off_w4 + (k - 8192 - 16384)];
-        __nv_bfloat16 b = __float2bfloat16_rn(v);
-        wb[k] = *reinterpret_cast<uint16_t*>(&b);
+constexpr int M = 128;           // cells per tile
+constexpr int NWG = 2;           // tile pipelines per CTA
+constexpr int THREADS = 128 * NWG;
+constexpr int TMEM_COLS = 128 * NWG;
+
+// shared memory map (bytes).  A buffers first, weight images next, FP32 params
+// last; the allocation is the full 227 KB so that every address an MMA can form
+// from these bases stays inside it.
+constexpr int A_BYTES = M * 128 * 2;                 // 128 rows x 128 BF16 = 32 KB
+constexpr int OFF_A = 0;                             // per WG: X then Y
+constexpr int OFF_W2 = OFF_A + NWG * 2 * A_BYTES;    // 128 x 64  BF16 = 16 KB
+constexpr int OFF_W3 = OFF_W2 + 128 * 64 * 2;        // 128 x 128 BF16 = 32 KB
+constexpr int OFF_W4 = OFF_W3 + 128 * 128 * 2;       // 64 x 128  BF16 = 16 KB
+constexpr int OFF_P = OFF_W4 + 64 * 128 * 2;         // FP32 parameters
+constexpr int P_W1 = 0, P_B1 = 128, P_B2 = 192, P_B3 = 320, P_B4 = 448, P_W5 = 512, P_B5 = 704, P_N = 708;
+constexpr int OFF_BAR = (OFF_P + P_N * 4 + 15) / 16 * 16;
+constexpr int OFF_TMEM_SLOT = OFF_BAR + 8 * (1 + NWG);
+constexpr int SMEM_USED = OFF_TMEM_SLOT + 16;
+constexpr int SMEM_ALLOC = 227 * 1024;
+static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
+static_assert(SMEM_USED <= SMEM_ALLOC, "shared memory");
+
+constexpr int W_IMG_ELEMS = 128 * 64 + 128 * 128 + 64 * 128;   // BF16 image in global memory
+constexpr long long WAIT_NS = 2000000000ll;                       // 2 s per wait
+
+// Blob offsets (FP32 master weights, row-major W[out][in]).
+constexpr int B_W1 = 0, B_B1 = 128, B_W2 = 192, B_B2 = B_W2 + 8192, B_W3 = B_B2 + 128, B_B3 = B_W3 + 16384,
+              B_W4 = B_B3 + 128, B_B4 = B_W4 + 8192, B_W5 = B_B4 + 64, B_B5 = B_W5 + 192;
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
+    // both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    // start address >> 4 (bits 0-13), leading byte offset >> 4 (16-29), stride byte
+    // offset >> 4 (32-45), fixed 0b001 at bits 46-48, base offset 0, no swizzle.
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ long long gtime() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = gtime();
+    while (!mbar_try(bar, parity))
+        if (gtime() - t0 > WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
+
+// Warpgroup-wide AND (named barrier wg+1): every thread of the group gets the same
+// verdict, so a timeout seen by one thread makes the whole group leave together.
+__device__ __forceinline__ bool wg_all(int wg, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, %2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(wg + 1)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float tanh_fast(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Store 8 consecutive features (k0..k0+7, k0 % 8 == 0) of row m into an A operand
+// with R = 128 rows.
+__device__ __forceinline__ void store8(uint8_t* A, int m, int k0, const float* v) {
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+    uint4 u;
+    u.x = *reinterpret_cast<uint32_t*>(&p0);
+    u.y = *reinterpret_cast<uint32_t*>(&p1);
+    u.z = *reinterpret_cast<uint32_t*>(&p2);
+    u.w = *reinterpret_cast<uint32_t*>(&p3);
+    *reinterpret_cast<uint4*>(A + ((k0 >> 3) * (M / 8) + (m >> 3)) * 128 + (m & 7) * 16) = u;
+}
+
+// Issue D[128 x N] (+)= A[128 x K] * W[N x K]^T as K/16 MMAs.
+__device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_base, uint32_t w_base, int N, int K) {
+    const uint32_t idesc = idesc_bf16(M, N);
+    const uint32_t a_lbo = (M / 8) * 128, w_lbo = (N / 8) * 128;
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t a = smem_desc(a_base + ks * 2 * a_lbo, a_lbo, 128);
+        const uint64_t b = smem_desc(w_base + ks * 2 * w_lbo, w_lbo, 128);
+        mma_bf16(d_tmem, a, b, idesc, ks > 0 ? 1u : 0u);
+    }
+}
+
+}  // namespace tc
+
+size_t bf16_weight_elems() { return tc::W_IMG_ELEMS; }
+
+// FP32 blob -> BF16 (round to nearest even) images of W2, W3, W4 in the core-matrix
+// layout above: element (n, k) of an N x K matrix at ((k/8) * N/8 + n/8) * 64 + (n%8) * 8 + k%8.
+__global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* __restrict__ img) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tc::W_IMG_ELEMS; e += gridDim.x * blockDim.x) {
+        int N, K, src, base, loc;
+        if (e < 8192) { N = 128; K = 64; src = tc::B_W2; base = 0; loc = e; }
+        else if (e < 8192 + 16384) { N = 128; K = 128; src = tc::B_W3; base = 8192; loc = e - 8192; }
+        else { N = 64; K = 128; src = tc::B_W4; base = 8192 + 16384; loc = e - 8192 - 16384; }
+        const int n = loc / K, k = loc % K;
+        __nv_bfloat16 b = __float2bfloat16_rn(w32[src + n * K + k]);
+        img[base + ((k >> 3) * (N >> 3) + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = *reinterpret_cast<uint16_t*>(&b);
     }
 }
 
@@ -30,10 +206,165 @@ cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, cudaS
     return cudaGetLastError();
 }
 
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, int nx, int ny,
+             float* __restrict__ out3, DevRecord* __restrict__ rec) {
+    using namespace tc;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
+    const long long N = (long long)nx * ny;
+    const long long ntiles = (N + M - 1) / M;
+    float* P = reinterpret_cast<float*>(sm + OFF_P);
+    const uint32_t bar_w = saddr(sm + OFF_BAR);
+    const uint32_t bar_mma = saddr(sm + OFF_BAR + 8 * (1 + wg));
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_TMEM_SLOT);
+
+    if (tid == 0) {
+        mbar_init(bar_w, 1);
+        for (int g = 0; g < NWG; ++g) mbar_init(saddr(sm + OFF_BAR + 8 * (1 + g)), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // small FP32 parameters
+    for (int k = tid; k < 128; k += THREADS) P[P_W1 + k] = w32[B_W1 + k];
+    for (int k = tid; k < 64; k += THREADS) P[P_B1 + k] = w32[B_B1 + k];
+    for (int k = tid; k < 128; k += THREADS) P[P_B2 + k] = w32[B_B2 + k];
+    for (int k = tid; k < 128; k += THREADS) P[P_B3 + k] = w32[B_B3 + k];
+    for (int k = tid; k < 64; k += THREADS) P[P_B4 + k] = w32[B_B4 + k];
+    for (int k = tid; k < 192; k += THREADS) P[P_W5 + k] = w32[B_W5 + k];
+    for (int k = tid; k < 3; k += THREADS) P[P_B5 + k] = w32[B_B5 + k];
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    if (tid == 0) {
+        // weight images: one bulk async copy per matrix onto the mbarrier
+        const uint32_t bytes = W_IMG_ELEMS * 2;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(bytes) : "memory");
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(wimg);
+        const uint32_t dst[3] = {saddr(sm + OFF_W2), saddr(sm + OFF_W3), saddr(sm + OFF_W4)};
+        const uint32_t len[3] = {128 * 64 * 2, 128 * 128 * 2, 64 * 128 * 2};
+        uint32_t off = 0;
+        for (int k = 0; k < 3; ++k) {
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                             dst[k]),
+                         "l"(src + off), "r"(len[k]), "r"(bar_w)
+                         : "memory");
+            off += len[k];
+        }
+    }
+    bool ok = __syncthreads_and(mbar_wait(bar_w, 0)) != 0;
+
+    uint8_t* AX = sm + OFF_A + wg * 2 * A_BYTES;
+    uint8_t* AY = AX + A_BYTES;
+    const uint32_t ax = saddr(AX), ay = saddr(AY);
+    const uint32_t d_tmem = tmem + wg * 128;                               // this WG's columns
+    const uint32_t my_lane_tmem = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + wg * 128;
+    uint32_t phase = 0;
+    int pending = 0;  // MMA batches committed but not yet waited for
+
+    for (long long tile = (long long)blockIdx.x * NWG + wg; ok && tile < ntiles; tile += (long long)gridDim.x * NWG) {
+        const long long c = tile * M + t;
+        const long long cc = c < N ? c : N - 1;
+        const int x = (int)(cc % nx), y = (int)(cc / nx);
+        const float xh = 2.0f * ((float)x + 0.5f) / (float)nx - 1.0f;
+        const float yh = 2.0f * ((float)y + 0.5f) / (float)ny - 1.0f;
+
+        // ---- layer 1 on FMA: A1 (128 x 64) into AX
+#pragma unroll
+        for (int k0 = 0; k0 < 64; k0 += 8) {
+            float h[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = k0 + j;
+                h[j] = tanh_fast(fmaf(P[P_W1 + 2 * o], xh, fmaf(P[P_W1 + 2 * o + 1], yh, P[P_B1 + o])));
+            }
+            store8(AX, t, k0, h);
+        }
+        // ---- layers 2..4: MMA, then epilogue
+        float o0 = P[P_B5 + 0], o1 = P[P_B5 + 1], o2 = P[P_B5 + 2];
+#pragma unroll 1
+        for (int layer = 2; layer <= 4 && ok; ++layer) {
+            fence_async_smem();
+            tc_before_sync();
+            wg_bar(wg);
+            if (t == 0) {
+                tc_after_sync();
+                if (layer == 2) issue_layer(d_tmem, ax, saddr(sm + OFF_W2), 128, 64);
+                else if (layer == 3) issue_layer(d_tmem, ay, saddr(sm + OFF_W3), 128, 128);
+                else issue_layer(d_tmem, ax, saddr(sm + OFF_W4), 64, 128);
+                mma_commit(bar_mma);
+            }
+            pending = 1;
+            ok = wg_all(wg, mbar_wait(bar_mma, phase));
+            if (!ok) break;
+            pending = 0;
+            phase ^= 1;
+            tc_after_sync();
+            const int nout = layer == 4 ? 64 : 128;
+            const float* bias = P + (layer == 2 ? P_B2 : (layer == 3 ? P_B3 : P_B4));
+            uint8_t* dst = layer == 2 ? AY : AX;   // layer 3's output overwrites A1 (consumed)
+#pragma unroll 1
+            for (int c0 = 0; c0 < nout; c0 += 32) {
+                float v[32];
+                tmem_ld32(my_lane_tmem + c0, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = tanh_fast(v[j] + bias[c0 + j]);
+                if (layer < 4) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        o0 = fmaf(P[P_W5 + 0 * 64 + c0 + j], v[j], o0);
+                        o1 = fmaf(P[P_W5 + 1 * 64 + c0 + j], v[j], o1);
+                        o2 = fmaf(P[P_W5 + 2 * 64 + c0 + j], v[j], o2);
+                    }
+                }
+            }
+        }
+        if (!ok) break;
+        if (c < N) {
+            out3[c] = o0;
+            out3[N + c] = o1;
+            out3[2 * N + c] = o2;
+        }
+    }
+    if (!ok) {
+        if (t == 0) atomicCAS(&rec->status, PL_OK, PL_ERR_TIMEOUT);
+        if (pending) (void)mbar_wait(bar_mma, phase);  // let MMAs in flight finish before TMEM is freed
+    }
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+}
+
 cudaError_t launch_mlp_tc(const LatticeView& v, cudaStream_t s) {
-    (void)v;
-    (void)s;
-    return cudaErrorNotSupported;
+    if (v.storage == PL_F64) return cudaErrorInvalidValue;  // FP32 scratch only
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_ALLOC);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long N = (long long)v.nx * v.ny;
+    const long long tiles = (N + tc::M - 1) / tc::M;
+    long long grid = (tiles + tc::NWG - 1) / tc::NWG;
+    if (grid > sms) grid = sms;
+    k_mlp_tc<<<(int)grid, tc::THREADS, tc::SMEM_ALLOC, s>>>(v.wbf16, v.w32, v.nx, v.ny, static_cast<float*>(v.out3),
+                                                             v.rec);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace pl

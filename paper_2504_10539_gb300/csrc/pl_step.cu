@@ -1,148 +1,354 @@
 // Lattice kernels of the time step (arXiv 2504.10539 Sec. II-A, Eq. 1) and
 // of the initial state (Sec. III-A).
 //
-// Storage: structure of arrays, 9 planes of nx*ny populations (x fastest),
-// two buffers (two-lattice "push": read the post-streaming state of buffer
-// src, write the next post-streaming state into buffer 1-src).  Reads of a
-// step never alias its writes, so a CTA may recompute its neighbours' density
-// from their populations without racing with them: the result is identical
-// whatever the launch order.
+// Storage: structure of arrays, 9 planes of ny rows of `pitch` populations
+// (x fastest, pitch = nx rounded up to 8), two buffers: a step reads the
+// post-streaming state of buffer src and writes the next post-streaming state
+// into buffer 1-src ("push").  Reads never alias writes, so neighbouring strips
+// may recompute each other's densities without racing.
 //
-// Fused step kernel, one pass over HBM per step:
-//   - a CTA owns a strip of TX-2 columns and TY rows; thread t handles column
-//     x0-1+t (the two edge threads only supply the pseudopotential halo);
-//   - it walks its rows bottom to top ("rolling window"), keeping three rows of
-//     psi in a 4-slot shared-memory ring, so each cell's populations are read
-//     from HBM once and only the two halo rows/columns are read twice (from L2);
-//   - per owned cell: rho, psi, the Shan-Chen force from the 3x3 psi stencil,
-//     the force-shifted equilibrium, BGK relaxation, and the push to the 8
-//     neighbours with periodic wrap, all in registers.
+// FP16-offset storage keeps h_i = f_i - w_i rho_ref.  The step works on the
+// offsets directly: rho = sum h_i + rho_ref (the weights sum to one), the
+// momentum is sum c_i h_i (the offsets cancel), and the relaxation
+// h_i* = h_i + omega (f_i^eq - w_i rho_ref - h_i) needs the equilibrium minus the
+// same offset, which folds into its isotropic part.  FP32/FP64 storage is the
+// same code with rho_ref = 0.
+//
+// Fused step kernel ("strip walker"), one pass over HBM per step:
+//   - a warp owns a strip of 60 columns; lane l holds the column pair
+//     (x0-2+2l, x0-1+2l), so lanes 1..30 own cells and lanes 0 and 31 carry the
+//     halo; loads and stores of a pair are one aligned vector access;
+//   - the warp walks its rows bottom to top, keeping the pseudopotential of three
+//     rows in registers; left/right neighbours come from warp shuffles, so there
+//     is no shared memory and no barrier;
+//   - per cell: rho, psi, Shan-Chen force from the 3x3 psi stencil, force-shifted
+//     equilibrium, BGK relaxation, and the push to the 8 neighbours; a shifted
+//     plane is realigned with one shuffle so that its store is again one vector
+//     access per pair.  Lanes 0 and 31 also relax their inner halo cell, whose
+//     value the neighbouring owned lane pushes into its own columns;
+//   - the grid is persistent: the (strip, row) pairs of the lattice are split into
+//     equal contiguous ranges, one per warp, so every warp does the same work.
 #include "pl_device.cuh"
 #include "pl_kernels.h"
 
 namespace pl {
 
-template <int MODE>
-__global__ void __launch_bounds__(256) k_step(const typename Traits<MODE>::S* __restrict__ fin,
-                                              typename Traits<MODE>::S* __restrict__ fout, int nx, int ny,
-                                              long long plane, int ty, typename Traits<MODE>::R G,
-                                              typename Traits<MODE>::R tau, typename Traits<MODE>::R omega,
-                                              typename Traits<MODE>::R rho0, typename Traits<MODE>::R rho_ref) {
-    using S = typename Traits<MODE>::S;
-    using R = typename Traits<MODE>::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* psi_s = reinterpret_cast<R*>(smem_raw);  // [4][TX]
+constexpr int STRIP = 60;          // owned columns per warp
+constexpr int STEP_THREADS = 128;  // 4 independent warps per CTA
 
-    const int TX = blockDim.x;
-    const int t = threadIdx.x;
-    const int x0 = blockIdx.x * (TX - 2);
-    const int xg = x0 - 1 + t;
-    const int xc = wrapi(xg, nx);
-    const bool owner = (t >= 1) && (t <= TX - 2) && (xg < nx);
-    const int xm = xc == 0 ? nx - 1 : xc - 1;
-    const int xp = xc == nx - 1 ? 0 : xc + 1;
-    const int y0 = blockIdx.y * ty;
-    const int rows = min(ty, ny - y0);
-    const R inv_rho0 = R(1) / rho0;
-
-    R off[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) off[i] = wq<R>(i) * rho_ref;
-
-    R Pn[9], Pc[9], Pp[9];
-    R rho_p = R(0);
-    {
-        const S* b = fin + (long long)wrapi(y0 - 1, ny) * nx + xc;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Pn[i] = decode<MODE>(b[i * plane], off[i]);
+template <int MODE> struct Pair;
+template <> struct Pair<PL_F64> {
+    using T = double2;
+    __device__ static __forceinline__ void split(T v, double& a, double& b) { a = v.x; b = v.y; }
+    __device__ static __forceinline__ T make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct Pair<PL_F32> {
+    using T = float2;
+    __device__ static __forceinline__ void split(T v, float& a, float& b) { a = v.x; b = v.y; }
+    __device__ static __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<PL_F16_OFFSET> {
+    using T = __half2;
+    __device__ static __forceinline__ void split(T v, float& a, float& b) {
+        const float2 f = __half22float2(v);
+        a = f.x;
+        b = f.y;
     }
-    for (int k = 0; k <= rows + 1; ++k) {
+    __device__ static __forceinline__ T make(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+template <int MODE>
+__device__ __forceinline__ typename Traits<MODE>::R to_r(typename Traits<MODE>::S v) {
+    if constexpr (MODE == PL_F16_OFFSET) return __half2float(v);
+    else return v;
+}
+template <int MODE>
+__device__ __forceinline__ typename Traits<MODE>::S from_r(typename Traits<MODE>::R v) {
+    if constexpr (MODE == PL_F16_OFFSET) return __float2half_rn(v);
+    else return v;
+}
+
+// psi = rho0 (1 - exp(-rho/rho0)).  FP16 storage uses the hardware exp2; its
+// cancellation error in the vapour (~1e-6 relative) is far below the storage's.
+template <int MODE>
+__device__ __forceinline__ typename Traits<MODE>::R psi_step(typename Traits<MODE>::R rho, typename Traits<MODE>::R rho0,
+                                                             typename Traits<MODE>::R inv_rho0) {
+    if constexpr (MODE == PL_F16_OFFSET) {
+        float e;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-rho * inv_rho0 * 1.4426950408889634f));
+        return rho0 * (1.0f - e);
+    } else {
+        return psi_of(rho, rho0, inv_rho0);
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ typename Traits<MODE>::R recip(typename Traits<MODE>::R v) {
+    if constexpr (MODE == PL_F16_OFFSET) return __fdividef(1.0f, v);
+    else return typename Traits<MODE>::R(1) / v;
+}
+
+template <typename R>
+struct StepK {
+    R G, tau, omega, rho0, inv_rho0, rho_ref;
+};
+
+// One cell: populations h[9] (offset space), density rho, force (fx, fy) -> o[9].
+template <int MODE>
+__device__ __forceinline__ void collide_cell(const typename Traits<MODE>::R (&h)[9], typename Traits<MODE>::R rho,
+                                             typename Traits<MODE>::R fx, typename Traits<MODE>::R fy,
+                                             const StepK<typename Traits<MODE>::R>& k,
+                                             typename Traits<MODE>::R (&o)[9]) {
+    using R = typename Traits<MODE>::R;
+    const R jx = (h[1] - h[3]) + (h[5] - h[6]) + (h[8] - h[7]);
+    const R jy = (h[2] - h[4]) + (h[5] + h[6]) - (h[7] + h[8]);
+    const R inv = recip<MODE>(rho);
+    const R ux = (jx + k.tau * fx) * inv;  // u + tau F / rho
+    const R uy = (jy + k.tau * fy) * inv;
+    const R Ap = rho * (R(1) - R(1.5) * (ux * ux + uy * uy)) - k.rho_ref;
+    const R t3 = R(3) * rho, t45 = R(4.5) * rho;
+    const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
+    const R pp = ux + uy, pm = ux - uy;
+    const R Sx = Ap + t45 * ux * ux, Dx = t3 * ux;
+    const R Sy = Ap + t45 * uy * uy, Dy = t3 * uy;
+    const R Sp = Ap + t45 * pp * pp, Dp = t3 * pp;
+    const R Sm = Ap + t45 * pm * pm, Dm = t3 * pm;
+    R fe[9];
+    fe[0] = w0 * Ap;
+    fe[1] = w1 * (Sx + Dx);
+    fe[3] = w1 * (Sx - Dx);
+    fe[2] = w1 * (Sy + Dy);
+    fe[4] = w1 * (Sy - Dy);
+    fe[5] = w2 * (Sp + Dp);
+    fe[7] = w2 * (Sp - Dp);
+    fe[8] = w2 * (Sm + Dm);
+    fe[6] = w2 * (Sm - Dm);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Pc[i] = Pn[i];
-        if (k <= rows) {  // prefetch the next row while this one is processed
-            int rn = y0 + k;
+    for (int i = 0; i < 9; ++i) o[i] = h[i] + k.omega * (fe[i] - h[i]);
+}
+
+template <typename R>
+struct PsiRow {
+    R L, a, b, Rr;  // left neighbour, first cell, second cell, right neighbour
+};
+
+template <int MODE>
+struct WalkArgs {
+    const typename Traits<MODE>::S* fin;
+    typename Traits<MODE>::S* fout;
+    int nx, ny, pitch, nstrips, chunks;
+    long long plane;
+    StepK<typename Traits<MODE>::R> k;
+};
+
+template <int MODE>
+__device__ __forceinline__ void load_row(const WalkArgs<MODE>& a, int r, int cA, int cB, bool vec,
+                                         typename Pair<MODE>::T (&P)[9]) {
+    using S = typename Traits<MODE>::S;
+    using PT = typename Pair<MODE>::T;
+    const S* row = a.fin + (long long)r * a.pitch;
+    if (vec) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = *reinterpret_cast<const PT*>(row + i * a.plane + cA);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const S* p = row + i * a.plane;
+            P[i] = Pair<MODE>::make(to_r<MODE>(p[cA]), to_r<MODE>(p[cB]));
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_pair(const WalkArgs<MODE>& a, int i, int r, int d0, bool svec, bool own0,
+                                           bool own1, typename Traits<MODE>::R v0, typename Traits<MODE>::R v1) {
+    using S = typename Traits<MODE>::S;
+    using PT = typename Pair<MODE>::T;
+    S* p = a.fout + i * a.plane + (long long)r * a.pitch + d0;
+    if (svec) {
+        *reinterpret_cast<PT*>(p) = Pair<MODE>::make(v0, v1);
+    } else {
+        if (own0) p[0] = from_r<MODE>(v0);
+        if (own1) p[1] = from_r<MODE>(v1);
+    }
+}
+
+// Rows [r0, r1) of strip `strip`.
+template <int MODE>
+__device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
+    using R = typename Traits<MODE>::R;
+    using PT = typename Pair<MODE>::T;
+    const int nx = a.nx, ny = a.ny;
+    const int ua = strip * STRIP - 2 + 2 * lane;  // unwrapped first column of this lane's pair
+    const int cA = wrapi(ua, nx), cB = wrapi(ua + 1, nx);
+    const bool vec = (cB == cA + 1) && ((cA & 1) == 0);
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
+    const bool svec = own0 && own1 && vec;
+    const R w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
+
+    PT Nx[9];
+    load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
+    R hp[2][9];           // previous row (to be relaxed), decoded
+    R rho_p0 = 0, rho_p1 = 0;
+    PsiRow<R> A{}, B{}, C{};
+    const int nrows = r1 - r0;
+    for (int k = 0; k <= nrows + 1; ++k) {
+        PT Cur[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Cur[i] = Nx[i];
+        if (k <= nrows) {
+            int rn = r0 + k;
             if (rn >= ny) rn -= ny;
-            const S* b = fin + (long long)rn * nx + xc;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) Pn[i] = decode<MODE>(b[i * plane], off[i]);
+            load_row<MODE>(a, rn, cA, cB, vec, Nx);  // prefetch the next row
         }
-        R rho_c = ((Pc[0] + Pc[1]) + (Pc[2] + Pc[3])) + ((Pc[4] + Pc[5]) + (Pc[6] + Pc[7])) + Pc[8];
-        psi_s[(k & 3) * TX + t] = psi_of(rho_c, rho0, inv_rho0);
-        __syncthreads();
-        if (k >= 2 && owner) {
-            const int y = y0 + k - 2;
-            const R* sm = psi_s + ((k - 2) & 3) * TX;  // row y-1
-            const R* s0 = psi_s + ((k - 1) & 3) * TX;  // row y
-            const R* sp = psi_s + (k & 3) * TX;        // row y+1
-            const R w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
-            const R sx = w1 * (s0[t + 1] - s0[t - 1]) + w2 * ((sp[t + 1] - sp[t - 1]) + (sm[t + 1] - sm[t - 1]));
-            const R sy = w1 * (sp[t] - sm[t]) + w2 * ((sp[t + 1] + sp[t - 1]) - (sm[t + 1] + sm[t - 1]));
-            const R gpsi = -G * s0[t];
-            const R Fx = gpsi * sx, Fy = gpsi * sy;
-
-            const R rho = rho_p;
-            const R inv = R(1) / rho;
-            const R jx = (Pp[1] - Pp[3]) + (Pp[5] - Pp[6]) + (Pp[8] - Pp[7]);
-            const R jy = (Pp[2] - Pp[4]) + (Pp[5] + Pp[6]) - (Pp[7] + Pp[8]);
-            const R ux = (jx + tau * Fx) * inv;  // u + tau F / rho
-            const R uy = (jy + tau * Fy) * inv;
-            const R usq = R(1.5) * (ux * ux + uy * uy);
-            R out[9];
+        R hc[2][9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const R cu = R(cx(i)) * ux + R(cy(i)) * uy;
-                const R feq = wq<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq);
-                out[i] = Pp[i] + omega * (feq - Pp[i]);
+        for (int i = 0; i < 9; ++i) Pair<MODE>::split(Cur[i], hc[0][i], hc[1][i]);
+        const R rho0c = (((hc[0][0] + hc[0][1]) + (hc[0][2] + hc[0][3])) + ((hc[0][4] + hc[0][5]) + (hc[0][6] + hc[0][7])) +
+                         hc[0][8]) + a.k.rho_ref;
+        const R rho1c = (((hc[1][0] + hc[1][1]) + (hc[1][2] + hc[1][3])) + ((hc[1][4] + hc[1][5]) + (hc[1][6] + hc[1][7])) +
+                         hc[1][8]) + a.k.rho_ref;
+        A = B;
+        B = C;
+        C.a = psi_step<MODE>(rho0c, a.k.rho0, a.k.inv_rho0);
+        C.b = psi_step<MODE>(rho1c, a.k.rho0, a.k.inv_rho0);
+        C.L = __shfl_up_sync(0xffffffffu, C.b, 1);
+        C.Rr = __shfl_down_sync(0xffffffffu, C.a, 1);
+        if (k >= 2) {
+            // relax row y = r0 + k - 2 with psi rows A (y-1), B (y), C (y+1)
+            int y = r0 + k - 2;
+            if (y >= ny) y -= ny;
+            R o[2][9];
+            {
+                const R sx = w1 * (B.b - B.L) + w2 * ((C.b - C.L) + (A.b - A.L));
+                const R sy = w1 * (C.a - A.a) + w2 * ((C.b + C.L) - (A.b + A.L));
+                const R g = -a.k.G * B.a;
+                collide_cell<MODE>(hp[0], rho_p0, g * sx, g * sy, a.k, o[0]);
             }
-            const long long ry = (long long)y * nx;
-            const long long rm = (long long)(y == 0 ? ny - 1 : y - 1) * nx;
-            const long long rp = (long long)(y == ny - 1 ? 0 : y + 1) * nx;
-            fout[0 * plane + ry + xc] = encode<MODE>(out[0], off[0]);
-            fout[1 * plane + ry + xp] = encode<MODE>(out[1], off[1]);
-            fout[2 * plane + rp + xc] = encode<MODE>(out[2], off[2]);
-            fout[3 * plane + ry + xm] = encode<MODE>(out[3], off[3]);
-            fout[4 * plane + rm + xc] = encode<MODE>(out[4], off[4]);
-            fout[5 * plane + rp + xp] = encode<MODE>(out[5], off[5]);
-            fout[6 * plane + rp + xm] = encode<MODE>(out[6], off[6]);
-            fout[7 * plane + rm + xm] = encode<MODE>(out[7], off[7]);
-            fout[8 * plane + rm + xp] = encode<MODE>(out[8], off[8]);
+            {
+                const R sx = w1 * (B.Rr - B.a) + w2 * ((C.Rr - C.a) + (A.Rr - A.a));
+                const R sy = w1 * (C.b - A.b) + w2 * ((C.Rr + C.a) - (A.Rr + A.a));
+                const R g = -a.k.G * B.b;
+                collide_cell<MODE>(hp[1], rho_p1, g * sx, g * sy, a.k, o[1]);
+            }
+            if constexpr (MODE == PL_F16_OFFSET) {
+                // Mass-conserving rounding: the rest population absorbs the FP16 rounding
+                // residual of the 8 moving populations of its cell, so the stored mass of a
+                // cell carries one rounding instead of nine.
+                R res0 = R(0), res1 = R(0);
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    const float2 q = __half22float2(__floats2half2_rn(o[0][i], o[1][i]));
+                    res0 += q.x - o[0][i];
+                    res1 += q.y - o[1][i];
+                }
+                o[0][0] -= res0;
+                o[1][0] -= res1;
+            }
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            // c_x = 0 planes: own pair
+            store_pair<MODE>(a, 0, y, ua, svec, own0, own1, o[0][0], o[1][0]);
+            store_pair<MODE>(a, 2, yp, ua, svec, own0, own1, o[0][2], o[1][2]);
+            store_pair<MODE>(a, 4, ym, ua, svec, own0, own1, o[0][4], o[1][4]);
+            // c_x = +1 planes: (left lane's second cell, own first cell)
+            {
+                const R l1 = __shfl_up_sync(0xffffffffu, o[1][1], 1);
+                const R l5 = __shfl_up_sync(0xffffffffu, o[1][5], 1);
+                const R l8 = __shfl_up_sync(0xffffffffu, o[1][8], 1);
+                store_pair<MODE>(a, 1, y, ua, svec, own0, own1, l1, o[0][1]);
+                store_pair<MODE>(a, 5, yp, ua, svec, own0, own1, l5, o[0][5]);
+                store_pair<MODE>(a, 8, ym, ua, svec, own0, own1, l8, o[0][8]);
+            }
+            // c_x = -1 planes: (own second cell, right lane's first cell)
+            {
+                const R r3 = __shfl_down_sync(0xffffffffu, o[0][3], 1);
+                const R r6 = __shfl_down_sync(0xffffffffu, o[0][6], 1);
+                const R r7 = __shfl_down_sync(0xffffffffu, o[0][7], 1);
+                store_pair<MODE>(a, 3, y, ua, svec, own0, own1, o[1][3], r3);
+                store_pair<MODE>(a, 6, yp, ua, svec, own0, own1, o[1][6], r6);
+                store_pair<MODE>(a, 7, ym, ua, svec, own0, own1, o[1][7], r7);
+            }
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Pp[i] = Pc[i];
-        rho_p = rho_c;
+        for (int i = 0; i < 9; ++i) {
+            hp[0][i] = hc[0][i];
+            hp[1][i] = hc[1][i];
+        }
+        rho_p0 = rho0c;
+        rho_p1 = rho1c;
     }
 }
 
-StepTiling default_tiling(int nx, int ny) {
-    StepTiling t;
-    int tx = ((nx + 2 + 31) / 32) * 32;
-    t.tx = tx > 128 ? 128 : tx;
-    t.ty = ny < 32 ? ny : 32;
-    (void)ny;
-    return t;
+// Warp w walks strip (w mod nstrips) over row chunk (w / nstrips); the rows are cut
+// into `chunks` equal chunks, the same cut in every strip.  All warps of a row chunk
+// start together and advance one row per iteration, so horizontally adjacent strips
+// touch the sectors they share (halo columns, partial sectors at strip edges) at the
+// same time and those are served from L2, and each row of a plane is read as one
+// contiguous sweep.
+template <int MODE>
+__global__ void __launch_bounds__(STEP_THREADS) k_step(WalkArgs<MODE> a) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
+    const int strip = (int)(warp % a.nstrips);
+    const long long chunk = warp / a.nstrips;
+    if (chunk >= a.chunks) return;
+    const int r0 = (int)(chunk * a.ny / a.chunks);
+    const int r1 = (int)((chunk + 1) * a.ny / a.chunks);
+    if (r1 > r0) walk_segment<MODE>(a, strip, r0, r1, lane);
 }
 
 template <int MODE>
-static cudaError_t launch_step_t(const LatticeView& v, const PhysParams& p, int src, StepTiling tl, cudaStream_t s) {
+static cudaError_t launch_step_t(const LatticeView& v, const PhysParams& p, int src, cudaStream_t s) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
-    dim3 grid((v.nx + tl.tx - 3) / (tl.tx - 2), (v.ny + tl.ty - 1) / tl.ty);
-    size_t smem = 4 * tl.tx * sizeof(R);
-    k_step<MODE><<<grid, tl.tx, smem, s>>>(static_cast<const S*>(v.pops[src]), static_cast<S*>(v.pops[1 - src]), v.nx,
-                                           v.ny, v.plane, tl.ty, R(p.G), R(p.tau), R(1.0 / p.tau), R(p.rho0),
-                                           R(p.rho_ref));
+    static int blocks_per_sm = 0, sms = 0;
+    if (!blocks_per_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_step<MODE>, STEP_THREADS, 0);
+        if (e != cudaSuccess || blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    WalkArgs<MODE> a;
+    a.fin = static_cast<const S*>(v.pops[src]);
+    a.fout = static_cast<S*>(v.pops[1 - src]);
+    a.nx = v.nx;
+    a.ny = v.ny;
+    a.pitch = v.pitch;
+    a.nstrips = (v.nx + STRIP - 1) / STRIP;
+    a.plane = v.plane;
+    a.k = StepK<R>{R(p.G), R(p.tau), R(1.0 / p.tau), R(p.rho0), R(1.0 / p.rho0),
+                   MODE == PL_F16_OFFSET ? R(p.rho_ref) : R(0)};
+    // as many row chunks per strip as keep every warp resident, and chunks of at
+    // least 8 rows (a chunk also reads its two halo rows)
+    const long long capacity = (long long)blocks_per_sm * sms * (STEP_THREADS / 32);
+    long long chunks = capacity / a.nstrips;
+    const long long max_chunks = v.ny / 8 > 0 ? v.ny / 8 : 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    a.chunks = (int)chunks;
+    const long long warps = chunks * a.nstrips;
+    const long long blocks = (warps + (STEP_THREADS / 32) - 1) / (STEP_THREADS / 32);
+    k_step<MODE><<<(int)blocks, STEP_THREADS, 0, s>>>(a);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step(const LatticeView& v, const PhysParams& p, int src, StepTiling tl, cudaStream_t s) {
-    if (tl.tx < 32 || tl.tx > 256 || (tl.tx & 31) || tl.ty < 1) return cudaErrorInvalidValue;
+    (void)tl;
     switch (v.storage) {
-        case PL_F64: return launch_step_t<PL_F64>(v, p, src, tl, s);
-        case PL_F32: return launch_step_t<PL_F32>(v, p, src, tl, s);
-        case PL_F16_OFFSET: return launch_step_t<PL_F16_OFFSET>(v, p, src, tl, s);
+        case PL_F64: return launch_step_t<PL_F64>(v, p, src, s);
+        case PL_F32: return launch_step_t<PL_F32>(v, p, src, s);
+        case PL_F16_OFFSET: return launch_step_t<PL_F16_OFFSET>(v, p, src, s);
     }
     return cudaErrorInvalidValue;
+}
+
+StepTiling default_tiling(int nx, int ny) {
+    (void)nx;
+    (void)ny;
+    return StepTiling{STEP_THREADS, STRIP};
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -154,7 +360,7 @@ __device__ __forceinline__ double min_image(double d, double n) {
 }
 
 template <int MODE>
-__global__ void k_init_droplets(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, long long plane,
+__global__ void k_init_droplets(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
                                 const pl_droplet* __restrict__ d, int n, double rho_in, double rho_out, double width,
                                 double noise_amp, uint64_t seed, double rho_ref) {
     using R = typename Traits<MODE>::R;
@@ -172,33 +378,35 @@ __global__ void k_init_droplets(typename Traits<MODE>::S* __restrict__ f, int nx
             best = phi > best ? phi : best;
         }
         const double rho = rho_out + (rho_in - rho_out) * best + noise_amp * (2.0 * uniform01_at(seed, (uint64_t)c) - 1.0);
+        const long long o = (long long)y * pitch + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const double fi = wq<double>(i) * rho;
-            f[i * plane + c] = encode<MODE>(R(fi), R(wq<double>(i) * rho_ref));
-        }
+        for (int i = 0; i < 9; ++i) f[i * plane + o] = encode<MODE>(R(wq<double>(i) * rho), R(wq<double>(i) * rho_ref));
     }
 }
 
 template <int MODE>
-__global__ void k_init_from_rho(typename Traits<MODE>::S* __restrict__ f, long long N, long long plane,
+__global__ void k_init_from_rho(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
                                 const double* __restrict__ rho, double rho_ref) {
     using R = typename Traits<MODE>::R;
+    const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const long long o = (c / nx) * pitch + c % nx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i * plane + c] = encode<MODE>(R(wq<double>(i) * rho[c]), R(wq<double>(i) * rho_ref));
+        for (int i = 0; i < 9; ++i) f[i * plane + o] = encode<MODE>(R(wq<double>(i) * rho[c]), R(wq<double>(i) * rho_ref));
     }
 }
 
-// FP64 exchange format <-> storage, one plane per launch (plane index `i`).
+// FP64 dense exchange array <-> one pitched storage plane (plane index `i`).
 template <int MODE>
-__global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, long long N, long long plane, int i,
-                                double* __restrict__ buf, int to_f64, double rho_ref) {
+__global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
+                                int i, double* __restrict__ buf, int to_f64, double rho_ref) {
     using R = typename Traits<MODE>::R;
     const R off = R(wq<double>(i) * rho_ref);
+    const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        if (to_f64) buf[c] = (double)decode<MODE>(f[i * plane + c], off);
-        else f[i * plane + c] = encode<MODE>(R(buf[c]), off);
+        const long long o = i * plane + (c / nx) * pitch + c % nx;
+        if (to_f64) buf[c] = (double)decode<MODE>(f[o], off);
+        else f[o] = encode<MODE>(R(buf[c]), off);
     }
 }
 
@@ -207,67 +415,60 @@ static int grid_for(long long N) {
     return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
+template <int MODE>
+static void init_droplets_t(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in, double rho_out,
+                            double width, double noise_amp, uint64_t seed, cudaStream_t s) {
+    using S = typename Traits<MODE>::S;
+    k_init_droplets<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(
+        static_cast<S*>(v.pops[cur]), v.nx, v.ny, v.pitch, v.plane, v.droplets, n, rho_in, rho_out, width, noise_amp,
+        seed, p.rho_ref);
+}
+
 cudaError_t launch_init_droplets(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in,
                                  double rho_out, double width, double noise_amp, uint64_t seed, cudaStream_t s) {
-    const long long N = (long long)v.nx * v.ny;
     switch (v.storage) {
-        case PL_F64:
-            k_init_droplets<PL_F64><<<grid_for(N), 256, 0, s>>>(static_cast<double*>(v.pops[cur]), v.nx, v.ny, v.plane,
-                                                               v.droplets, n, rho_in, rho_out, width, noise_amp, seed,
-                                                               p.rho_ref);
-            break;
-        case PL_F32:
-            k_init_droplets<PL_F32><<<grid_for(N), 256, 0, s>>>(static_cast<float*>(v.pops[cur]), v.nx, v.ny, v.plane,
-                                                               v.droplets, n, rho_in, rho_out, width, noise_amp, seed,
-                                                               p.rho_ref);
-            break;
-        case PL_F16_OFFSET:
-            k_init_droplets<PL_F16_OFFSET><<<grid_for(N), 256, 0, s>>>(static_cast<__half*>(v.pops[cur]), v.nx, v.ny,
-                                                                      v.plane, v.droplets, n, rho_in, rho_out, width,
-                                                                      noise_amp, seed, p.rho_ref);
-            break;
+        case PL_F64: init_droplets_t<PL_F64>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
+        case PL_F32: init_droplets_t<PL_F32>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
+        case PL_F16_OFFSET: init_droplets_t<PL_F16_OFFSET>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
         default: return cudaErrorInvalidValue;
     }
     note_launches(1);
     return cudaGetLastError();
+}
+
+template <int MODE>
+static void init_rho_t(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho, cudaStream_t s) {
+    using S = typename Traits<MODE>::S;
+    k_init_from_rho<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.ny,
+                                                                           v.pitch, v.plane, d_rho, p.rho_ref);
 }
 
 cudaError_t launch_init_from_rho(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho,
                                  cudaStream_t s) {
-    const long long N = (long long)v.nx * v.ny;
     switch (v.storage) {
-        case PL_F64:
-            k_init_from_rho<PL_F64><<<grid_for(N), 256, 0, s>>>(static_cast<double*>(v.pops[cur]), N, v.plane, d_rho, p.rho_ref);
-            break;
-        case PL_F32:
-            k_init_from_rho<PL_F32><<<grid_for(N), 256, 0, s>>>(static_cast<float*>(v.pops[cur]), N, v.plane, d_rho, p.rho_ref);
-            break;
-        case PL_F16_OFFSET:
-            k_init_from_rho<PL_F16_OFFSET><<<grid_for(N), 256, 0, s>>>(static_cast<__half*>(v.pops[cur]), N, v.plane,
-                                                                      d_rho, p.rho_ref);
-            break;
+        case PL_F64: init_rho_t<PL_F64>(v, p, cur, d_rho, s); break;
+        case PL_F32: init_rho_t<PL_F32>(v, p, cur, d_rho, s); break;
+        case PL_F16_OFFSET: init_rho_t<PL_F16_OFFSET>(v, p, cur, d_rho, s); break;
         default: return cudaErrorInvalidValue;
     }
     note_launches(1);
     return cudaGetLastError();
 }
 
+template <int MODE>
+static void convert_t(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int i, int to_f64,
+                      cudaStream_t s) {
+    using S = typename Traits<MODE>::S;
+    k_plane_convert<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.ny,
+                                                                           v.pitch, v.plane, i, d_buf, to_f64, p.rho_ref);
+}
+
 cudaError_t launch_state_convert(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int i, int to_f64,
                                  cudaStream_t s) {
-    const long long N = (long long)v.nx * v.ny;
     switch (v.storage) {
-        case PL_F64:
-            k_plane_convert<PL_F64><<<grid_for(N), 256, 0, s>>>(static_cast<double*>(v.pops[cur]), N, v.plane, i, d_buf,
-                                                               to_f64, p.rho_ref);
-            break;
-        case PL_F32:
-            k_plane_convert<PL_F32><<<grid_for(N), 256, 0, s>>>(static_cast<float*>(v.pops[cur]), N, v.plane, i, d_buf,
-                                                               to_f64, p.rho_ref);
-            break;
-        case PL_F16_OFFSET:
-            k_plane_convert<PL_F16_OFFSET><<<grid_for(N), 256, 0, s>>>(static_cast<__half*>(v.pops[cur]), N, v.plane, i,
-                                                                      d_buf, to_f64, p.rho_ref);
-            break;
+        case PL_F64: convert_t<PL_F64>(v, p, cur, d_buf, i, to_f64, s); break;
+        case PL_F32: convert_t<PL_F32>(v, p, cur, d_buf, i, to_f64, s); break;
+        case PL_F16_OFFSET: convert_t<PL_F16_OFFSET>(v, p, cur, d_buf, i, to_f64, s); break;
         default: return cudaErrorInvalidValue;
     }
     note_launches(1);

@@ -105,9 +105,17 @@ def field_droplets(n: int, nx: int, ny: int, rmin: float, rmax: float, seed: int
     return [(float(a), float(b), float(c)) for a, b, c in zip(cx, cy, r)]
 
 
+# Coexistence densities of the scheme at G = -5.5, tau = 0.8 (plateaus of a relaxed
+# flat interface).  The field starts there: started from 2.0 / 0.15, the relaxation
+# transient at tau = 0.8 drives the vapour density negative within 100 steps.
+FIELD_RHO_IN, FIELD_RHO_OUT = 2.2727, 0.0743
+
+
 def field_4096(storage: int = F16_OFFSET, seed: int = 3, side: int = 4096, n_drop: int = 400) -> Lattice:
     return Lattice(side, side, storage=storage, tau=0.8,
                    droplets=field_droplets(n_drop, side, side, 8.0, 40.0, 100 + seed),
+                   rho_in=FIELD_RHO_IN, rho_out=FIELD_RHO_OUT,
+                   rho_ref=0.5 * (FIELD_RHO_IN + FIELD_RHO_OUT),
                    seed=seed, steps=5000, K=100, mlp=MLP_BF16, weight_seed=10 + seed)
 
 
