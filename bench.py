@@ -267,15 +267,19 @@ def run_gb300(args):
         return res, lat
 
     storage = wl.F16_OFFSET if args.storage == "f16" else wl.F32
+    def measure_drift(lat, K):
+        """Relative mass drift |M - M0| / M0 after the timed region: one more interval,
+        read before and after its correction (whose projection targets M0)."""
+        lat.step(K)
+        pre = lat.metrics()
+        lat.correct()
+        post = lat.metrics()
+        M0 = post["mass0"]
+        return {"pre_correction": abs(pre["mass"] - M0) / M0, "post_correction": abs(post["mass"] - M0) / M0,
+                "after_steps": post["step"]}
+
     main, lat = time_workload(storage, args.steps, args.warmup, True)
-    # mass drift after the timed region: one more interval, read before and after its correction
-    lat.step(main["job"].K)
-    pre = lat.metrics()
-    lat.correct()
-    post = lat.metrics()
-    M0 = post["mass0"]
-    drift = {"pre_correction": abs(pre["mass"] - M0) / M0, "post_correction": abs(post["mass"] - M0) / M0,
-             "after_steps": post["step"]}
+    drift = measure_drift(lat, main["job"].K)
     job = main["job"]
     K = job.K
     cells = job.cells
@@ -310,13 +314,14 @@ def run_gb300(args):
     fp32 = None
     if not args.no_fp32:
         r32, lat32 = time_workload(wl.F32, max(3, args.steps // 2), 1, False)
+        drift32 = measure_drift(lat32, K)
         lat32.close()
         del lat32
         torch.cuda.empty_cache()
         v32 = cells * K * max(3, args.steps // 2) * world / (r32["t_ms"] / 1e3) / 1e6
         a32 = cells * BYTES_PER_UPDATE[wl.F32] / (r32["step_kernel_ms"] / 1e3) / 1e9
         fp32 = {"value": v32, "unit": "MLUPS", "step_kernel_GBps": a32, "frac": a32 / peak,
-                "speedup_f16_over_f32": value / v32}
+                "speedup_f16_over_f32": value / v32, "mass_drift": drift32}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

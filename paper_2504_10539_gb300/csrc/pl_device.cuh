@@ -78,6 +78,31 @@ __device__ __forceinline__ double uniform01_at(uint64_t seed, uint64_t k) {
     return (double)(splitmix64_at(seed, k) >> 11) * (1.0 / 9007199254740992.0);
 }
 
+// MurmurHash3's 32-bit finaliser (Appleby), used as a counter-based source of dither bits.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// Stochastic rounding of two FP32 values to FP16, packed (a -> low half, b -> high half):
+// 13 dither bits are added below the FP16 mantissa's last bit and the result is truncated,
+// so E[rounded] = value for values in the normal FP16 range (|v| >= 2^-14).  Bits 0-12 of
+// rnd dither a, bits 16-28 dither b.
+__device__ __forceinline__ __half2 sr_pack_half2(float a, float b, uint32_t rnd) {
+    const float da = __uint_as_float(__float_as_uint(a) + (rnd & 0x1FFFu));
+    const float db = __uint_as_float(__float_as_uint(b) + ((rnd >> 16) & 0x1FFFu));
+    uint32_t r;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(db), "f"(da));
+    return *reinterpret_cast<__half2*>(&r);
+}
+__device__ __forceinline__ __half sr_half(float a, uint32_t rnd) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(a) + (rnd & 0x1FFFu)));
+}
+
 // Per-lattice device record: reductions land here, later kernels read them,
 // the host copies it out for pl_metrics.
 struct DevRecord {

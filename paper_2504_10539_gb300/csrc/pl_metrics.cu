@@ -325,8 +325,10 @@ __global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, int nx, i
         feq9<R>(r, jxc / r, jyc / r, fo);
         const long long o = (c / nx) * pitch + c % nx;
         if constexpr (MODE == PL_F16_OFFSET) {
-            // stored offsets h_i + (f_i^eq' - f_i^eq), with the rest population absorbing the
-            // FP16 rounding residual of the other eight (one rounding per cell's mass)
+            // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
+            // nearest, the rest population taking the cell's corrected stored mass minus their
+            // rounded values and rounded stochastically, so that small per-cell changes
+            // (below half an FP16 step) are realised on average instead of being rounded away
             float hn[9];
             float res = 0.0f;
 #pragma unroll
@@ -337,7 +339,8 @@ __global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, int nx, i
                 res += __half2float(q) - hn[i];
                 f[i * plane + o] = q;
             }
-            f[o] = __float2half_rn(hn[0] - res);
+            const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u));
+            f[o] = sr_half(hn[0] - res, rnd);
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {

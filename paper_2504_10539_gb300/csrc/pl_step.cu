@@ -190,7 +190,7 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
     PT Nx[9];
     load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
     R hp[2][9];           // previous row (to be relaxed), decoded
-    R rho_p0 = 0, rho_p1 = 0;
+    R rho_p0 = 0, rho_p1 = 0, sh_p0 = 0, sh_p1 = 0;
     PsiRow<R> A{}, B{}, C{};
     const int nrows = r1 - r0;
     for (int k = 0; k <= nrows + 1; ++k) {
@@ -205,10 +205,13 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
         R hc[2][9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) Pair<MODE>::split(Cur[i], hc[0][i], hc[1][i]);
-        const R rho0c = (((hc[0][0] + hc[0][1]) + (hc[0][2] + hc[0][3])) + ((hc[0][4] + hc[0][5]) + (hc[0][6] + hc[0][7])) +
-                         hc[0][8]) + a.k.rho_ref;
-        const R rho1c = (((hc[1][0] + hc[1][1]) + (hc[1][2] + hc[1][3])) + ((hc[1][4] + hc[1][5]) + (hc[1][6] + hc[1][7])) +
-                         hc[1][8]) + a.k.rho_ref;
+        // stored (offset-space) sums of the two cells, and their densities
+        const R sh0c = (((hc[0][0] + hc[0][1]) + (hc[0][2] + hc[0][3])) + ((hc[0][4] + hc[0][5]) + (hc[0][6] + hc[0][7])) +
+                        hc[0][8]);
+        const R sh1c = (((hc[1][0] + hc[1][1]) + (hc[1][2] + hc[1][3])) + ((hc[1][4] + hc[1][5]) + (hc[1][6] + hc[1][7])) +
+                        hc[1][8]);
+        const R rho0c = sh0c + a.k.rho_ref;
+        const R rho1c = sh1c + a.k.rho_ref;
         A = B;
         B = C;
         C.a = psi_step<MODE>(rho0c, a.k.rho0, a.k.inv_rho0);
@@ -232,23 +235,42 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
                 const R g = -a.k.G * B.b;
                 collide_cell<MODE>(hp[1], rho_p1, g * sx, g * sy, a.k, o[1]);
             }
+            if constexpr (MODE == PL_F32) {
+                // BGK conserves mass; take the rest population from that balance so the
+                // FP32 weights (which do not sum to one exactly) leave no systematic drift.
+                o[0][0] = sh_p0 - ((((o[0][1] + o[0][2]) + (o[0][3] + o[0][4])) + ((o[0][5] + o[0][6]) + (o[0][7] + o[0][8]))));
+                o[1][0] = sh_p1 - ((((o[1][1] + o[1][2]) + (o[1][3] + o[1][4])) + ((o[1][5] + o[1][6]) + (o[1][7] + o[1][8]))));
+            }
+            __half2 rest16;
             if constexpr (MODE == PL_F16_OFFSET) {
-                // Mass-conserving rounding: the rest population absorbs the FP16 rounding
-                // residual of the 8 moving populations of its cell, so the stored mass of a
-                // cell carries one rounding instead of nine.
-                R res0 = R(0), res1 = R(0);
+                // Mass-conserving FP16 storage: the 8 moving populations are rounded to
+                // nearest; the rest population takes the cell's stored mass minus their
+                // rounded values, and is rounded stochastically (unbiased), so the stored
+                // mass changes by one zero-mean rounding per cell and step.
+                float q0 = 0.0f, q1 = 0.0f;
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const float2 q = __half22float2(__floats2half2_rn(o[0][i], o[1][i]));
-                    res0 += q.x - o[0][i];
-                    res1 += q.y - o[1][i];
+                    q0 += q.x;
+                    q1 += q.y;
                 }
-                o[0][0] -= res0;
-                o[1][0] -= res1;
+                const uint32_t rnd = fmix32(__float_as_uint(hp[0][0]) ^ (__float_as_uint(hp[1][1]) * 0x9E3779B1u) ^
+                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du));
+                rest16 = sr_pack_half2(sh_p0 - q0, sh_p1 - q1, rnd);
             }
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             // c_x = 0 planes: own pair
-            store_pair<MODE>(a, 0, y, ua, svec, own0, own1, o[0][0], o[1][0]);
+            if constexpr (MODE == PL_F16_OFFSET) {
+                __half* p = a.fout + (long long)y * a.pitch + ua;
+                if (svec) {
+                    *reinterpret_cast<__half2*>(p) = rest16;
+                } else {
+                    if (own0) p[0] = __low2half(rest16);
+                    if (own1) p[1] = __high2half(rest16);
+                }
+            } else {
+                store_pair<MODE>(a, 0, y, ua, svec, own0, own1, o[0][0], o[1][0]);
+            }
             store_pair<MODE>(a, 2, yp, ua, svec, own0, own1, o[0][2], o[1][2]);
             store_pair<MODE>(a, 4, ym, ua, svec, own0, own1, o[0][4], o[1][4]);
             // c_x = +1 planes: (left lane's second cell, own first cell)
@@ -277,6 +299,8 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
         }
         rho_p0 = rho0c;
         rho_p1 = rho1c;
+        sh_p0 = sh0c;
+        sh_p1 = sh1c;
     }
 }
 
