@@ -183,6 +183,25 @@ PL_API int pl_get_mlp_field(pl_lattice* lat, double* host_out3);
 PL_API int pl_get_state(pl_lattice* lat, double* host_f, int64_t* step);
 PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
 
+/* Allocation-free metrics (the paper has no counterpart: this serves callers that
+ * cannot allocate device memory - code running inside an allocator or pool callback,
+ * or a host that must not grow its device footprint after start-up - and therefore
+ * cannot hand the library the scratch buffer that pl_lattice_create carves up).
+ * Computes the Eq. 9-15 metrics and the mass (no Laplace fields: NaN; mass0: NaN,
+ * step: 0) of populations that the caller passes at dev_pops (device memory, element
+ * type given by `storage`, 9 planes of ny rows of `pitch` >= nx elements, x fastest,
+ * FP16-offset values h_i = f_i - w_i*rho_ref) and writes the record to host memory at
+ * `out`.  Its scratch (density field, block partials, record) is a static device array
+ * of 8.07 MB that every GPU loading the library keeps until the process exits; it calls
+ * no cudaMalloc, cudaFree or allocating library routine.  Lattices above 1,048,576
+ * cells are rejected with PL_ERR_BUDGET (and a message on stderr).  The first call on a
+ * device looks up the array's device address with that device current; make that first
+ * call before any stream capture.  All calls share the one array: calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  Enqueues on `stream` and synchronises it. */
+PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32_t ny, int32_t pitch, int32_t storage,
+                              double rho_ref, double threshold, void* stream, pl_metric_record* out);
+
 /* Sticky lattice status (PL_OK or the first device-detected error).  Synchronises. */
 PL_API int pl_lattice_status(pl_lattice* lat);
 

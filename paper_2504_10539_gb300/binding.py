@@ -99,6 +99,7 @@ def _L():
             "pl_get_state": (ctypes.c_int, [vp, P(d), P(i64)]),
             "pl_set_state": (ctypes.c_int, [vp, P(d), i64]),
             "pl_lattice_status": (ctypes.c_int, [vp]),
+            "pl_metrics_noalloc": (ctypes.c_int, [vp, i32, i32, i32, i32, d, d, vp, P(pl_metric_record)]),
             "pl_destroy": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sigs.items():
@@ -228,6 +229,15 @@ def pl_set_state(h, f: np.ndarray, step: int = 0):
 
 def pl_lattice_status(h) -> int:
     return _L().pl_lattice_status(ctypes.c_void_p(h))
+
+
+def pl_metrics_noalloc(dev_ptr: int, nx: int, ny: int, pitch: int, storage: int, rho_ref: float,
+                       threshold: float, stream: int) -> dict:
+    """Metrics of caller-held populations without any device allocation (static scratch)."""
+    m = pl_metric_record()
+    _chk("pl_metrics_noalloc", _L().pl_metrics_noalloc(ctypes.c_void_p(dev_ptr), nx, ny, pitch, storage, rho_ref,
+                                                        threshold, ctypes.c_void_p(stream), ctypes.byref(m)))
+    return m.as_dict()
 
 
 def pl_destroy(h):

@@ -6,6 +6,11 @@
 // of cells, reduces them by a fixed warp-shuffle tree into one partial per
 // block, and a one-block kernel folds the partials in block order.  The result
 // does not depend on scheduling, so repeated runs are bit-identical.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
 #include "pl_device.cuh"
 #include "pl_kernels.h"
 
@@ -390,4 +395,130 @@ cudaError_t launch_correction(const LatticeView& v, const PhysParams& p, int cur
     return cudaErrorInvalidValue;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Allocation-free metrics (pl_metrics_noalloc).  Some callers cannot allocate device memory
+// at all: code running where cudaMalloc is forbidden or unavailable (inside another
+// library's allocator or its stream-ordered pool callbacks, or a host that must not grow
+// its device footprint after start-up), or code that owns no scratch buffer to lend.  For
+// them this variant of the metric reduction keeps its scratch - the density field, the
+// per-block partials and the record - in one file-scope __device__ array instead of in a
+// caller buffer.  Every GPU that loads the library holds the array until the process exits.
+
+constexpr long long NOALLOC_MAX_CELLS = 1ll << 20;  // largest lattice: 1,048,576 cells
+constexpr int NOALLOC_BLOCKS = 1024;                 // reduction blocks (partials capacity)
+constexpr size_t NOALLOC_RHO_BYTES = (size_t)NOALLOC_MAX_CELLS * sizeof(double);
+constexpr size_t NOALLOC_PART_BYTES = (size_t)NOALLOC_BLOCKS * PARTIAL_STRIDE * sizeof(double);
+constexpr size_t NOALLOC_BYTES = NOALLOC_RHO_BYTES + NOALLOC_PART_BYTES + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Density of every cell from populations in the library's layout, into a dense array.
+template <int MODE>
+__global__ void k_density_noalloc(const typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch,
+                                  long long plane, typename Traits<MODE>::R rho_ref,
+                                  typename Traits<MODE>::R* __restrict__ rho) {
+    using R = typename Traits<MODE>::R;
+    const long long N = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const long long o = (c / nx) * pitch + c % nx;
+        R P[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
+        rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+    }
+}
+
+template <int MODE>
+static void metrics_noalloc_t(const void* pops, int nx, int ny, int pitch, double rho_ref, double threshold,
+                              unsigned char* scratch, DevRecord* rec, cudaStream_t s) {
+    using S = typename Traits<MODE>::S;
+    using R = typename Traits<MODE>::R;
+    const long long N = (long long)nx * ny;
+    long long nb = (N + RB_THREADS - 1) / RB_THREADS;
+    if (nb > NOALLOC_BLOCKS) nb = NOALLOC_BLOCKS;
+    R* rho = reinterpret_cast<R*>(scratch);
+    double* partials = reinterpret_cast<double*>(scratch + NOALLOC_RHO_BYTES);
+    k_density_noalloc<MODE><<<(int)nb, RB_THREADS, 0, s>>>(static_cast<const S*>(pops), nx, ny, pitch,
+                                                           (long long)pitch * ny, R(rho_ref), rho);
+    k_grad_reduce<R><<<(int)nb, RB_THREADS, 0, s>>>(rho, nx, ny, nullptr, threshold, partials);
+    k_final_metrics<<<1, RB_THREADS, 0, s>>>(partials, (int)nb, rec, 0);
+    note_launches(3);
+}
+static_assert(sizeof(DevRecord) <= 256, "record slot of the static scratch");
+
 }  // namespace pl
+
+namespace {
+// Device address of g_noalloc_scratch, looked up once per device (with that device current).
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+}  // namespace
+
+extern "C" PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32_t ny, int32_t pitch, int32_t storage,
+                                         double rho_ref, double threshold, void* stream, pl_metric_record* out) {
+    using namespace pl;
+    if (!dev_pops || !out || nx < 1 || ny < 1 || pitch < nx || !std::isfinite(rho_ref) || !std::isfinite(threshold))
+        return PL_ERR_INVALID_ARG;
+    if (storage != PL_F64 && storage != PL_F32 && storage != PL_F16_OFFSET) return PL_ERR_INVALID_ARG;
+    const size_t esize = storage == PL_F64 ? 8 : (storage == PL_F32 ? 4 : 2);
+    if ((uintptr_t)dev_pops % esize) return PL_ERR_INVALID_ARG;
+    if ((long long)nx * ny > NOALLOC_MAX_CELLS) {
+        std::fprintf(stderr, "pl_metrics_noalloc: lattice of %lld cells exceeds the %lld-cell maximum of the "
+                             "static scratch\n", (long long)nx * ny, NOALLOC_MAX_CELLS);
+        return PL_ERR_BUDGET;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return PL_ERR_CUDA;
+    }
+    unsigned char* scratch;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                (void)cudaGetLastError();
+                return PL_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+    }
+    DevRecord* rec = reinterpret_cast<DevRecord*>(scratch + NOALLOC_RHO_BYTES + NOALLOC_PART_BYTES);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = cudaMemsetAsync(rec, 0, sizeof(DevRecord), s);  // the record starts at zero on every call
+    if (e == cudaSuccess) {
+        switch (storage) {
+            case PL_F64: metrics_noalloc_t<PL_F64>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
+            case PL_F32: metrics_noalloc_t<PL_F32>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
+            default: metrics_noalloc_t<PL_F16_OFFSET>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
+        }
+        e = cudaGetLastError();
+    }
+    DevRecord r;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&r, rec, sizeof(r), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return PL_ERR_CUDA;
+    }
+    const double N = (double)nx * (double)ny;
+    std::memset(out, 0, sizeof(*out));
+    out->mass = r.mass;
+    out->count = r.count;
+    out->W = (double)r.count / N;
+    out->G_max = r.gmax;
+    out->delta_rho = r.rho_max - r.rho_min;
+    out->W_eff = r.gmax > 0.0 ? r.sum_g / (r.gmax * N) : 0.0;
+    out->E_int = r.sum_g2;
+    out->rho_max = r.rho_max;
+    out->rho_min = r.rho_min;
+    out->sum_g = r.sum_g;
+    out->sum_g2 = r.sum_g2;
+    out->R_eq = out->rho_in = out->rho_out = out->p_in = out->p_out = out->dP = NAN;
+    out->mass0 = NAN;
+    return PL_OK;
+}
