@@ -2,22 +2,24 @@
 """Throughput benchmark of the coupled PINN-LBM droplet hot path on GB300.
 
 Metric: MLUPS (million lattice-cell updates per second) and the HBM-roofline
-fraction of the fused collide-stream kernel, FP16-offset storage against plain
-FP32 storage.
+fraction of the fused collide-stream kernel; batched FP16-offset storage against
+plain per-lattice FP32 storage; p50/p99 job latency of a served request stream.
 
-One bench step = one coupling interval of the method (arXiv 2504.10539 Sec. II-C):
-K = 100 time steps of Eq. 1, one interface correction (network inference on
-every cell + projection + apply) and the interface metrics (Eqs. 9-16), read
-back to the host.  Workload: the 4096x4096 periodic coalescence field
-(400 droplets, radii U[8,40], tau = 0.8, G = -5.5), FP16-offset populations
-with FP32 arithmetic and the BF16 tensor-core network (FP32 network until the
-tensor-core kernel is in), synthetic seeded input.  Both population buffers
-(2 x 302 MB) exceed the 129 MB L2, so no L2 flush is needed between steps.
+One bench step = one coupling interval (arXiv 2504.10539 Sec. II-C) of the batched
+workload: 256 independent periodic droplet lattices (side U{64..1024}, G U[-6,-5],
+tau over the stable part of U[0.6,1.2], one centred droplet R U[0.1,0.35] side),
+FP16-offset populations, FP32 arithmetic, BF16 tcgen05 network: K = 100 time steps
+of every lattice, one interface correction (network inference on every cell +
+projection + apply) and the metrics of every lattice, as one replayed CUDA graph.
+The populations (2 x ~1.8 GB) exceed the 129 MB L2, so no flush is needed.
 
---impl reference times the FP64 CPU oracle (test infrastructure) on the host
-cores on a bounded crop of the same workload.
-Multi-GPU (torchrun): every rank runs an independent replica of the field
-(weak scaling, no collective on the data path).
+Also reported: the same 256 lattices run one by one with FP32 storage through the
+single-lattice API ("fp32_plain"); a served Poisson request stream (continuous
+batching, p50/p99 latency, offered vs served MLUPS); the single 4096x4096 droplet
+field with FP16 and FP32 storage (step-kernel HBM fractions); the FP64 CPU oracle on
+a bounded sample (cpu_baseline).  --impl reference times that oracle alone.
+Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no
+collective on the data path).
 """
 import argparse
 import ctypes
@@ -28,7 +30,6 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -44,21 +45,34 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--side", type=int, default=4096)
-    ap.add_argument("--mlp", default="auto", choices=["auto", "bf16", "f32"])
+    ap.add_argument("--lattices", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--field-side", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
-    ap.add_argument("--storage", default="f16", choices=["f16", "f32"],
-                    help="storage of the timed workload (profiling aid; the headline is f16)")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-field", action="store_true")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dist_max(dist, v, device):
+    """Maximum of v over the ranks of the process group (v itself without one)."""
+    import torch
+    if dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(updates_per_rank, t_ms_max, world):
+    """Whole-job throughput: the cell updates all ranks processed over the slowest rank's time."""
+    return updates_per_rank * world / (t_ms_max / 1e3) / 1e6
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -95,11 +109,8 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 8:
-                rows.append(parts)
+        rows = [[p.strip() for p in line.split(",")] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 8]
         os.unlink(self.path)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
@@ -116,57 +127,58 @@ class ClockSampler:
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
 
 
 def step_kernel_hash():
     h = hashlib.sha1()
-    for f in ("pl_step.cu", "pl_device.cuh"):
+    for f in ("pl_step.cu", "pl_device.cuh", "pl_kernels.h"):
         h.update(open(os.path.join(ROOT, "paper_2504_10539_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(storage, side):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if it
-    was taken on the current kernel source; else None."""
+def profiled_traffic(key, units):
+    """DRAM bytes of one step-kernel launch scaled from the committed ncu summary (taken on a
+    smaller case; traffic grows with the cells updated), if it was taken on the current
+    kernel source; else None."""
     p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get("%s_%d" % (STORAGE_NAME[storage], side))
+    e = json.load(open(p)).get(key)
     if not e or e.get("kernel_sha1") != step_kernel_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return e["dram_bytes_per_cell_update"] * units
 
 
-def cpu_sample_workload(side):
-    from paper_2504_10539_gb300 import workloads as wl
-    # same droplet density and radius distribution as the full field
-    n_drop = max(1, round(400 * (side / 4096.0) ** 2))
-    return wl.field_4096(storage=wl.F16_OFFSET, side=side, n_drop=n_drop)
-
-
-def time_oracle(job, steps, budget_s=None):
-    """Run the FP64 oracle on `job` for `steps` bench steps (K LBM steps + correction +
-    metrics each) or until budget_s elapsed; returns (updates, seconds, steps_done)."""
+def oracle_interval(job, blob):
+    """One coupling interval of `job` on the FP64 oracle: returns (cell updates, seconds)."""
     import oracle as O
     f = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
                                       job.noise_amp, job.seed))
     M0 = O.mass(f)
-    blob = job.weights()
-    done = 0
     t0 = time.perf_counter()
-    while done < steps:
-        O.step(f, job.K, job.G, job.tau, job.rho0)
-        O.correct(f, blob, job.beta_rho, job.beta_u, M0, O.MLP_F64)
-        O.metrics_rho(O.density(f))
-        done += 1
-        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+    O.step(f, job.K, job.G, job.tau, job.rho0)
+    O.correct(f, blob, job.beta_rho, job.beta_u, M0, O.MLP_F64)
+    O.metrics_rho(O.density(f))
+    return job.cells * job.K, time.perf_counter() - t0
+
+
+def cpu_sample(jobs, budget_s):
+    """The oracle on the batch's lattices, smallest first, one interval each, until budget_s."""
+    import oracle as O
+    O.set_num_threads(os.cpu_count() or 1)
+    blob = jobs[0].weights()
+    upd = secs = 0.0
+    done = []
+    for job in sorted(jobs, key=lambda j: j.cells):
+        u, s = oracle_interval(job, blob)
+        upd += u
+        secs += s
+        done.append("%dx%d" % (job.nx, job.ny))
+        if secs > budget_s:
             break
-    dt = time.perf_counter() - t0
-    return job.cells * job.K * done, dt, done
+    return upd, secs, done, O.num_threads()
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -175,23 +187,27 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    from paper_2504_10539_gb300 import workloads as wl
     import oracle as O
-    job = cpu_sample_workload(512)
     O.set_num_threads(os.cpu_count() or 1)
-    # each bench step is one coupling interval on the 512x512 crop
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        time_oracle(job, 1)
-    upd, dt, done = time_oracle(job, args.steps)
-    mlups = upd / dt / 1e6
+    jobs = sorted(wl.batch_256(n=args.lattices, seed=4), key=lambda j: j.cells)
+    blob = jobs[0].weights()
+    for k in range(min(args.warmup, 1)):
+        oracle_interval(jobs[k % len(jobs)], blob)
+    upd = secs = 0.0
+    for k in range(args.steps):   # each step: one interval of one lattice, smallest lattices in turn
+        u, s = oracle_interval(jobs[k % 8], blob)
+        upd += u
+        secs += s
+    mlups = upd / secs / 1e6
     line = {
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
-        "steps": done, "warmup": args.warmup, "ms_per_step": dt * 1e3 / done, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "field_%d crop 512x512 (FP64 CPU oracle)" % args.side, "K": job.K,
-                   "droplets": len(job.droplets)},
+        "config": {"workload": "batch_%d (FP64 CPU oracle, bounded sample)" % args.lattices, "K": 100},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
-                         "sample": "512x512 crop of the droplet field (%d droplets), %d coupling intervals of "
-                                   "K=%d steps + FP64 network correction + metrics" % (len(job.droplets), done, job.K)},
+                         "sample": "one coupling interval (K=100 steps + FP64 network correction + metrics) per "
+                                   "step on the 8 smallest lattices of the batch in turn"},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -203,6 +219,7 @@ def run_gb300(args):
     import numpy as np
     import torch
     from paper_2504_10539_gb300 import binding as B
+    from paper_2504_10539_gb300 import serve as S
     from paper_2504_10539_gb300 import workloads as wl
 
     rank, world, local = dist_env()
@@ -218,147 +235,178 @@ def run_gb300(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return dist_max(dist, v, "cuda")
 
-    mlp = {"auto": wl.MLP_BF16, "bf16": wl.MLP_BF16, "f32": wl.MLP_F32}[args.mlp]
-
-    def build(storage):
-        job = wl.field_4096(storage=storage, seed=3 + rank, side=args.side)
-        job.mlp = mlp
-        return job, B.Lattice.from_workload(job)
-
-    def time_workload(storage, steps, warmup, with_clocks):
-        job, lat = build(storage)
-        s = lat.stream
-        K = job.K
-        for _ in range(warmup):
-            lat.step(K)
-            lat.correct()
-            lat.metrics()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        clocks = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local])
-                              if "CUDA_VISIBLE_DEVICES" in os.environ else local) if with_clocks else None
-        barrier()
-        if clocks:
-            clocks.start()
-        l0 = B.pl_kernel_launches()
-        e0.record(s)
-        for k in range(steps):
-            ev[k][0].record(s)
-            lat.step(K)                  # K fused collide-stream launches
-            ev[k][1].record(s)
-            lat.correct()                # network + projection + apply
-            m = lat.metrics()            # Eqs. 9-16, FP64 record to the host
-        e1.record(s)
-        e1.synchronize()
-        launches = B.pl_kernel_launches() - l0
-        clk = clocks.stop() if clocks else None
-        barrier()
-        t_ms = max_over_ranks(e0.elapsed_time(e1))
-        step_ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / K  # per step-kernel launch
-        assert m["status"] == 0, m
-        res = {"job": job, "t_ms": t_ms, "step_kernel_ms": step_ms, "launches": launches, "clocks": clk,
-               "metrics": m}
-        return res, lat
-
-    storage = wl.F16_OFFSET if args.storage == "f16" else wl.F32
-    def measure_drift(lat, K):
-        """Relative mass drift |M - M0| / M0 after the timed region: one more interval,
-        read before and after its correction (whose projection targets M0)."""
-        lat.step(K)
-        pre = lat.metrics()
-        lat.correct()
-        post = lat.metrics()
-        M0 = post["mass0"]
-        return {"pre_correction": abs(pre["mass"] - M0) / M0, "post_correction": abs(post["mass"] - M0) / M0,
-                "after_steps": post["step"]}
-
-    main, lat = time_workload(storage, args.steps, args.warmup, True)
-    drift = measure_drift(lat, main["job"].K)
-    job = main["job"]
-    K = job.K
-    cells = job.cells
-    updates = cells * K * args.steps * world
-    value = updates / (main["t_ms"] / 1e3) / 1e6
     peak, peak_kind = measured_peaks()
-    achieved = cells * BYTES_PER_UPDATE[storage] / (main["step_kernel_ms"] / 1e3) / 1e9
-    traffic = profiled_traffic(storage, args.side)
+    gpu_index = local
+    if "CUDA_VISIBLE_DEVICES" in os.environ:
+        gpu_index = int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local])
 
-    # end to end through the C ABI with host buffers: new network weights uploaded each
-    # interval (the paper retrains per coupling round), metrics record read back
+    # --------------------------------------------------------------- batched FP16 (headline)
+    K = 100
+    n_int = args.warmup + args.steps + 2
+    jobs = wl.batch_256(n=args.lattices, seed=4 + rank, steps=n_int * K, K=K)
+    blob = np.ascontiguousarray(jobs[0].weights())
+    cells = sum(j.cells for j in jobs)
+    budget = B.pl_batch_overhead_bytes(len(jobs) + 1) + sum(B.pl_batch_job_bytes(B.job_params(j)) for j in jobs)
+    bt = B.Batch(wl.F16_OFFSET, wl.MLP_BF16, K, budget + (64 << 20), max_jobs=len(jobs) + 1)
+    bt.set_weights(blob)
+    for j in jobs:
+        assert bt.submit(j) is not None
+    rows_per_chunk = bt.autotune()
+    for _ in range(args.warmup):
+        bt.advance(1)
+    B.pl_batch_interval_times(bt.h)
+    clocks = ClockSampler(gpu_index)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    clocks.start()
+    l0 = B.pl_kernel_launches()
+    e0.record(bt.stream)
+    step_ms, int_ms = [], []
+    for _ in range(args.steps):
+        bt.advance(1)
+        s_ms, i_ms = B.pl_batch_interval_times(bt.h)   # events recorded inside the replayed interval
+        step_ms.append(s_ms)
+        int_ms.append(i_ms)
+    e1.record(bt.stream)
+    e1.synchronize()
+    launches = B.pl_kernel_launches() - l0
+    clk = clocks.stop()
+    barrier()
+    t_ms = max_over_ranks(e0.elapsed_time(e1))
+    value = aggregate_mlups(cells * K * args.steps, t_ms, world)
+    step_launch_ms = statistics.mean(step_ms) / K
+    achieved = cells * BYTES_PER_UPDATE[wl.F16_OFFSET] / (step_launch_ms / 1e3) / 1e9
+    live = B.pl_batch_metrics(bt.h)
+    statuses = sorted({r["status"] for r in live})
+    drift = max(abs(r["metrics"]["mass"] - r["metrics"]["mass0"]) / r["metrics"]["mass0"] for r in live)
+
+    # end to end through the C ABI with host buffers: the weights uploaded from host memory
+    # each interval (the paper retrains per coupling round) and every job's metric record read
     e2e = None
     if not args.no_e2e:
-        blob = np.ascontiguousarray(job.weights())
-        rec = B.pl_metric_record()
-        n_e2e = max(3, min(args.steps, 10))
+        n_e2e = min(args.steps, 5)
+        rec_bytes = ctypes.sizeof(B.pl_job_result) * len(jobs)
         barrier()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
-            B.pl_set_mlp_weights(lat.h, blob)
-            B.pl_step(lat.h, K)
-            B.pl_apply_correction(lat.h)
-            B.pl_metrics(lat.h)
+            B.pl_batch_set_mlp_weights(bt.h, blob)
+            B.pl_batch_advance(bt.h, 1)
+            B.pl_batch_metrics(bt.h)
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": cells * K * n_e2e * world / t_e2e / 1e6, "unit": "MLUPS",
-               "h2d_bytes_per_step": int(blob.nbytes), "d2h_bytes_per_step": ctypes.sizeof(rec)}
-    lat.close()
-    del lat
+               "h2d_bytes_per_step": int(blob.nbytes), "d2h_bytes_per_step": int(rec_bytes)}
+    bt.close()
+    del bt
     torch.cuda.empty_cache()
 
+    # --------------------------------------------------------------- plain per-lattice FP32
     fp32 = None
     if not args.no_fp32:
-        r32, lat32 = time_workload(wl.F32, max(3, args.steps // 2), 1, False)
-        drift32 = measure_drift(lat32, K)
-        lat32.close()
-        del lat32
+        lats = []
+        t_plain = 0.0
+        n_plain = 2
+        for j in jobs:
+            j32 = wl.Lattice(**{**j.__dict__, "storage": wl.F32, "mlp": wl.MLP_BF16})
+            lat = B.Lattice(B.job_params(j32))
+            lat.init_droplets(j32.droplets, j32.rho_in, j32.rho_out, j32.width, j32.noise_amp, j32.seed)
+            lat.set_weights(blob)
+            lat.run(K, K)                              # warm-up interval (graph capture)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(lat.stream)
+            lat.run(n_plain * K, K)
+            ev1.record(lat.stream)
+            ev1.synchronize()
+            t_plain += ev0.elapsed_time(ev1)
+            lat.close()
+            del lat
         torch.cuda.empty_cache()
-        v32 = cells * K * max(3, args.steps // 2) * world / (r32["t_ms"] / 1e3) / 1e6
-        a32 = cells * BYTES_PER_UPDATE[wl.F32] / (r32["step_kernel_ms"] / 1e3) / 1e9
-        fp32 = {"value": v32, "unit": "MLUPS", "step_kernel_GBps": a32, "frac": a32 / peak,
-                "speedup_f16_over_f32": value / v32, "mass_drift": drift32}
+        v32 = cells * K * n_plain / (t_plain / 1e3) / 1e6
+        fp32 = {"value": v32, "unit": "MLUPS", "form": "each lattice alone, single-lattice API, FP32 storage, "
+                                                       "BF16 network, graph per interval",
+                "speedup_batched_f16_over_plain_f32": value / v32}
 
+    # --------------------------------------------------------------- served request stream
+    serving = None
+    if not args.no_serve and rank == 0:
+        reqs = wl.serve_poisson(n_requests=args.serve_requests, seed=5)
+        srv = S.Server(wl.F16_OFFSET, wl.MLP_BF16, K, 150 * (1 << 30), reqs[0].job.weights(), max_jobs=1024)
+        out = srv.run(reqs, max_wall_s=240.0)
+        srv.close()
+        torch.cuda.empty_cache()
+        serving = {k: out[k] for k in ("jobs_done", "jobs_submitted", "p50_latency_s", "p99_latency_s",
+                                       "p50_queue_wait_s", "served_mlups", "offered_mlups", "elapsed_s",
+                                       "peak_active_jobs")}
+        serving["statuses"] = {str(k): v for k, v in out["statuses"].items()}
+        serving["workload"] = ("Poisson 200 req/s, side U{64..2048 step 32}, 1-8 droplets, G U[-6,-5], "
+                               "steps U[1000,20000] rounded up to K=100, 150 GB budget, %d requests"
+                               % args.serve_requests)
+
+    # --------------------------------------------------------------- single 4096^2 field
+    field = None
+    if not args.no_field:
+        field = {}
+        for st in (wl.F16_OFFSET, wl.F32):
+            job = wl.field_4096(storage=st, side=args.field_side)
+            job.mlp = wl.MLP_BF16
+            lat = B.Lattice.from_workload(job)
+            lat.step(K)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+            for a, b in ev:
+                a.record(lat.stream)
+                lat.step(K)
+                b.record(lat.stream)
+                lat.correct()
+            m = lat.metrics()
+            ms = statistics.mean(a.elapsed_time(b) for a, b in ev) / K
+            gbs = job.cells * BYTES_PER_UPDATE[st] / (ms / 1e3) / 1e9
+            field[STORAGE_NAME[st]] = {"step_kernel_ms": ms, "GBps": gbs, "frac": gbs / peak,
+                                       "mlups_steps_only": job.cells / (ms / 1e3) / 1e6,
+                                       "mass_drift_post_correction": abs(m["mass"] - m["mass0"]) / m["mass0"],
+                                       "traffic": profiled_traffic("%s_field" % STORAGE_NAME[st], job.cells)}
+            lat.close()
+            del lat
+            torch.cuda.empty_cache()
+
+    # --------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        import oracle as O
-        O.set_num_threads(os.cpu_count() or 1)
-        sjob = cpu_sample_workload(512)
-        upd, dt, done = time_oracle(sjob, 20, budget_s=12.0)
-        cpu = {"value": upd / dt / 1e6, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
-               "sample": "512x512 crop of the field (%d droplets), %d coupling intervals of K=%d steps + FP64 "
-                         "network correction + metrics, %.1f s" % (len(sjob.droplets), done, sjob.K, dt)}
+        upd, secs, done, cores = cpu_sample(jobs, 12.0)
+        cpu = {"value": upd / secs / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle, one coupling interval (K=100 steps + FP64 network correction + metrics) of "
+                         "the %d smallest lattices of the batch (%s), %.1f s" % (len(done), ", ".join(done), secs)}
 
     if rank == 0:
-        clk = main["clocks"] or {}
         line = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": main["t_ms"] / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "field_%d" % args.side, "lattice": "%dx%d periodic D2Q9" % (args.side, args.side),
-                       "storage": STORAGE_NAME[storage], "network": {wl.MLP_BF16: "bf16-tcgen05",
-                                                                     wl.MLP_F32: "f32-simt"}[mlp],
-                       "droplets": len(job.droplets), "tau": job.tau, "G": job.G, "K": K,
-                       "step": "K lattice steps + correction + metrics",
-                       "l2": "inputs larger than L2 (2 x %.0f MB populations)" % (cells * 18 / 1e6),
+            "config": {"workload": "batch_%d" % len(jobs), "lattices": len(jobs), "cells": cells,
+                       "storage": "f16_offset", "network": "bf16-tcgen05", "K": K,
+                       "step": "one coupling interval: K lattice steps + correction + metrics of every lattice "
+                               "(one CUDA graph replay)",
+                       "rows_per_chunk": rows_per_chunk,
+                       "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (cells * 18 / 1e9),
                        "parallelism": "replicas x%d" % world},
-            "roofline": {"bound": "hbm", "kernel": "k_step<%s>" % STORAGE_NAME[storage], "achieved": achieved,
-                         "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                         "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[storage],
-                         "step_kernel_ms": main["step_kernel_ms"]},
+            "roofline": {"bound": "hbm", "kernel": "k_step<f16_offset> (batched)", "achieved": achieved,
+                         "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": profiled_traffic("f16_offset_batch", cells),
+                         "algorithmic_bytes_per_launch": cells * BYTES_PER_UPDATE[wl.F16_OFFSET],
+                         "step_kernel_ms": step_launch_ms,
+                         "interval_ms_mean": statistics.mean(int_ms)},
             "e2e": e2e,
-            "gpu_launches": main["launches"],
+            "gpu_launches": launches,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons", [])},
             "fp32_plain": fp32,
+            "serving": serving,
+            "field_4096": field,
             "cpu_baseline": cpu,
-            "final_metrics": {k: main["metrics"][k] for k in ("mass", "mass0", "W", "G_max", "W_eff", "E_int")},
-            "mass_drift": drift,
+            "batch_checks": {"statuses": statuses, "max_mass_drift_post_correction": drift},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

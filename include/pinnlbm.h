@@ -208,6 +208,76 @@ PL_API int pl_lattice_status(pl_lattice* lat);
 /* Free the handle; the caller's device memory is not touched. */
 PL_API int pl_destroy(pl_lattice* lat);
 
+/* Self-test of the device-side failure detection: one thread waits, with the bounded
+ * mbarrier wait used by the tensor-core kernel, on a barrier that nothing arrives on;
+ * after limit_ns (<= 5 s) the wait gives up and the kernel writes PL_ERR_TIMEOUT to the
+ * caller's device int at dev_status.  Returns that status (PL_ERR_TIMEOUT when the
+ * detection works).  Synchronises `stream`. */
+PL_API int pl_selftest_wait_timeout(void* dev_status, int64_t limit_ns, void* stream);
+
+/* ---------------------------------------------------------------------------------
+ * Batched and served lattices (many independent droplet-relaxation jobs of different
+ * sizes advancing together; Sec. II-C's coupling loop applied to every job).
+ *
+ * A batch owns one caller buffer: a fixed head (pl_batch_overhead_bytes) and an arena
+ * from which each admitted job's lattice memory (pl_batch_job_bytes) is carved.  The
+ * buffer size is the device-memory budget: a job that does not fit is refused with
+ * PL_ERR_BUDGET and may be resubmitted after others retire.  All jobs of a batch share
+ * the storage type, the network arithmetic, the network weights and the correction
+ * interval K.  The batch advances in intervals of K steps; each interval runs, for every
+ * active job, K time steps, one interface correction and the metrics, as one replayed
+ * CUDA graph whose kernels read the device-resident job table.  A job's step count is
+ * rounded up to a multiple of K; it retires at the end of the interval that reaches it.
+ * Each job's results are bit-identical whether it runs alone or with others.
+ * --------------------------------------------------------------------------------- */
+typedef struct pl_batch pl_batch;
+
+/* Result of a retired job: its id, steps taken, size, status and final metrics. */
+typedef struct pl_job_result {
+    int64_t id;
+    int64_t steps;
+    int32_t nx, ny;
+    int32_t status;   /* PL_OK or the job's sticky error (e.g. PL_ERR_NONPHYSICAL) */
+    int32_t pad;
+    pl_metric_record metrics;
+} pl_job_result;
+
+/* Bytes of the fixed head of a batch holding up to max_jobs jobs (weights, job table,
+ * droplet staging); the rest of the caller buffer is the arena. */
+PL_API int pl_batch_overhead_bytes(int32_t max_jobs, size_t* bytes_out);
+/* Arena bytes one job with these parameters takes. */
+PL_API int pl_batch_job_bytes(const pl_params* p, size_t* bytes_out);
+/* Create a batch over caller memory dev_mem[0, bytes) (256-byte aligned) on `stream`. */
+PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_jobs, void* dev_mem, size_t bytes,
+                           void* stream, pl_batch** out);
+/* Network weights shared by all jobs (layout of pl_set_mlp_weights). */
+PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* host_blob, size_t n);
+/* Admit one job: lattice parameters (storage must match the batch), initial droplets
+ * (as pl_lattice_init_droplets) and the number of steps.  PL_ERR_BUDGET if its memory or
+ * a job slot is not available now.  Writes the job id. */
+PL_API int pl_batch_submit(pl_batch* b, const pl_params* p, const pl_droplet* droplets, int n, double rho_in,
+                           double rho_out, double width, double noise_amp, uint64_t seed, int64_t steps,
+                           int64_t* job_id);
+/* Advance every active job by `intervals` intervals of K steps (asynchronous). */
+PL_API int pl_batch_advance(pl_batch* b, int32_t intervals);
+/* Collect up to max results of retired jobs, oldest first.  Synchronises the stream. */
+PL_API int pl_batch_poll(pl_batch* b, pl_job_result* out, int32_t max, int32_t* n_out);
+/* Active jobs, their total cells, and arena use. */
+PL_API int pl_batch_info(pl_batch* b, int32_t* active, int64_t* cells, size_t* arena_used, size_t* arena_total);
+/* Populations of an active job in the exchange format, and its step count.  Synchronises. */
+PL_API int pl_batch_get_state(pl_batch* b, int64_t job_id, double* host_f, int64_t* steps);
+/* Choose the step kernel's decomposition (rows per warp chunk) for the current job mix by
+ * timing candidates (cached per storage and total-cells octave; force = 1 re-times). */
+PL_API int pl_batch_autotune(pl_batch* b, int32_t force, int32_t* rows_per_chunk);
+/* Latest metric records (as of the last completed interval) of up to max active jobs, in
+ * admission order.  Synchronises the stream. */
+PL_API int pl_batch_metrics(pl_batch* b, pl_job_result* out, int32_t max, int32_t* n_out);
+/* Device time of the last interval: its K step launches and the whole interval (steps,
+ * correction, metrics), from events recorded inside the interval.  Synchronises. */
+PL_API int pl_batch_interval_times(pl_batch* b, float* steps_ms, float* interval_ms);
+/* Free the handle; the caller's device memory is not touched. */
+PL_API int pl_batch_destroy(pl_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,16 @@ class pl_metric_record(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class pl_job_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("steps", ctypes.c_int64), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32), ("metrics", pl_metric_record)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "metrics")}
+        d["metrics"] = self.metrics.as_dict()
+        return d
+
+
 class PLError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -100,7 +110,22 @@ def _L():
             "pl_set_state": (ctypes.c_int, [vp, P(d), i64]),
             "pl_lattice_status": (ctypes.c_int, [vp]),
             "pl_metrics_noalloc": (ctypes.c_int, [vp, i32, i32, i32, i32, d, d, vp, P(pl_metric_record)]),
+            "pl_batch_overhead_bytes": (ctypes.c_int, [i32, P(sz)]),
+            "pl_batch_job_bytes": (ctypes.c_int, [P(pl_params), P(sz)]),
+            "pl_batch_create": (ctypes.c_int, [i32, i32, i32, i32, vp, sz, vp, P(vp)]),
+            "pl_batch_set_mlp_weights": (ctypes.c_int, [vp, P(ctypes.c_float), sz]),
+            "pl_batch_submit": (ctypes.c_int, [vp, P(pl_params), P(pl_droplet), ctypes.c_int, d, d, d, d, u64, i64,
+                                               P(i64)]),
+            "pl_batch_advance": (ctypes.c_int, [vp, i32]),
+            "pl_batch_poll": (ctypes.c_int, [vp, P(pl_job_result), i32, P(i32)]),
+            "pl_batch_info": (ctypes.c_int, [vp, P(i32), P(i64), P(sz), P(sz)]),
+            "pl_batch_get_state": (ctypes.c_int, [vp, i64, P(d), P(i64)]),
+            "pl_batch_autotune": (ctypes.c_int, [vp, i32, P(i32)]),
+            "pl_batch_metrics": (ctypes.c_int, [vp, P(pl_job_result), i32, P(i32)]),
+            "pl_batch_interval_times": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float)]),
+            "pl_batch_destroy": (ctypes.c_int, [vp]),
             "pl_destroy": (ctypes.c_int, [vp]),
+            "pl_selftest_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
         }
         for name, (res, args) in sigs.items():
             if hasattr(L, name):
@@ -244,6 +269,11 @@ def pl_destroy(h):
     return _chk("pl_destroy", _L().pl_destroy(ctypes.c_void_p(h)))
 
 
+def pl_selftest_wait_timeout(dev_status_ptr: int, limit_ns: int, stream: int = 0) -> int:
+    """Runs the bounded-wait self-test; returns the status it reports (PL_ERR_TIMEOUT expected)."""
+    return _L().pl_selftest_wait_timeout(ctypes.c_void_p(dev_status_ptr), int(limit_ns), ctypes.c_void_p(stream))
+
+
 # ----------------------------------------------------------------------------- owner of one lattice
 
 class Lattice:
@@ -313,6 +343,155 @@ class Lattice:
     def close(self):
         if getattr(self, "h", None):
             pl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------- batches of lattices
+
+def pl_batch_overhead_bytes(max_jobs: int) -> int:
+    n = ctypes.c_size_t()
+    _chk("pl_batch_overhead_bytes", _L().pl_batch_overhead_bytes(max_jobs, ctypes.byref(n)))
+    return n.value
+
+
+def pl_batch_job_bytes(p: pl_params) -> int:
+    n = ctypes.c_size_t()
+    _chk("pl_batch_job_bytes", _L().pl_batch_job_bytes(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def pl_batch_create(storage: int, mlp: int, K: int, max_jobs: int, dev_ptr: int, nbytes: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _chk("pl_batch_create", _L().pl_batch_create(storage, mlp, K, max_jobs, ctypes.c_void_p(dev_ptr), nbytes,
+                                                  ctypes.c_void_p(stream), ctypes.byref(h)))
+    return h.value
+
+
+def pl_batch_set_mlp_weights(h, blob: np.ndarray):
+    b = np.ascontiguousarray(blob, dtype=np.float32)
+    return _chk("pl_batch_set_mlp_weights", _L().pl_batch_set_mlp_weights(
+        ctypes.c_void_p(h), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+
+
+def pl_batch_submit(h, p: pl_params, droplets, rho_in, rho_out, width, noise_amp, seed, steps):
+    """Returns the job id, or None when the batch has no room for it now (PL_ERR_BUDGET)."""
+    n = len(droplets)
+    arr = (pl_droplet * max(n, 1))(*[pl_droplet(*map(float, dd)) for dd in droplets])
+    jid = ctypes.c_int64()
+    st = _L().pl_batch_submit(ctypes.c_void_p(h), ctypes.byref(p), arr, n, rho_in, rho_out, width, noise_amp,
+                              seed & (2 ** 64 - 1), steps, ctypes.byref(jid))
+    if st == PL_ERR_BUDGET:
+        return None
+    _chk("pl_batch_submit", st)
+    return jid.value
+
+
+def pl_batch_advance(h, intervals: int = 1):
+    return _chk("pl_batch_advance", _L().pl_batch_advance(ctypes.c_void_p(h), intervals))
+
+
+def pl_batch_poll(h, max_results: int = 1024):
+    out = (pl_job_result * max(max_results, 1))()
+    n = ctypes.c_int32()
+    _chk("pl_batch_poll", _L().pl_batch_poll(ctypes.c_void_p(h), out, max_results, ctypes.byref(n)))
+    return [out[k].as_dict() for k in range(n.value)]
+
+
+def pl_batch_info(h) -> dict:
+    a, c, u, t = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_size_t(), ctypes.c_size_t()
+    _chk("pl_batch_info", _L().pl_batch_info(ctypes.c_void_p(h), ctypes.byref(a), ctypes.byref(c), ctypes.byref(u),
+                                              ctypes.byref(t)))
+    return {"active": a.value, "cells": c.value, "arena_used": u.value, "arena_total": t.value}
+
+
+def pl_batch_get_state(h, job_id: int, nx: int, ny: int):
+    out = np.empty((9, ny, nx), dtype=np.float64)
+    step = ctypes.c_int64()
+    _chk("pl_batch_get_state", _L().pl_batch_get_state(ctypes.c_void_p(h), job_id, _dptr(out), ctypes.byref(step)))
+    return out, step.value
+
+
+def pl_batch_autotune(h, force: bool = False) -> int:
+    r = ctypes.c_int32()
+    _chk("pl_batch_autotune", _L().pl_batch_autotune(ctypes.c_void_p(h), int(force), ctypes.byref(r)))
+    return r.value
+
+
+def pl_batch_metrics(h, max_results: int = 4096):
+    out = (pl_job_result * max(max_results, 1))()
+    n = ctypes.c_int32()
+    _chk("pl_batch_metrics", _L().pl_batch_metrics(ctypes.c_void_p(h), out, max_results, ctypes.byref(n)))
+    return [out[k].as_dict() for k in range(n.value)]
+
+
+def pl_batch_interval_times(h):
+    s, t = ctypes.c_float(), ctypes.c_float()
+    _chk("pl_batch_interval_times", _L().pl_batch_interval_times(ctypes.c_void_p(h), ctypes.byref(s),
+                                                                  ctypes.byref(t)))
+    return s.value, t.value
+
+
+def pl_batch_destroy(h):
+    return _chk("pl_batch_destroy", _L().pl_batch_destroy(ctypes.c_void_p(h)))
+
+
+def job_params(job) -> pl_params:
+    """C parameters of a ``workloads.Lattice`` description."""
+    return pl_params_default(job.nx, job.ny, storage=job.storage, mlp=job.mlp, G=job.G, tau=job.tau, rho0=job.rho0,
+                             rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u)
+
+
+class Batch:
+    """A batch over a torch-allocated device buffer of `budget_bytes` (the device budget)."""
+
+    def __init__(self, storage: int, mlp: int, K: int, budget_bytes: int, max_jobs: int = 1024, device="cuda",
+                 stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.mem = torch.empty(int(budget_bytes), dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.mem.device)
+        self.stream.wait_stream(torch.cuda.current_stream(self.mem.device))
+        self.K = K
+        self.h = pl_batch_create(storage, mlp, K, max_jobs, self.mem.data_ptr(), int(budget_bytes),
+                                 self.stream.cuda_stream)
+        self.jobs = {}
+
+    def set_weights(self, blob):
+        pl_batch_set_mlp_weights(self.h, blob)
+
+    def submit(self, job, steps=None):
+        jid = pl_batch_submit(self.h, job_params(job), job.droplets, job.rho_in, job.rho_out, job.width,
+                              job.noise_amp, job.seed, int(steps if steps is not None else job.steps))
+        if jid is not None:
+            self.jobs[jid] = job
+        return jid
+
+    def advance(self, intervals=1):
+        pl_batch_advance(self.h, intervals)
+
+    def poll(self):
+        return pl_batch_poll(self.h)
+
+    def info(self):
+        return pl_batch_info(self.h)
+
+    def state(self, jid):
+        job = self.jobs[jid]
+        return pl_batch_get_state(self.h, jid, job.nx, job.ny)
+
+    def autotune(self, force=False):
+        return pl_batch_autotune(self.h, force)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pl_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

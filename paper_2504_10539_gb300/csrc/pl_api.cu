@@ -1,9 +1,9 @@
-// C ABI of the PINN-LBM hot path (declared in include/pinnlbm.h).
+// C ABI of the PINN-LBM hot path, single-lattice calls (declared in include/pinnlbm.h).
 //
-// Host-side bookkeeping only: argument checks, carving the caller's device
-// buffer, stream-ordered launches of the kernels, CUDA-graph capture of the
-// coupled run, and the few synchronising read-backs.  No device memory is
-// allocated here: everything lives in the buffer the caller passes in.
+// Host-side bookkeeping only: argument checks, carving the caller's device buffer,
+// the lattice's one-entry job table, stream-ordered launches of the table kernels,
+// CUDA-graph capture of the coupled run, and the few synchronising read-backs.  No
+// device memory is allocated here: everything lives in the buffer the caller passes in.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -15,60 +15,15 @@
 #include <utility>
 #include <vector>
 
-#include "pinnlbm.h"
-#include "pl_device.cuh"
-#include "pl_kernels.h"
+#include "pl_host.h"
 
 namespace pl {
-cudaError_t launch_mlp_simt(const LatticeView& v, int mlp_mode, cudaStream_t s);
-cudaError_t launch_mlp_tc(const LatticeView& v, cudaStream_t s);
 
-cudaError_t launch_mlp_field(const LatticeView& v, int mlp_mode, cudaStream_t s) {
-    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(v, s);
-    return launch_mlp_simt(v, mlp_mode, s);
-}
-}  // namespace pl
+thread_local int g_last_cuda_error = 0;
 
-namespace pl {
 static std::atomic<long long> g_launches{0};
 void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
-}  // namespace pl
-
-using namespace pl;
-
-static thread_local int g_last_cuda_error = 0;
-
-// On failure: remember the error for pl_last_cuda_error() and clear the
-// runtime's last-error slot so that it does not surface in a later call.
-#define PL_CUDA(call)                                         \
-    do {                                                      \
-        cudaError_t e_ = (call);                              \
-        if (e_ != cudaSuccess) {                              \
-            g_last_cuda_error = (int)e_;                      \
-            (void)cudaGetLastError();                         \
-            return PL_ERR_CUDA;                               \
-        }                                                     \
-    } while (0)
-
-namespace {
-
-constexpr size_t ALIGN = 256;
-inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
-
-size_t storage_bytes(int storage) { return storage == PL_F64 ? 8 : (storage == PL_F32 ? 4 : 2); }
-size_t scratch_elem_bytes(int storage) { return storage == PL_F64 ? 8 : 4; }
-// Stored rows are padded to a multiple of 8 populations so that every row, and
-// every even column pair, is aligned for vector access.
-int row_pitch(int nx) { return (nx + 7) / 8 * 8; }
-size_t plane_elems(const pl_params* p) { return (size_t)row_pitch(p->nx) * p->ny; }
-
-constexpr int MLP_BLOB = 64 * 2 + 64 + 128 * 64 + 128 + 128 * 128 + 128 + 64 * 128 + 64 + 3 * 64 + 3;
-constexpr int MAX_RED_BLOCKS = 1024;
-
-struct Layout {
-    size_t pops[2], scratch, partials, rec, w32, wbf16, droplets, total;
-};
 
 int check_params(const pl_params* p) {
     if (!p) return PL_ERR_INVALID_ARG;
@@ -84,45 +39,164 @@ int check_params(const pl_params* p) {
     return PL_OK;
 }
 
-Layout layout_for(const pl_params* p) {
-    Layout L;
+LatLayout lattice_layout(const pl_params* p) {
+    LatLayout L;
     const size_t N = (size_t)p->nx * p->ny;
+    L.pitch = row_pitch(p->nx);
+    L.plane = (long long)L.pitch * p->ny;
+    L.red_blocks = red_blocks_for((long long)N);
     size_t o = 0;
     for (int b = 0; b < 2; ++b) {
         L.pops[b] = o;
-        o = align_up(o + 9 * plane_elems(p) * storage_bytes(p->storage));
+        o = align_up(o + 9 * (size_t)L.plane * storage_bytes(p->storage));
     }
     L.scratch = o;  // rho, jx, jy, g, out3[3]: 7 fields (also >= 8N bytes for FP64 staging)
     o = align_up(o + 7 * N * scratch_elem_bytes(p->storage));
     L.partials = o;
-    o = align_up(o + (size_t)MAX_RED_BLOCKS * 8 * sizeof(double));
+    o = align_up(o + (size_t)L.red_blocks * PARTIAL_STRIDE * sizeof(double));
     L.rec = o;
     o = align_up(o + sizeof(DevRecord));
-    L.w32 = o;
-    o = align_up(o + (size_t)MLP_BLOB * sizeof(float));
-    L.wbf16 = o;
-    o = align_up(o + bf16_weight_elems() * sizeof(uint16_t));
-    L.droplets = o;
-    o = align_up(o + (size_t)PL_MAX_DROPLETS * sizeof(pl_droplet));
     L.total = o;
     return L;
 }
 
-}  // namespace
+void fill_desc(LatDesc& d, const pl_params* p, const LatLayout& L, char* base) {
+    std::memset(&d, 0, sizeof(d));
+    const size_t N = (size_t)p->nx * p->ny;
+    const size_t se = scratch_elem_bytes(p->storage);
+    d.pops[0] = base + L.pops[0];
+    d.pops[1] = base + L.pops[1];
+    char* sc = base + L.scratch;
+    d.rho = sc;
+    d.jx = sc + 1 * N * se;
+    d.jy = sc + 2 * N * se;
+    d.g = sc + 3 * N * se;
+    d.out3 = sc + 4 * N * se;
+    d.partials = reinterpret_cast<double*>(base + L.partials);
+    d.rec = reinterpret_cast<DevRecord*>(base + L.rec);
+    d.plane = L.plane;
+    d.nx = p->nx;
+    d.ny = p->ny;
+    d.pitch = L.pitch;
+    d.phase = 0;
+    d.nstrips = (p->nx + STRIP - 1) / STRIP;
+    d.chunks = 1;
+    d.red_blocks = L.red_blocks;
+    d.has_centre = 0;
+    d.G = p->G;
+    d.tau = p->tau;
+    d.rho0 = p->rho0;
+    d.rho_ref = p->rho_ref;
+    d.beta_rho = p->beta_rho;
+    d.beta_u = p->beta_u;
+    d.threshold = p->threshold;
+    d.width = 2.0;
+}
 
-struct GraphKey {
-    int K, parity, nsteps;
-    bool operator<(const GraphKey& o) const {
-        if (K != o.K) return K < o.K;
-        if (parity != o.parity) return parity < o.parity;
-        return nsteps < o.nsteps;
+void set_chunks(LatDesc& d, int rows_per_chunk) {
+    if (rows_per_chunk < 1) rows_per_chunk = 1;
+    int c = (d.ny + rows_per_chunk - 1) / rows_per_chunk;
+    d.chunks = c < 1 ? 1 : c;
+}
+
+void set_chunks_single(LatDesc& d, int storage) {
+    long long chunks = (long long)step_capacity_warps(storage) / d.nstrips;
+    const long long max_chunks = d.ny / 8 > 0 ? d.ny / 8 : 1;
+    if (chunks > max_chunks) chunks = max_chunks;
+    if (chunks < 1) chunks = 1;
+    d.chunks = (int)chunks;
+}
+
+// Device region of a table: header | descriptors | warp_pre | blk_pre | tile_pre | seq[2].
+static size_t tab_off_desc(int cap) { (void)cap; return align_up(sizeof(TabHeader)); }
+static size_t tab_off_warp(int cap) { return align_up(tab_off_desc(cap) + (size_t)cap * sizeof(LatDesc)); }
+static size_t tab_off_blk(int cap) { return align_up(tab_off_warp(cap) + (size_t)(cap + 1) * sizeof(long long)); }
+static size_t tab_off_tile(int cap) { return align_up(tab_off_blk(cap) + (size_t)(cap + 1) * sizeof(int)); }
+static size_t tab_off_seq(int cap) { return align_up(tab_off_tile(cap) + (size_t)(cap + 1) * sizeof(long long)); }
+
+size_t Table::bytes(int c) { return align_up(tab_off_seq(c) + 2 * sizeof(unsigned)); }
+
+void Table::carve(char* base, int capacity) {
+    cap = capacity;
+    dev = base;
+    view.hdr = reinterpret_cast<const TabHeader*>(base);
+    view.d = reinterpret_cast<const LatDesc*>(base + tab_off_desc(cap));
+    view.warp_pre = reinterpret_cast<const long long*>(base + tab_off_warp(cap));
+    view.blk_pre = reinterpret_cast<const int*>(base + tab_off_blk(cap));
+    view.tile_pre = reinterpret_cast<const long long*>(base + tab_off_tile(cap));
+    view.seq = reinterpret_cast<unsigned*>(base + tab_off_seq(cap));
+    staging.assign(tab_off_seq(cap), 0);
+}
+
+cudaError_t Table::upload(cudaStream_t s) {
+    const int n = (int)d.size();
+    if (n > cap) return cudaErrorInvalidValue;
+    std::memset(staging.data(), 0, staging.size());
+    long long* wp = reinterpret_cast<long long*>(staging.data() + tab_off_warp(cap));
+    int* bp = reinterpret_cast<int*>(staging.data() + tab_off_blk(cap));
+    long long* tp = reinterpret_cast<long long*>(staging.data() + tab_off_tile(cap));
+    wp[0] = 0;
+    bp[0] = 0;
+    tp[0] = 0;
+    for (int j = 0; j < n; ++j) {
+        const long long N = (long long)d[j].nx * d[j].ny;
+        wp[j + 1] = wp[j] + (long long)d[j].nstrips * d[j].chunks;
+        bp[j + 1] = bp[j] + d[j].red_blocks;
+        tp[j + 1] = tp[j] + (N + MLP_TILE - 1) / MLP_TILE;
     }
+    TabHeader h;
+    h.n = n;
+    h.total_warps = wp[n];
+    h.total_blocks = bp[n];
+    h.total_tiles = tp[n];
+    total_warps = wp[n];
+    total_blocks = bp[n];
+    total_tiles = tp[n];
+    std::memcpy(staging.data(), &h, sizeof(h));
+    if (n) std::memcpy(staging.data() + tab_off_desc(cap), d.data(), (size_t)n * sizeof(LatDesc));
+    return cudaMemcpyAsync(dev, staging.data(), staging.size(), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t Table::reset_seq(cudaStream_t s) { return cudaMemsetAsync(dev + tab_off_seq(cap), 0, 2 * sizeof(unsigned), s); }
+
+}  // namespace pl
+
+using namespace pl;
+
+namespace {
+
+// Lattice buffer: lattice arrays | table (1 entry) | weights FP32 | weights BF16 | droplets.
+struct SingleLayout {
+    LatLayout lat;
+    size_t table, w32, wbf16, droplets, total;
 };
 
+SingleLayout single_layout(const pl_params* p) {
+    SingleLayout S;
+    S.lat = lattice_layout(p);
+    size_t o = S.lat.total;
+    S.table = o;
+    o = align_up(o + Table::bytes(1));
+    S.w32 = o;
+    o = align_up(o + (size_t)MLP_BLOB * sizeof(float));
+    S.wbf16 = o;
+    o = align_up(o + bf16_weight_elems() * sizeof(uint16_t));
+    S.droplets = o;
+    o = align_up(o + (size_t)PL_MAX_DROPLETS * sizeof(pl_droplet));
+    S.total = o;
+    return S;
+}
+
+struct GraphKey {
+    int K, parity;
+    bool operator<(const GraphKey& o) const { return K != o.K ? K < o.K : parity < o.parity; }
+};
 struct GraphEntry {
     cudaGraphExec_t exec;
     long long kernels;  // kernel nodes per replay
 };
+
+}  // namespace
 
 struct pl_lattice {
     pl_params p;
@@ -130,14 +204,15 @@ struct pl_lattice {
     char* base;
     size_t bytes;
     cudaStream_t stream;
-    LatticeView v;
-    StepTiling tiling;
-    int cur;                 // buffer holding the current post-streaming state
+    SingleLayout S;
+    LatticeView v;     // per-lattice kernels (init, state exchange)
+    Table tab;         // one-entry job table for the table kernels
+    float* w32;
+    uint16_t* wbf16;
+    int cur;           // buffer holding the current post-streaming state
     long long step;
     int initialised;
     int weights_set;
-    int has_centre;
-    double cx0, cy0, width;
     std::vector<pl_droplet> h_droplets;
     std::vector<float> h_weights;
     std::map<GraphKey, GraphEntry> graphs;
@@ -194,7 +269,7 @@ int pl_lattice_bytes(const pl_params* p, size_t* bytes_out) {
     int st = check_params(p);
     if (st) return st;
     if (!bytes_out) return PL_ERR_INVALID_ARG;
-    *bytes_out = layout_for(p).total;
+    *bytes_out = single_layout(p).total;
     return PL_OK;
 }
 
@@ -202,8 +277,8 @@ int pl_lattice_create(const pl_params* p, void* dev_mem, size_t bytes, void* str
     int st = check_params(p);
     if (st) return st;
     if (!dev_mem || !out || ((uintptr_t)dev_mem % ALIGN) != 0) return PL_ERR_INVALID_ARG;
-    Layout Ly = layout_for(p);
-    if (bytes < Ly.total) return PL_ERR_BUDGET;
+    SingleLayout S = single_layout(p);
+    if (bytes < S.total) return PL_ERR_BUDGET;
     pl_lattice* L = new (std::nothrow) pl_lattice();
     if (!L) return PL_ERR_BUDGET;
     L->p = *p;
@@ -211,40 +286,45 @@ int pl_lattice_create(const pl_params* p, void* dev_mem, size_t bytes, void* str
     L->base = static_cast<char*>(dev_mem);
     L->bytes = bytes;
     L->stream = static_cast<cudaStream_t>(stream);
-    const size_t N = (size_t)p->nx * p->ny;
-    const size_t se = scratch_elem_bytes(p->storage);
+    L->S = S;
+    LatDesc d;
+    fill_desc(d, p, S.lat, L->base);
+    set_chunks_single(d, p->storage);
+    L->tab.carve(L->base + S.table, 1);
+    L->tab.d.assign(1, d);
     LatticeView& v = L->v;
     v.nx = p->nx;
     v.ny = p->ny;
     v.storage = p->storage;
-    v.pitch = row_pitch(p->nx);
-    v.plane = (long long)plane_elems(p);
-    v.pops[0] = L->base + Ly.pops[0];
-    v.pops[1] = L->base + Ly.pops[1];
-    char* sc = L->base + Ly.scratch;
-    v.rho = sc;
-    v.jx = sc + 1 * N * se;
-    v.jy = sc + 2 * N * se;
-    v.g = sc + 3 * N * se;
-    v.out3 = sc + 4 * N * se;
-    v.partials = reinterpret_cast<double*>(L->base + Ly.partials);
-    v.max_blocks = MAX_RED_BLOCKS;
-    v.rec = reinterpret_cast<DevRecord*>(L->base + Ly.rec);
-    v.w32 = reinterpret_cast<const float*>(L->base + Ly.w32);
-    v.wbf16 = reinterpret_cast<const uint16_t*>(L->base + Ly.wbf16);
-    v.droplets = reinterpret_cast<const pl_droplet*>(L->base + Ly.droplets);
-    L->tiling = default_tiling(p->nx, p->ny);
+    v.pitch = S.lat.pitch;
+    v.plane = S.lat.plane;
+    v.pops[0] = d.pops[0];
+    v.pops[1] = d.pops[1];
+    v.rho = d.rho;
+    v.rec = d.rec;
+    v.droplets = reinterpret_cast<const pl_droplet*>(L->base + S.droplets);
+    L->w32 = reinterpret_cast<float*>(L->base + S.w32);
+    L->wbf16 = reinterpret_cast<uint16_t*>(L->base + S.wbf16);
     L->cur = 0;
     L->step = 0;
     L->initialised = 0;
     L->weights_set = 0;
-    L->has_centre = 0;
     *out = L;
     return PL_OK;
 }
 
-static int reset_record(pl_lattice* L) {
-    PL_CUDA(cudaMemsetAsync(L->v.rec, 0, sizeof(DevRecord), L->stream));
+// Table upload + record/counter reset + M0, after a new state has been written to buffer 0.
+static int finish_init(pl_lattice* L, int has_centre, double cx, double cy, double width) {
+    LatDesc& d = L->tab.d[0];
+    d.phase = 0;
+    d.has_centre = has_centre;
+    d.cx = cx;
+    d.cy = cy;
+    d.width = width;
+    L->cur = 0;
+    PL_CUDA(L->tab.upload(L->stream));
+    PL_CUDA(L->tab.reset_seq(L->stream));
+    PL_CUDA(launch_metrics_tab(L->tab.view, L->p.storage, 0, 1, 0, L->stream));
     return PL_OK;
 }
 
@@ -260,19 +340,13 @@ int pl_lattice_init_droplets(pl_lattice* L, const pl_droplet* d, int n, double r
     if (n > 0)
         PL_CUDA(cudaMemcpyAsync(const_cast<pl_droplet*>(L->v.droplets), L->h_droplets.data(), n * sizeof(pl_droplet),
                                 cudaMemcpyHostToDevice, L->stream));
-    int st = reset_record(L);
+    PL_CUDA(cudaMemsetAsync(L->v.rec, 0, sizeof(DevRecord), L->stream));
+    PL_CUDA(launch_init_droplets(L->v, L->phys, 0, n, rho_in, rho_out, width, noise_amp, seed, L->stream));
+    int st = finish_init(L, n == 1, n == 1 ? d[0].cx : 0.0, n == 1 ? d[0].cy : 0.0, width);
     if (st) return st;
-    L->cur = 0;
-    PL_CUDA(launch_init_droplets(L->v, L->phys, L->cur, n, rho_in, rho_out, width, noise_amp, seed, L->stream));
-    PL_CUDA(launch_metrics(L->v, L->phys, L->cur, 0, 0.0, 0.0, width, 1, L->stream));
     L->step = 0;
     L->initialised = 1;
-    L->has_centre = n == 1;  // the Laplace measurement is defined for a single droplet
-    L->cx0 = n > 0 ? d[0].cx : 0.0;
-    L->cy0 = n > 0 ? d[0].cy : 0.0;
-    L->width = width;
-    // keep the host copy alive until the copy has been consumed
-    PL_CUDA(cudaStreamSynchronize(L->stream));
+    PL_CUDA(cudaStreamSynchronize(L->stream));  // the host copies may be released now
     return PL_OK;
 }
 
@@ -281,16 +355,14 @@ int pl_lattice_init_rho(pl_lattice* L, const double* host_rho) {
     drop_graphs(L);
     const size_t N = (size_t)L->p.nx * L->p.ny;
     double* staging = static_cast<double*>(L->v.rho);  // scratch holds >= 8N bytes
-    int st = reset_record(L);
-    if (st) return st;
-    L->cur = 0;
+    PL_CUDA(cudaMemsetAsync(L->v.rec, 0, sizeof(DevRecord), L->stream));
     PL_CUDA(cudaMemcpyAsync(staging, host_rho, N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
-    PL_CUDA(launch_init_from_rho(L->v, L->phys, L->cur, staging, L->stream));
-    PL_CUDA(launch_metrics(L->v, L->phys, L->cur, 0, 0.0, 0.0, 2.0, 1, L->stream));
+    PL_CUDA(launch_init_from_rho(L->v, L->phys, 0, staging, L->stream));
+    int st = finish_init(L, 0, 0.0, 0.0, 2.0);
+    if (st) return st;
     PL_CUDA(cudaStreamSynchronize(L->stream));
     L->step = 0;
     L->initialised = 1;
-    L->has_centre = 0;
     return PL_OK;
 }
 
@@ -299,16 +371,15 @@ int pl_set_mlp_weights(pl_lattice* L, const float* blob, size_t n) {
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(blob[k])) return PL_ERR_INVALID_ARG;
     L->h_weights.assign(blob, blob + n);
-    PL_CUDA(cudaMemcpyAsync(const_cast<float*>(L->v.w32), L->h_weights.data(), n * sizeof(float),
-                            cudaMemcpyHostToDevice, L->stream));
-    PL_CUDA(launch_convert_weights_bf16(L->v.w32, const_cast<uint16_t*>(L->v.wbf16), L->stream));
+    PL_CUDA(cudaMemcpyAsync(L->w32, L->h_weights.data(), n * sizeof(float), cudaMemcpyHostToDevice, L->stream));
+    PL_CUDA(launch_convert_weights_bf16(L->w32, L->wbf16, L->stream));
     L->weights_set = 1;
     return PL_OK;
 }
 
 static int do_steps(pl_lattice* L, int n) {
     for (int k = 0; k < n; ++k) {
-        PL_CUDA(launch_step(L->v, L->phys, L->cur, L->tiling, L->stream));
+        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, L->cur, L->stream));
         L->cur ^= 1;
     }
     L->step += n;
@@ -324,18 +395,19 @@ int pl_step(pl_lattice* L, int32_t n) {
 int pl_apply_correction(pl_lattice* L) {
     if (!L) return PL_ERR_INVALID_ARG;
     if (!L->initialised || !L->weights_set) return PL_ERR_STATE;
-    PL_CUDA(launch_correction(L->v, L->phys, L->cur, L->p.mlp, L->stream));
+    PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, L->cur, L->p.mlp, L->w32, L->wbf16, L->stream));
     return PL_OK;
 }
 
-// Enqueue (or capture) the launches of `nsteps` steps starting at step count
-// `step0`, with a correction after every step whose count is a multiple of K.
+// Enqueue (or capture) the launches of `nsteps` steps starting at step count `step0`
+// and buffer `parity`, with a correction after every step whose count is a multiple of K.
 static int enqueue_run(pl_lattice* L, int nsteps, int K, long long step0, int parity) {
     int cur = parity;
     for (int s = 1; s <= nsteps; ++s) {
-        PL_CUDA(launch_step(L->v, L->phys, cur, L->tiling, L->stream));
+        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, cur, L->stream));
         cur ^= 1;
-        if (K > 0 && ((step0 + s) % K) == 0) PL_CUDA(launch_correction(L->v, L->phys, cur, L->p.mlp, L->stream));
+        if (K > 0 && ((step0 + s) % K) == 0)
+            PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, cur, L->p.mlp, L->w32, L->wbf16, L->stream));
     }
     return PL_OK;
 }
@@ -344,78 +416,70 @@ int pl_run(pl_lattice* L, int32_t nsteps, int32_t K) {
     if (!L || nsteps < 0 || K < 0) return PL_ERR_INVALID_ARG;
     if (!L->initialised || (K > 0 && !L->weights_set)) return PL_ERR_STATE;
     if (nsteps == 0) return PL_OK;
-    // Graph unit: one correction interval aligned to multiples of K (or 1 step
-    // without corrections).  Leading/trailing partial intervals run eagerly.
+    if (K == 0) return do_steps(L, nsteps);
+    // Graph unit: one correction interval aligned to multiples of K.  Leading/trailing
+    // partial intervals run eagerly.
     int done = 0;
-    if (K > 0) {
-        int lead = (int)((K - (L->step % K)) % K);
-        if (lead > nsteps) lead = nsteps;
-        if (lead > 0) {
-            int st = enqueue_run(L, lead, K, L->step, L->cur);
-            if (st) return st;
-            L->cur ^= (lead & 1);
-            L->step += lead;
-            done = lead;
-        }
-        int chunks = (nsteps - done) / K;
-        // The legacy default stream cannot be captured: enqueue eagerly there.
-        const bool capturable = L->stream != nullptr && L->stream != cudaStreamLegacy &&
-                                L->stream != cudaStreamPerThread;
-        if (chunks > 0 && !capturable) {
-            int st = enqueue_run(L, chunks * K, K, L->step, L->cur);
-            if (st) return st;
-            L->cur ^= ((chunks * K) & 1);
-            L->step += (long long)chunks * K;
-            done += chunks * K;
-            chunks = 0;
-        }
-        if (chunks > 0) {
-            for (int c = 0; c < chunks; ++c) {
-                GraphKey key{K, L->cur, K};
-                auto it = L->graphs.find(key);
-                if (it == L->graphs.end()) {
-                    cudaGraph_t g;
-                    PL_CUDA(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
-                    const long long before = launches_total();
-                    int st = enqueue_run(L, K, K, 0, L->cur);
-                    const long long captured = launches_total() - before;
-                    note_launches(-captured);  // captured, not executed: counted at each replay
-                    cudaError_t ce = cudaStreamEndCapture(L->stream, &g);
-                    if (st) return st;
-                    PL_CUDA(ce);
-                    cudaGraphExec_t ge;
-                    cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
-                    cudaGraphDestroy(g);
-                    PL_CUDA(ie);
-                    it = L->graphs.emplace(key, GraphEntry{ge, captured}).first;
-                }
-                PL_CUDA(cudaGraphLaunch(it->second.exec, L->stream));
-                note_launches(it->second.kernels);
-                L->cur ^= (K & 1);
-                L->step += K;
-            }
-            done += chunks * K;
-        }
-        int tail = nsteps - done;
-        if (tail > 0) {
-            int st = enqueue_run(L, tail, K, L->step, L->cur);
-            if (st) return st;
-            L->cur ^= (tail & 1);
-            L->step += tail;
-        }
-        return PL_OK;
+    int lead = (int)((K - (L->step % K)) % K);
+    if (lead > nsteps) lead = nsteps;
+    if (lead > 0) {
+        int st = enqueue_run(L, lead, K, L->step, L->cur);
+        if (st) return st;
+        L->cur ^= (lead & 1);
+        L->step += lead;
+        done = lead;
     }
-    return do_steps(L, nsteps);
+    int chunks = (nsteps - done) / K;
+    // The legacy default stream cannot be captured: enqueue eagerly there.
+    const bool capturable =
+        L->stream != nullptr && L->stream != cudaStreamLegacy && L->stream != cudaStreamPerThread;
+    if (chunks > 0 && !capturable) {
+        int st = enqueue_run(L, chunks * K, K, L->step, L->cur);
+        if (st) return st;
+        L->cur ^= ((chunks * K) & 1);
+        L->step += (long long)chunks * K;
+        done += chunks * K;
+        chunks = 0;
+    }
+    for (int c = 0; c < chunks; ++c) {
+        GraphKey key{K, L->cur};
+        auto it = L->graphs.find(key);
+        if (it == L->graphs.end()) {
+            cudaGraph_t g;
+            PL_CUDA(cudaStreamBeginCapture(L->stream, cudaStreamCaptureModeThreadLocal));
+            const long long before = launches_total();
+            int st = enqueue_run(L, K, K, 0, L->cur);
+            const long long captured = launches_total() - before;
+            note_launches(-captured);  // captured, not executed: counted at each replay
+            cudaError_t ce = cudaStreamEndCapture(L->stream, &g);
+            if (st) return st;
+            PL_CUDA(ce);
+            cudaGraphExec_t ge;
+            cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+            cudaGraphDestroy(g);
+            PL_CUDA(ie);
+            it = L->graphs.emplace(key, GraphEntry{ge, captured}).first;
+        }
+        PL_CUDA(cudaGraphLaunch(it->second.exec, L->stream));
+        note_launches(it->second.kernels);
+        L->cur ^= (K & 1);
+        L->step += K;
+    }
+    done += chunks * K;
+    const int tail = nsteps - done;
+    if (tail > 0) {
+        int st = enqueue_run(L, tail, K, L->step, L->cur);
+        if (st) return st;
+        L->cur ^= (tail & 1);
+        L->step += tail;
+    }
+    return PL_OK;
 }
 
-int pl_metrics(pl_lattice* L, pl_metric_record* out) {
-    if (!L || !out) return PL_ERR_INVALID_ARG;
-    if (!L->initialised) return PL_ERR_STATE;
-    PL_CUDA(launch_metrics(L->v, L->phys, L->cur, L->has_centre, L->cx0, L->cy0, L->width, 0, L->stream));
-    DevRecord r;
-    PL_CUDA(cudaMemcpyAsync(&r, L->v.rec, sizeof(r), cudaMemcpyDeviceToHost, L->stream));
-    PL_CUDA(cudaStreamSynchronize(L->stream));
-    const double N = (double)L->p.nx * (double)L->p.ny;
+}  // extern "C"
+
+void pl::record_to_metrics(const DevRecord& r, int nx, int ny, int laplace, pl_metric_record* out) {
+    const double N = (double)nx * (double)ny;
     std::memset(out, 0, sizeof(*out));
     out->mass = r.mass;
     out->count = r.count;
@@ -428,7 +492,7 @@ int pl_metrics(pl_lattice* L, pl_metric_record* out) {
     out->rho_min = r.rho_min;
     out->sum_g = r.sum_g;
     out->sum_g2 = r.sum_g2;
-    if (L->has_centre) {
+    if (laplace) {
         out->R_eq = r.R_eq;
         out->rho_in = r.rho_in;
         out->rho_out = r.rho_out;
@@ -439,9 +503,22 @@ int pl_metrics(pl_lattice* L, pl_metric_record* out) {
         out->R_eq = out->rho_in = out->rho_out = out->p_in = out->p_out = out->dP = NAN;
     }
     out->mass0 = r.mass0;
-    out->step = L->step;
     out->status = r.status;
     out->corrections = r.applied;
+}
+
+extern "C" {
+
+int pl_metrics(pl_lattice* L, pl_metric_record* out) {
+    if (!L || !out) return PL_ERR_INVALID_ARG;
+    if (!L->initialised) return PL_ERR_STATE;
+    const int lap = L->tab.d[0].has_centre;
+    PL_CUDA(launch_metrics_tab(L->tab.view, L->p.storage, L->cur, 0, lap, L->stream));
+    DevRecord r;
+    PL_CUDA(cudaMemcpyAsync(&r, L->v.rec, sizeof(r), cudaMemcpyDeviceToHost, L->stream));
+    PL_CUDA(cudaStreamSynchronize(L->stream));
+    record_to_metrics(r, L->p.nx, L->p.ny, lap, out);
+    out->step = L->step;
     return PL_OK;
 }
 
@@ -449,7 +526,7 @@ int pl_get_rho(pl_lattice* L, double* host_rho) {
     if (!L || !host_rho) return PL_ERR_INVALID_ARG;
     if (!L->initialised) return PL_ERR_STATE;
     const size_t N = (size_t)L->p.nx * L->p.ny;
-    PL_CUDA(launch_metrics(L->v, L->phys, L->cur, 0, 0.0, 0.0, 2.0, 0, L->stream));
+    PL_CUDA(launch_metrics_tab(L->tab.view, L->p.storage, L->cur, 0, 0, L->stream));
     if (L->p.storage == PL_F64) {
         PL_CUDA(cudaMemcpyAsync(host_rho, L->v.rho, N * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
         PL_CUDA(cudaStreamSynchronize(L->stream));
@@ -464,15 +541,16 @@ int pl_get_rho(pl_lattice* L, double* host_rho) {
 
 int pl_get_mlp_field(pl_lattice* L, double* host_out3) {
     if (!L || !host_out3) return PL_ERR_INVALID_ARG;
-    if (!L->weights_set) return PL_ERR_STATE;
+    if (!L->weights_set || !L->initialised) return PL_ERR_STATE;
     const size_t N3 = 3 * (size_t)L->p.nx * L->p.ny;
-    PL_CUDA(launch_mlp_field(L->v, L->p.mlp, L->stream));
+    PL_CUDA(launch_mlp_tab(L->tab.view, L->p.storage, L->p.mlp, L->w32, L->wbf16, L->stream));
+    const void* out3 = L->tab.d[0].out3;
     if (L->p.storage == PL_F64) {
-        PL_CUDA(cudaMemcpyAsync(host_out3, L->v.out3, N3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        PL_CUDA(cudaMemcpyAsync(host_out3, out3, N3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
         PL_CUDA(cudaStreamSynchronize(L->stream));
     } else {
         std::vector<float> tmp(N3);
-        PL_CUDA(cudaMemcpyAsync(tmp.data(), L->v.out3, N3 * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
+        PL_CUDA(cudaMemcpyAsync(tmp.data(), out3, N3 * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
         PL_CUDA(cudaStreamSynchronize(L->stream));
         for (size_t c = 0; c < N3; ++c) host_out3[c] = tmp[c];
     }
@@ -500,15 +578,18 @@ int pl_set_state(pl_lattice* L, const double* host_f, int64_t step) {
         if (!std::isfinite(host_f[k])) return PL_ERR_INVALID_ARG;
     drop_graphs(L);
     double* staging = static_cast<double*>(L->v.rho);
-    if (!L->initialised) {
-        int st = reset_record(L);
-        if (st) return st;
-    }
+    const int fresh = !L->initialised;
+    if (fresh) PL_CUDA(cudaMemsetAsync(L->v.rec, 0, sizeof(DevRecord), L->stream));
     for (int i = 0; i < 9; ++i) {
         PL_CUDA(cudaMemcpyAsync(staging, host_f + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
         PL_CUDA(launch_state_convert(L->v, L->phys, L->cur, staging, i, 0, L->stream));
     }
-    if (!L->initialised) PL_CUDA(launch_metrics(L->v, L->phys, L->cur, 0, 0.0, 0.0, 2.0, 1, L->stream));
+    if (fresh) {
+        // a state written into buffer cur: make it buffer 0's (phase 0) view consistent
+        if (L->cur != 0) return PL_ERR_STATE;
+        int st = finish_init(L, 0, 0.0, 0.0, 2.0);
+        if (st) return st;
+    }
     PL_CUDA(cudaStreamSynchronize(L->stream));
     L->step = step;
     L->initialised = 1;
@@ -529,6 +610,17 @@ int pl_destroy(pl_lattice* L) {
     drop_graphs(L);
     delete L;
     return PL_OK;
+}
+
+int pl_selftest_wait_timeout(void* dev_status, int64_t limit_ns, void* stream) {
+    if (!dev_status || ((uintptr_t)dev_status % sizeof(int)) || limit_ns < 0 || limit_ns > 5000000000ll)
+        return PL_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PL_CUDA(launch_selftest_wait(static_cast<int*>(dev_status), (long long)limit_ns, s));
+    int st = 0;
+    PL_CUDA(cudaMemcpyAsync(&st, dev_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PL_CUDA(cudaStreamSynchronize(s));
+    return st;
 }
 
 }  // extern "C"

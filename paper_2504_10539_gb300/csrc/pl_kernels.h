@@ -1,4 +1,13 @@
 // Internal launcher interface between the C ABI (pl_api.cu) and the kernels.
+//
+// Every kernel of the hot path is table-driven: it reads a device-resident job
+// table (one LatDesc per lattice, plus prefix sums of each lattice's work units)
+// and loops over virtual work units with a fixed, persistent grid.  A single
+// lattice is a table of one; a batch is a table of many.  Because the grids do
+// not depend on the table's contents, one captured CUDA graph stays valid while
+// the host rewrites the table between replays (jobs admitted and retired).
+// Every per-lattice decomposition (reduction blocks, MLP tiles) depends on that
+// lattice alone, so each lattice's results are bit-identical alone and in a mix.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -14,24 +23,16 @@ struct DevRecord;
 void note_launches(long long n);
 long long launches_total();
 
-// Geometry of one lattice's arrays inside caller memory.
+// Geometry of one lattice's arrays inside caller memory (per-lattice kernels:
+// initial state and state exchange).
 struct LatticeView {
     int nx, ny;
     int storage;
     int pitch;         // elements per stored row (nx rounded up to a multiple of 8)
     long long plane;   // elements per population plane (pitch*ny)
     void* pops[2];     // two-lattice population buffers, 9 planes each
-    // scratch fields, element type = double for F64 storage, float otherwise
-    void* rho;
-    void* jx;
-    void* jy;
-    void* g;
-    void* out3;        // network outputs rho^, u^_x, u^_y (3 planes)
-    double* partials;  // per-block reduction partials
-    int max_blocks;    // capacity of partials (blocks)
+    void* rho;         // scratch (>= 8 nx ny bytes), used as FP64 staging
     DevRecord* rec;
-    const float* w32;        // FP32 weight blob (device)
-    const uint16_t* wbf16;   // BF16 tensor-core operand copy of W2..W4 (device)
     const pl_droplet* droplets;
 };
 
@@ -39,30 +40,79 @@ struct PhysParams {
     double G, tau, rho0, rho_ref, beta_rho, beta_u, threshold;
 };
 
-// Step kernel tiling: TX threads per CTA (TX-2 owned columns), TY rows per CTA.
-struct StepTiling {
-    int tx, ty;
+// One lattice of a job table.
+struct LatDesc {
+    void* pops[2];          // population buffers
+    void* rho;              // scratch fields (double for FP64 storage, float otherwise)
+    void* jx;
+    void* jy;
+    void* g;
+    void* out3;             // network outputs rho^, u^x, u^y (3 planes of nx*ny)
+    double* partials;       // reduction partials, red_blocks x 8
+    DevRecord* rec;
+    long long plane;        // elements per population plane
+    int nx, ny, pitch;
+    int phase;              // buffer holding the state when the launch parity is 0
+    int nstrips, chunks;    // step decomposition: nstrips x chunks warps
+    int red_blocks;         // reduction blocks, a function of nx*ny only
+    int has_centre;         // Laplace measurement defined (single droplet)
+    unsigned seq0;          // table step count when the lattice joined (its own count = seq - seq0)
+    int pad0;
+    double G, tau, rho0, rho_ref, beta_rho, beta_u, threshold;
+    double cx, cy, width;   // droplet centre and profile width (Laplace)
 };
-StepTiling default_tiling(int nx, int ny);
 
+struct TabHeader {
+    int n;                  // lattices in the table
+    int total_blocks;       // sum of red_blocks
+    long long total_warps;  // sum of nstrips * chunks
+    long long total_tiles;  // sum of ceil(nx*ny / 128)
+};
+
+// Device arrays of a table (capacity cap lattices; prefix arrays have cap+1 entries).
+struct TableView {
+    const TabHeader* hdr;
+    const LatDesc* d;
+    const long long* warp_pre;
+    const int* blk_pre;
+    const long long* tile_pre;
+    // Step sequence counter in two slots: a step of parity p reads seq[p] and writes
+    // seq[p^1] = seq[p] + 1 (the slot it does not read), so the count advances on the
+    // device, also under graph replay.  Feeds the FP16 stochastic-rounding dither.
+    unsigned* seq;
+};
+
+constexpr int RB_THREADS = 256;         // threads of a reduction block
+constexpr int RB_MAX_BLOCKS = 1024;     // reduction blocks per lattice (max)
+constexpr int PARTIAL_STRIDE = 8;       // doubles per block partial
+constexpr int MLP_TILE = 128;           // cells per network tile
+constexpr int STRIP = 60;               // owned columns per step warp
+
+int red_blocks_for(long long cells);
+int step_capacity_warps(int storage);   // resident warps of the step kernel on this device
+
+// Per-lattice kernels.
 cudaError_t launch_init_droplets(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in,
                                  double rho_out, double width, double noise_amp, uint64_t seed, cudaStream_t s);
 cudaError_t launch_init_from_rho(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho,
                                  cudaStream_t s);
-cudaError_t launch_step(const LatticeView& v, const PhysParams& p, int src, StepTiling t, cudaStream_t s);
 // Convert population plane `plane` of buffer `cur` to (to_f64=1) or from (0) the FP64 array d_buf[nx*ny].
 cudaError_t launch_state_convert(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int plane,
                                  int to_f64, cudaStream_t s);
 
-// Metrics: moments + gradient reductions (+ Laplace when has_centre).
-cudaError_t launch_metrics(const LatticeView& v, const PhysParams& p, int cur, int has_centre, double cx,
-                           double cy, double width, int set_mass0, cudaStream_t s);
-int reduction_blocks(const LatticeView& v);
+// Table kernels (all lattices of a table share `storage`).
+cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s);
+// Metrics of every lattice: moments, Eq. 16 gradient, Eqs. 9-15 sums (+ Laplace where defined).
+cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
+                               cudaStream_t s);
+// Network field of every lattice (BF16 tensor cores or SIMT), then the correction.
+cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, const float* w32, const uint16_t* wbf16,
+                           cudaStream_t s);
+cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, const float* w32,
+                                  const uint16_t* wbf16, cudaStream_t s);
 
-// Correction: network field + 3 reduction phases + apply.
-cudaError_t launch_correction(const LatticeView& v, const PhysParams& p, int cur, int mlp_mode, cudaStream_t s);
-cudaError_t launch_mlp_field(const LatticeView& v, int mlp_mode, cudaStream_t s);
 cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, cudaStream_t s);
+cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t s);
 size_t bf16_weight_elems();
 
 }  // namespace pl

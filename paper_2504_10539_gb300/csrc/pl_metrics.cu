@@ -1,11 +1,15 @@
 // Interface metrics (arXiv 2504.10539 Sec. II-D Eqs. 9-13, discretised in
-// Sec. IV-E Eqs. 14-16), the mass, and the Laplace measurement.
+// Sec. IV-E Eqs. 14-16), the mass, the Laplace measurement, and the interface
+// correction (Sec. II-C step 3), for every lattice of a job table.
 //
-// Two-level deterministic reductions: a fixed grid of RB blocks accumulates
-// per-thread FP64 partial sums / extrema over a fixed grid-stride assignment
-// of cells, reduces them by a fixed warp-shuffle tree into one partial per
-// block, and a one-block kernel folds the partials in block order.  The result
-// does not depend on scheduling, so repeated runs are bit-identical.
+// Segmented, deterministic two-level reductions: lattice j owns red_blocks(j)
+// virtual blocks (a function of its size only); virtual block b of lattice j
+// accumulates FP64 partial sums / extrema over cells b*256+t, b*256+t+R*256, ...
+// (R = red_blocks(j)), reduces them by a fixed warp-shuffle tree into one partial,
+// and one block per lattice folds that lattice's partials in block order.  The
+// result depends on the lattice alone: it is the same whatever else is in the
+// table and however the persistent grid is scheduled, so repeated runs are
+// bit-identical and a lattice gives the same numbers alone and in a batch.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -16,37 +20,61 @@
 
 namespace pl {
 
-constexpr int RB_THREADS = 256;
-constexpr int RB_MAX_BLOCKS = 1024;
-constexpr int PARTIAL_STRIDE = 8;  // doubles per block partial
+constexpr int RED_GRID = 152 * 8;  // persistent grid of the reduction kernels
 
-int reduction_blocks(const LatticeView& v) {
-    long long N = (long long)v.nx * v.ny;
-    long long b = (N + RB_THREADS - 1) / RB_THREADS;
-    if (b > v.max_blocks) b = v.max_blocks;
+int red_blocks_for(long long cells) {
+    long long b = (cells + RB_THREADS - 1) / RB_THREADS;
     if (b > RB_MAX_BLOCKS) b = RB_MAX_BLOCKS;
     return (int)(b < 1 ? 1 : b);
 }
 
-// rho = sum_i f_i and j = sum_i f_i c_i per cell, from the decoded stored state.
-template <int MODE>
-__global__ void k_moments(const typename Traits<MODE>::S* __restrict__ f, int nx, int pitch, long long N,
-                          long long plane, typename Traits<MODE>::R rho_ref, typename Traits<MODE>::R* __restrict__ rho,
-                          typename Traits<MODE>::R* __restrict__ jx, typename Traits<MODE>::R* __restrict__ jy) {
-    using R = typename Traits<MODE>::R;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const long long o = (c / nx) * pitch + c % nx;
-        R P[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
-        rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
-        jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
-        jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
+__device__ __forceinline__ int find_blk(const int* __restrict__ pre, int n, int v) {
+    int lo = 0, hi = n;  // pre[lo] <= v < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= v) lo = mid;
+        else hi = mid;
     }
+    return lo;
 }
 
-// Eq. 16 gradient magnitude (central differences, periodic, dx = dy = 1), stored
+// Virtual block vb of the table -> lattice j, local block lb.
+struct BlkMap {
+    int j, lb;
+};
+__device__ __forceinline__ BlkMap map_blk(const TableView& t, int n, int vb) {
+    BlkMap m;
+    m.j = find_blk(t.blk_pre, n, vb);
+    m.lb = vb - t.blk_pre[m.j];
+    return m;
+}
+
+__device__ __forceinline__ long long pop_offset(long long c, int nx, int pitch) { return (c / nx) * pitch + c % nx; }
+
+// ---------------------------------------------------------------------------------------------
+// Per-array kernels (one lattice given by raw pointers), used by pl_metrics_noalloc.
+
+// Eq. 16 gradient magnitude (central differences, periodic, dx = dy = 1), optionally stored
 // to g, and the per-block partials {sum rho, max g, sum g, sum g^2, max rho, min rho, count(g > thr)}.
+template <typename R>
+__device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int nx, int ny, long long c,
+                                                R* __restrict__ g, double threshold, double (&v)[7]) {
+    const int x = (int)(c % nx), y = (int)(c / nx);
+    const long long row = c - x;
+    const R gx = (rho[row + (x == nx - 1 ? 0 : x + 1)] - rho[row + (x == 0 ? nx - 1 : x - 1)]) / R(2);
+    const R gy = (rho[(long long)(y == ny - 1 ? 0 : y + 1) * nx + x] - rho[(long long)(y == 0 ? ny - 1 : y - 1) * nx + x]) / R(2);
+    const R gm = sqrt(gx * gx + gy * gy);
+    if (g) g[c] = gm;
+    const double r = (double)rho[c], gd = (double)gm;
+    v[0] += r;
+    v[1] = fmax(v[1], gd);
+    v[2] += gd;
+    v[3] += gd * gd;
+    v[4] = fmax(v[4], r);
+    v[5] = fmin(v[5], r);
+    v[6] += gd > threshold ? 1.0 : 0.0;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(RB_THREADS) k_grad_reduce(const R* __restrict__ rho, int nx, int ny,
                                                             R* __restrict__ g, double threshold,
@@ -55,31 +83,15 @@ __global__ void __launch_bounds__(RB_THREADS) k_grad_reduce(const R* __restrict_
     const long long N = (long long)nx * ny;
     double v[7] = {0.0, 0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
     const int op[7] = {0, 1, 0, 0, 1, 2, 0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % nx), y = (int)(c / nx);
-        const long long row = c - x;
-        const R gx = (rho[row + (x == nx - 1 ? 0 : x + 1)] - rho[row + (x == 0 ? nx - 1 : x - 1)]) / R(2);
-        const R gy = (rho[(long long)(y == ny - 1 ? 0 : y + 1) * nx + x] - rho[(long long)(y == 0 ? ny - 1 : y - 1) * nx + x]) / R(2);
-        const R gm = sqrt(gx * gx + gy * gy);
-        if (g) g[c] = gm;
-        const double r = (double)rho[c], gd = (double)gm;
-        v[0] += r;
-        v[1] = fmax(v[1], gd);
-        v[2] += gd;
-        v[3] += gd * gd;
-        v[4] = fmax(v[4], r);
-        v[5] = fmin(v[5], r);
-        v[6] += gd > threshold ? 1.0 : 0.0;
-    }
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        grad_accumulate(rho, nx, ny, c, g, threshold, v);
     block_reduce<7>(v, op, sm);
     if (threadIdx.x == 0)
         for (int k = 0; k < 7; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
 }
 
-// Fold the block partials into the lattice record.
-__global__ void __launch_bounds__(RB_THREADS) k_final_metrics(const double* __restrict__ partials, int nb,
-                                                              DevRecord* rec, int set_mass0) {
-    __shared__ double sm[7 * 32];
+__device__ __forceinline__ void fold_metric_partials(const double* __restrict__ partials, int nb, DevRecord* rec,
+                                                     int set_mass0, double* sm) {
     double v[7] = {0.0, 0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
     const int op[7] = {0, 1, 0, 0, 1, 2, 0};
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
@@ -103,13 +115,95 @@ __global__ void __launch_bounds__(RB_THREADS) k_final_metrics(const double* __re
         rec->count = (long long)v[6];
         rec->rho_in = v[4];   // starting estimates of the Laplace iteration
         rec->rho_out = v[5];
-        if (set_mass0) rec->mass0 = v[0];
+        // 1: record M0; 2: record M0 only where none is recorded yet (newly admitted lattices)
+        if (set_mass0 == 1 || (set_mass0 == 2 && rec->mass0 == 0.0)) rec->mass0 = v[0];
     }
 }
 
-// Laplace measurement about (cx, cy) (build-defined estimator, Sec. III-A set-up):
-// R_eq = sqrt((M - N rho_out) / (pi (rho_in - rho_out))); inner cells d < R_eq/2,
-// outer cells d > R_eq + 4 width; means of rho and of p = rho/3 + G psi^2/6.
+__global__ void __launch_bounds__(RB_THREADS) k_final_metrics(const double* __restrict__ partials, int nb,
+                                                              DevRecord* rec, int set_mass0) {
+    __shared__ double sm[7 * 32];
+    fold_metric_partials(partials, nb, rec, set_mass0, sm);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Table kernels: metrics.
+
+// rho = sum_i f_i and j = sum_i f_i c_i per cell, from the decoded stored state.
+template <int MODE>
+__global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity) {
+    using S = typename Traits<MODE>::S;
+    using R = typename Traits<MODE>::R;
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const S* f = static_cast<const S*>(d.pops[d.phase ^ parity]);
+        R* rho = static_cast<R*>(d.rho);
+        R* jx = static_cast<R*>(d.jx);
+        R* jy = static_cast<R*>(d.jy);
+        const R rho_ref = R(d.rho_ref);
+        const long long N = (long long)d.nx * d.ny;
+        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+            const long long o = pop_offset(c, d.nx, d.pitch);
+            R P[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o], wq<R>(i) * rho_ref);
+            rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+            jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
+            jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
+        }
+    }
+}
+
+// Also counts non-physical cells (rho <= 0 or not finite) in partial slot 7.
+template <typename R>
+__global__ void __launch_bounds__(RB_THREADS) k_grad_tab(TableView t) {
+    __shared__ double sm[8 * 32];
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    const int op7[7] = {0, 1, 0, 0, 1, 2, 0};
+    const int op1[1] = {0};
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const long long N = (long long)d.nx * d.ny;
+        const R* rho = static_cast<const R*>(d.rho);
+        double v[7] = {0.0, 0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
+        double bad[1] = {0.0};
+        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+            grad_accumulate(rho, d.nx, d.ny, c, static_cast<R*>(d.g), d.threshold, v);
+            const double r = (double)rho[c];
+            bad[0] += (r > 0.0 && isfinite(r)) ? 0.0 : 1.0;
+        }
+        block_reduce<7>(v, op7, sm);
+        block_reduce<1>(bad, op1, sm + 7 * 32);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 7; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
+            d.partials[m.lb * PARTIAL_STRIDE + 7] = bad[0];
+        }
+    }
+}
+
+// Folds the metric partials; a lattice with any non-physical cell gets the sticky status
+// PL_ERR_NONPHYSICAL (its neighbours in the table are not affected).
+__global__ void __launch_bounds__(RB_THREADS) k_final_metrics_tab(TableView t, int set_mass0) {
+    __shared__ double sm[8 * 32];
+    const int n = t.hdr->n;
+    const int op1[1] = {0};
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const LatDesc& d = t.d[j];
+        fold_metric_partials(d.partials, d.red_blocks, d.rec, set_mass0, sm);
+        double bad[1] = {0.0};
+        for (int b = threadIdx.x; b < d.red_blocks; b += blockDim.x) bad[0] += d.partials[b * PARTIAL_STRIDE + 7];
+        block_reduce<1>(bad, op1, sm + 7 * 32);
+        if (threadIdx.x == 0 && bad[0] > 0.0 && d.rec->status == PL_OK) d.rec->status = PL_ERR_NONPHYSICAL;
+    }
+}
+
+// Laplace measurement about the droplet centre (single-droplet lattices; build-defined
+// estimator, Sec. III-A set-up): R_eq = sqrt((M - N rho_out) / (pi (rho_in - rho_out)));
+// inner cells d < R_eq/2, outer cells d > R_eq + 4 width; means of rho and of the bulk
+// pressure p = rho/3 + G psi^2/6.
 __device__ __forceinline__ double min_image_d(double d, double n) {
     double a = fabs(fmod(d, n));
     return a > 0.5 * n ? n - a : a;
@@ -120,277 +214,326 @@ __device__ __forceinline__ double laplace_req(const DevRecord* rec, long long N)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(RB_THREADS) k_laplace_region(const R* __restrict__ rho, int nx, int ny, double cx,
-                                                               double cy, double width, double G, double rho0,
-                                                               const DevRecord* __restrict__ rec,
-                                                               double* __restrict__ partials) {
+__global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
     __shared__ double sm[6 * 32];
-    const long long N = (long long)nx * ny;
-    const double Req = laplace_req(rec, N);
-    double v[6] = {0, 0, 0, 0, 0, 0};  // inner: sum rho, sum p, n; outer: sum rho, sum p, n
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
     const int op[6] = {0, 0, 0, 0, 0, 0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(c % nx), y = (int)(c / nx);
-        const double dx = min_image_d((double)x - cx, (double)nx), dy = min_image_d((double)y - cy, (double)ny);
-        const double d = sqrt(dx * dx + dy * dy);
-        const double r = (double)rho[c];
-        const double ps = -rho0 * expm1(-r / rho0);
-        const double p = r / 3.0 + G * ps * ps / 6.0;
-        if (d < 0.5 * Req) { v[0] += r; v[1] += p; v[2] += 1.0; }
-        if (d > Req + 4.0 * width) { v[3] += r; v[4] += p; v[5] += 1.0; }
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        if (!d.has_centre) continue;
+        const long long N = (long long)d.nx * d.ny;
+        const double Req = laplace_req(d.rec, N);
+        const R* rho = static_cast<const R*>(d.rho);
+        double v[6] = {0, 0, 0, 0, 0, 0};  // inner: sum rho, sum p, n; outer: sum rho, sum p, n
+        // geometry and pressure in the lattice's arithmetic type, sums in FP64
+        const R nxr = R(d.nx), nyr = R(d.ny), cxr = R(d.cx), cyr = R(d.cy), rho0 = R(d.rho0), G = R(d.G);
+        const R inner = R(0.5 * Req), outer = R(Req + 4.0 * d.width);
+        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+            const int x = (int)(c % d.nx), y = (int)(c / d.nx);
+            R ax = fabs(R(x) - cxr), ay = fabs(R(y) - cyr);
+            if (ax >= nxr) ax = fmod(ax, nxr);
+            if (ay >= nyr) ay = fmod(ay, nyr);
+            if (ax > R(0.5) * nxr) ax = nxr - ax;  // minimum image
+            if (ay > R(0.5) * nyr) ay = nyr - ay;
+            const R dd = sqrt(ax * ax + ay * ay);
+            const R r = rho[c];
+            const R ps = -rho0 * expm1(-r / rho0);
+            const double rd = (double)r, p = (double)(r / R(3) + G * ps * ps / R(6));
+            if (dd < inner) { v[0] += rd; v[1] += p; v[2] += 1.0; }
+            if (dd > outer) { v[3] += rd; v[4] += p; v[5] += 1.0; }
+        }
+        block_reduce<6>(v, op, sm);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 6; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
-    block_reduce<6>(v, op, sm);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
 }
 
-__global__ void __launch_bounds__(RB_THREADS) k_laplace_final(const double* __restrict__ partials, int nb, long long N,
-                                                              DevRecord* rec) {
+__global__ void __launch_bounds__(RB_THREADS) k_laplace_final(TableView t) {
     __shared__ double sm[6 * 32];
-    double v[6] = {0, 0, 0, 0, 0, 0};
+    const int n = t.hdr->n;
     const int op[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-        for (int k = 0; k < 6; ++k) v[k] += partials[b * PARTIAL_STRIDE + k];
-    block_reduce<6>(v, op, sm);
-    if (threadIdx.x == 0) {
-        rec->R_eq = laplace_req(rec, N);
-        rec->rho_in = v[2] > 0 ? v[0] / v[2] : NAN;
-        rec->p_in = v[2] > 0 ? v[1] / v[2] : NAN;
-        rec->rho_out = v[5] > 0 ? v[3] / v[5] : NAN;
-        rec->p_out = v[5] > 0 ? v[4] / v[5] : NAN;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const LatDesc& d = t.d[j];
+        if (!d.has_centre) continue;
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        for (int b = threadIdx.x; b < d.red_blocks; b += blockDim.x)
+            for (int k = 0; k < 6; ++k) v[k] += d.partials[b * PARTIAL_STRIDE + k];
+        block_reduce<6>(v, op, sm);
+        if (threadIdx.x == 0) {
+            DevRecord* rec = d.rec;
+            rec->R_eq = laplace_req(rec, (long long)d.nx * d.ny);
+            rec->rho_in = v[2] > 0 ? v[0] / v[2] : NAN;
+            rec->p_in = v[2] > 0 ? v[1] / v[2] : NAN;
+            rec->rho_out = v[5] > 0 ? v[3] / v[5] : NAN;
+            rec->p_out = v[5] > 0 ? v[4] / v[5] : NAN;
+        }
     }
 }
 
 template <int MODE>
-static cudaError_t metrics_t(const LatticeView& v, const PhysParams& p, int cur, int has_centre, double cx, double cy,
-                             double width, int set_mass0, cudaStream_t s) {
-    using S = typename Traits<MODE>::S;
+static cudaError_t metrics_t(const TableView& t, int parity, int set_mass0, int laplace, cudaStream_t s) {
     using R = typename Traits<MODE>::R;
-    const long long N = (long long)v.nx * v.ny;
-    const int nb = reduction_blocks(v);
-    R* rho = static_cast<R*>(v.rho);
-    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), v.nx, v.pitch, N, v.plane,
-                                              R(p.rho_ref), rho, static_cast<R*>(v.jx), static_cast<R*>(v.jy));
-    k_grad_reduce<R><<<nb, RB_THREADS, 0, s>>>(rho, v.nx, v.ny, static_cast<R*>(v.g), p.threshold, v.partials);
-    k_final_metrics<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec, set_mass0);
-    if (has_centre) {
+    k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+    k_grad_tab<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_final_metrics_tab<<<RED_GRID, RB_THREADS, 0, s>>>(t, set_mass0);
+    int launches = 3;
+    if (laplace) {
         for (int it = 0; it < 2; ++it) {
-            k_laplace_region<R><<<nb, RB_THREADS, 0, s>>>(rho, v.nx, v.ny, cx, cy, width, p.G, p.rho0, v.rec, v.partials);
-            k_laplace_final<<<1, RB_THREADS, 0, s>>>(v.partials, nb, N, v.rec);
+            k_laplace_region<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+            k_laplace_final<<<RED_GRID, RB_THREADS, 0, s>>>(t);
         }
+        launches += 4;
     }
-    note_launches(has_centre ? 7 : 3);
+    note_launches(launches);
     return cudaGetLastError();
 }
 
-cudaError_t launch_metrics(const LatticeView& v, const PhysParams& p, int cur, int has_centre, double cx, double cy,
-                           double width, int set_mass0, cudaStream_t s) {
-    switch (v.storage) {
-        case PL_F64: return metrics_t<PL_F64>(v, p, cur, has_centre, cx, cy, width, set_mass0, s);
-        case PL_F32: return metrics_t<PL_F32>(v, p, cur, has_centre, cx, cy, width, set_mass0, s);
-        case PL_F16_OFFSET: return metrics_t<PL_F16_OFFSET>(v, p, cur, has_centre, cx, cy, width, set_mass0, s);
+cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
+                               cudaStream_t s) {
+    switch (storage) {
+        case PL_F64: return metrics_t<PL_F64>(t, parity, set_mass0, laplace, s);
+        case PL_F32: return metrics_t<PL_F32>(t, parity, set_mass0, laplace, s);
+        case PL_F16_OFFSET: return metrics_t<PL_F16_OFFSET>(t, parity, set_mass0, laplace, s);
     }
     return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------------------------
-// Interface correction reductions and apply (Sec. II-C step 3; the operator is the build's
-// reading, the paper gives none):
+// Interface correction (Sec. II-C step 3; the operator is the build's reading, the paper
+// gives none):
 //   m = g / G_max; drho_raw = beta_rho m (rho^ - rho)
 //   drho = drho_raw - m (sum drho_raw + (M - M0)) / sum m;  rho' = rho + drho
 //   dj_raw = beta_u m (rho' u^ - j); dj = dj_raw - m sum dj_raw / sum m;  u' = (j + dj) / rho'
 //   f_i += f_i^eq(rho', u') - f_i^eq(rho, u) on cells with m > 0.
 
 template <typename R>
-__global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(const R* __restrict__ rho, const R* __restrict__ g,
-                                                           const R* __restrict__ out3, long long N, double beta_rho,
-                                                           const DevRecord* __restrict__ rec,
-                                                           double* __restrict__ partials) {
+__global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
     __shared__ double sm[3 * 32];
-    const double gmax = rec->gmax;
-    double v[3] = {0, 0, 0};  // sum m, sum drho_raw, sum rho
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
     const int op[3] = {0, 0, 0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const double r = (double)rho[c];
-        const double m = gmax > 0.0 ? (double)g[c] / gmax : 0.0;
-        v[0] += m;
-        v[1] += beta_rho * m * ((double)out3[c] - r);
-        v[2] += r;
-    }
-    block_reduce<3>(v, op, sm);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
-}
-
-__global__ void __launch_bounds__(RB_THREADS) k_corr_final1(const double* __restrict__ partials, int nb, DevRecord* rec) {
-    __shared__ double sm[3 * 32];
-    double v[3] = {0, 0, 0};
-    const int op[3] = {0, 0, 0};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-        for (int k = 0; k < 3; ++k) v[k] += partials[b * PARTIAL_STRIDE + k];
-    block_reduce<3>(v, op, sm);
-    if (threadIdx.x == 0) {
-        rec->sum_m = v[0];
-        rec->sum_dr = v[1];
-        rec->mass_now = v[2];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const long long N = (long long)d.nx * d.ny;
+        const R* rho = static_cast<const R*>(d.rho);
+        const R* g = static_cast<const R*>(d.g);
+        const R* out3 = static_cast<const R*>(d.out3);
+        const R gmax = R(d.rec->gmax), beta_rho = R(d.beta_rho);
+        double v[3] = {0, 0, 0};  // sum m, sum drho_raw, sum rho
+        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+            const R r = rho[c];
+            const R mm = gmax > R(0) ? g[c] / gmax : R(0);
+            v[0] += (double)mm;
+            v[1] += (double)(beta_rho * mm * (out3[c] - r));
+            v[2] += (double)r;
+        }
+        block_reduce<3>(v, op, sm);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
 }
 
-// Per-cell corrected density and raw momentum change, shared by the second
-// reduction and the apply pass so both see identical values.
+__global__ void __launch_bounds__(RB_THREADS) k_corr_final1(TableView t) {
+    __shared__ double sm[3 * 32];
+    const int n = t.hdr->n;
+    const int op[3] = {0, 0, 0};
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const LatDesc& d = t.d[j];
+        double v[3] = {0, 0, 0};
+        for (int b = threadIdx.x; b < d.red_blocks; b += blockDim.x)
+            for (int k = 0; k < 3; ++k) v[k] += d.partials[b * PARTIAL_STRIDE + k];
+        block_reduce<3>(v, op, sm);
+        if (threadIdx.x == 0) {
+            d.rec->sum_m = v[0];
+            d.rec->sum_dr = v[1];
+            d.rec->mass_now = v[2];
+        }
+    }
+}
+
+// Per-cell corrected density and raw momentum change, shared by the second reduction and
+// the apply pass so both see identical values.
+// Per-cell arithmetic runs in the lattice's arithmetic type R (FP32 for FP32/FP16 storage,
+// FP64 for FP64 storage); only the lattice-wide sums are FP64.
+template <typename R>
 struct CellCorr {
-    double m, rhop, djx_raw, djy_raw;
+    R m, rhop, djx_raw, djy_raw;
 };
 template <typename R>
-__device__ __forceinline__ CellCorr cell_corr(long long c, const R* rho, const R* jx, const R* jy, const R* g,
-                                              const R* out3, long long N, double beta_rho, double beta_u,
-                                              const DevRecord* rec) {
-    CellCorr q;
-    const double r = (double)rho[c];
-    q.m = (double)g[c] / rec->gmax;
-    const double dr_raw = beta_rho * q.m * ((double)out3[c] - r);
-    const double dr = dr_raw - q.m * (rec->sum_dr + (rec->mass_now - rec->mass0)) / rec->sum_m;
+struct CorrK {
+    R gmax, proj, beta_rho, beta_u;  // proj = (sum drho_raw + M - M0) / sum m
+};
+template <typename R>
+__device__ __forceinline__ CorrK<R> corr_constants(const DevRecord* rec, double beta_rho, double beta_u) {
+    CorrK<R> k;
+    k.gmax = R(rec->gmax);
+    k.proj = R((rec->sum_dr + (rec->mass_now - rec->mass0)) / rec->sum_m);
+    k.beta_rho = R(beta_rho);
+    k.beta_u = R(beta_u);
+    return k;
+}
+template <typename R>
+__device__ __forceinline__ CellCorr<R> cell_corr(long long c, const R* rho, const R* jx, const R* jy, const R* g,
+                                                 const R* out3, long long N, const CorrK<R>& k) {
+    CellCorr<R> q;
+    const R r = rho[c];
+    q.m = g[c] / k.gmax;
+    const R dr = k.beta_rho * q.m * (out3[c] - r) - q.m * k.proj;
     q.rhop = r + dr;
-    q.djx_raw = beta_u * q.m * (q.rhop * (double)out3[N + c] - (double)jx[c]);
-    q.djy_raw = beta_u * q.m * (q.rhop * (double)out3[2 * N + c] - (double)jy[c]);
+    q.djx_raw = k.beta_u * q.m * (q.rhop * out3[N + c] - jx[c]);
+    q.djy_raw = k.beta_u * q.m * (q.rhop * out3[2 * N + c] - jy[c]);
     return q;
 }
 
 template <typename R>
-__global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(const R* __restrict__ rho, const R* __restrict__ jx,
-                                                           const R* __restrict__ jy, const R* __restrict__ g,
-                                                           const R* __restrict__ out3, long long N, double beta_rho,
-                                                           double beta_u, const DevRecord* __restrict__ rec,
-                                                           double* __restrict__ partials) {
+__global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(TableView t) {
     __shared__ double sm[3 * 32];
-    double v[3] = {0, 0, 0};  // sum djx_raw, sum djy_raw, reject flag
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
     const int op[3] = {0, 0, 1};
-    if (rec->sum_m > 0.0) {
-        for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-            const CellCorr q = cell_corr(c, rho, jx, jy, g, out3, N, beta_rho, beta_u, rec);
-            v[0] += q.djx_raw;
-            v[1] += q.djy_raw;
-            const bool ok = q.rhop > 0.0 && isfinite(q.rhop) && isfinite(q.djx_raw) && isfinite(q.djy_raw);
-            v[2] = fmax(v[2], ok ? 0.0 : 1.0);
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const long long N = (long long)d.nx * d.ny;
+        double v[3] = {0, 0, 0};  // sum djx_raw, sum djy_raw, reject flag
+        if (d.rec->sum_m > 0.0) {
+            const CorrK<R> k = corr_constants<R>(d.rec, d.beta_rho, d.beta_u);
+            for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+                const CellCorr<R> q = cell_corr(c, static_cast<const R*>(d.rho), static_cast<const R*>(d.jx),
+                                                static_cast<const R*>(d.jy), static_cast<const R*>(d.g),
+                                                static_cast<const R*>(d.out3), N, k);
+                v[0] += (double)q.djx_raw;
+                v[1] += (double)q.djy_raw;
+                const bool ok = q.rhop > R(0) && isfinite(q.rhop) && isfinite(q.djx_raw) && isfinite(q.djy_raw);
+                v[2] = fmax(v[2], ok ? 0.0 : 1.0);
+            }
         }
+        block_reduce<3>(v, op, sm);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
-    block_reduce<3>(v, op, sm);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 3; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
 }
 
-__global__ void __launch_bounds__(RB_THREADS) k_corr_final2(const double* __restrict__ partials, int nb, DevRecord* rec) {
+__global__ void __launch_bounds__(RB_THREADS) k_corr_final2(TableView t) {
     __shared__ double sm[3 * 32];
-    double v[3] = {0, 0, 0};
+    const int n = t.hdr->n;
     const int op[3] = {0, 0, 1};
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        v[0] += partials[b * PARTIAL_STRIDE + 0];
-        v[1] += partials[b * PARTIAL_STRIDE + 1];
-        v[2] = fmax(v[2], partials[b * PARTIAL_STRIDE + 2]);
-    }
-    block_reduce<3>(v, op, sm);
-    if (threadIdx.x == 0) {
-        rec->sum_jx = v[0];
-        rec->sum_jy = v[1];
-        rec->reject = v[2] > 0.0 ? 1 : 0;
-        if (v[2] > 0.0) {
-            if (rec->status == PL_OK) rec->status = PL_ERR_NONPHYSICAL;
-        } else if (rec->sum_m > 0.0) {
-            rec->applied += 1;
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const LatDesc& d = t.d[j];
+        double v[3] = {0, 0, 0};
+        for (int b = threadIdx.x; b < d.red_blocks; b += blockDim.x) {
+            v[0] += d.partials[b * PARTIAL_STRIDE + 0];
+            v[1] += d.partials[b * PARTIAL_STRIDE + 1];
+            v[2] = fmax(v[2], d.partials[b * PARTIAL_STRIDE + 2]);
+        }
+        block_reduce<3>(v, op, sm);
+        if (threadIdx.x == 0) {
+            DevRecord* rec = d.rec;
+            rec->sum_jx = v[0];
+            rec->sum_jy = v[1];
+            rec->reject = v[2] > 0.0 ? 1 : 0;
+            if (v[2] > 0.0) {
+                if (rec->status == PL_OK) rec->status = PL_ERR_NONPHYSICAL;
+            } else if (rec->sum_m > 0.0) {
+                rec->applied += 1;
+            }
         }
     }
 }
 
 template <typename R>
-__device__ __forceinline__ void feq9(double rho, double ux, double uy, double (&fe)[9]) {
-    const double usq = 1.5 * (ux * ux + uy * uy);
+__device__ __forceinline__ void feq9(R rho, R ux, R uy, R (&fe)[9]) {
+    const R usq = R(1.5) * (ux * ux + uy * uy);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const double cu = cx(i) * ux + cy(i) * uy;
-        fe[i] = wq<double>(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - usq);
+        const R cu = R(cx(i)) * ux + R(cy(i)) * uy;
+        fe[i] = wq<R>(i) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - usq);
     }
 }
 
 template <int MODE>
-__global__ void k_corr_apply(typename Traits<MODE>::S* __restrict__ f, int nx, int pitch, long long plane,
-                             const typename Traits<MODE>::R* __restrict__ rho, const typename Traits<MODE>::R* __restrict__ jx,
-                             const typename Traits<MODE>::R* __restrict__ jy, const typename Traits<MODE>::R* __restrict__ g,
-                             const typename Traits<MODE>::R* __restrict__ out3, long long N, double beta_rho,
-                             double beta_u, double rho_ref, const DevRecord* __restrict__ rec) {
+__global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int parity) {
+    using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
-    if (rec->reject || !(rec->sum_m > 0.0)) return;
-    const double sjx = rec->sum_jx / rec->sum_m, sjy = rec->sum_jy / rec->sum_m;
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        if (!((double)g[c] > 0.0)) continue;
-        const CellCorr q = cell_corr(c, rho, jx, jy, g, out3, N, beta_rho, beta_u, rec);
-        const double djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
-        const double r = (double)rho[c], jxc = (double)jx[c], jyc = (double)jy[c];
-        double fn[9], fo[9];
-        feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
-        feq9<R>(r, jxc / r, jyc / r, fo);
-        const long long o = (c / nx) * pitch + c % nx;
-        if constexpr (MODE == PL_F16_OFFSET) {
-            // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
-            // nearest, the rest population taking the cell's corrected stored mass minus their
-            // rounded values and rounded stochastically, so that small per-cell changes
-            // (below half an FP16 step) are realised on average instead of being rounded away
-            float hn[9];
-            float res = 0.0f;
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    const uint32_t seq = t.seq[parity];
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const DevRecord* rec = d.rec;
+        if (rec->reject || !(rec->sum_m > 0.0)) continue;
+        const long long N = (long long)d.nx * d.ny;
+        const R* rho = static_cast<const R*>(d.rho);
+        const R* jx = static_cast<const R*>(d.jx);
+        const R* jy = static_cast<const R*>(d.jy);
+        const R* g = static_cast<const R*>(d.g);
+        const R* out3 = static_cast<const R*>(d.out3);
+        S* f = static_cast<S*>(d.pops[d.phase ^ parity]);
+        const R sjx = R(rec->sum_jx / rec->sum_m), sjy = R(rec->sum_jy / rec->sum_m);
+        const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u);
+        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+            if (!(g[c] > R(0))) continue;
+            const CellCorr<R> q = cell_corr(c, rho, jx, jy, g, out3, N, k);
+            const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
+            const R r = rho[c], jxc = jx[c], jyc = jy[c];
+            R fn[9], fo[9];
+            feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
+            feq9<R>(r, jxc / r, jyc / r, fo);
+            const long long o = pop_offset(c, d.nx, d.pitch);
+            if constexpr (MODE == PL_F16_OFFSET) {
+                // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
+                // nearest, the rest population taking the cell's corrected stored mass minus their
+                // rounded values and rounded stochastically, so that small per-cell changes
+                // (below half an FP16 step) are realised on average instead of being rounded away
+                float hn[9];
+                float res = 0.0f;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) hn[i] = __half2float(f[i * plane + o]) + (float)(fn[i] - fo[i]);
+                for (int i = 0; i < 9; ++i) hn[i] = __half2float(f[i * d.plane + o]) + (fn[i] - fo[i]);
 #pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                const __half q = __float2half_rn(hn[i]);
-                res += __half2float(q) - hn[i];
-                f[i * plane + o] = q;
-            }
-            const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u));
-            f[o] = sr_half(hn[0] - res, rnd);
-        } else {
+                for (int i = 1; i < 9; ++i) {
+                    const __half qh = __float2half_rn(hn[i]);
+                    res += __half2float(qh) - hn[i];
+                    f[i * d.plane + o] = qh;
+                }
+                const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u) ^
+                                            ((seq - d.seq0) * 0x27D4EB2Fu));
+                f[o] = sr_half(hn[0] - res, rnd);
+            } else {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const R off = R(wq<double>(i) * rho_ref);
-                const double fi = (double)decode<MODE>(f[i * plane + o], off);
-                f[i * plane + o] = encode<MODE>(R(fi + (fn[i] - fo[i])), off);
+                for (int i = 0; i < 9; ++i) {
+                    const R off = R(wq<double>(i) * d.rho_ref);
+                    const R fi = decode<MODE>(f[i * d.plane + o], off);
+                    f[i * d.plane + o] = encode<MODE>(fi + (fn[i] - fo[i]), off);
+                }
             }
         }
     }
 }
 
 template <int MODE>
-static cudaError_t correction_t(const LatticeView& v, const PhysParams& p, int cur, int mlp_mode, cudaStream_t s) {
-    using S = typename Traits<MODE>::S;
+static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, const float* w32, const uint16_t* wbf16,
+                                cudaStream_t s) {
     using R = typename Traits<MODE>::R;
-    const long long N = (long long)v.nx * v.ny;
-    const int nb = reduction_blocks(v);
-    R* rho = static_cast<R*>(v.rho);
-    R* jx = static_cast<R*>(v.jx);
-    R* jy = static_cast<R*>(v.jy);
-    R* g = static_cast<R*>(v.g);
-    R* out3 = static_cast<R*>(v.out3);
-    cudaError_t e = launch_mlp_field(v, mlp_mode, s);
+    cudaError_t e = launch_mlp_tab(t, MODE, mlp_mode, w32, wbf16, s);
     if (e != cudaSuccess) return e;
-    k_moments<MODE><<<nb, RB_THREADS, 0, s>>>(static_cast<const S*>(v.pops[cur]), v.nx, v.pitch, N, v.plane, R(p.rho_ref),
-                                              rho, jx, jy);
-    k_grad_reduce<R><<<nb, RB_THREADS, 0, s>>>(rho, v.nx, v.ny, g, p.threshold, v.partials);
-    k_final_metrics<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec, 0);
-    k_corr_sums1<R><<<nb, RB_THREADS, 0, s>>>(rho, g, out3, N, p.beta_rho, v.rec, v.partials);
-    k_corr_final1<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec);
-    k_corr_sums2<R><<<nb, RB_THREADS, 0, s>>>(rho, jx, jy, g, out3, N, p.beta_rho, p.beta_u, v.rec, v.partials);
-    k_corr_final2<<<1, RB_THREADS, 0, s>>>(v.partials, nb, v.rec);
-    long long blocks = (N + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_corr_apply<MODE><<<(int)blocks, 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.pitch, v.plane, rho, jx, jy, g, out3, N,
-                                                   p.beta_rho, p.beta_u, p.rho_ref, v.rec);
+    k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+    k_grad_tab<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_final_metrics_tab<<<RED_GRID, RB_THREADS, 0, s>>>(t, 0);
+    k_corr_sums1<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_corr_final1<<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_corr_sums2<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_corr_final2<<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_corr_apply<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
     note_launches(8);
     return cudaGetLastError();
 }
 
-cudaError_t launch_correction(const LatticeView& v, const PhysParams& p, int cur, int mlp_mode, cudaStream_t s) {
-    switch (v.storage) {
-        case PL_F64: return correction_t<PL_F64>(v, p, cur, mlp_mode, s);
-        case PL_F32: return correction_t<PL_F32>(v, p, cur, mlp_mode, s);
-        case PL_F16_OFFSET: return correction_t<PL_F16_OFFSET>(v, p, cur, mlp_mode, s);
+cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, const float* w32,
+                                  const uint16_t* wbf16, cudaStream_t s) {
+    switch (storage) {
+        case PL_F64: return correction_t<PL_F64>(t, parity, mlp_mode, w32, wbf16, s);
+        case PL_F32: return correction_t<PL_F32>(t, parity, mlp_mode, w32, wbf16, s);
+        case PL_F16_OFFSET: return correction_t<PL_F16_OFFSET>(t, parity, mlp_mode, w32, wbf16, s);
     }
     return cudaErrorInvalidValue;
 }

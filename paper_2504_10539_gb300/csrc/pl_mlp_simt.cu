@@ -3,17 +3,21 @@
 // tanh on the hidden layers, linear output.  Input: the cell centre mapped to
 // [-1, 1] (x^ = 2 (x + 0.5) / nx - 1).
 //
-// One thread per cell.  Activations live in shared memory, feature-major
-// ([feature][thread]) so that a warp's accesses are consecutive; each thread
-// accumulates 16 outputs at a time in registers while the weights (the same
-// for every thread) are broadcast from the read-only cache.
+// One thread per cell, 64 cells per block, persistent over the table's half tiles
+// (a 128-cell tile of lattice j is two 64-cell halves).  Activations live in shared
+// memory, feature-major ([feature][thread]) so that a warp's accesses are
+// consecutive; each thread accumulates 16 outputs at a time in registers while the
+// weights (the same for every thread) are broadcast from the read-only cache.
 #include "pl_device.cuh"
 #include "pl_kernels.h"
 
 namespace pl {
 
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s);
+
 constexpr int MLP_THREADS = 64;
 constexpr int MLP_CHUNK = 16;
+constexpr int MLP_GRID = 152 * 8;
 
 template <typename R>
 __device__ __forceinline__ R act_tanh(R z);
@@ -42,14 +46,24 @@ __device__ __forceinline__ void dense(const float* __restrict__ W, const float* 
     }
 }
 
+__device__ __forceinline__ int find_tile_s(const long long* __restrict__ pre, int n, long long v) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restrict__ w, int nx, int ny,
-                                                          R* __restrict__ out3) {
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restrict__ w, TableView tab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* bufA = reinterpret_cast<R*>(smem_raw);     // [128][MLP_THREADS]
     R* bufB = bufA + 128 * MLP_THREADS;            // [128][MLP_THREADS]
-    const long long N = (long long)nx * ny;
     const int t = threadIdx.x;
+    const int nlat = tab.hdr->n;
+    const long long halves = 2 * tab.hdr->total_tiles;
     // blob offsets
     const float* W1 = w;
     const float* b1 = W1 + 64 * 2;
@@ -61,8 +75,14 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
     const float* b4 = W4 + 64 * 128;
     const float* W5 = b4 + 64;
     const float* b5 = W5 + 3 * 64;
-    for (long long base = (long long)blockIdx.x * MLP_THREADS; base < N; base += (long long)gridDim.x * MLP_THREADS) {
-        const long long c = base + t;
+    for (long long vh = blockIdx.x; vh < halves; vh += gridDim.x) {
+        const long long tile = vh >> 1;
+        const int j = find_tile_s(tab.tile_pre, nlat, tile);
+        const LatDesc& d = tab.d[j];
+        const int nx = d.nx, ny = d.ny;
+        const long long N = (long long)nx * ny;
+        R* out3 = static_cast<R*>(d.out3);
+        const long long c = (tile - tab.tile_pre[j]) * MLP_TILE + (vh & 1) * MLP_THREADS + t;
         const long long cc = c < N ? c : N - 1;
         const int x = (int)(cc % nx), y = (int)(cc / nx);
         bufA[0 * MLP_THREADS + t] = R(2) * (R(x) + R(0.5)) / R(nx) - R(1);
@@ -81,30 +101,29 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
 }
 
 template <typename R>
-static cudaError_t mlp_simt_t(const LatticeView& v, cudaStream_t s) {
+static cudaError_t mlp_simt_t(const TableView& t, const float* w32, cudaStream_t s) {
     const size_t smem = 2 * 128 * MLP_THREADS * sizeof(R);
-    static bool attr_set = false;  // per-process, per-instantiation
+    static bool attr_set = false;  // per process and instantiation (one device)
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_mlp_simt<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const long long N = (long long)v.nx * v.ny;
-    long long blocks = (N + MLP_THREADS - 1) / MLP_THREADS;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_mlp_simt<R><<<(int)blocks, MLP_THREADS, smem, s>>>(v.w32, v.nx, v.ny, static_cast<R*>(v.out3));
+    k_mlp_simt<R><<<MLP_GRID, MLP_THREADS, smem, s>>>(w32, t);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_simt(const LatticeView& v, int mlp_mode, cudaStream_t s) {
-    // The output element type follows the lattice's scratch type.
-    if (v.storage == PL_F64) {
+cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, const float* w32, const uint16_t* wbf16,
+                           cudaStream_t s) {
+    // The output element type follows the lattice's scratch type: double for FP64 storage.
+    if (storage == PL_F64) {
         if (mlp_mode != PL_MLP_F64) return cudaErrorInvalidValue;
-        return mlp_simt_t<double>(v, s);
+        return mlp_simt_t<double>(t, w32, s);
     }
+    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(t, w32, wbf16, s);
     if (mlp_mode != PL_MLP_F32) return cudaErrorInvalidValue;
-    return mlp_simt_t<float>(v, s);
+    return mlp_simt_t<float>(t, w32, s);
 }
 
 }  // namespace pl

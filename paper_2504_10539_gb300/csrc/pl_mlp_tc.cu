@@ -97,11 +97,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns = WAIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = gtime();
     while (!mbar_try(bar, parity))
-        if (gtime() - t0 > WAIT_NS) return false;
+        if (gtime() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -206,14 +206,26 @@ cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, cudaS
     return cudaGetLastError();
 }
 
+__device__ __forceinline__ int find_tile(const long long* __restrict__ pre, int n, long long v) {
+    int lo = 0, hi = n;  // pre[lo] <= v < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Persistent over the table's 128-cell tiles (tile v of the table belongs to the lattice j
+// with tile_pre[j] <= v < tile_pre[j+1]; tiles never straddle lattices).
 __global__ void __launch_bounds__(tc::THREADS, 1)
-    k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, int nx, int ny,
-             float* __restrict__ out3, DevRecord* __restrict__ rec) {
+    k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, TableView tab) {
     using namespace tc;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
-    const long long N = (long long)nx * ny;
-    const long long ntiles = (N + M - 1) / M;
+    const int nlat = tab.hdr->n;
+    const long long ntiles = tab.hdr->total_tiles;
+    if ((long long)blockIdx.x * NWG >= ntiles) return;  // no tile for this CTA: skip set-up
     float* P = reinterpret_cast<float*>(sm + OFF_P);
     const uint32_t bar_w = saddr(sm + OFF_BAR);
     const uint32_t bar_mma = saddr(sm + OFF_BAR + 8 * (1 + wg));
@@ -268,8 +280,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     uint32_t phase = 0;
     int pending = 0;  // MMA batches committed but not yet waited for
 
+    DevRecord* last_rec = nullptr;
     for (long long tile = (long long)blockIdx.x * NWG + wg; ok && tile < ntiles; tile += (long long)gridDim.x * NWG) {
-        const long long c = tile * M + t;
+        const int lj = find_tile(tab.tile_pre, nlat, tile);
+        const LatDesc& ld = tab.d[lj];
+        const int nx = ld.nx, ny = ld.ny;
+        const long long N = (long long)nx * ny;
+        float* out3 = static_cast<float*>(ld.out3);
+        last_rec = ld.rec;
+        const long long c = (tile - tab.tile_pre[lj]) * M + t;
         const long long cc = c < N ? c : N - 1;
         const int x = (int)(cc % nx), y = (int)(cc / nx);
         const float xh = 2.0f * ((float)x + 0.5f) / (float)nx - 1.0f;
@@ -336,7 +355,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
     }
     if (!ok) {
-        if (t == 0) atomicCAS(&rec->status, PL_OK, PL_ERR_TIMEOUT);
+        if (t == 0 && last_rec) atomicCAS(&last_rec->status, PL_OK, PL_ERR_TIMEOUT);
         if (pending) (void)mbar_wait(bar_mma, phase);  // let MMAs in flight finish before TMEM is freed
     }
     tc_before_sync();
@@ -346,23 +365,34 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-cudaError_t launch_mlp_tc(const LatticeView& v, cudaStream_t s) {
-    if (v.storage == PL_F64) return cudaErrorInvalidValue;  // FP32 scratch only
-    static bool attr_set = false;
-    if (!attr_set) {
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing arrives on;
+// the wait gives up after limit_ns and the kernel reports PL_ERR_TIMEOUT in *status.
+__global__ void k_selftest_wait(int* status, long long limit_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = tc::saddr(&bar);
+    tc::mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *status = tc::mbar_wait(b, 0, limit_ns) ? PL_OK : PL_ERR_TIMEOUT;
+}
+
+cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t s) {
+    k_selftest_wait<<<1, 1, 0, s>>>(d_status, limit_ns);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s) {
+    static int sms = 0;
+    if (!sms) {
         cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_ALLOC);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
     }
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long N = (long long)v.nx * v.ny;
-    const long long tiles = (N + tc::M - 1) / tc::M;
-    long long grid = (tiles + tc::NWG - 1) / tc::NWG;
-    if (grid > sms) grid = sms;
-    k_mlp_tc<<<(int)grid, tc::THREADS, tc::SMEM_ALLOC, s>>>(v.wbf16, v.w32, v.nx, v.ny, static_cast<float*>(v.out3),
-                                                             v.rec);
+    // persistent: one CTA per SM (CTAs without a tile return before any set-up)
+    k_mlp_tc<<<sms, tc::THREADS, tc::SMEM_ALLOC, s>>>(wbf16, w32, t);
     note_launches(1);
     return cudaGetLastError();
 }

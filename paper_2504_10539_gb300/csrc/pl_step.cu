@@ -33,7 +33,6 @@
 
 namespace pl {
 
-constexpr int STRIP = 60;          // owned columns per warp
 constexpr int STEP_THREADS = 128;  // 4 independent warps per CTA
 
 template <int MODE> struct Pair;
@@ -139,6 +138,7 @@ struct WalkArgs {
     int nx, ny, pitch, nstrips, chunks;
     long long plane;
     StepK<typename Traits<MODE>::R> k;
+    uint32_t seq;  // step sequence number (dither of the FP16 stochastic rounding)
 };
 
 template <int MODE>
@@ -255,7 +255,8 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
                     q1 += q.y;
                 }
                 const uint32_t rnd = fmix32(__float_as_uint(hp[0][0]) ^ (__float_as_uint(hp[1][1]) * 0x9E3779B1u) ^
-                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du));
+                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^
+                                            (a.seq * 0x27D4EB2Fu));
                 rest16 = sr_pack_half2(sh_p0 - q0, sh_p1 - q1, rnd);
             }
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
@@ -304,75 +305,97 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
     }
 }
 
-// Warp w walks strip (w mod nstrips) over row chunk (w / nstrips); the rows are cut
-// into `chunks` equal chunks, the same cut in every strip.  All warps of a row chunk
-// start together and advance one row per iteration, so horizontally adjacent strips
-// touch the sectors they share (halo columns, partial sectors at strip edges) at the
-// same time and those are served from L2, and each row of a plane is read as one
-// contiguous sweep.
-template <int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) k_step(WalkArgs<MODE> a) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5;
-    const int strip = (int)(warp % a.nstrips);
-    const long long chunk = warp / a.nstrips;
-    if (chunk >= a.chunks) return;
-    const int r0 = (int)(chunk * a.ny / a.chunks);
-    const int r1 = (int)((chunk + 1) * a.ny / a.chunks);
-    if (r1 > r0) walk_segment<MODE>(a, strip, r0, r1, lane);
+// Persistent table kernel: physical warp w processes virtual warps w, w+P, w+2P, ...
+// Virtual warp v belongs to the lattice j with warp_pre[j] <= v < warp_pre[j+1]; its
+// local index l walks strip (l mod nstrips) over row chunk (l / nstrips).  The rows of a
+// lattice are cut into equal chunks, the same cut in every strip, so the warps of one
+// chunk (consecutive virtual warps) start together and advance one row per iteration:
+// horizontally adjacent strips touch the sectors they share (halo columns, partial
+// sectors at strip edges) at the same time and those are served from L2, and each row
+// of a plane is read as one contiguous sweep.
+__device__ __forceinline__ int find_seg(const long long* __restrict__ pre, int n, long long v) {
+    int lo = 0, hi = n;  // pre[lo] <= v < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= v) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int MODE>
-static cudaError_t launch_step_t(const LatticeView& v, const PhysParams& p, int src, cudaStream_t s) {
+__global__ void __launch_bounds__(STEP_THREADS) k_step(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
-    static int blocks_per_sm = 0, sms = 0;
-    if (!blocks_per_sm) {
-        int dev = 0;
+    const int lane = threadIdx.x & 31;
+    const long long P = (long long)gridDim.x * (STEP_THREADS / 32);
+    const long long total = t.hdr->total_warps;
+    const int n = t.hdr->n;
+    const uint32_t seq = t.seq[parity];
+    if (blockIdx.x == 0 && threadIdx.x == 0) t.seq[parity ^ 1] = seq + 1u;
+    for (long long vw = ((long long)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5; vw < total; vw += P) {
+        const int j = find_seg(t.warp_pre, n, vw);
+        const LatDesc& d = t.d[j];
+        const long long local = vw - t.warp_pre[j];
+        const int strip = (int)(local % d.nstrips);
+        const long long chunk = local / d.nstrips;
+        const int r0 = (int)(chunk * d.ny / d.chunks);
+        const int r1 = (int)((chunk + 1) * d.ny / d.chunks);
+        if (r1 <= r0) continue;
+        WalkArgs<MODE> a;
+        const int src = d.phase ^ parity;
+        a.fin = static_cast<const S*>(d.pops[src]);
+        a.fout = static_cast<S*>(d.pops[1 - src]);
+        a.nx = d.nx;
+        a.ny = d.ny;
+        a.pitch = d.pitch;
+        a.nstrips = d.nstrips;
+        a.chunks = d.chunks;
+        a.plane = d.plane;
+        a.k = StepK<R>{R(d.G), R(d.tau), R(1.0 / d.tau), R(d.rho0), R(1.0 / d.rho0),
+                       MODE == PL_F16_OFFSET ? R(d.rho_ref) : R(0)};
+        a.seq = seq - d.seq0;  // the lattice's own step count: the same alone or in a batch
+        walk_segment<MODE>(a, strip, r0, r1, lane);
+    }
+}
+
+template <int MODE>
+static int capacity_t() {
+    static int cap = 0;
+    if (!cap) {
+        int dev = 0, sms = 0, bps = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_step<MODE>, STEP_THREADS, 0);
-        if (e != cudaSuccess || blocks_per_sm < 1) blocks_per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_step<MODE>, STEP_THREADS, 0) != cudaSuccess || bps < 1)
+            bps = 1;
+        cap = bps * sms * (STEP_THREADS / 32);
     }
-    WalkArgs<MODE> a;
-    a.fin = static_cast<const S*>(v.pops[src]);
-    a.fout = static_cast<S*>(v.pops[1 - src]);
-    a.nx = v.nx;
-    a.ny = v.ny;
-    a.pitch = v.pitch;
-    a.nstrips = (v.nx + STRIP - 1) / STRIP;
-    a.plane = v.plane;
-    a.k = StepK<R>{R(p.G), R(p.tau), R(1.0 / p.tau), R(p.rho0), R(1.0 / p.rho0),
-                   MODE == PL_F16_OFFSET ? R(p.rho_ref) : R(0)};
-    // as many row chunks per strip as keep every warp resident, and chunks of at
-    // least 8 rows (a chunk also reads its two halo rows)
-    const long long capacity = (long long)blocks_per_sm * sms * (STEP_THREADS / 32);
-    long long chunks = capacity / a.nstrips;
-    const long long max_chunks = v.ny / 8 > 0 ? v.ny / 8 : 1;
-    if (chunks > max_chunks) chunks = max_chunks;
-    if (chunks < 1) chunks = 1;
-    a.chunks = (int)chunks;
-    const long long warps = chunks * a.nstrips;
-    const long long blocks = (warps + (STEP_THREADS / 32) - 1) / (STEP_THREADS / 32);
-    k_step<MODE><<<(int)blocks, STEP_THREADS, 0, s>>>(a);
+    return cap;
+}
+
+int step_capacity_warps(int storage) {
+    switch (storage) {
+        case PL_F64: return capacity_t<PL_F64>();
+        case PL_F32: return capacity_t<PL_F32>();
+        default: return capacity_t<PL_F16_OFFSET>();
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_step_t(const TableView& t, int parity, cudaStream_t s) {
+    const int blocks = capacity_t<MODE>() / (STEP_THREADS / 32);
+    k_step<MODE><<<blocks, STEP_THREADS, 0, s>>>(t, parity);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(const LatticeView& v, const PhysParams& p, int src, StepTiling tl, cudaStream_t s) {
-    (void)tl;
-    switch (v.storage) {
-        case PL_F64: return launch_step_t<PL_F64>(v, p, src, s);
-        case PL_F32: return launch_step_t<PL_F32>(v, p, src, s);
-        case PL_F16_OFFSET: return launch_step_t<PL_F16_OFFSET>(v, p, src, s);
+cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s) {
+    switch (storage) {
+        case PL_F64: return launch_step_t<PL_F64>(t, parity, s);
+        case PL_F32: return launch_step_t<PL_F32>(t, parity, s);
+        case PL_F16_OFFSET: return launch_step_t<PL_F16_OFFSET>(t, parity, s);
     }
     return cudaErrorInvalidValue;
-}
-
-StepTiling default_tiling(int nx, int ny) {
-    (void)nx;
-    (void)ny;
-    return StepTiling{STEP_THREADS, STRIP};
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -1,0 +1,165 @@
+"""Batched lattices: job table, segmented reductions, graph-replayed intervals,
+admission against a device budget, retirement, fault isolation.
+
+The central property: a job's result does not depend on what else is in the batch
+(its reductions are decomposed by its own size only, and its FP16 dither follows its
+own step count), so alone and in a mix its state is bit-identical.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+K = 20
+
+
+def jobs_mix(storage, mlp=wl.MLP_F32):
+    specs = [(64, 64, 1.0, -5.5), (96, 40, 0.9, -5.3), (130, 70, 1.0, -5.0), (200, 150, 1.1, -5.8),
+             (61, 61, 1.0, -5.5), (256, 256, 0.95, -5.5)]
+    out = []
+    for k, (nx, ny, tau, G) in enumerate(specs):
+        out.append(wl.Lattice(nx, ny, storage=storage, G=G, tau=tau, mlp=mlp,
+                              droplets=[(nx / 2, ny / 2, min(nx, ny) / 4)], seed=40 + k, steps=100 * K, K=K))
+    return out
+
+
+def budget_for(jobs, max_jobs=64):
+    return B.pl_batch_overhead_bytes(max_jobs) + sum(B.pl_batch_job_bytes(B.job_params(j)) for j in jobs) + (1 << 20)
+
+
+@pytest.mark.parametrize("storage", [B.PL_F32, B.PL_F16_OFFSET])
+def test_job_alone_and_in_mix_is_bit_identical(storage):
+    jobs = jobs_mix(storage)
+    blob = wl.mlp_weights(61)
+    mix = B.Batch(storage, B.PL_MLP_F32, K, budget_for(jobs))
+    mix.set_weights(blob)
+    ids = [mix.submit(j) for j in jobs]
+    assert all(i is not None for i in ids)
+    mix.advance(3)
+    for job, jid in zip(jobs, ids):
+        alone = B.Batch(storage, B.PL_MLP_F32, K, budget_for([job]))
+        alone.set_weights(blob)
+        aid = alone.submit(job)
+        alone.advance(3)
+        fa, sa = alone.state(aid)
+        fm, sm = mix.state(jid)
+        assert sa == sm == 3 * K
+        assert np.array_equal(fa, fm), (job.nx, job.ny)
+        alone.close()
+    mix.close()
+
+
+def test_job_admitted_later_matches_alone():
+    jobs = jobs_mix(B.PL_F16_OFFSET)
+    blob = wl.mlp_weights(62)
+    mix = B.Batch(B.PL_F16_OFFSET, B.PL_MLP_F32, K, budget_for(jobs))
+    mix.set_weights(blob)
+    first = mix.submit(jobs[0])
+    mix.advance(2)
+    late = mix.submit(jobs[3])            # joins after 2 intervals
+    mix.advance(2)
+    alone = B.Batch(B.PL_F16_OFFSET, B.PL_MLP_F32, K, budget_for([jobs[3]]))
+    alone.set_weights(blob)
+    aid = alone.submit(jobs[3])
+    alone.advance(2)
+    assert np.array_equal(alone.state(aid)[0], mix.state(late)[0])
+    assert mix.state(first)[1] == 4 * K
+
+
+def test_batch_matches_single_lattice_api():
+    job = jobs_mix(B.PL_F32)[3]
+    blob = wl.mlp_weights(63)
+    bt = B.Batch(B.PL_F32, B.PL_MLP_F32, K, budget_for([job]))
+    bt.set_weights(blob)
+    jid = bt.submit(job)
+    bt.advance(4)
+    lat = B.Lattice(B.job_params(job))
+    lat.init_droplets(job.droplets, job.rho_in, job.rho_out, job.width, job.noise_amp, job.seed)
+    lat.set_weights(blob)
+    lat.run(4 * K, K)
+    assert np.array_equal(bt.state(jid)[0], lat.state()[0])
+
+
+def test_batch_job_matches_oracle():
+    job = jobs_mix(B.PL_F32)[1]
+    blob = wl.mlp_weights(64)
+    bt = B.Batch(B.PL_F32, B.PL_MLP_F32, K, budget_for([job]))
+    bt.set_weights(blob)
+    jid = bt.submit(job)
+    bt.advance(5)
+    f = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
+                                      job.noise_amp, job.seed))
+    M0 = O.mass(f)
+    assert O.run(f, 5 * K, job.G, job.tau, K=K, blob=blob, mode=O.MLP_F64, M0=M0) == 0
+    ro = O.density(f)
+    err = np.abs(O.density(bt.state(jid)[0]) - ro).max() / np.abs(ro).max()
+    assert err < 1e-4, err
+
+
+def test_retirement_results_and_budget():
+    jobs = jobs_mix(B.PL_F16_OFFSET)[:3]
+    blob = wl.mlp_weights(65)
+    one = B.pl_batch_job_bytes(B.job_params(jobs[2]))
+    # room for the largest job plus a little: the second submission must wait
+    bt = B.Batch(B.PL_F16_OFFSET, B.PL_MLP_F32, K, B.pl_batch_overhead_bytes(8) + one + 4096, max_jobs=8)
+    bt.set_weights(blob)
+    a = bt.submit(jobs[2], steps=2 * K)
+    assert a is not None
+    assert bt.submit(jobs[2], steps=K) is None          # PL_ERR_BUDGET: no room now
+    bt.advance(1)
+    assert bt.poll() == []
+    bt.advance(1)
+    res = bt.poll()
+    assert [r["id"] for r in res] == [a] and res[0]["steps"] == 2 * K and res[0]["status"] == 0
+    m = res[0]["metrics"]
+    assert m["corrections"] == 2 and abs(m["mass"] - m["mass0"]) <= 1e-6 * m["mass0"]
+    assert bt.info()["active"] == 0 and bt.info()["arena_used"] == 0
+    b2 = bt.submit(jobs[2], steps=33)                    # now it fits; 33 steps round up to 2 K
+    assert b2 is not None
+    bt.advance(2)
+    assert bt.poll()[0]["steps"] == 2 * K
+
+
+def test_fault_in_one_job_leaves_the_others_untouched():
+    jobs = jobs_mix(B.PL_F32)[:3]
+    bad = wl.Lattice(80, 80, storage=B.PL_F32, mlp=wl.MLP_F32, droplets=[(40.0, 40.0, 15.0)], rho_in=2.0,
+                     rho_out=-0.5, seed=9, steps=100 * K, K=K)   # negative vapour density
+    blob = wl.mlp_weights(66)
+    mix = B.Batch(B.PL_F32, B.PL_MLP_F32, K, budget_for(jobs + [bad]))
+    mix.set_weights(blob)
+    ids = [mix.submit(j) for j in jobs]
+    bid = mix.submit(bad, steps=2 * K)
+    mix.advance(2)
+    res = {r["id"]: r for r in mix.poll()}
+    assert res[bid]["status"] == B.PL_ERR_NONPHYSICAL
+    for job, jid in zip(jobs, ids):
+        alone = B.Batch(B.PL_F32, B.PL_MLP_F32, K, budget_for([job]))
+        alone.set_weights(blob)
+        aid = alone.submit(job)
+        alone.advance(2)
+        assert np.array_equal(alone.state(aid)[0], mix.state(jid)[0])
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    jobs = jobs_mix(B.PL_F16_OFFSET)
+    blob = wl.mlp_weights(67)
+    a = B.Batch(B.PL_F16_OFFSET, B.PL_MLP_F32, K, budget_for(jobs))
+    a.set_weights(blob)
+    ids = [a.submit(j) for j in jobs]
+    r = a.autotune(force=True)
+    assert r in (8, 16, 24, 32, 48, 64, 96, 128)
+    a.advance(2)
+    b = B.Batch(B.PL_F16_OFFSET, B.PL_MLP_F32, K, budget_for(jobs))
+    b.set_weights(blob)
+    idb = [b.submit(j) for j in jobs]
+    b.advance(2)
+    for x, y, j in zip(ids, idb, jobs):
+        assert np.array_equal(a.state(x)[0], b.state(y)[0])
