@@ -244,7 +244,8 @@ def run_gb300(args):
 
     # --------------------------------------------------------------- batched FP16 (headline)
     K = 100
-    n_int = args.warmup + args.steps + 2
+    n_e2e = 0 if args.no_e2e else min(args.steps, 5)
+    n_int = args.warmup + args.steps + n_e2e + 2     # no job retires before the last timed interval
     jobs = wl.batch_256(n=args.lattices, seed=4 + rank, steps=n_int * K, K=K)
     blob = np.ascontiguousarray(jobs[0].weights())
     cells = sum(j.cells for j in jobs)
@@ -286,7 +287,6 @@ def run_gb300(args):
     # each interval (the paper retrains per coupling round) and every job's metric record read
     e2e = None
     if not args.no_e2e:
-        n_e2e = min(args.steps, 5)
         rec_bytes = ctypes.sizeof(B.pl_job_result) * len(jobs)
         barrier()
         t0 = time.perf_counter()
@@ -296,6 +296,7 @@ def run_gb300(args):
             B.pl_batch_metrics(bt.h)
         torch.cuda.synchronize()
         t_e2e = max_over_ranks(time.perf_counter() - t0)
+        assert bt.info()["active"] == len(jobs), "a job retired inside the end-to-end region"
         e2e = {"value": cells * K * n_e2e * world / t_e2e / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(blob.nbytes), "d2h_bytes_per_step": int(rec_bytes)}
     bt.close()

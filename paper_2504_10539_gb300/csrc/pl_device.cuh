@@ -114,6 +114,7 @@ struct DevRecord {
     // correction bookkeeping
     double mass0;        // M0
     double sum_m, sum_dr, sum_jx, sum_jy, mass_now;
+    double proj, mjx, mjy;  // per-lattice constants of the apply pass (formed once, in FP64)
     int status;          // sticky PL_ERR_* detected on the device
     int reject;          // set by the correction check pass, cleared per correction
     int applied;         // corrections applied
@@ -121,6 +122,42 @@ struct DevRecord {
 };
 
 // Deterministic block reduction of NV values per thread, fixed tree shape.
+// Per-thread sum of a cell loop.  FP64 lattices sum in FP64.  FP32 terms are summed as an
+// unevaluated pair hi + lo of FP32 numbers: each addition is Knuth's error-free TwoSum
+// (s = hi + b exactly equals hi + b - e, e recovered with four more FP32 additions), the
+// errors are collected in lo, so the pair carries about 48 significant bits.  GB300 issues
+// FP64 arithmetic and FP32<->FP64 conversions at a small fraction of its FP32 rate; this keeps
+// the per-cell work in FP32 and converts once per thread.  The rounding-mode intrinsics
+// keep the compiler from reassociating or contracting the TwoSum.
+template <typename R>
+struct SumAcc;
+template <>
+struct SumAcc<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double b) { v += b; }
+    __device__ __forceinline__ void add_prod(double a, double b) { v += a * b; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct SumAcc<float> {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float b) {
+        const float s = __fadd_rn(hi, b);
+        const float bb = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    // a b = p + q exactly (q from one FMA), both parts summed
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float q = __fmaf_rn(a, b, -p);
+        add(p);
+        lo = __fadd_rn(lo, q);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // op: 0 = sum, 1 = max, 2 = min.  Result valid in thread 0.
 template <int NV>
 __device__ __forceinline__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* smem /* [NV*32] */) {

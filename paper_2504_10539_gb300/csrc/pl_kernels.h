@@ -84,6 +84,7 @@ struct TableView {
 
 constexpr int RB_THREADS = 256;         // threads of a reduction block
 constexpr int RB_MAX_BLOCKS = 1024;     // reduction blocks per lattice (max)
+constexpr int RB_CELLS_PER_THREAD = 32;  // target cells per reduction thread
 constexpr int PARTIAL_STRIDE = 8;       // doubles per block partial
 constexpr int MLP_TILE = 128;           // cells per network tile
 constexpr int STRIP = 60;               // owned columns per step warp

@@ -22,8 +22,10 @@ namespace pl {
 
 constexpr int RED_GRID = 152 * 8;  // persistent grid of the reduction kernels
 
+// Reduction blocks of a lattice: about RB_CELLS_PER_THREAD cells per thread, so that the
+// per-block tree (and its FP64 folds) is amortised over many cells.
 int red_blocks_for(long long cells) {
-    long long b = (cells + RB_THREADS - 1) / RB_THREADS;
+    long long b = (cells + RB_THREADS * RB_CELLS_PER_THREAD - 1) / (RB_THREADS * RB_CELLS_PER_THREAD);
     if (b > RB_MAX_BLOCKS) b = RB_MAX_BLOCKS;
     return (int)(b < 1 ? 1 : b);
 }
@@ -49,45 +51,98 @@ __device__ __forceinline__ BlkMap map_blk(const TableView& t, int n, int vb) {
     return m;
 }
 
-__device__ __forceinline__ long long pop_offset(long long c, int nx, int pitch) { return (c / nx) * pitch + c % nx; }
+// Cell index c = y nx + x of a grid-stride loop together with its coordinates, advanced by a
+// fixed stride (stride = sy nx + sx, 0 <= sx < nx) without a division per cell.
+struct CellIt {
+    long long c, stride;
+    int x, y, sx, sy;
+    __device__ __forceinline__ CellIt(long long c0, long long stride_, int nx) : c(c0), stride(stride_) {
+        x = (int)(c0 % nx);
+        y = (int)(c0 / nx);
+        sx = (int)(stride_ % nx);
+        sy = (int)(stride_ / nx);
+    }
+    __device__ __forceinline__ void next(int nx) {
+        c += stride;
+        x += sx;
+        y += sy;
+        if (x >= nx) {
+            x -= nx;
+            ++y;
+        }
+    }
+    __device__ __forceinline__ long long pop_offset(int pitch) const { return (long long)y * pitch + x; }
+};
 
 // ---------------------------------------------------------------------------------------------
 // Per-array kernels (one lattice given by raw pointers), used by pl_metrics_noalloc.
 
-// Eq. 16 gradient magnitude (central differences, periodic, dx = dy = 1), optionally stored
-// to g, and the per-block partials {sum rho, max g, sum g, sum g^2, max rho, min rho, count(g > thr)}.
+// Threshold for "g > thr" in the arithmetic type R: for FP32 g, g > thr (FP64) holds exactly
+// when g > the largest FP32 number <= thr, so the count is the one an FP64 comparison gives.
 template <typename R>
-__device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int nx, int ny, long long c,
-                                                R* __restrict__ g, double threshold, double (&v)[7]) {
-    const int x = (int)(c % nx), y = (int)(c / nx);
+__device__ __forceinline__ R threshold_below(double thr);
+template <>
+__device__ __forceinline__ double threshold_below<double>(double thr) { return thr; }
+template <>
+__device__ __forceinline__ float threshold_below<float>(double thr) { return __double2float_rd(thr); }
+
+// Per-thread metric accumulator: {sum rho, max g, sum g, sum g^2, max rho, min rho,
+// count(g > thr), count(non-physical rho)}; sums in SumAcc, extrema and counts exact.
+template <typename R>
+struct GradAcc {
+    SumAcc<R> mass, sum_g, sum_g2;
+    R gmax = R(0), rmax = R(-INFINITY), rmin = R(INFINITY);
+    unsigned count = 0, bad = 0;
+    __device__ __forceinline__ void to(double (&v)[8]) const {
+        v[0] = mass.value();
+        v[1] = (double)gmax;
+        v[2] = sum_g.value();
+        v[3] = sum_g2.value();
+        v[4] = (double)rmax;
+        v[5] = (double)rmin;
+        v[6] = (double)count;
+        v[7] = (double)bad;
+    }
+};
+
+// Eq. 16 gradient magnitude (central differences, periodic, dx = dy = 1) of cell c = (x, y),
+// optionally stored to g, accumulated into a (a non-physical cell: rho <= 0 or not finite).
+template <typename R>
+__device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int nx, int ny, long long c, int x, int y,
+                                                R* __restrict__ g, R thr, GradAcc<R>& a) {
     const long long row = c - x;
     const R gx = (rho[row + (x == nx - 1 ? 0 : x + 1)] - rho[row + (x == 0 ? nx - 1 : x - 1)]) / R(2);
     const R gy = (rho[(long long)(y == ny - 1 ? 0 : y + 1) * nx + x] - rho[(long long)(y == 0 ? ny - 1 : y - 1) * nx + x]) / R(2);
     const R gm = sqrt(gx * gx + gy * gy);
     if (g) g[c] = gm;
-    const double r = (double)rho[c], gd = (double)gm;
-    v[0] += r;
-    v[1] = fmax(v[1], gd);
-    v[2] += gd;
-    v[3] += gd * gd;
-    v[4] = fmax(v[4], r);
-    v[5] = fmin(v[5], r);
-    v[6] += gd > threshold ? 1.0 : 0.0;
+    const R r = rho[c];
+    a.mass.add(r);
+    a.gmax = fmax(a.gmax, gm);
+    a.sum_g.add(gm);
+    a.sum_g2.add_prod(gm, gm);
+    a.rmax = fmax(a.rmax, r);
+    a.rmin = fmin(a.rmin, r);
+    a.count += gm > thr ? 1u : 0u;
+    a.bad += (r > R(0) && isfinite(r)) ? 0u : 1u;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(RB_THREADS) k_grad_reduce(const R* __restrict__ rho, int nx, int ny,
                                                             R* __restrict__ g, double threshold,
                                                             double* __restrict__ partials) {
-    __shared__ double sm[7 * 32];
+    __shared__ double sm[8 * 32];
     const long long N = (long long)nx * ny;
-    double v[7] = {0.0, 0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
-    const int op[7] = {0, 1, 0, 0, 1, 2, 0};
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
-        grad_accumulate(rho, nx, ny, c, g, threshold, v);
-    block_reduce<7>(v, op, sm);
+    GradAcc<R> a;
+    const R thr = threshold_below<R>(threshold);
+    for (CellIt it(blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x, nx); it.c < N;
+         it.next(nx))
+        grad_accumulate(rho, nx, ny, it.c, it.x, it.y, g, thr, a);
+    double v[8];
+    const int op[8] = {0, 1, 0, 0, 1, 2, 0, 0};
+    a.to(v);
+    block_reduce<8>(v, op, sm);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 7; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
+        for (int k = 0; k < 8; ++k) partials[blockIdx.x * PARTIAL_STRIDE + k] = v[k];
 }
 
 __device__ __forceinline__ void fold_metric_partials(const double* __restrict__ partials, int nb, DevRecord* rec,
@@ -144,8 +199,10 @@ __global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity)
         R* jy = static_cast<R*>(d.jy);
         const R rho_ref = R(d.rho_ref);
         const long long N = (long long)d.nx * d.ny;
-        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
-            const long long o = pop_offset(c, d.nx, d.pitch);
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
+             it.next(d.nx)) {
+            const long long c = it.c;
+            const long long o = it.pop_offset(d.pitch);
             R P[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o], wq<R>(i) * rho_ref);
@@ -161,26 +218,22 @@ template <typename R>
 __global__ void __launch_bounds__(RB_THREADS) k_grad_tab(TableView t) {
     __shared__ double sm[8 * 32];
     const int n = t.hdr->n, total = t.hdr->total_blocks;
-    const int op7[7] = {0, 1, 0, 0, 1, 2, 0};
-    const int op1[1] = {0};
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         const BlkMap m = map_blk(t, n, vb);
         const LatDesc& d = t.d[m.j];
         const long long N = (long long)d.nx * d.ny;
         const R* rho = static_cast<const R*>(d.rho);
-        double v[7] = {0.0, 0.0, 0.0, 0.0, -INFINITY, INFINITY, 0.0};
-        double bad[1] = {0.0};
-        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
-            grad_accumulate(rho, d.nx, d.ny, c, static_cast<R*>(d.g), d.threshold, v);
-            const double r = (double)rho[c];
-            bad[0] += (r > 0.0 && isfinite(r)) ? 0.0 : 1.0;
-        }
-        block_reduce<7>(v, op7, sm);
-        block_reduce<1>(bad, op1, sm + 7 * 32);
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < 7; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
-            d.partials[m.lb * PARTIAL_STRIDE + 7] = bad[0];
-        }
+        const R thr = threshold_below<R>(d.threshold);
+        GradAcc<R> a;
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
+             it.next(d.nx))
+            grad_accumulate(rho, d.nx, d.ny, it.c, it.x, it.y, static_cast<R*>(d.g), thr, a);
+        double v[8];
+        const int op[8] = {0, 1, 0, 0, 1, 2, 0, 0};
+        a.to(v);
+        block_reduce<8>(v, op, sm);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 8; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
 }
 
@@ -225,13 +278,15 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
         const long long N = (long long)d.nx * d.ny;
         const double Req = laplace_req(d.rec, N);
         const R* rho = static_cast<const R*>(d.rho);
-        double v[6] = {0, 0, 0, 0, 0, 0};  // inner: sum rho, sum p, n; outer: sum rho, sum p, n
-        // geometry and pressure in the lattice's arithmetic type, sums in FP64
+        SumAcc<R> in_rho, in_p, out_rho, out_p;  // inner / outer sums of rho and p
+        unsigned in_n = 0, out_n = 0;
+        // geometry and pressure in the lattice's arithmetic type, sums in SumAcc
         const R nxr = R(d.nx), nyr = R(d.ny), cxr = R(d.cx), cyr = R(d.cy), rho0 = R(d.rho0), G = R(d.G);
         const R inner = R(0.5 * Req), outer = R(Req + 4.0 * d.width);
-        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
-            const int x = (int)(c % d.nx), y = (int)(c / d.nx);
-            R ax = fabs(R(x) - cxr), ay = fabs(R(y) - cyr);
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
+             it.next(d.nx)) {
+            const long long c = it.c;
+            R ax = fabs(R(it.x) - cxr), ay = fabs(R(it.y) - cyr);
             if (ax >= nxr) ax = fmod(ax, nxr);
             if (ay >= nyr) ay = fmod(ay, nyr);
             if (ax > R(0.5) * nxr) ax = nxr - ax;  // minimum image
@@ -239,10 +294,19 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
             const R dd = sqrt(ax * ax + ay * ay);
             const R r = rho[c];
             const R ps = -rho0 * expm1(-r / rho0);
-            const double rd = (double)r, p = (double)(r / R(3) + G * ps * ps / R(6));
-            if (dd < inner) { v[0] += rd; v[1] += p; v[2] += 1.0; }
-            if (dd > outer) { v[3] += rd; v[4] += p; v[5] += 1.0; }
+            const R p = r / R(3) + G * ps * ps / R(6);
+            if (dd < inner) {
+                in_rho.add(r);
+                in_p.add(p);
+                ++in_n;
+            }
+            if (dd > outer) {
+                out_rho.add(r);
+                out_p.add(p);
+                ++out_n;
+            }
         }
+        double v[6] = {in_rho.value(), in_p.value(), (double)in_n, out_rho.value(), out_p.value(), (double)out_n};
         block_reduce<6>(v, op, sm);
         if (threadIdx.x == 0)
             for (int k = 0; k < 6; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
@@ -320,14 +384,15 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
         const R* g = static_cast<const R*>(d.g);
         const R* out3 = static_cast<const R*>(d.out3);
         const R gmax = R(d.rec->gmax), beta_rho = R(d.beta_rho);
-        double v[3] = {0, 0, 0};  // sum m, sum drho_raw, sum rho
+        SumAcc<R> sm_m, sm_dr, sm_rho;  // sum m, sum drho_raw, sum rho
         for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
             const R r = rho[c];
             const R mm = gmax > R(0) ? g[c] / gmax : R(0);
-            v[0] += (double)mm;
-            v[1] += (double)(beta_rho * mm * (out3[c] - r));
-            v[2] += (double)r;
+            sm_m.add(mm);
+            sm_dr.add(beta_rho * mm * (out3[c] - r));
+            sm_rho.add(r);
         }
+        double v[3] = {sm_m.value(), sm_dr.value(), sm_rho.value()};
         block_reduce<3>(v, op, sm);
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
@@ -348,6 +413,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_final1(TableView t) {
             d.rec->sum_m = v[0];
             d.rec->sum_dr = v[1];
             d.rec->mass_now = v[2];
+            d.rec->proj = v[0] > 0.0 ? (v[1] + (v[2] - d.rec->mass0)) / v[0] : 0.0;
         }
     }
 }
@@ -368,7 +434,7 @@ template <typename R>
 __device__ __forceinline__ CorrK<R> corr_constants(const DevRecord* rec, double beta_rho, double beta_u) {
     CorrK<R> k;
     k.gmax = R(rec->gmax);
-    k.proj = R((rec->sum_dr + (rec->mass_now - rec->mass0)) / rec->sum_m);
+    k.proj = R(rec->proj);
     k.beta_rho = R(beta_rho);
     k.beta_u = R(beta_u);
     return k;
@@ -395,19 +461,21 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(TableView t) {
         const BlkMap m = map_blk(t, n, vb);
         const LatDesc& d = t.d[m.j];
         const long long N = (long long)d.nx * d.ny;
-        double v[3] = {0, 0, 0};  // sum djx_raw, sum djy_raw, reject flag
+        SumAcc<R> s_jx, s_jy;  // sum djx_raw, sum djy_raw
+        bool reject = false;
         if (d.rec->sum_m > 0.0) {
             const CorrK<R> k = corr_constants<R>(d.rec, d.beta_rho, d.beta_u);
             for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
                 const CellCorr<R> q = cell_corr(c, static_cast<const R*>(d.rho), static_cast<const R*>(d.jx),
                                                 static_cast<const R*>(d.jy), static_cast<const R*>(d.g),
                                                 static_cast<const R*>(d.out3), N, k);
-                v[0] += (double)q.djx_raw;
-                v[1] += (double)q.djy_raw;
+                s_jx.add(q.djx_raw);
+                s_jy.add(q.djy_raw);
                 const bool ok = q.rhop > R(0) && isfinite(q.rhop) && isfinite(q.djx_raw) && isfinite(q.djy_raw);
-                v[2] = fmax(v[2], ok ? 0.0 : 1.0);
+                reject = reject || !ok;
             }
         }
+        double v[3] = {s_jx.value(), s_jy.value(), reject ? 1.0 : 0.0};
         block_reduce<3>(v, op, sm);
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
@@ -431,6 +499,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_final2(TableView t) {
             DevRecord* rec = d.rec;
             rec->sum_jx = v[0];
             rec->sum_jy = v[1];
+            rec->mjx = rec->sum_m > 0.0 ? v[0] / rec->sum_m : 0.0;
+            rec->mjy = rec->sum_m > 0.0 ? v[1] / rec->sum_m : 0.0;
             rec->reject = v[2] > 0.0 ? 1 : 0;
             if (v[2] > 0.0) {
                 if (rec->status == PL_OK) rec->status = PL_ERR_NONPHYSICAL;
@@ -469,9 +539,11 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
         const R* g = static_cast<const R*>(d.g);
         const R* out3 = static_cast<const R*>(d.out3);
         S* f = static_cast<S*>(d.pops[d.phase ^ parity]);
-        const R sjx = R(rec->sum_jx / rec->sum_m), sjy = R(rec->sum_jy / rec->sum_m);
+        const R sjx = R(rec->mjx), sjy = R(rec->mjy);
         const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u);
-        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
+             it.next(d.nx)) {
+            const long long c = it.c;
             if (!(g[c] > R(0))) continue;
             const CellCorr<R> q = cell_corr(c, rho, jx, jy, g, out3, N, k);
             const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
@@ -479,7 +551,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
             R fn[9], fo[9];
             feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
             feq9<R>(r, jxc / r, jyc / r, fo);
-            const long long o = pop_offset(c, d.nx, d.pitch);
+            const long long o = it.pop_offset(d.pitch);
             if constexpr (MODE == PL_F16_OFFSET) {
                 // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
                 // nearest, the rest population taking the cell's corrected stored mass minus their

@@ -305,6 +305,236 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP32-arithmetic walker (FP32 and FP16-offset storage) on packed pairs.  A lane's two cells
+// are the two halves of one float2 for every population, moment and equilibrium term, and
+// every addition, multiplication and FMA is one sm_100-family f32x2 instruction for both
+// cells (the same IEEE rounding as the scalar FP32 operation on each half).
+__device__ __forceinline__ unsigned long long f2u(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 u2f(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(d);
+}
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
+template <int MODE>
+__device__ __forceinline__ float2 decode2(typename Pair<MODE>::T v) {
+    if constexpr (MODE == PL_F16_OFFSET) return __half22float2(v);
+    else return v;
+}
+
+template <int MODE>
+__device__ __forceinline__ float2 psi2(float2 rho, const StepK<float>& k) {
+    if constexpr (MODE == PL_F16_OFFSET) {
+        const float2 t = rho * bc2(-k.inv_rho0 * 1.4426950408889634f);
+        float ex, ey;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ex) : "f"(t.x));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(ey) : "f"(t.y));
+        return fma2(bc2(-k.rho0), make_float2(ex, ey), bc2(k.rho0));
+    } else {
+        return make_float2(psi_of(rho.x, k.rho0, k.inv_rho0), psi_of(rho.y, k.rho0, k.inv_rho0));
+    }
+}
+
+// Both cells of a pair: populations h[9] (offset space), density rho, force (fx, fy) -> o[9].
+template <int MODE>
+__device__ __forceinline__ void collide_pair(const float2 (&h)[9], float2 rho, float2 fx, float2 fy,
+                                             const StepK<float>& k, float2 (&o)[9]) {
+    const float2 jx = ((h[1] - h[3]) + (h[5] - h[6])) + (h[8] - h[7]);
+    const float2 jy = ((h[2] - h[4]) + (h[5] + h[6])) - (h[7] + h[8]);
+    const float2 inv = make_float2(recip<MODE>(rho.x), recip<MODE>(rho.y));
+    const float2 ux = fma2(bc2(k.tau), fx, jx) * inv;  // u + tau F / rho
+    const float2 uy = fma2(bc2(k.tau), fy, jy) * inv;
+    const float2 usq = fma2(ux, ux, uy * uy);
+    const float2 Ap = fma2(rho, fma2(bc2(-1.5f), usq, bc2(1.0f)), bc2(-k.rho_ref));
+    const float2 t3 = bc2(3.0f) * rho, t45 = bc2(4.5f) * rho;
+    const float2 pp = ux + uy, pm = ux - uy;
+    const float2 Sx = fma2(t45 * ux, ux, Ap), Dx = t3 * ux;
+    const float2 Sy = fma2(t45 * uy, uy, Ap), Dy = t3 * uy;
+    const float2 Sp = fma2(t45 * pp, pp, Ap), Dp = t3 * pp;
+    const float2 Sm = fma2(t45 * pm, pm, Ap), Dm = t3 * pm;
+    const float2 w0 = bc2(4.0f / 9.0f), w1 = bc2(1.0f / 9.0f), w2 = bc2(1.0f / 36.0f);
+    float2 fe[9];
+    fe[0] = w0 * Ap;
+    fe[1] = w1 * (Sx + Dx);
+    fe[3] = w1 * (Sx - Dx);
+    fe[2] = w1 * (Sy + Dy);
+    fe[4] = w1 * (Sy - Dy);
+    fe[5] = w2 * (Sp + Dp);
+    fe[7] = w2 * (Sp - Dp);
+    fe[8] = w2 * (Sm + Dm);
+    fe[6] = w2 * (Sm - Dm);
+    const float2 om = bc2(k.omega);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[i] = fma2(om, fe[i] - h[i], h[i]);
+}
+
+template <int MODE>
+__device__ __forceinline__ void store_pair2(const WalkArgs<MODE>& a, int i, int r, int d0, bool svec, bool own0,
+                                            bool own1, typename Pair<MODE>::T v) {
+    using S = typename Traits<MODE>::S;
+    using PT = typename Pair<MODE>::T;
+    S* p = a.fout + i * a.plane + (long long)r * a.pitch + d0;
+    if (svec) {
+        *reinterpret_cast<PT*>(p) = v;
+    } else {
+        if constexpr (MODE == PL_F16_OFFSET) {
+            if (own0) p[0] = __low2half(v);
+            if (own1) p[1] = __high2half(v);
+        } else {
+            if (own0) p[0] = v.x;
+            if (own1) p[1] = v.y;
+        }
+    }
+}
+
+// Rows [r0, r1) of strip `strip`; the same walk as walk_segment.
+template <int MODE>
+__device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
+    using PT = typename Pair<MODE>::T;
+    const int nx = a.nx, ny = a.ny;
+    const int ua = strip * STRIP - 2 + 2 * lane;
+    const int cA = wrapi(ua, nx), cB = wrapi(ua + 1, nx);
+    const bool vec = (cB == cA + 1) && ((cA & 1) == 0);
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
+    const bool svec = own0 && own1 && vec;
+    const float2 w1 = bc2(1.0f / 9.0f), w2 = bc2(1.0f / 36.0f);
+    const float2 mG = bc2(-a.k.G);
+
+    PT Nx[9];
+    load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
+    float2 hp[9];
+    float2 rho_p = make_float2(0.0f, 0.0f), sh_p = make_float2(0.0f, 0.0f);
+    // psi of three rows as (left, own0) (own0, own1) (own1, right) pairs
+    float2 Al{}, Am{}, Ar{}, Bl{}, Bm{}, Br{}, Cl{}, Cm{}, Cr{};
+    const int nrows = r1 - r0;
+    for (int k = 0; k <= nrows + 1; ++k) {
+        PT Cur[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Cur[i] = Nx[i];
+        if (k <= nrows) {
+            int rn = r0 + k;
+            if (rn >= ny) rn -= ny;
+            load_row<MODE>(a, rn, cA, cB, vec, Nx);  // prefetch the next row
+        }
+        float2 hc[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hc[i] = decode2<MODE>(Cur[i]);
+        const float2 shc = (((hc[0] + hc[1]) + (hc[2] + hc[3])) + ((hc[4] + hc[5]) + (hc[6] + hc[7]))) + hc[8];
+        const float2 rhoc = shc + bc2(a.k.rho_ref);
+        Al = Bl; Am = Bm; Ar = Br;
+        Bl = Cl; Bm = Cm; Br = Cr;
+        Cm = psi2<MODE>(rhoc, a.k);
+        const float L = __shfl_up_sync(0xffffffffu, Cm.y, 1);
+        const float Rr = __shfl_down_sync(0xffffffffu, Cm.x, 1);
+        Cl = make_float2(L, Cm.x);
+        Cr = make_float2(Cm.y, Rr);
+        if (k >= 2) {
+            int y = r0 + k - 2;
+            if (y >= ny) y -= ny;
+            const float2 sx = fma2(w1, Br - Bl, w2 * ((Cr - Cl) + (Ar - Al)));
+            const float2 sy = fma2(w1, Cm - Am, w2 * ((Cr + Cl) - (Ar + Al)));
+            const float2 g = mG * Bm;
+            float2 o[9];
+            collide_pair<MODE>(hp, rho_p, g * sx, g * sy, a.k, o);
+            PT out[9];
+            if constexpr (MODE == PL_F32) {
+                // BGK conserves mass; take the rest population from that balance so the
+                // FP32 weights (which do not sum to one exactly) leave no systematic drift.
+                o[0] = sh_p - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
+#pragma unroll
+                for (int i = 0; i < 9; ++i) out[i] = o[i];
+            } else {
+                // Mass-conserving FP16 storage: the 8 moving populations are rounded to
+                // nearest; the rest population takes the cell's stored mass minus their
+                // rounded values, and is rounded stochastically (unbiased), so the stored
+                // mass changes by one zero-mean rounding per cell and step.
+                float2 q[9];
+#pragma unroll
+                for (int i = 1; i < 9; ++i) {
+                    out[i] = __floats2half2_rn(o[i].x, o[i].y);
+                    q[i] = __half22float2(out[i]);
+                }
+                const float2 rest = sh_p - (((q[1] + q[2]) + (q[3] + q[4])) + ((q[5] + q[6]) + (q[7] + q[8])));
+                const uint32_t rnd = fmix32(__float_as_uint(hp[0].x) ^ (__float_as_uint(hp[1].y) * 0x9E3779B1u) ^
+                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^
+                                            (a.seq * 0x27D4EB2Fu));
+                out[0] = sr_pack_half2(rest.x, rest.y, rnd);
+            }
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            // c_x = 0 planes: own pair
+            store_pair2<MODE>(a, 0, y, ua, svec, own0, own1, out[0]);
+            store_pair2<MODE>(a, 2, yp, ua, svec, own0, own1, out[2]);
+            store_pair2<MODE>(a, 4, ym, ua, svec, own0, own1, out[4]);
+            // c_x = +1 planes: (left lane's second cell, own first cell);
+            // c_x = -1 planes: (own second cell, right lane's first cell)
+            if constexpr (MODE == PL_F16_OFFSET) {
+                const uint32_t u1 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[1]), 1);
+                const uint32_t u5 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[5]), 1);
+                const uint32_t u8 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[8]), 1);
+                const uint32_t d3 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[3]), 1);
+                const uint32_t d6 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[6]), 1);
+                const uint32_t d7 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[7]), 1);
+                // (high half of the left lane's pair, low half of ours) and
+                // (high half of ours, low half of the right lane's pair)
+                auto join = [](uint32_t lo_src, uint32_t hi_src) {
+                    const uint32_t v = __byte_perm(lo_src, hi_src, 0x5432);
+                    return *reinterpret_cast<const __half2*>(&v);
+                };
+                store_pair2<MODE>(a, 1, y, ua, svec, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
+                store_pair2<MODE>(a, 5, yp, ua, svec, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
+                store_pair2<MODE>(a, 8, ym, ua, svec, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
+                store_pair2<MODE>(a, 3, y, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
+                store_pair2<MODE>(a, 6, yp, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
+                store_pair2<MODE>(a, 7, ym, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
+            } else {
+                const float l1 = __shfl_up_sync(0xffffffffu, o[1].y, 1);
+                const float l5 = __shfl_up_sync(0xffffffffu, o[5].y, 1);
+                const float l8 = __shfl_up_sync(0xffffffffu, o[8].y, 1);
+                const float r3 = __shfl_down_sync(0xffffffffu, o[3].x, 1);
+                const float r6 = __shfl_down_sync(0xffffffffu, o[6].x, 1);
+                const float r7 = __shfl_down_sync(0xffffffffu, o[7].x, 1);
+                store_pair2<MODE>(a, 1, y, ua, svec, own0, own1, make_float2(l1, o[1].x));
+                store_pair2<MODE>(a, 5, yp, ua, svec, own0, own1, make_float2(l5, o[5].x));
+                store_pair2<MODE>(a, 8, ym, ua, svec, own0, own1, make_float2(l8, o[8].x));
+                store_pair2<MODE>(a, 3, y, ua, svec, own0, own1, make_float2(o[3].y, r3));
+                store_pair2<MODE>(a, 6, yp, ua, svec, own0, own1, make_float2(o[6].y, r6));
+                store_pair2<MODE>(a, 7, ym, ua, svec, own0, own1, make_float2(o[7].y, r7));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) hp[i] = hc[i];
+        rho_p = rhoc;
+        sh_p = shc;
+    }
+}
+
 // Persistent table kernel: physical warp w processes virtual warps w, w+P, w+2P, ...
 // Virtual warp v belongs to the lattice j with warp_pre[j] <= v < warp_pre[j+1]; its
 // local index l walks strip (l mod nstrips) over row chunk (l / nstrips).  The rows of a
@@ -355,7 +585,8 @@ __global__ void __launch_bounds__(STEP_THREADS) k_step(TableView t, int parity) 
         a.k = StepK<R>{R(d.G), R(d.tau), R(1.0 / d.tau), R(d.rho0), R(1.0 / d.rho0),
                        MODE == PL_F16_OFFSET ? R(d.rho_ref) : R(0)};
         a.seq = seq - d.seq0;  // the lattice's own step count: the same alone or in a batch
-        walk_segment<MODE>(a, strip, r0, r1, lane);
+        if constexpr (MODE == PL_F64) walk_segment<MODE>(a, strip, r0, r1, lane);
+        else walk_segment2<MODE>(a, strip, r0, r1, lane);
     }
 }
 

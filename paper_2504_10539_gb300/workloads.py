@@ -119,11 +119,20 @@ def field_4096(storage: int = F16_OFFSET, seed: int = 3, side: int = 4096, n_dro
                    seed=seed, steps=5000, K=100, mlp=MLP_BF16, weight_seed=10 + seed)
 
 
+# Stability of the scheme for a droplet started at 2.0 / 0.15 (the batch's initial state):
+# smallest tau (step 0.05) at which FP64 oracle runs of 2000 steps on 256x256, with one
+# centred droplet of radius 0.1 and 0.35 of the side, kept every density positive and
+# finite.  Small droplets are the less stable ones: G = -5 -> 0.65, -5.25 -> 0.8, -5.5 ->
+# 0.85, -5.75 -> 0.9, -6 -> 0.95 (large droplets: 0.6, 0.7, 0.8, 0.85, 0.9).  Below it the
+# relaxation transient drives the vapour density negative within a few hundred steps.
+TAU_STABLE_G = (5.0, 5.25, 5.5, 5.75, 6.0)          # -G
+TAU_STABLE_MIN = (0.70, 0.85, 0.90, 0.95, 1.00)     # the small-droplet bound + 0.05
+
+
 def tau_min_stable(G: float) -> float:
-    """Smallest tau at which a droplet started at 2.0 / 0.15 stays positive, as found by
-    FP64 oracle runs on 64x64 (G = -5 -> 0.6, -5.25 -> 0.7, -5.5 -> 0.8, -5.75 and -6 -> 0.9);
-    the line 0.6 + 0.4 (-G - 5) bounds those points from above."""
-    return 0.6 + 0.4 * max(0.0, -G - 5.0)
+    """Smallest tau used for coupling strength G: the measured bound above plus a 0.05
+    margin, interpolated linearly in G."""
+    return float(np.interp(-G, TAU_STABLE_G, TAU_STABLE_MIN))
 
 
 def batch_256(n: int = 256, seed: int = 4, steps: int = 2000, K: int = 100,
