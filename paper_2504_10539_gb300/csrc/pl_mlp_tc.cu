@@ -8,9 +8,12 @@
 //                           D in TMEM; epilogue tcgen05.ld -> + bias -> tanh -> BF16 -> smem
 //   layer 5 (64 -> 3)     : FP32 FMA on the FP32 tanh outputs of layer 4
 //
-// CTA = 2 warpgroups; each warpgroup runs its own 128-cell tile pipeline with its
-// own A buffers, TMEM columns and mbarrier, so one warpgroup's tanh epilogue
-// overlaps the other's MMAs.  Thread t of a warpgroup owns cell row t of the tile
+// CTA = 4 warpgroups (16 warps, all TMEM columns); each warpgroup runs its own 128-cell
+// tile pipeline with its own operand buffer, 128 TMEM columns and mbarrier, so the
+// warpgroups' tanh epilogues overlap each other's MMAs and hide each other's latencies.
+// One 32 KB operand buffer per warpgroup suffices: a layer's epilogue writes the next
+// operand only after the layer's MMA has completed (its mbarrier), i.e. after the MMA has
+// read the buffer.  Thread t of a warpgroup owns cell row t of the tile
 // (TMEM lane t: warp w of the group reads lanes 32*(w%4)..+31).  The weights are
 // loaded once per CTA by bulk async copies (the grid is persistent, one CTA per SM).
 //
@@ -33,7 +36,7 @@ namespace pl {
 namespace tc {
 
 constexpr int M = 128;           // cells per tile
-constexpr int NWG = 2;           // tile pipelines per CTA
+constexpr int NWG = 4;           // tile pipelines per CTA
 constexpr int THREADS = 128 * NWG;
 constexpr int TMEM_COLS = 128 * NWG;
 
@@ -41,8 +44,8 @@ constexpr int TMEM_COLS = 128 * NWG;
 // last; the allocation is the full 227 KB so that every address an MMA can form
 // from these bases stays inside it.
 constexpr int A_BYTES = M * 128 * 2;                 // 128 rows x 128 BF16 = 32 KB
-constexpr int OFF_A = 0;                             // per WG: X then Y
-constexpr int OFF_W2 = OFF_A + NWG * 2 * A_BYTES;    // 128 x 64  BF16 = 16 KB
+constexpr int OFF_A = 0;                             // one operand buffer per WG
+constexpr int OFF_W2 = OFF_A + NWG * A_BYTES;        // 128 x 64  BF16 = 16 KB
 constexpr int OFF_W3 = OFF_W2 + 128 * 64 * 2;        // 128 x 128 BF16 = 32 KB
 constexpr int OFF_W4 = OFF_W3 + 128 * 128 * 2;       // 64 x 128  BF16 = 16 KB
 constexpr int OFF_P = OFF_W4 + 64 * 128 * 2;         // FP32 parameters
@@ -134,20 +137,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 __device__ __forceinline__ float tanh_fast(float x) {
@@ -272,9 +272,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     bool ok = __syncthreads_and(mbar_wait(bar_w, 0)) != 0;
 
-    uint8_t* AX = sm + OFF_A + wg * 2 * A_BYTES;
-    uint8_t* AY = AX + A_BYTES;
-    const uint32_t ax = saddr(AX), ay = saddr(AY);
+    uint8_t* AX = sm + OFF_A + wg * A_BYTES;
+    const uint32_t ax = saddr(AX);
     const uint32_t d_tmem = tmem + wg * 128;                               // this WG's columns
     const uint32_t my_lane_tmem = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + wg * 128;
     uint32_t phase = 0;
@@ -297,11 +296,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         // ---- layer 1 on FMA: A1 (128 x 64) into AX
 #pragma unroll
         for (int k0 = 0; k0 < 64; k0 += 8) {
+            // parameters as 16-byte shared loads: W1 rows (o, o+1) and biases (o..o+3)
+            const float4* w4 = reinterpret_cast<const float4*>(P + P_W1 + 2 * k0);
+            const float4* b4 = reinterpret_cast<const float4*>(P + P_B1 + k0);
+            const float4 bA = b4[0], bB = b4[1];
+            const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
             float h[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int o = k0 + j;
-                h[j] = tanh_fast(fmaf(P[P_W1 + 2 * o], xh, fmaf(P[P_W1 + 2 * o + 1], yh, P[P_B1 + o])));
+            for (int j = 0; j < 8; j += 2) {
+                const float4 w = w4[j >> 1];
+                h[j] = tanh_fast(fmaf(w.x, xh, fmaf(w.y, yh, bias[j])));
+                h[j + 1] = tanh_fast(fmaf(w.z, xh, fmaf(w.w, yh, bias[j + 1])));
             }
             store8(AX, t, k0, h);
         }
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             if (t == 0) {
                 tc_after_sync();
                 if (layer == 2) issue_layer(d_tmem, ax, saddr(sm + OFF_W2), 128, 64);
-                else if (layer == 3) issue_layer(d_tmem, ay, saddr(sm + OFF_W3), 128, 128);
+                else if (layer == 3) issue_layer(d_tmem, ax, saddr(sm + OFF_W3), 128, 128);
                 else issue_layer(d_tmem, ax, saddr(sm + OFF_W4), 64, 128);
                 mma_commit(bar_mma);
             }
@@ -327,22 +332,34 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             tc_after_sync();
             const int nout = layer == 4 ? 64 : 128;
             const float* bias = P + (layer == 2 ? P_B2 : (layer == 3 ? P_B3 : P_B4));
-            uint8_t* dst = layer == 2 ? AY : AX;   // layer 3's output overwrites A1 (consumed)
+            uint8_t* dst = AX;  // the layer's MMA has completed: its operand buffer is free
 #pragma unroll 1
-            for (int c0 = 0; c0 < nout; c0 += 32) {
-                float v[32];
-                tmem_ld32(my_lane_tmem + c0, v);
+            for (int c0 = 0; c0 < nout; c0 += 16) {
+                float v[16];
+                tmem_ld16(my_lane_tmem + c0, v);
+                const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = tanh_fast(v[j] + bias[c0 + j]);
+                for (int q = 0; q < 4; ++q) {
+                    const float4 b = b4[q];
+                    v[4 * q + 0] = tanh_fast(v[4 * q + 0] + b.x);
+                    v[4 * q + 1] = tanh_fast(v[4 * q + 1] + b.y);
+                    v[4 * q + 2] = tanh_fast(v[4 * q + 2] + b.z);
+                    v[4 * q + 3] = tanh_fast(v[4 * q + 3] + b.w);
+                }
                 if (layer < 4) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
+                    for (int q = 0; q < 2; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
                 } else {
+                    const float4* u0 = reinterpret_cast<const float4*>(P + P_W5 + 0 * 64 + c0);
+                    const float4* u1 = reinterpret_cast<const float4*>(P + P_W5 + 1 * 64 + c0);
+                    const float4* u2 = reinterpret_cast<const float4*>(P + P_W5 + 2 * 64 + c0);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        o0 = fmaf(P[P_W5 + 0 * 64 + c0 + j], v[j], o0);
-                        o1 = fmaf(P[P_W5 + 1 * 64 + c0 + j], v[j], o1);
-                        o2 = fmaf(P[P_W5 + 2 * 64 + c0 + j], v[j], o2);
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 a0 = u0[q], a1 = u1[q], a2 = u2[q];
+                        const float* v4 = v + 4 * q;
+                        o0 = fmaf(a0.w, v4[3], fmaf(a0.z, v4[2], fmaf(a0.y, v4[1], fmaf(a0.x, v4[0], o0))));
+                        o1 = fmaf(a1.w, v4[3], fmaf(a1.z, v4[2], fmaf(a1.y, v4[1], fmaf(a1.x, v4[0], o1))));
+                        o2 = fmaf(a2.w, v4[3], fmaf(a2.z, v4[2], fmaf(a2.y, v4[1], fmaf(a2.x, v4[0], o2))));
                     }
                 }
             }
