@@ -394,14 +394,16 @@ __device__ __forceinline__ void collide_pair(const float2 (&h)[9], float2 rho, f
     for (int i = 0; i < 9; ++i) o[i] = fma2(om, fe[i] - h[i], h[i]);
 }
 
+// Store of a lane's pair.  `split` lanes (a pair that wraps around the lattice edge, is
+// not 2-element aligned, or owns one cell only) store element by element; every other lane
+// owns both cells or neither, so the warp takes one branch and the vector store is
+// predicated by ownership (the halo lanes 0 and 31 own nothing).
 template <int MODE>
-__device__ __forceinline__ void store_pair2(const WalkArgs<MODE>& a, int i, int r, int d0, bool svec, bool own0,
-                                            bool own1, typename Pair<MODE>::T v) {
-    using S = typename Traits<MODE>::S;
+__device__ __forceinline__ void store_pair2(typename Traits<MODE>::S* p, bool split, bool own0, bool own1,
+                                            typename Pair<MODE>::T v) {
     using PT = typename Pair<MODE>::T;
-    S* p = a.fout + i * a.plane + (long long)r * a.pitch + d0;
-    if (svec) {
-        *reinterpret_cast<PT*>(p) = v;
+    if (!split) {
+        if (own0) *reinterpret_cast<PT*>(p) = v;
     } else {
         if constexpr (MODE == PL_F16_OFFSET) {
             if (own0) p[0] = __low2half(v);
@@ -423,16 +425,14 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
     const bool vec = (cB == cA + 1) && ((cA & 1) == 0);
     const bool mid = lane >= 1 && lane <= 30;
     const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
-    const bool svec = own0 && own1 && vec;
-    const float2 w1 = bc2(1.0f / 9.0f), w2 = bc2(1.0f / 36.0f);
-    const float2 mG = bc2(-a.k.G);
+    const bool split = !(vec && own0 == own1);
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
 
     PT Nx[9];
     load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
-    float2 hp[9];
+    float2 hp[9];  // previous row (to be relaxed), decoded
     float2 rho_p = make_float2(0.0f, 0.0f), sh_p = make_float2(0.0f, 0.0f);
-    // psi of three rows as (left, own0) (own0, own1) (own1, right) pairs
-    float2 Al{}, Am{}, Ar{}, Bl{}, Bm{}, Br{}, Cl{}, Cm{}, Cr{};
+    PsiRow<float> A{}, B{}, C{};
     const int nrows = r1 - r0;
     for (int k = 0; k <= nrows + 1; ++k) {
         PT Cur[9];
@@ -448,21 +448,24 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
         for (int i = 0; i < 9; ++i) hc[i] = decode2<MODE>(Cur[i]);
         const float2 shc = (((hc[0] + hc[1]) + (hc[2] + hc[3])) + ((hc[4] + hc[5]) + (hc[6] + hc[7]))) + hc[8];
         const float2 rhoc = shc + bc2(a.k.rho_ref);
-        Al = Bl; Am = Bm; Ar = Br;
-        Bl = Cl; Bm = Cm; Br = Cr;
-        Cm = psi2<MODE>(rhoc, a.k);
-        const float L = __shfl_up_sync(0xffffffffu, Cm.y, 1);
-        const float Rr = __shfl_down_sync(0xffffffffu, Cm.x, 1);
-        Cl = make_float2(L, Cm.x);
-        Cr = make_float2(Cm.y, Rr);
+        A = B;
+        B = C;
+        const float2 ps = psi2<MODE>(rhoc, a.k);
+        C.a = ps.x;
+        C.b = ps.y;
+        C.L = __shfl_up_sync(0xffffffffu, C.b, 1);
+        C.Rr = __shfl_down_sync(0xffffffffu, C.a, 1);
         if (k >= 2) {
             int y = r0 + k - 2;
             if (y >= ny) y -= ny;
-            const float2 sx = fma2(w1, Br - Bl, w2 * ((Cr - Cl) + (Ar - Al)));
-            const float2 sy = fma2(w1, Cm - Am, w2 * ((Cr + Cl) - (Ar + Al)));
-            const float2 g = mG * Bm;
+            // Shan-Chen force of both cells from the 3x3 psi stencil (rows A = y-1, B = y, C = y+1)
+            const float sx0 = w1 * (B.b - B.L) + w2 * ((C.b - C.L) + (A.b - A.L));
+            const float sy0 = w1 * (C.a - A.a) + w2 * ((C.b + C.L) - (A.b + A.L));
+            const float sx1 = w1 * (B.Rr - B.a) + w2 * ((C.Rr - C.a) + (A.Rr - A.a));
+            const float sy1 = w1 * (C.b - A.b) + w2 * ((C.Rr + C.a) - (A.Rr + A.a));
+            const float g0 = -a.k.G * B.a, g1 = -a.k.G * B.b;
             float2 o[9];
-            collide_pair<MODE>(hp, rho_p, g * sx, g * sy, a.k, o);
+            collide_pair<MODE>(hp, rho_p, make_float2(g0 * sx0, g1 * sx1), make_float2(g0 * sy0, g1 * sy1), a.k, o);
             PT out[9];
             if constexpr (MODE == PL_F32) {
                 // BGK conserves mass; take the rest population from that balance so the
@@ -482,16 +485,16 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
                     q[i] = __half22float2(out[i]);
                 }
                 const float2 rest = sh_p - (((q[1] + q[2]) + (q[3] + q[4])) + ((q[5] + q[6]) + (q[7] + q[8])));
-                const uint32_t rnd = fmix32(__float_as_uint(hp[0].x) ^ (__float_as_uint(hp[1].y) * 0x9E3779B1u) ^
-                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^
-                                            (a.seq * 0x27D4EB2Fu));
+                // dither: a hash of the cell pair's position and the lattice's step count
+                const uint32_t rnd =
+                    fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
                 out[0] = sr_pack_half2(rest.x, rest.y, rnd);
             }
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             // c_x = 0 planes: own pair
-            store_pair2<MODE>(a, 0, y, ua, svec, own0, own1, out[0]);
-            store_pair2<MODE>(a, 2, yp, ua, svec, own0, own1, out[2]);
-            store_pair2<MODE>(a, 4, ym, ua, svec, own0, own1, out[4]);
+            store_pair2<MODE>(a.fout + 0 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, out[0]);
+            store_pair2<MODE>(a.fout + 2 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, out[2]);
+            store_pair2<MODE>(a.fout + 4 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, out[4]);
             // c_x = +1 planes: (left lane's second cell, own first cell);
             // c_x = -1 planes: (own second cell, right lane's first cell)
             if constexpr (MODE == PL_F16_OFFSET) {
@@ -507,12 +510,12 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
                     const uint32_t v = __byte_perm(lo_src, hi_src, 0x5432);
                     return *reinterpret_cast<const __half2*>(&v);
                 };
-                store_pair2<MODE>(a, 1, y, ua, svec, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
-                store_pair2<MODE>(a, 5, yp, ua, svec, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
-                store_pair2<MODE>(a, 8, ym, ua, svec, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
-                store_pair2<MODE>(a, 3, y, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
-                store_pair2<MODE>(a, 6, yp, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
-                store_pair2<MODE>(a, 7, ym, ua, svec, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
+                store_pair2<MODE>(a.fout + 1 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
+                store_pair2<MODE>(a.fout + 5 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
+                store_pair2<MODE>(a.fout + 8 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
+                store_pair2<MODE>(a.fout + 3 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
+                store_pair2<MODE>(a.fout + 6 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
+                store_pair2<MODE>(a.fout + 7 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
             } else {
                 const float l1 = __shfl_up_sync(0xffffffffu, o[1].y, 1);
                 const float l5 = __shfl_up_sync(0xffffffffu, o[5].y, 1);
@@ -520,12 +523,12 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
                 const float r3 = __shfl_down_sync(0xffffffffu, o[3].x, 1);
                 const float r6 = __shfl_down_sync(0xffffffffu, o[6].x, 1);
                 const float r7 = __shfl_down_sync(0xffffffffu, o[7].x, 1);
-                store_pair2<MODE>(a, 1, y, ua, svec, own0, own1, make_float2(l1, o[1].x));
-                store_pair2<MODE>(a, 5, yp, ua, svec, own0, own1, make_float2(l5, o[5].x));
-                store_pair2<MODE>(a, 8, ym, ua, svec, own0, own1, make_float2(l8, o[8].x));
-                store_pair2<MODE>(a, 3, y, ua, svec, own0, own1, make_float2(o[3].y, r3));
-                store_pair2<MODE>(a, 6, yp, ua, svec, own0, own1, make_float2(o[6].y, r6));
-                store_pair2<MODE>(a, 7, ym, ua, svec, own0, own1, make_float2(o[7].y, r7));
+                store_pair2<MODE>(a.fout + 1 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, make_float2(l1, o[1].x));
+                store_pair2<MODE>(a.fout + 5 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, make_float2(l5, o[5].x));
+                store_pair2<MODE>(a.fout + 8 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, make_float2(l8, o[8].x));
+                store_pair2<MODE>(a.fout + 3 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, make_float2(o[3].y, r3));
+                store_pair2<MODE>(a.fout + 6 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, make_float2(o[6].y, r6));
+                store_pair2<MODE>(a.fout + 7 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, make_float2(o[7].y, r7));
             }
         }
 #pragma unroll
