@@ -415,17 +415,19 @@ __device__ __forceinline__ void store_pair2(typename Traits<MODE>::S* p, bool sp
     }
 }
 
-// Rows [r0, r1) of strip `strip`; the same walk as walk_segment.
-template <int MODE>
-__device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
+// Rows [r0, r1) of strip `strip`; the same walk as walk_segment.  FAST: every lane's pair
+// is an aligned vector and owns both of its cells or neither (all strips but a ragged last
+// one), so loads and stores need no element-wise path.
+template <int MODE, bool FAST>
+__device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
     using PT = typename Pair<MODE>::T;
     const int nx = a.nx, ny = a.ny;
     const int ua = strip * STRIP - 2 + 2 * lane;
     const int cA = wrapi(ua, nx), cB = wrapi(ua + 1, nx);
-    const bool vec = (cB == cA + 1) && ((cA & 1) == 0);
+    const bool vec = FAST || ((cB == cA + 1) && ((cA & 1) == 0));
     const bool mid = lane >= 1 && lane <= 30;
     const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
-    const bool split = !(vec && own0 == own1);
+    const bool split = !FAST && !(vec && own0 == own1);
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
 
     PT Nx[9];
@@ -536,6 +538,18 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
         rho_p = rhoc;
         sh_p = shc;
     }
+}
+
+template <int MODE>
+__device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
+    const int ua = strip * STRIP - 2 + 2 * lane;
+    const int cA = wrapi(ua, a.nx), cB = wrapi(ua + 1, a.nx);
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool fast = (cB == cA + 1) && ((cA & 1) == 0) && (!mid || ua + 1 < a.nx);
+    // (FP32 storage is bound by HBM, not by issue: it keeps one copy of the walk and its
+    // register count, and with it four blocks per SM)
+    if (MODE == PL_F16_OFFSET && __all_sync(0xffffffffu, fast)) walk_impl2<MODE, true>(a, strip, r0, r1, lane);
+    else walk_impl2<MODE, false>(a, strip, r0, r1, lane);
 }
 
 // Persistent table kernel: physical warp w processes virtual warps w, w+P, w+2P, ...
