@@ -115,6 +115,7 @@ struct DevRecord {
     double mass0;        // M0
     double sum_m, sum_dr, sum_jx, sum_jy, mass_now;
     double proj, mjx, mjy;  // per-lattice constants of the apply pass (formed once, in FP64)
+    long long fix_n;        // FP16 mass restoration: signed number of rest populations shifted by one unit
     int status;          // sticky PL_ERR_* detected on the device
     int reject;          // set by the correction check pass, cleared per correction
     int applied;         // corrections applied

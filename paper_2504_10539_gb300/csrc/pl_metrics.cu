@@ -582,6 +582,128 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP16-offset storage: mass restoration after a correction (a storage measure of this
+// implementation; the paper has no reduced-precision storage).  The projection returns the
+// mass to M0 in exact arithmetic, but the apply pass stores each corrected rest population
+// with one stochastic rounding, which leaves the stored mass off by a zero-mean sum of about
+// ulp * sqrt(cells).  Shifting the stored rest population h_0 of n cells by one FP16 unit
+// u = 2^-12 is exact when 1/4 + u <= |h_0| <= 1/2 - u (the value stays in the binade
+// [1/4, 1/2], whose spacing is u), so n = round((M - M0) / u) such shifts restore the mass to
+// within u/2.  The n cells are the first candidates in a fixed order: by reduction block,
+// within a block by thread, within a thread by loop index; the result is deterministic and
+// the same for a lattice alone or in a batch.
+
+constexpr float FIX_U = 1.0f / 4096.0f;
+
+__device__ __forceinline__ bool fix_candidate(__half h) {
+    const float a = fabsf(__half2float(h));
+    return a >= 0.25f + FIX_U && a <= 0.5f - FIX_U;
+}
+
+__device__ __forceinline__ bool fix_active(const DevRecord* rec) { return !rec->reject && rec->sum_m > 0.0; }
+
+// Pass 1: stored sum of the offsets (per cell in FP32 - nine FP16 offsets below 2 in
+// magnitude sum there to within 2^-24, far below u - then error-free pair sums over cells)
+// and the candidates, per block.
+__global__ void __launch_bounds__(RB_THREADS) k_fix_scan(TableView t, int parity) {
+    __shared__ double sm[2 * 32];
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    const int op[2] = {0, 0};
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        if (!fix_active(d.rec)) continue;
+        const __half* f = static_cast<const __half*>(d.pops[d.phase ^ parity]);
+        const long long N = (long long)d.nx * d.ny;
+        SumAcc<float> sh;
+        unsigned cand = 0;
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
+             it.next(d.nx)) {
+            const long long o = it.pop_offset(d.pitch);
+            float s = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) s += __half2float(f[i * d.plane + o]);
+            sh.add(s);
+            cand += fix_candidate(f[o]) ? 1u : 0u;
+        }
+        double v[2] = {sh.value(), (double)cand};
+        block_reduce<2>(v, op, sm);
+        if (threadIdx.x == 0) {
+            d.partials[m.lb * PARTIAL_STRIDE + 0] = v[0];
+            d.partials[m.lb * PARTIAL_STRIDE + 1] = v[1];
+        }
+    }
+}
+
+// Pass 2, one thread per lattice: stored mass M = sum h + N rho_ref, n = round((M - M0)/u)
+// (limited by the candidates available), and each block's first candidate index.
+__global__ void k_fix_final(TableView t) {
+    const int n = t.hdr->n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const LatDesc& d = t.d[j];
+        DevRecord* rec = d.rec;
+        rec->fix_n = 0;
+        if (!fix_active(rec)) continue;
+        double sum_h = 0.0, cand = 0.0;
+        for (int b = 0; b < d.red_blocks; ++b) {
+            sum_h += d.partials[b * PARTIAL_STRIDE + 0];
+            d.partials[b * PARTIAL_STRIDE + 2] = cand;  // candidates before block b
+            cand += d.partials[b * PARTIAL_STRIDE + 1];
+        }
+        const double M = sum_h + (double)d.nx * (double)d.ny * d.rho_ref;
+        long long k = llrint((M - rec->mass0) / (double)FIX_U);
+        const long long c = (long long)cand;
+        if (k > c) k = c;
+        if (k < -c) k = -c;
+        rec->fix_n = k;
+    }
+}
+
+// Pass 3: shift the chosen rest populations by -sign(n) u.
+__global__ void __launch_bounds__(RB_THREADS) k_fix_apply(TableView t, int parity) {
+    __shared__ unsigned scan[RB_THREADS];
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        const long long k = d.rec->fix_n;
+        if (k == 0 || !fix_active(d.rec)) continue;
+        const long long kk = k < 0 ? -k : k;
+        const long long before = (long long)d.partials[m.lb * PARTIAL_STRIDE + 2];
+        const long long mine = (long long)d.partials[m.lb * PARTIAL_STRIDE + 1];
+        long long quota = kk - before;
+        if (quota <= 0) continue;                   // uniform over the block
+        if (quota > mine) quota = mine;
+        __half* f = static_cast<__half*>(d.pops[d.phase ^ parity]);
+        const long long N = (long long)d.nx * d.ny;
+        const long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x, stride = (long long)d.red_blocks * RB_THREADS;
+        unsigned cnt = 0;
+        for (CellIt it(c0, stride, d.nx); it.c < N; it.next(d.nx)) cnt += fix_candidate(f[it.pop_offset(d.pitch)]) ? 1u : 0u;
+        // exclusive scan of the per-thread counts (Hillis-Steele in shared memory)
+        scan[threadIdx.x] = cnt;
+        __syncthreads();
+        for (int off = 1; off < RB_THREADS; off <<= 1) {
+            const unsigned add = threadIdx.x >= off ? scan[threadIdx.x - off] : 0u;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        const long long first = (long long)scan[threadIdx.x] - cnt;   // candidates of lower threads
+        __syncthreads();
+        long long take = quota - first;
+        if (take > (long long)cnt) take = cnt;
+        const float du = k > 0 ? -FIX_U : FIX_U;
+        for (CellIt it(c0, stride, d.nx); it.c < N && take > 0; it.next(d.nx)) {
+            __half* h0 = f + it.pop_offset(d.pitch);
+            if (fix_candidate(*h0)) {
+                *h0 = __float2half_rn(__half2float(*h0) + du);
+                --take;
+            }
+        }
+    }
+}
+
 template <int MODE>
 static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, const float* w32, const uint16_t* wbf16,
                                 cudaStream_t s) {
@@ -597,6 +719,12 @@ static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, co
     k_corr_final2<<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_corr_apply<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
     note_launches(8);
+    if constexpr (MODE == PL_F16_OFFSET) {
+        k_fix_scan<<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+        k_fix_final<<<(RED_GRID + 127) / 128, 128, 0, s>>>(t);
+        k_fix_apply<<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+        note_launches(3);
+    }
     return cudaGetLastError();
 }
 

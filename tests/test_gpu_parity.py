@@ -181,6 +181,32 @@ def test_single_correction_matches_oracle(storage, tol):
     assert abs(m1["mass"] - m0["mass0"]) <= (1e-12 if storage == F64 else 1e-6) * m0["mass0"]
 
 
+@pytest.mark.parametrize("nx,ny", [(48, 48), (67, 35), (130, 70)])
+def test_f16_correction_matches_oracle_and_restores_mass(nx, ny):
+    """FP16-offset storage: the correction of the stored state agrees with the oracle's
+    correction of the same (decoded) state to the FP16 rounding of the stored offsets, and
+    the stored mass returns to M0 within 1e-6 even on small lattices (the stochastic
+    rounding of the apply pass alone leaves ~ulp sqrt(N) / M ~ 1e-5 there)."""
+    lat = lattice(nx, ny, F16, beta_rho=0.3, beta_u=0.05)
+    lat.init_droplets([(nx / 2, ny / 2, min(nx, ny) / 4)], 2.0, 0.15, 2.0, 0.01, 9)
+    lat.step(40)
+    f0, _ = lat.state()
+    m0 = lat.metrics()
+    blob = wl.mlp_weights(42)
+    lat.set_weights(blob)
+    lat.correct()
+    f1, _ = lat.state()
+    fo = f0.copy()
+    assert O.correct(fo, blob, 0.3, 0.05, m0["mass0"], O.MLP_F64) == 0
+    # offsets below 1 in magnitude: FP16 spacing <= 2^-11; a moving population is rounded to
+    # nearest (<= 2^-12), the rest population stochastically (< 2^-11) and possibly shifted
+    # by one unit 2^-12 by the mass restoration
+    assert np.abs(f1 - fo).max() <= 2.0 ** -11 + 2.0 ** -12
+    m1 = lat.metrics()
+    assert m1["corrections"] == 1 and m1["status"] == 0
+    assert abs(m1["mass"] - m0["mass0"]) <= 1e-6 * m0["mass0"]
+
+
 def test_nonphysical_correction_leaves_state_and_sets_status():
     n = 32
     lat = lattice(n, n, F64, beta_rho=1.0, beta_u=0.0)
