@@ -1,0 +1,95 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the benchmark times.
+
+The oracle cannot run the full workloads in a test's time, so these checks sample:
+
+* the 4096x4096 coalescence field: one step of the whole field on the GPU (FP16-offset and
+  FP32 storage), compared on windows against the oracle's step of the same window.  A cell's
+  post-streaming value depends on populations at most two cells away (streaming from a
+  neighbour whose force reads its neighbours' density), so the window interior at distance
+  >= 3 from the window edge is exact even though the oracle treats the window as periodic.
+  Windows are placed at random, including across the periodic boundary.
+* the 256-lattice batch: all 256 lattices in one table, one coupling interval of K = 1 step
+  (step + correction + metrics: the same table kernels and grids the benchmark replays with
+  K = 100); the smallest lattices are compared whole against the oracle's step + correction,
+  every lattice must end with status OK and its mass at M0.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+MARGIN = 3
+WIN = 48
+
+
+def window(f, x0, y0, n):
+    """n x n window of f[9][ny][nx] starting at (x0, y0), periodic."""
+    _, ny, nx = f.shape
+    ys = (y0 + np.arange(n)) % ny
+    xs = (x0 + np.arange(n)) % nx
+    return f[:, ys][:, :, xs]
+
+
+# absolute bounds (|f| <= ~1.2): FP16 offsets below 1 in magnitude have a spacing of at most
+# 2^-11 (the stochastically rounded rest population is within one spacing, the moving ones
+# within half of one); FP32 storage: a few FP32 roundings of values near 1
+@pytest.mark.parametrize("storage,tol", [(wl.F16_OFFSET, 2.0 ** -11), (wl.F32, 2e-6)])
+def test_field_4096_one_step_sampled_windows(storage, tol):
+    job = wl.field_4096(storage=storage)
+    lat = B.Lattice.from_workload(job)
+    f0, _ = lat.state()
+    lat.step(1)
+    f1, step = lat.state()
+    assert step == 1
+    rng = np.random.default_rng(7)
+    corners = [(0, 0), (job.nx - WIN // 2, job.ny - WIN // 2)] + [tuple(rng.integers(0, job.nx, 2)) for _ in range(6)]
+    worst = 0.0
+    for x0, y0 in corners:
+        w0 = window(f0, x0, y0, WIN).copy()
+        O.step(w0, 1, job.G, job.tau)
+        w1 = window(f1, x0, y0, WIN)
+        inner = (slice(None), slice(MARGIN, WIN - MARGIN), slice(MARGIN, WIN - MARGIN))
+        err = np.abs(w1[inner] - w0[inner]).max()
+        worst = max(worst, err)
+    assert worst <= tol, worst
+
+
+def test_batch_256_one_interval_sampled_lattices():
+    K = 1
+    jobs = wl.batch_256(steps=K, K=K)
+    blob = jobs[0].weights()
+    budget = B.pl_batch_overhead_bytes(len(jobs)) + sum(B.pl_batch_job_bytes(B.job_params(j)) for j in jobs) + (64 << 20)
+    bt = B.Batch(wl.F16_OFFSET, wl.MLP_BF16, K, budget, max_jobs=len(jobs))
+    bt.set_weights(blob)
+    ids = [bt.submit(j, steps=4 * K) for j in jobs]
+    assert all(i is not None for i in ids)
+    order = sorted(range(len(jobs)), key=lambda k: jobs[k].cells)
+    f0 = {k: bt.state(ids[k])[0] for k in order[:6]}
+    bt.advance(1)
+    live = {r["id"]: r for r in B.pl_batch_metrics(bt.h)}
+    assert len(live) == len(jobs)
+    for k, jid in enumerate(ids):
+        m = live[jid]["metrics"]
+        assert live[jid]["status"] == 0, (k, live[jid])
+        assert m["corrections"] == 1
+        assert abs(m["mass"] - m["mass0"]) <= 1e-6 * m["mass0"], k
+    for k in order[:6]:
+        j = jobs[k]
+        fo = f0[k].copy()
+        M0 = live[ids[k]]["metrics"]["mass0"]
+        O.step(fo, 1, j.G, j.tau)
+        assert O.correct(fo, blob, j.beta_rho, j.beta_u, M0, O.MLP_BF16) == 0
+        f1, step = bt.state(ids[k])
+        assert step == K
+        # FP16 offsets (spacing <= 2^-11 below 1) after one step and one correction, the
+        # network in BF16 on both sides (the oracle emulates the BF16 rounding)
+        assert np.abs(f1 - fo).max() <= 3e-3, (k, j.nx, np.abs(f1 - fo).max())
+    bt.close()
