@@ -429,9 +429,20 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
     const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
     const bool split = !FAST && !(vec && own0 == own1);
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    // FAST strips index their lattice with 32-bit element offsets (the caller checks that 9
+    // planes fit): each access is one multiply-add of the plane offset plus one widening
+    // address computation, instead of 64-bit arithmetic per access.
+    using S = typename Traits<MODE>::S;
+    const uint32_t planeU = (uint32_t)a.plane, pitchU = (uint32_t)a.pitch;
+    auto load_fast = [&](int r, PT (&P)[9]) {
+        const uint32_t off = (uint32_t)r * pitchU + (uint32_t)cA;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = *reinterpret_cast<const PT*>(a.fin + (off + (uint32_t)i * planeU));
+    };
 
     PT Nx[9];
-    load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
+    if constexpr (FAST) load_fast(wrapi(r0 - 1, ny), Nx);
+    else load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
     float2 hp[9];  // previous row (to be relaxed), decoded
     float2 rho_p = make_float2(0.0f, 0.0f), sh_p = make_float2(0.0f, 0.0f);
     PsiRow<float> A{}, B{}, C{};
@@ -443,7 +454,8 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
         if (k <= nrows) {
             int rn = r0 + k;
             if (rn >= ny) rn -= ny;
-            load_row<MODE>(a, rn, cA, cB, vec, Nx);  // prefetch the next row
+            if constexpr (FAST) load_fast(rn, Nx);  // prefetch the next row
+            else load_row<MODE>(a, rn, cA, cB, vec, Nx);
         }
         float2 hc[9];
 #pragma unroll
@@ -493,10 +505,14 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
                 out[0] = sr_pack_half2(rest.x, rest.y, rnd);
             }
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            auto dst = [&](int i, int row) -> S* {
+                if constexpr (FAST) return a.fout + ((uint32_t)row * pitchU + (uint32_t)ua + (uint32_t)i * planeU);
+                else return a.fout + i * a.plane + (long long)row * a.pitch + ua;
+            };
             // c_x = 0 planes: own pair
-            store_pair2<MODE>(a.fout + 0 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, out[0]);
-            store_pair2<MODE>(a.fout + 2 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, out[2]);
-            store_pair2<MODE>(a.fout + 4 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, out[4]);
+            store_pair2<MODE>(dst(0, y), split, own0, own1, out[0]);
+            store_pair2<MODE>(dst(2, yp), split, own0, own1, out[2]);
+            store_pair2<MODE>(dst(4, ym), split, own0, own1, out[4]);
             // c_x = +1 planes: (left lane's second cell, own first cell);
             // c_x = -1 planes: (own second cell, right lane's first cell)
             if constexpr (MODE == PL_F16_OFFSET) {
@@ -512,12 +528,12 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
                     const uint32_t v = __byte_perm(lo_src, hi_src, 0x5432);
                     return *reinterpret_cast<const __half2*>(&v);
                 };
-                store_pair2<MODE>(a.fout + 1 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
-                store_pair2<MODE>(a.fout + 5 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
-                store_pair2<MODE>(a.fout + 8 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
-                store_pair2<MODE>(a.fout + 3 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
-                store_pair2<MODE>(a.fout + 6 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
-                store_pair2<MODE>(a.fout + 7 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
+                store_pair2<MODE>(dst(1, y), split, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
+                store_pair2<MODE>(dst(5, yp), split, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
+                store_pair2<MODE>(dst(8, ym), split, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
+                store_pair2<MODE>(dst(3, y), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
+                store_pair2<MODE>(dst(6, yp), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
+                store_pair2<MODE>(dst(7, ym), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
             } else {
                 const float l1 = __shfl_up_sync(0xffffffffu, o[1].y, 1);
                 const float l5 = __shfl_up_sync(0xffffffffu, o[5].y, 1);
@@ -525,12 +541,12 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
                 const float r3 = __shfl_down_sync(0xffffffffu, o[3].x, 1);
                 const float r6 = __shfl_down_sync(0xffffffffu, o[6].x, 1);
                 const float r7 = __shfl_down_sync(0xffffffffu, o[7].x, 1);
-                store_pair2<MODE>(a.fout + 1 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, make_float2(l1, o[1].x));
-                store_pair2<MODE>(a.fout + 5 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, make_float2(l5, o[5].x));
-                store_pair2<MODE>(a.fout + 8 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, make_float2(l8, o[8].x));
-                store_pair2<MODE>(a.fout + 3 * a.plane + (long long)y * a.pitch + ua, split, own0, own1, make_float2(o[3].y, r3));
-                store_pair2<MODE>(a.fout + 6 * a.plane + (long long)yp * a.pitch + ua, split, own0, own1, make_float2(o[6].y, r6));
-                store_pair2<MODE>(a.fout + 7 * a.plane + (long long)ym * a.pitch + ua, split, own0, own1, make_float2(o[7].y, r7));
+                store_pair2<MODE>(dst(1, y), split, own0, own1, make_float2(l1, o[1].x));
+                store_pair2<MODE>(dst(5, yp), split, own0, own1, make_float2(l5, o[5].x));
+                store_pair2<MODE>(dst(8, ym), split, own0, own1, make_float2(l8, o[8].x));
+                store_pair2<MODE>(dst(3, y), split, own0, own1, make_float2(o[3].y, r3));
+                store_pair2<MODE>(dst(6, yp), split, own0, own1, make_float2(o[6].y, r6));
+                store_pair2<MODE>(dst(7, ym), split, own0, own1, make_float2(o[7].y, r7));
             }
         }
 #pragma unroll
@@ -545,7 +561,7 @@ __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1
     const int ua = strip * STRIP - 2 + 2 * lane;
     const int cA = wrapi(ua, a.nx), cB = wrapi(ua + 1, a.nx);
     const bool mid = lane >= 1 && lane <= 30;
-    const bool fast = (cB == cA + 1) && ((cA & 1) == 0) && (!mid || ua + 1 < a.nx);
+    const bool fast = (cB == cA + 1) && ((cA & 1) == 0) && (!mid || ua + 1 < a.nx) && 9ll * a.plane <= 0xFFFFFFFFll;
     // (FP32 storage is bound by HBM, not by issue: it keeps one copy of the walk and its
     // register count, and with it four blocks per SM)
     if (MODE == PL_F16_OFFSET && __all_sync(0xffffffffu, fast)) walk_impl2<MODE, true>(a, strip, r0, r1, lane);
