@@ -5,7 +5,8 @@
 // 2 -> 64 -> 128 -> 128 -> 64 -> 3, tanh on the hidden layers, linear output.
 //   layer 1 (2 -> 64)     : FP32 FMA per cell, tanh, rounded to BF16 (A operand of layer 2)
 //   layers 2, 3, 4        : tcgen05.mma kind::f16, M = 128 cells, N = 128/128/64, K = 64/128/128,
-//                           D in TMEM; epilogue tcgen05.ld -> + bias -> tanh -> BF16 -> smem
+//                           plus one K = 16 step that adds the bias (ones x [b_hi, b_lo]);
+//                           D in TMEM; epilogue tcgen05.ld -> tanh -> BF16 -> smem
 //   layer 5 (64 -> 3)     : FP32 FMA on the FP32 tanh outputs of layer 4
 //
 // CTA = 4 warpgroups (16 warps, all TMEM columns); each warpgroup runs its own 128-cell
@@ -48,8 +49,11 @@ constexpr int OFF_A = 0;                             // one operand buffer per W
 constexpr int OFF_W2 = OFF_A + NWG * A_BYTES;        // 128 x 64  BF16 = 16 KB
 constexpr int OFF_W3 = OFF_W2 + 128 * 64 * 2;        // 128 x 128 BF16 = 32 KB
 constexpr int OFF_W4 = OFF_W3 + 128 * 128 * 2;       // 64 x 128  BF16 = 16 KB
-constexpr int OFF_P = OFF_W4 + 64 * 128 * 2;         // FP32 parameters
-constexpr int P_W1 = 0, P_B1 = 128, P_B2 = 192, P_B3 = 320, P_B4 = 448, P_W5 = 512, P_B5 = 704, P_N = 708;
+constexpr int WB_ELEMS = (128 + 128 + 64) * 16;      // bias blocks of layers 2-4: N x 16 BF16
+constexpr int OFF_WB = OFF_W4 + 64 * 128 * 2;        // (bias split hi + lo in K columns 0 and 1)
+constexpr int OFF_ONES = OFF_WB + WB_ELEMS * 2;      // 128 x 16 BF16 A operand: columns 0, 1 = 1
+constexpr int OFF_P = OFF_ONES + M * 16 * 2;         // FP32 parameters
+constexpr int P_W1 = 0, P_B1 = 128, P_W5 = 192, P_B5 = 384, P_N = 388;  // layers 2-4 biases: in the MMA
 constexpr int OFF_BAR = (OFF_P + P_N * 4 + 15) / 16 * 16;
 constexpr int OFF_TMEM_SLOT = OFF_BAR + 8 * (1 + NWG);
 constexpr int SMEM_USED = OFF_TMEM_SLOT + 16;
@@ -57,7 +61,7 @@ constexpr int SMEM_ALLOC = 227 * 1024;
 static_assert(OFF_BAR % 8 == 0, "mbarrier alignment");
 static_assert(SMEM_USED <= SMEM_ALLOC, "shared memory");
 
-constexpr int W_IMG_ELEMS = 128 * 64 + 128 * 128 + 64 * 128;   // BF16 image in global memory
+constexpr int W_IMG_ELEMS = 128 * 64 + 128 * 128 + 64 * 128 + WB_ELEMS;   // BF16 image in global memory
 constexpr long long WAIT_NS = 2000000000ll;                       // 2 s per wait
 
 // Blob offsets (FP32 master weights, row-major W[out][in]).
@@ -171,8 +175,11 @@ __device__ __forceinline__ void store8(uint8_t* A, int m, int k0, const float* v
     *reinterpret_cast<uint4*>(A + ((k0 >> 3) * (M / 8) + (m >> 3)) * 128 + (m & 7) * 16) = u;
 }
 
-// Issue D[128 x N] (+)= A[128 x K] * W[N x K]^T as K/16 MMAs.
-__device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_base, uint32_t w_base, int N, int K) {
+// Issue D[128 x N] = A[128 x K] * W[N x K]^T + bias as K/16 + 1 MMAs: the bias enters the
+// FP32 accumulator through one more K = 16 step, a block of ones (columns 0 and 1) times the
+// bias split into BF16 high and low parts (b = b_hi + b_lo to 2^-16 relative).
+__device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_base, uint32_t w_base, int N, int K,
+                                            uint32_t ones_base, uint32_t bias_base) {
     const uint32_t idesc = idesc_bf16(M, N);
     const uint32_t a_lbo = (M / 8) * 128, w_lbo = (N / 8) * 128;
     for (int ks = 0; ks < K / 16; ++ks) {
@@ -180,6 +187,7 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_base, ui
         const uint64_t b = smem_desc(w_base + ks * 2 * w_lbo, w_lbo, 128);
         mma_bf16(d_tmem, a, b, idesc, ks > 0 ? 1u : 0u);
     }
+    mma_bf16(d_tmem, smem_desc(ones_base, a_lbo, 128), smem_desc(bias_base, w_lbo, 128), idesc, 1u);
 }
 
 }  // namespace tc
@@ -187,15 +195,31 @@ __device__ __forceinline__ void issue_layer(uint32_t d_tmem, uint32_t a_base, ui
 size_t bf16_weight_elems() { return tc::W_IMG_ELEMS; }
 
 // FP32 blob -> BF16 (round to nearest even) images of W2, W3, W4 in the core-matrix
-// layout above: element (n, k) of an N x K matrix at ((k/8) * N/8 + n/8) * 64 + (n%8) * 8 + k%8.
+// layout above: element (n, k) of an N x K matrix at ((k/8) * N/8 + n/8) * 64 + (n%8) * 8 + k%8;
+// then the bias blocks of layers 2, 3, 4 (N x 16, same layout): column 0 = bf16(b),
+// column 1 = bf16(b - bf16(b)), the other columns 0.
 __global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* __restrict__ img) {
+    constexpr int NW = 8192 + 16384 + 8192;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tc::W_IMG_ELEMS; e += gridDim.x * blockDim.x) {
-        int N, K, src, base, loc;
-        if (e < 8192) { N = 128; K = 64; src = tc::B_W2; base = 0; loc = e; }
-        else if (e < 8192 + 16384) { N = 128; K = 128; src = tc::B_W3; base = 8192; loc = e - 8192; }
-        else { N = 64; K = 128; src = tc::B_W4; base = 8192 + 16384; loc = e - 8192 - 16384; }
+        int N, K, base, loc;
+        float v;
+        if (e < NW) {
+            int src;
+            if (e < 8192) { N = 128; K = 64; src = tc::B_W2; base = 0; loc = e; }
+            else if (e < 8192 + 16384) { N = 128; K = 128; src = tc::B_W3; base = 8192; loc = e - 8192; }
+            else { N = 64; K = 128; src = tc::B_W4; base = 8192 + 16384; loc = e - 8192 - 16384; }
+            v = w32[src + (loc / K) * K + loc % K];
+        } else {
+            int src;
+            K = 16;
+            if (e < NW + 2048) { N = 128; src = tc::B_B2; base = NW; loc = e - NW; }
+            else if (e < NW + 4096) { N = 128; src = tc::B_B3; base = NW + 2048; loc = e - NW - 2048; }
+            else { N = 64; src = tc::B_B4; base = NW + 4096; loc = e - NW - 4096; }
+            const float b = w32[src + loc / 16], hi = __bfloat162float(__float2bfloat16_rn(b));
+            v = loc % 16 == 0 ? b : (loc % 16 == 1 ? b - hi : 0.0f);
+        }
         const int n = loc / K, k = loc % K;
-        __nv_bfloat16 b = __float2bfloat16_rn(w32[src + n * K + k]);
+        __nv_bfloat16 b = __float2bfloat16_rn(v);
         img[base + ((k >> 3) * (N >> 3) + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = *reinterpret_cast<uint16_t*>(&b);
     }
 }
@@ -245,11 +269,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     // small FP32 parameters
     for (int k = tid; k < 128; k += THREADS) P[P_W1 + k] = w32[B_W1 + k];
     for (int k = tid; k < 64; k += THREADS) P[P_B1 + k] = w32[B_B1 + k];
-    for (int k = tid; k < 128; k += THREADS) P[P_B2 + k] = w32[B_B2 + k];
-    for (int k = tid; k < 128; k += THREADS) P[P_B3 + k] = w32[B_B3 + k];
-    for (int k = tid; k < 64; k += THREADS) P[P_B4 + k] = w32[B_B4 + k];
     for (int k = tid; k < 192; k += THREADS) P[P_W5 + k] = w32[B_W5 + k];
     for (int k = tid; k < 3; k += THREADS) P[P_B5 + k] = w32[B_B5 + k];
+    // the ones block (A operand of the bias step): element (m, k) at
+    // ((k/8) * M/8 + m/8) * 64 + (m%8) * 8 + k%8, 1 in columns 0 and 1
+    {
+        uint16_t* ones = reinterpret_cast<uint16_t*>(sm + OFF_ONES);
+        for (int e = tid; e < M * 16; e += THREADS) {
+            const int m = e / 16, k = e % 16;
+            ones[((k >> 3) * (M / 8) + (m >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = k < 2 ? 0x3F80u : 0u;  // BF16 1.0
+        }
+    }
+    fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
@@ -259,10 +290,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const uint32_t bytes = W_IMG_ELEMS * 2;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(bytes) : "memory");
         const uint8_t* src = reinterpret_cast<const uint8_t*>(wimg);
-        const uint32_t dst[3] = {saddr(sm + OFF_W2), saddr(sm + OFF_W3), saddr(sm + OFF_W4)};
-        const uint32_t len[3] = {128 * 64 * 2, 128 * 128 * 2, 64 * 128 * 2};
+        const uint32_t dst[4] = {saddr(sm + OFF_W2), saddr(sm + OFF_W3), saddr(sm + OFF_W4), saddr(sm + OFF_WB)};
+        const uint32_t len[4] = {128 * 64 * 2, 128 * 128 * 2, 64 * 128 * 2, WB_ELEMS * 2};
         uint32_t off = 0;
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 4; ++k) {
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                              dst[k]),
                          "l"(src + off), "r"(len[k]), "r"(bar_w)
@@ -319,9 +350,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             wg_bar(wg);
             if (t == 0) {
                 tc_after_sync();
-                if (layer == 2) issue_layer(d_tmem, ax, saddr(sm + OFF_W2), 128, 64);
-                else if (layer == 3) issue_layer(d_tmem, ax, saddr(sm + OFF_W3), 128, 128);
-                else issue_layer(d_tmem, ax, saddr(sm + OFF_W4), 64, 128);
+                const uint32_t ones = saddr(sm + OFF_ONES), wb = saddr(sm + OFF_WB);
+                if (layer == 2) issue_layer(d_tmem, ax, saddr(sm + OFF_W2), 128, 64, ones, wb);
+                else if (layer == 3) issue_layer(d_tmem, ax, saddr(sm + OFF_W3), 128, 128, ones, wb + 128 * 16 * 2);
+                else issue_layer(d_tmem, ax, saddr(sm + OFF_W4), 64, 128, ones, wb + 256 * 16 * 2);
                 mma_commit(bar_mma);
             }
             pending = 1;
@@ -331,21 +363,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             phase ^= 1;
             tc_after_sync();
             const int nout = layer == 4 ? 64 : 128;
-            const float* bias = P + (layer == 2 ? P_B2 : (layer == 3 ? P_B3 : P_B4));
             uint8_t* dst = AX;  // the layer's MMA has completed: its operand buffer is free
 #pragma unroll 1
             for (int c0 = 0; c0 < nout; c0 += 16) {
                 float v[16];
                 tmem_ld16(my_lane_tmem + c0, v);
-                const float4* b4 = reinterpret_cast<const float4*>(bias + c0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 b = b4[q];
-                    v[4 * q + 0] = tanh_fast(v[4 * q + 0] + b.x);
-                    v[4 * q + 1] = tanh_fast(v[4 * q + 1] + b.y);
-                    v[4 * q + 2] = tanh_fast(v[4 * q + 2] + b.z);
-                    v[4 * q + 3] = tanh_fast(v[4 * q + 3] + b.w);
-                }
+                for (int j = 0; j < 16; ++j) v[j] = tanh_fast(v[j]);  // the bias is in the accumulator
                 if (layer < 4) {
 #pragma unroll
                     for (int q = 0; q < 2; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
