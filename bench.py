@@ -181,6 +181,16 @@ def cpu_sample(jobs, budget_s):
     return upd, secs, done, O.num_threads()
 
 
+def batch_config(n_lattices, cells, K, world):
+    """The workload keys both arms report (the GPU arm adds its launch configuration)."""
+    return {"workload": "batch_%d" % n_lattices, "lattices": n_lattices, "cells": cells,
+            "storage": "f16_offset", "network": "bf16-tcgen05", "K": K,
+            "step": "one coupling interval: K lattice steps + correction + metrics of every lattice "
+                    "(one CUDA graph replay)",
+            "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (cells * 18 / 1e9),
+            "parallelism": "replicas x%d" % world}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args):
@@ -204,7 +214,9 @@ def run_reference(args):
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "batch_%d (FP64 CPU oracle, bounded sample)" % args.lattices, "K": 100},
+        "config": dict(batch_config(args.lattices, sum(j.cells for j in jobs), 100, 1),
+                       sample="FP64 CPU oracle: each step one coupling interval of one of the 8 smallest "
+                              "lattices in turn"),
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": O.num_threads(), "kind": "oracle",
                          "sample": "one coupling interval (K=100 steps + FP64 network correction + metrics) per "
                                    "step on the 8 smallest lattices of the batch in turn"},
@@ -386,13 +398,7 @@ def run_gb300(args):
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch_%d" % len(jobs), "lattices": len(jobs), "cells": cells,
-                       "storage": "f16_offset", "network": "bf16-tcgen05", "K": K,
-                       "step": "one coupling interval: K lattice steps + correction + metrics of every lattice "
-                               "(one CUDA graph replay)",
-                       "rows_per_chunk": rows_per_chunk,
-                       "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (cells * 18 / 1e9),
-                       "parallelism": "replicas x%d" % world},
+            "config": dict(batch_config(len(jobs), cells, K, world), rows_per_chunk=rows_per_chunk),
             "roofline": {"bound": "hbm", "kernel": "k_step<f16_offset> (batched)", "achieved": achieved,
                          "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": profiled_traffic("f16_offset_batch", cells),
