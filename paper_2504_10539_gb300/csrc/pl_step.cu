@@ -33,7 +33,18 @@
 
 namespace pl {
 
-constexpr int STEP_THREADS = 128;  // 4 independent warps per CTA
+// Launch shape of the step kernel.  Its warps are independent (no shared memory, no
+// barrier).  FP16-offset: one-warp blocks, with the registers capped (96, a few bytes of
+// stack) so that 21 warps fit on an SM instead of 16: that storage is bound by the latency of
+// its instruction chains, and 5 more warps hide more of it (0.855 -> 0.806 ms per batched step).
+// FP32/FP64: blocks of four warps, 4 (FP32) or 2 (FP64) of them per SM, the occupancy their
+// register counts give anyway (FP32 is bound by HBM; one-warp blocks were slower there).
+template <int MODE>
+struct StepCfg {
+    static constexpr int threads = MODE == PL_F16_OFFSET ? 32 : 128;
+    static constexpr int min_blocks = MODE == PL_F16_OFFSET ? 17 : (MODE == PL_F32 ? 4 : 2);
+};
+constexpr int STEP_THREADS = 128;  // the largest block of the step kernel
 
 template <int MODE> struct Pair;
 template <> struct Pair<PL_F64> {
@@ -587,16 +598,17 @@ __device__ __forceinline__ int find_seg(const long long* __restrict__ pre, int n
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(STEP_THREADS) k_step(TableView t, int parity) {
+__global__ void __launch_bounds__(StepCfg<MODE>::threads, StepCfg<MODE>::min_blocks) k_step(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
     const int lane = threadIdx.x & 31;
-    const long long P = (long long)gridDim.x * (STEP_THREADS / 32);
+    constexpr int TH = StepCfg<MODE>::threads;
+    const long long P = (long long)gridDim.x * (TH / 32);
     const long long total = t.hdr->total_warps;
     const int n = t.hdr->n;
     const uint32_t seq = t.seq[parity];
     if (blockIdx.x == 0 && threadIdx.x == 0) t.seq[parity ^ 1] = seq + 1u;
-    for (long long vw = ((long long)blockIdx.x * STEP_THREADS + threadIdx.x) >> 5; vw < total; vw += P) {
+    for (long long vw = ((long long)blockIdx.x * TH + threadIdx.x) >> 5; vw < total; vw += P) {
         const int j = find_seg(t.warp_pre, n, vw);
         const LatDesc& d = t.d[j];
         const long long local = vw - t.warp_pre[j];
@@ -630,9 +642,10 @@ static int capacity_t() {
         int dev = 0, sms = 0, bps = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_step<MODE>, STEP_THREADS, 0) != cudaSuccess || bps < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_step<MODE>, StepCfg<MODE>::threads, 0) != cudaSuccess ||
+            bps < 1)
             bps = 1;
-        cap = bps * sms * (STEP_THREADS / 32);
+        cap = bps * sms * (StepCfg<MODE>::threads / 32);
     }
     return cap;
 }
@@ -647,8 +660,8 @@ int step_capacity_warps(int storage) {
 
 template <int MODE>
 static cudaError_t launch_step_t(const TableView& t, int parity, cudaStream_t s) {
-    const int blocks = capacity_t<MODE>() / (STEP_THREADS / 32);
-    k_step<MODE><<<blocks, STEP_THREADS, 0, s>>>(t, parity);
+    const int blocks = capacity_t<MODE>() / (StepCfg<MODE>::threads / 32);
+    k_step<MODE><<<blocks, StepCfg<MODE>::threads, 0, s>>>(t, parity);
     note_launches(1);
     return cudaGetLastError();
 }
