@@ -521,6 +521,19 @@ __device__ __forceinline__ void feq9(R rho, R ux, R uy, R (&fe)[9]) {
     }
 }
 
+// FP16 mass restoration (below): one FP16 unit of the binade [1/4, 1/2), and the rest
+// populations that can move by exactly one unit without leaving it.
+constexpr float FIX_U = 1.0f / 4096.0f;
+
+__device__ __forceinline__ bool fix_candidate(__half h) {
+    const float a = fabsf(__half2float(h));
+    return a >= 0.25f + FIX_U && a <= 0.5f - FIX_U;
+}
+
+// FP16-offset lattices also accumulate, per block, the stored mass of the corrected state
+// (per cell in FP32 - nine FP16 offsets below 2 in magnitude sum there to within 2^-24 - then
+// error-free pair sums over cells) and the number of restoration candidates, into partial
+// slots 0 and 1, for the mass restoration that follows.
 template <int MODE>
 __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
@@ -541,10 +554,22 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
         S* f = static_cast<S*>(d.pops[d.phase ^ parity]);
         const R sjx = R(rec->mjx), sjy = R(rec->mjy);
         const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u);
+        SumAcc<float> stored;  // FP16 only: stored mass after the correction, and candidates
+        unsigned cand = 0;
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
             const long long c = it.c;
-            if (!(g[c] > R(0))) continue;
+            if (!(g[c] > R(0))) {
+                if constexpr (MODE == PL_F16_OFFSET) {
+                    const long long o = it.pop_offset(d.pitch);
+                    float sc = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) sc += __half2float(f[i * d.plane + o]);
+                    stored.add(sc);
+                    cand += fix_candidate(f[o]) ? 1u : 0u;
+                }
+                continue;
+            }
             const CellCorr<R> q = cell_corr(c, rho, jx, jy, g, out3, N, k);
             const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
             const R r = rho[c], jxc = jx[c], jyc = jy[c];
@@ -558,18 +583,23 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
                 // rounded values and rounded stochastically, so that small per-cell changes
                 // (below half an FP16 step) are realised on average instead of being rounded away
                 float hn[9];
-                float res = 0.0f;
+                float res = 0.0f, sq = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hn[i] = __half2float(f[i * d.plane + o]) + (fn[i] - fo[i]);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const __half qh = __float2half_rn(hn[i]);
-                    res += __half2float(qh) - hn[i];
+                    const float qf = __half2float(qh);
+                    res += qf - hn[i];
+                    sq += qf;
                     f[i * d.plane + o] = qh;
                 }
                 const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u) ^
                                             ((seq - d.seq0) * 0x27D4EB2Fu));
-                f[o] = sr_half(hn[0] - res, rnd);
+                const __half h0 = sr_half(hn[0] - res, rnd);
+                f[o] = h0;
+                stored.add(sq + __half2float(h0));
+                cand += fix_candidate(h0) ? 1u : 0u;
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
@@ -577,6 +607,16 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
                     const R fi = decode<MODE>(f[i * d.plane + o], off);
                     f[i * d.plane + o] = encode<MODE>(fi + (fn[i] - fo[i]), off);
                 }
+            }
+        }
+        if constexpr (MODE == PL_F16_OFFSET) {
+            __shared__ double sm[2 * 32];
+            const int op[2] = {0, 0};
+            double v[2] = {stored.value(), (double)cand};
+            block_reduce<2>(v, op, sm);
+            if (threadIdx.x == 0) {
+                d.partials[m.lb * PARTIAL_STRIDE + 0] = v[0];
+                d.partials[m.lb * PARTIAL_STRIDE + 1] = v[1];
             }
         }
     }
@@ -594,49 +634,11 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
 // within a block by thread, within a thread by loop index; the result is deterministic and
 // the same for a lattice alone or in a batch.
 
-constexpr float FIX_U = 1.0f / 4096.0f;
-
-__device__ __forceinline__ bool fix_candidate(__half h) {
-    const float a = fabsf(__half2float(h));
-    return a >= 0.25f + FIX_U && a <= 0.5f - FIX_U;
-}
 
 __device__ __forceinline__ bool fix_active(const DevRecord* rec) { return !rec->reject && rec->sum_m > 0.0; }
 
-// Pass 1: stored sum of the offsets (per cell in FP32 - nine FP16 offsets below 2 in
-// magnitude sum there to within 2^-24, far below u - then error-free pair sums over cells)
-// and the candidates, per block.
-__global__ void __launch_bounds__(RB_THREADS) k_fix_scan(TableView t, int parity) {
-    __shared__ double sm[2 * 32];
-    const int n = t.hdr->n, total = t.hdr->total_blocks;
-    const int op[2] = {0, 0};
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-        const BlkMap m = map_blk(t, n, vb);
-        const LatDesc& d = t.d[m.j];
-        if (!fix_active(d.rec)) continue;
-        const __half* f = static_cast<const __half*>(d.pops[d.phase ^ parity]);
-        const long long N = (long long)d.nx * d.ny;
-        SumAcc<float> sh;
-        unsigned cand = 0;
-        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
-             it.next(d.nx)) {
-            const long long o = it.pop_offset(d.pitch);
-            float s = 0.0f;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) s += __half2float(f[i * d.plane + o]);
-            sh.add(s);
-            cand += fix_candidate(f[o]) ? 1u : 0u;
-        }
-        double v[2] = {sh.value(), (double)cand};
-        block_reduce<2>(v, op, sm);
-        if (threadIdx.x == 0) {
-            d.partials[m.lb * PARTIAL_STRIDE + 0] = v[0];
-            d.partials[m.lb * PARTIAL_STRIDE + 1] = v[1];
-        }
-    }
-}
-
-// Pass 2, one thread per lattice: stored mass M = sum h + N rho_ref, n = round((M - M0)/u)
+// One thread per lattice (after the apply pass has left the stored sum and the candidates
+// of each block in partial slots 0 and 1): stored mass M = sum h + N rho_ref, n = round((M - M0)/u)
 // (limited by the candidates available), and each block's first candidate index.
 __global__ void k_fix_final(TableView t) {
     const int n = t.hdr->n;
@@ -660,7 +662,7 @@ __global__ void k_fix_final(TableView t) {
     }
 }
 
-// Pass 3: shift the chosen rest populations by -sign(n) u.
+// Shift the chosen rest populations by -sign(n) u.
 __global__ void __launch_bounds__(RB_THREADS) k_fix_apply(TableView t, int parity) {
     __shared__ unsigned scan[RB_THREADS];
     const int n = t.hdr->n, total = t.hdr->total_blocks;
@@ -720,10 +722,9 @@ static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, co
     k_corr_apply<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
     note_launches(8);
     if constexpr (MODE == PL_F16_OFFSET) {
-        k_fix_scan<<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
         k_fix_final<<<(RED_GRID + 127) / 128, 128, 0, s>>>(t);
         k_fix_apply<<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
-        note_launches(3);
+        note_launches(2);
     }
     return cudaGetLastError();
 }
