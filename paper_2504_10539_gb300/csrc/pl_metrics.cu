@@ -204,9 +204,19 @@ __global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity)
             const long long c = it.c;
             const long long o = it.pop_offset(d.pitch);
             R P[9];
+            if constexpr (MODE == PL_F16_OFFSET) {
+                // sum the stored offsets (exact to 2^-24 here) and add rho_ref once: decoding
+                // each population first would add nine roundings per cell, the same in every
+                // cell of a uniform phase, i.e. a bias of ~1e-7 in the lattice mass
 #pragma unroll
-            for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o], wq<R>(i) * rho_ref);
-            rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+                for (int i = 0; i < 9; ++i) P[i] = __half2float(f[i * d.plane + o]);
+                rho[c] = ((((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7]))) + P[8]) + rho_ref;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o], wq<R>(i) * rho_ref);
+                rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+            }
+            // sum_i c_i f_i: the offsets w_i rho_ref have no first moment
             jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
             jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
         }
@@ -439,17 +449,30 @@ __device__ __forceinline__ CorrK<R> corr_constants(const DevRecord* rec, double 
     k.beta_u = R(beta_u);
     return k;
 }
+// The cell's fields, loaded together (one memory round trip per cell).
+template <typename R>
+struct CellIn {
+    R r, jx, jy, g, rh, ux, uy;  // rho, j, |grad rho|, network rho^, u^
+};
+template <typename R>
+__device__ __forceinline__ CellIn<R> cell_in(long long c, const R* rho, const R* jx, const R* jy, const R* g,
+                                             const R* out3, long long N) {
+    return CellIn<R>{rho[c], jx[c], jy[c], g[c], out3[c], out3[N + c], out3[2 * N + c]};
+}
+template <typename R>
+__device__ __forceinline__ CellCorr<R> cell_corr(const CellIn<R>& in, const CorrK<R>& k) {
+    CellCorr<R> q;
+    q.m = in.g / k.gmax;
+    const R dr = k.beta_rho * q.m * (in.rh - in.r) - q.m * k.proj;
+    q.rhop = in.r + dr;
+    q.djx_raw = k.beta_u * q.m * (q.rhop * in.ux - in.jx);
+    q.djy_raw = k.beta_u * q.m * (q.rhop * in.uy - in.jy);
+    return q;
+}
 template <typename R>
 __device__ __forceinline__ CellCorr<R> cell_corr(long long c, const R* rho, const R* jx, const R* jy, const R* g,
                                                  const R* out3, long long N, const CorrK<R>& k) {
-    CellCorr<R> q;
-    const R r = rho[c];
-    q.m = g[c] / k.gmax;
-    const R dr = k.beta_rho * q.m * (out3[c] - r) - q.m * k.proj;
-    q.rhop = r + dr;
-    q.djx_raw = k.beta_u * q.m * (q.rhop * out3[N + c] - jx[c]);
-    q.djy_raw = k.beta_u * q.m * (q.rhop * out3[2 * N + c] - jy[c]);
-    return q;
+    return cell_corr(cell_in(c, rho, jx, jy, g, out3, N), k);
 }
 
 template <typename R>
@@ -535,7 +558,7 @@ __device__ __forceinline__ bool fix_candidate(__half h) {
 // error-free pair sums over cells) and the number of restoration candidates, into partial
 // slots 0 and 1, for the mass restoration that follows.
 template <int MODE>
-__global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int parity) {
+__global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 3 : 1) k_corr_apply(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
     const int n = t.hdr->n, total = t.hdr->total_blocks;
@@ -559,24 +582,28 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
             const long long c = it.c;
-            if (!(g[c] > R(0))) {
+            const long long o = it.pop_offset(d.pitch);
+            // every load of the cell first, independent of each other
+            const CellIn<R> in = cell_in(c, rho, jx, jy, g, out3, N);
+            S fs[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) fs[i] = f[i * d.plane + o];
+            if (!(in.g > R(0))) {
                 if constexpr (MODE == PL_F16_OFFSET) {
-                    const long long o = it.pop_offset(d.pitch);
                     float sc = 0.0f;
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) sc += __half2float(f[i * d.plane + o]);
+                    for (int i = 0; i < 9; ++i) sc += __half2float(fs[i]);
                     stored.add(sc);
-                    cand += fix_candidate(f[o]) ? 1u : 0u;
+                    cand += fix_candidate(fs[0]) ? 1u : 0u;
                 }
                 continue;
             }
-            const CellCorr<R> q = cell_corr(c, rho, jx, jy, g, out3, N, k);
+            const CellCorr<R> q = cell_corr(in, k);
             const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
-            const R r = rho[c], jxc = jx[c], jyc = jy[c];
+            const R r = in.r, jxc = in.jx, jyc = in.jy;
             R fn[9], fo[9];
             feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
             feq9<R>(r, jxc / r, jyc / r, fo);
-            const long long o = it.pop_offset(d.pitch);
             if constexpr (MODE == PL_F16_OFFSET) {
                 // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
                 // nearest, the rest population taking the cell's corrected stored mass minus their
@@ -585,7 +612,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
                 float hn[9];
                 float res = 0.0f, sq = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hn[i] = __half2float(f[i * d.plane + o]) + (fn[i] - fo[i]);
+                for (int i = 0; i < 9; ++i) hn[i] = __half2float(fs[i]) + (fn[i] - fo[i]);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const __half qh = __float2half_rn(hn[i]);
@@ -604,7 +631,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_apply(TableView t, int pari
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const R off = R(wq<double>(i) * d.rho_ref);
-                    const R fi = decode<MODE>(f[i * d.plane + o], off);
+                    const R fi = decode<MODE>(fs[i], off);
                     f[i * d.plane + o] = encode<MODE>(fi + (fn[i] - fo[i]), off);
                 }
             }
@@ -653,7 +680,8 @@ __global__ void k_fix_final(TableView t) {
             d.partials[b * PARTIAL_STRIDE + 2] = cand;  // candidates before block b
             cand += d.partials[b * PARTIAL_STRIDE + 1];
         }
-        const double M = sum_h + (double)d.nx * (double)d.ny * d.rho_ref;
+        // the offsets are relative to the FP32 reference density the kernels use
+        const double M = sum_h + (double)d.nx * (double)d.ny * (double)(float)d.rho_ref;
         long long k = llrint((M - rec->mass0) / (double)FIX_U);
         const long long c = (long long)cand;
         if (k > c) k = c;
@@ -766,9 +794,15 @@ __global__ void k_density_noalloc(const typename Traits<MODE>::S* __restrict__ f
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const long long o = (c / nx) * pitch + c % nx;
         R P[9];
+        if constexpr (MODE == PL_F16_OFFSET) {  // offsets summed first, rho_ref added once
 #pragma unroll
-        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
-        rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+            for (int i = 0; i < 9; ++i) P[i] = __half2float(f[i * plane + o]);
+            rho[c] = ((((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7]))) + P[8]) + rho_ref;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
+            rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+        }
     }
 }
 
