@@ -47,7 +47,7 @@ class Server:
                 if jid is None:   # no room now: wait for retirements
                     break
                 waiting.popleft()
-                inflight[jid] = (r, now)
+                inflight[jid] = (r, now, intervals)
             if not inflight:
                 if reqs:
                     time.sleep(max(0.0, reqs[0].arrival_s - (time.perf_counter() - t0)))
@@ -57,10 +57,13 @@ class Server:
             intervals += 1
             for res in self.batch.poll():
                 done_at = time.perf_counter() - t0
-                r, adm = inflight.pop(res["id"])
+                r, adm, adm_interval = inflight.pop(res["id"])
                 lat.append(done_at - r.arrival_s)
                 queue_wait.append(adm - r.arrival_s)
                 work += r.job.nx * r.job.ny * res["steps"]
+                # the request (by arrival order) and its life on the device, in loop intervals
+                res.update(request=requests.index(r), admitted_s=adm, done_s=done_at,
+                           admitted_interval=adm_interval, done_interval=intervals)
                 results.append(res)
         elapsed = time.perf_counter() - t0
         arrivals = [r.arrival_s for r in requests]
