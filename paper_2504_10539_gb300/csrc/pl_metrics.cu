@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
         unsigned in_n = 0, out_n = 0;
         // geometry and pressure in the lattice's arithmetic type, sums in SumAcc
         const R nxr = R(d.nx), nyr = R(d.ny), cxr = R(d.cx), cyr = R(d.cy), rho0 = R(d.rho0), G = R(d.G);
+        const R inv_rho0 = R(1.0 / d.rho0), third = R(1.0 / 3.0), sixth = R(1.0 / 6.0);  // no divisions per cell
         const R inner = R(0.5 * Req), outer = R(Req + 4.0 * d.width);
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
@@ -303,8 +304,8 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
             if (ay > R(0.5) * nyr) ay = nyr - ay;
             const R dd = sqrt(ax * ax + ay * ay);
             const R r = rho[c];
-            const R ps = -rho0 * expm1(-r / rho0);
-            const R p = r / R(3) + G * ps * ps / R(6);
+            const R ps = -rho0 * expm1(-r * inv_rho0);
+            const R p = r * third + G * ps * ps * sixth;
             if (dd < inner) {
                 in_rho.add(r);
                 in_p.add(p);

@@ -44,7 +44,6 @@ struct StepCfg {
     static constexpr int threads = MODE == PL_F16_OFFSET ? 32 : 128;
     static constexpr int min_blocks = MODE == PL_F16_OFFSET ? 17 : (MODE == PL_F32 ? 4 : 2);
 };
-constexpr int STEP_THREADS = 128;  // the largest block of the step kernel
 
 template <int MODE> struct Pair;
 template <> struct Pair<PL_F64> {
