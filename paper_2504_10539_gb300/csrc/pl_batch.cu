@@ -149,7 +149,8 @@ struct pl_batch {
         int laplace;
     };
     std::vector<Pending> pending;
-    std::vector<float> h_weights;
+    float* h_weights;           // pinned staging of the FP32 weight blob
+    cudaEvent_t ev_w;           // its last upload (the buffer is rewritten only after it)
     std::vector<pl_droplet> h_drops;
     cudaEvent_t ev[3];          // interval start, end of the K steps, end of the interval
     DevRecord* h_live;          // pinned, max_jobs slots (pl_batch_metrics)
@@ -297,10 +298,15 @@ PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_
     b->rows_per_chunk = 32;
     b->h_records = nullptr;
     b->h_live = nullptr;
+    b->h_weights = nullptr;
+    b->ev_w = nullptr;
     b->ev[0] = b->ev[1] = b->ev[2] = nullptr;
-    // pinned host slots for records (host allocations; no device memory is allocated)
+    // pinned host slots for records and the weight upload (host allocations; no device
+    // memory is allocated)
     cudaError_t e = cudaMallocHost(&b->h_records, sizeof(DevRecord) * (size_t)max_jobs);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_live, sizeof(DevRecord) * (size_t)max_jobs);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_weights, sizeof(float) * (size_t)MLP_BLOB);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_w, cudaEventDisableTiming);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     for (int s = max_jobs - 1; s >= 0; --s) b->free_slots.push_back(s);
     // empty table on the device, step counter zero
@@ -311,6 +317,8 @@ PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_
         (void)cudaGetLastError();
         if (b->h_records) cudaFreeHost(b->h_records);
         if (b->h_live) cudaFreeHost(b->h_live);
+        if (b->h_weights) cudaFreeHost(b->h_weights);
+        if (b->ev_w) cudaEventDestroy(b->ev_w);
         for (int k = 0; k < 3; ++k)
             if (b->ev[k]) cudaEventDestroy(b->ev[k]);
         delete b;
@@ -325,9 +333,12 @@ PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* blob, size_t n) {
     if (!b || !blob || n != (size_t)MLP_BLOB) return PL_ERR_INVALID_ARG;
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(blob[k])) return PL_ERR_INVALID_ARG;
-    b->h_weights.assign(blob, blob + n);
+    // the pinned staging buffer may still feed the previous upload: wait for that one
+    PL_CUDA(cudaEventSynchronize(b->ev_w));
+    std::memcpy(b->h_weights, blob, n * sizeof(float));
     float* w32 = reinterpret_cast<float*>(b->base + b->H.w32);
-    PL_CUDA(cudaMemcpyAsync(w32, b->h_weights.data(), n * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+    PL_CUDA(cudaMemcpyAsync(w32, b->h_weights, n * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+    PL_CUDA(cudaEventRecord(b->ev_w, b->stream));
     PL_CUDA(launch_convert_weights_bf16(w32, reinterpret_cast<uint16_t*>(b->base + b->H.wbf16), b->stream));
     b->weights_set = 1;
     return PL_OK;
@@ -545,6 +556,8 @@ PL_API int pl_batch_destroy(pl_batch* b) {
     drop_graphs(b);
     if (b->h_records) cudaFreeHost(b->h_records);
     if (b->h_live) cudaFreeHost(b->h_live);
+    if (b->h_weights) cudaFreeHost(b->h_weights);
+    if (b->ev_w) cudaEventDestroy(b->ev_w);
     for (int k = 0; k < 3; ++k)
         if (b->ev[k]) cudaEventDestroy(b->ev[k]);
     delete b;
