@@ -207,25 +207,38 @@ static int autotune(pl_batch* b, int force) {
     cudaEvent_t e0, e1;
     PL_CUDA(cudaEventCreate(&e0));
     PL_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int best_r = b->rows_per_chunk;
-    for (int r : TUNE_CANDIDATES) {
-        b->rows_per_chunk = r;
-        rebuild_table(b);
-        int st = upload_table(b);
-        if (st) return st;
-        PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));  // warm-up
-        PL_CUDA(cudaEventRecord(e0, b->stream));
-        for (int k = 0; k < 3; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));
-        PL_CUDA(cudaEventRecord(e1, b->stream));
-        PL_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        PL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_r = r;
+    // Every trial launch reads the same buffer and writes the other (same parity): the state
+    // is unchanged.  The device is warmed up first (clocks ramp up under load), then every
+    // candidate is timed in two passes of opposite order, keeping its best time, so that no
+    // candidate profits from running later than the others.
+    const int nc = (int)(sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0]));
+    float t_best[sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0])];
+    for (int c = 0; c < nc; ++c) t_best[c] = 1e30f;
+    for (int k = 0; k < 20; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < nc; ++q) {
+            const int c = pass == 0 ? q : nc - 1 - q;
+            b->rows_per_chunk = TUNE_CANDIDATES[c];
+            rebuild_table(b);
+            int st = upload_table(b);
+            if (st) return st;
+            PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));  // warm-up
+            PL_CUDA(cudaEventRecord(e0, b->stream));
+            for (int k = 0; k < 3; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));
+            PL_CUDA(cudaEventRecord(e1, b->stream));
+            PL_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            PL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < t_best[c]) t_best[c] = ms;
         }
     }
+    int best_r = TUNE_CANDIDATES[0];
+    float best = 1e30f;
+    for (int c = 0; c < nc; ++c)
+        if (t_best[c] < best) {
+            best = t_best[c];
+            best_r = TUNE_CANDIDATES[c];
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->rows_per_chunk = best_r;
