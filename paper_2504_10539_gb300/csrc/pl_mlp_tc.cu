@@ -118,7 +118,7 @@ __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::a
 __device__ __forceinline__ void wg_bar(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(wg + 1) : "memory"); }
 
 // Warpgroup-wide AND (named barrier wg+1): every thread of the group gets the same
-// verdict, so a timeout seen by one thread makes the whole group leave together.
+// answer, so a timeout seen by one thread makes the whole group leave together.
 __device__ __forceinline__ bool wg_all(int wg, bool v) {
     uint32_t r;
     asm volatile(

@@ -510,7 +510,7 @@ def test_correction_moves_interface_density_toward_network():
 def test_correction_rejects_nonphysical_result():
     f = _droplet_state()
     f0 = f.copy()
-    # rho^ = 200 * tanh(tanh(tanh(tanh(2 x^)))) spans about +-100 across the box; the
+    # rho^ = 200 * tanh(tanh(tanh(tanh(2 x^)))) spans about +-100 across the domain; the
     # projection removes only the m-weighted mean, so interface cells on the left go negative
     dims = wl.MLP_DIMS
     blob = np.zeros(wl.mlp_blob_size(), dtype=np.float32)
