@@ -62,6 +62,14 @@ def lib():
         L.orc_mass.argtypes = [i, i, _dp]
         L.orc_run.restype = i
         L.orc_run.argtypes = [i, i, _dp, i, ctypes.c_long, i, d, d, d, _fp, i, d, d, d]
+        L.orc_mlp_blob_size_n.restype = ctypes.c_long
+        L.orc_mlp_blob_size_n.argtypes = [i]
+        L.orc_mlp_forward_n.argtypes = [_fp, i, i, _dp, _dp]
+        L.orc_mlp_field_n.argtypes = [i, i, _fp, i, i, vp, _dp]
+        L.orc_correct_n.restype = i
+        L.orc_correct_n.argtypes = [i, i, _dp, _fp, i, i, vp, d, d, d]
+        L.orc_run_n.restype = i
+        L.orc_run_n.argtypes = [i, i, _dp, i, ctypes.c_long, i, d, d, d, _fp, i, i, d, d, d]
         L.orc_num_threads.restype = i
         L.orc_set_num_threads.argtypes = [i]
         L.orc_lattice_tables.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
@@ -219,8 +227,10 @@ MLP_F64 = 0
 MLP_BF16 = 1
 
 
-def mlp_blob_size():
-    return lib().orc_mlp_blob_size()
+def mlp_blob_size(n_in=2):
+    """Weight blob length for n_in network inputs (2: the paper's (x^, y^); 11: with the
+    density stencil)."""
+    return lib().orc_mlp_blob_size_n(int(n_in))
 
 
 def mlp_forward(blob, xh, yh, mode=MLP_F64):
@@ -229,29 +239,43 @@ def mlp_forward(blob, xh, yh, mode=MLP_F64):
     return out
 
 
-def mlp_field(blob, nx, ny, mode=MLP_F64):
-    out = np.zeros((3, ny, nx))
-    lib().orc_mlp_field(nx, ny, _f(np.ascontiguousarray(blob, dtype=np.float32)), mode, _d(out))
+def mlp_forward_n(blob, inputs, mode=MLP_F64):
+    """Network on an explicit input vector (2 or 11 values)."""
+    x = np.ascontiguousarray(inputs, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_mlp_forward_n(_f(np.ascontiguousarray(blob, dtype=np.float32)), mode, int(x.size), _d(x), _d(out))
     return out
 
 
-def correct(f, blob, beta_rho, beta_u, M0, mode=MLP_F64, mlp_out=None):
+def mlp_field(blob, nx, ny, mode=MLP_F64, n_in=2, rho=None):
+    """Network outputs on every cell, (3, ny, nx); n_in = 11 reads the density field rho."""
+    out = np.zeros((3, ny, nx))
+    r = None
+    if n_in == 11:
+        r = np.ascontiguousarray(rho, dtype=np.float64)
+        assert r.shape == (ny, nx)
+    lib().orc_mlp_field_n(nx, ny, _f(np.ascontiguousarray(blob, dtype=np.float32)), mode, int(n_in),
+                          None if r is None else r.ctypes.data, _d(out))
+    return out
+
+
+def correct(f, blob, beta_rho, beta_u, M0, mode=MLP_F64, mlp_out=None, n_in=2):
     """Apply the interface correction to f in place; returns the status (0 or -4)."""
     _, ny, nx = f.shape
     b = np.ascontiguousarray(blob, dtype=np.float32)
     out3 = None
     if mlp_out is not None:
         out3 = np.ascontiguousarray(mlp_out, dtype=np.float64)
-    return lib().orc_correct(nx, ny, _d(f), _f(b), mode, None if out3 is None else out3.ctypes.data,
-                             beta_rho, beta_u, M0)
+    return lib().orc_correct_n(nx, ny, _d(f), _f(b), mode, int(n_in), None if out3 is None else out3.ctypes.data,
+                               beta_rho, beta_u, M0)
 
 
 def run(f, nsteps, G, tau, rho0=1.0, K=0, blob=None, mode=MLP_F64, beta_rho=0.1, beta_u=0.01,
-        M0=None, step0=0):
+        M0=None, step0=0, n_in=2):
     """Coupled run (Sec. II-C): nsteps of Eq. 1, correction after every K-th step."""
     _, ny, nx = f.shape
     if M0 is None:
         M0 = mass(f)
     b = None if blob is None else np.ascontiguousarray(blob, dtype=np.float32)
-    return lib().orc_run(nx, ny, _d(f), int(nsteps), int(step0), int(K), G, tau, rho0,
-                         None if b is None else _f(b), mode, beta_rho, beta_u, M0)
+    return lib().orc_run_n(nx, ny, _d(f), int(nsteps), int(step0), int(K), G, tau, rho0,
+                           None if b is None else _f(b), mode, int(n_in), beta_rho, beta_u, M0)

@@ -391,21 +391,27 @@ void orc_laplace(int nx, int ny, const double* rho, double cx, double cy, double
  * Network N(x, y) -> (rho, u_x, u_y) (Sec. II-B Eq. 2, Sec. III-B): inputs 2,
  * hidden [64, 128, 128, 64] with tanh, output 3 (linear: the paper lists tanh
  * for the hidden layers only).  Weight blob (float32, row-major W[out][in]):
- *   W1[64x2] b1[64] W2[128x64] b2[128] W3[128x128] b3[128] W4[64x128] b4[64] W5[3x64] b5[3].
+ *   W1[64 x n_in] b1[64] W2[128x64] b2[128] W3[128x128] b3[128] W4[64x128] b4[64] W5[3x64] b5[3].
+ * n_in = 2: the paper's inputs, the cell centre (x^, y^).  n_in = 11: a cell-feature
+ * stencil variant (not in the paper): (x^, y^) followed by the density of the cell and
+ * of its 8 neighbours, in the velocity order c_0 .. c_8, periodic.
  * mode 0: everything in FP64.
  * mode 1: BF16 emulation of the tensor-core form: h1, h2, h3 (the operands of
  *         layers 2-4) are rounded to BF16 (round to nearest even) after tanh,
  *         W2, W3, W4 are rounded to BF16, products and sums are FP64; layer 1,
  *         h4 and layer 5 stay at full precision.
  * ------------------------------------------------------------------------- */
-#define MLP_NIN 2
-static const int MLP_DIMS[6] = {MLP_NIN, 64, 128, 128, 64, 3};
+static const int MLP_HIDDEN[5] = {64, 128, 128, 64, 3};  /* outputs of layers 1..5 */
 
-long orc_mlp_blob_size(void) {
+static int mlp_dim(int n_in, int l) { return l == 0 ? n_in : MLP_HIDDEN[l - 1]; }  /* input width of layer l+1 */
+
+long orc_mlp_blob_size_n(int n_in) {
     long n = 0;
-    for (int l = 0; l < 5; ++l) n += (long)MLP_DIMS[l + 1] * MLP_DIMS[l] + MLP_DIMS[l + 1];
+    for (int l = 0; l < 5; ++l) n += (long)MLP_HIDDEN[l] * mlp_dim(n_in, l) + MLP_HIDDEN[l];
     return n;
 }
+
+long orc_mlp_blob_size(void) { return orc_mlp_blob_size_n(2); }
 
 /* Round a double to the nearest BF16 value (8 significant bits), ties to even. */
 double orc_round_bf16(double v) {
@@ -417,13 +423,13 @@ double orc_round_bf16(double v) {
     return ldexp(s, e - 8);
 }
 
-void orc_mlp_forward(const float* blob, int mode, double xh, double yh, double* out) {
+/* Forward pass on n_in inputs `in`; writes the 3 outputs. */
+void orc_mlp_forward_n(const float* blob, int mode, int n_in, const double* in, double* out) {
     double a[128], z[128];
-    a[0] = xh;
-    a[1] = yh;
+    for (int k = 0; k < n_in; ++k) a[k] = in[k];
     const float* p = blob;
     for (int l = 0; l < 5; ++l) {
-        int nin = MLP_DIMS[l], nout = MLP_DIMS[l + 1];
+        int nin = mlp_dim(n_in, l), nout = MLP_HIDDEN[l];
         const float* W = p;
         const float* b = p + (long)nout * nin;
         p = b + nout;
@@ -449,6 +455,11 @@ void orc_mlp_forward(const float* blob, int mode, double xh, double yh, double* 
     }
 }
 
+void orc_mlp_forward(const float* blob, int mode, double xh, double yh, double* out) {
+    const double in[2] = {xh, yh};
+    orc_mlp_forward_n(blob, mode, 2, in, out);
+}
+
 /* Network input for cell (x, y): the cell centre mapped to [-1, 1]
  * (the paper says only "x, y coordinates"; the normalisation is the reading used). */
 void orc_mlp_inputs(int nx, int ny, int x, int y, double* xh, double* yh) {
@@ -456,20 +467,38 @@ void orc_mlp_inputs(int nx, int ny, int x, int y, double* xh, double* yh) {
     *yh = 2.0 * ((double)y + 0.5) / (double)ny - 1.0;
 }
 
-void orc_mlp_field(int nx, int ny, const float* blob, int mode, double* out3) {
+/* The n_in inputs of cell (x, y); rho (nx*ny) is read only for n_in = 11. */
+void orc_mlp_features(int nx, int ny, const double* rho, int n_in, int x, int y, double* in) {
+    orc_mlp_inputs(nx, ny, x, y, &in[0], &in[1]);
+    if (n_in == 11) {
+        int cx[Q], cy[Q];
+        double w[Q];
+        orc_lattice_tables(cx, cy, w);
+        for (int i = 0; i < Q; ++i) {
+            int xn = (x + cx[i] + nx) % nx, yn = (y + cy[i] + ny) % ny;
+            in[2 + i] = rho[(long)yn * nx + xn];
+        }
+    }
+}
+
+void orc_mlp_field_n(int nx, int ny, const float* blob, int mode, int n_in, const double* rho, double* out3) {
     const long N = (long)nx * ny;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < ny; ++y) {
         for (int x = 0; x < nx; ++x) {
-            double xh, yh, o[3];
-            orc_mlp_inputs(nx, ny, x, y, &xh, &yh);
-            orc_mlp_forward(blob, mode, xh, yh, o);
+            double in[11], o[3];
+            orc_mlp_features(nx, ny, rho, n_in, x, y, in);
+            orc_mlp_forward_n(blob, mode, n_in, in, o);
             long c = (long)y * nx + x;
             out3[c] = o[0];
             out3[N + c] = o[1];
             out3[2 * N + c] = o[2];
         }
     }
+}
+
+void orc_mlp_field(int nx, int ny, const float* blob, int mode, double* out3) {
+    orc_mlp_field_n(nx, ny, blob, mode, 2, NULL, out3);
 }
 
 /* ---------------------------------------------------------------------------
@@ -489,8 +518,8 @@ void orc_mlp_field(int nx, int ny, const float* blob, int mode, double* out3) {
  * which case f is left unchanged.  The network's output field may be supplied
  * precomputed (out3 != NULL, layout of orc_mlp_field) or is evaluated here.
  * ------------------------------------------------------------------------- */
-int orc_correct(int nx, int ny, double* f, const float* blob, int mlp_mode, const double* out3_in,
-                double beta_rho, double beta_u, double M0) {
+int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, int n_in, const double* out3_in,
+                  double beta_rho, double beta_u, double M0) {
     const long N = (long)nx * ny;
     double* rho = (double*)malloc(sizeof(double) * N);
     double* jx = (double*)malloc(sizeof(double) * N);
@@ -507,7 +536,7 @@ int orc_correct(int nx, int ny, double* f, const float* blob, int mlp_mode, cons
     if (out3_in)
         memcpy(out3, out3_in, sizeof(double) * 3 * N);
     else
-        orc_mlp_field(nx, ny, blob, mlp_mode, out3);
+        orc_mlp_field_n(nx, ny, blob, mlp_mode, n_in, rho, out3);  /* the stencil reads this state */
 
     double gmax = 0.0;
     for (long c = 0; c < N; ++c)
@@ -552,6 +581,11 @@ int orc_correct(int nx, int ny, double* f, const float* blob, int mlp_mode, cons
     return status;
 }
 
+int orc_correct(int nx, int ny, double* f, const float* blob, int mlp_mode, const double* out3_in,
+                double beta_rho, double beta_u, double M0) {
+    return orc_correct_n(nx, ny, f, blob, mlp_mode, 2, out3_in, beta_rho, beta_u, M0);
+}
+
 /* Total mass sum_c sum_i f_i (cell order, directions 0..8 within a cell). */
 double orc_mass(int nx, int ny, const double* f) {
     const long N = (long)nx * ny;
@@ -571,13 +605,14 @@ double orc_mass(int nx, int ny, const double* f) {
  * lattice's step count on entry.  M0 is the reference mass of the projection.
  * Returns the first nonzero status (the run stops there), else 0.
  * ------------------------------------------------------------------------- */
-int orc_run(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
-            double rho0, const float* blob, int mlp_mode, double beta_rho, double beta_u, double M0) {
+int orc_run_n(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
+              double rho0, const float* blob, int mlp_mode, int n_in, double beta_rho, double beta_u, double M0) {
     const long N = (long)nx * ny;
     double* out3 = NULL;
-    if (K > 0 && blob) {
-        /* The network depends on coordinates and weights only, so its field is
-         * the same at every correction of this run. */
+    if (K > 0 && blob && n_in == 2) {
+        /* The paper's network depends on coordinates and weights only, so its field
+         * is the same at every correction of this run (the stencil variant reads the
+         * state and is evaluated at each correction). */
         out3 = (double*)malloc(sizeof(double) * 3 * N);
         orc_mlp_field(nx, ny, blob, mlp_mode, out3);
     }
@@ -585,8 +620,13 @@ int orc_run(int nx, int ny, double* f, int nsteps, long step0, int K, double G, 
     for (int s = 1; s <= nsteps && st == 0; ++s) {
         st = orc_step(nx, ny, f, 1, G, tau, rho0);
         if (st == 0 && K > 0 && blob && ((step0 + s) % K) == 0)
-            st = orc_correct(nx, ny, f, blob, mlp_mode, out3, beta_rho, beta_u, M0);
+            st = orc_correct_n(nx, ny, f, blob, mlp_mode, n_in, out3, beta_rho, beta_u, M0);
     }
     free(out3);
     return st;
+}
+
+int orc_run(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
+            double rho0, const float* blob, int mlp_mode, double beta_rho, double beta_u, double M0) {
+    return orc_run_n(nx, ny, f, nsteps, step0, K, G, tau, rho0, blob, mlp_mode, 2, beta_rho, beta_u, M0);
 }

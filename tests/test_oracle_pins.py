@@ -426,6 +426,59 @@ def test_mlp_single_path_composition():
     assert out[0] == 0.0 and out[2] == 0.0
 
 
+# ----------------------------------------------------------------------------- stencil-input network
+# A variant that is not in the paper: the network also reads the density of the cell and its
+# 8 neighbours (inputs 2..10, velocity order c_0..c_8, periodic).
+
+STENCIL_DIMS = (11, 64, 128, 128, 64, 3)
+
+
+def test_stencil_network_blob_size_and_zero_weights():
+    n = wl.mlp_blob_size(STENCIL_DIMS)
+    assert O.mlp_blob_size(11) == n == wl.mlp_blob_size() + 64 * 9
+    blob = np.zeros(n, dtype=np.float32)
+    blob[-3:] = [0.5, -0.25, 0.125]
+    out = O.mlp_forward_n(blob, np.arange(11) * 0.1, O.MLP_F64)
+    assert np.array_equal(out, [0.5, -0.25, 0.125])
+
+
+def test_stencil_network_gathers_each_neighbour_periodically():
+    """A single path from input 2 + i to output 0 gives tanh^4 of the density of neighbour
+    c_i, which numpy's roll of the density field fixes independently of the oracle's gather."""
+    nx, ny = 7, 5
+    rho = np.random.default_rng(31).uniform(0.1, 2.0, (ny, nx))
+    cx, cy, _ = O.lattice_tables()
+    offs = _offsets(STENCIL_DIMS)
+    for i in range(9):
+        blob = np.zeros(wl.mlp_blob_size(STENCIL_DIMS), dtype=np.float32)
+        blob[offs[0][0] + 0 * 11 + 2 + i] = 1.0
+        for l in range(1, 5):
+            blob[offs[l][0]] = 1.0          # W_l[0][0]
+        out = O.mlp_field(blob, nx, ny, O.MLP_F64, n_in=11, rho=rho)
+        neighbour = np.roll(rho, shift=(-int(cy[i]), -int(cx[i])), axis=(0, 1))
+        assert np.allclose(out[0], np.tanh(np.tanh(np.tanh(np.tanh(neighbour)))), rtol=0, atol=1e-15), i
+        assert np.all(out[1] == 0.0) and np.all(out[2] == 0.0)
+
+
+def test_stencil_network_is_odd_without_biases():
+    blob = wl.mlp_weights(24, dims=STENCIL_DIMS, zero_bias=True)
+    rng = np.random.default_rng(25)
+    for _ in range(20):
+        v = rng.uniform(-2, 2, 11)
+        assert np.allclose(O.mlp_forward_n(blob, -v), -O.mlp_forward_n(blob, v), rtol=0, atol=1e-14)
+
+
+def test_stencil_network_coupled_run_keeps_mass_and_momentum():
+    n = 32
+    f = O.init_equilibrium(O.init_rho(n, n, [(16.0, 16.0, 7.0)], 2.0, 0.15, 2.0, 0.01, 5))
+    M0 = O.mass(f)
+    P0 = np.array(O.momentum(f)).sum(axis=(1, 2))
+    blob = wl.mlp_weights(26, dims=STENCIL_DIMS)
+    assert O.run(f, 100, -5.5, 1.0, K=50, blob=blob, M0=M0, n_in=11) == 0
+    assert abs(O.mass(f) - M0) < 1e-12 * M0
+    assert np.abs(np.array(O.momentum(f)).sum(axis=(1, 2)) - P0).max() < 1e-10
+
+
 def test_mlp_bf16_emulation_close_to_fp64():
     blob = wl.mlp_weights(22)
     rng = np.random.default_rng(23)
