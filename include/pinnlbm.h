@@ -84,6 +84,11 @@ typedef struct pl_params {
     double beta_rho;  /* correction gain on density  (default 0.1)              */
     double beta_u;    /* correction gain on momentum (default 0.01)             */
     double threshold; /* Eq. 9 gradient threshold    (default 0.01)             */
+    int32_t mlp_in;   /* network inputs: 2 = the paper's cell centre (x^, y^)    */
+                      /* (default); 11 = (x^, y^) and the density of the cell   */
+                      /* and its 8 neighbours in velocity order c_0..c_8        */
+                      /* (a stencil variant the paper does not have)            */
+    int32_t reserved; /* 0                                                      */
 } pl_params;
 
 /* One droplet of the initial state: centre (cx, cy) in lattice units, radius r. */
@@ -143,9 +148,12 @@ PL_API int pl_lattice_init_rho(pl_lattice* lat, const double* host_rho);
 
 /* Network weights (Sec. III-B, 2 -> 64 -> 128 -> 128 -> 64 -> 3, tanh hidden, linear output):
  * FP32 blob W1[64x2] b1[64] W2[128x64] b2[128] W3[128x128] b3[128] W4[64x128] b4[64] W5[3x64] b5[3],
- * row-major W[out][in]; n must equal pl_mlp_blob_size().  Copied to the device
+ * row-major W[out][in]; n must equal pl_mlp_blob_size_for(params.mlp_in).  Copied to the device
  * (and converted to the tensor-core operand layout) on the lattice's stream. */
 PL_API int pl_mlp_blob_size(void);
+/* Blob length for a network with mlp_in inputs (2 or 11; W1 is 64 x mlp_in), or
+ * PL_ERR_INVALID_ARG for another input count. */
+PL_API int pl_mlp_blob_size_for(int32_t mlp_in);
 PL_API int pl_set_mlp_weights(pl_lattice* lat, const float* host_blob, size_t n);
 
 /* n >= 0 time steps of Eq. 1 on the device (no host synchronisation). */

@@ -37,7 +37,8 @@ class pl_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("mlp", ctypes.c_int32), ("G", ctypes.c_double), ("tau", ctypes.c_double),
                 ("rho0", ctypes.c_double), ("rho_ref", ctypes.c_double), ("beta_rho", ctypes.c_double),
-                ("beta_u", ctypes.c_double), ("threshold", ctypes.c_double)]
+                ("beta_u", ctypes.c_double), ("threshold", ctypes.c_double), ("mlp_in", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class pl_droplet(ctypes.Structure):
@@ -99,6 +100,7 @@ def _L():
             "pl_lattice_init_droplets": (ctypes.c_int, [vp, P(pl_droplet), ctypes.c_int, d, d, d, d, u64]),
             "pl_lattice_init_rho": (ctypes.c_int, [vp, P(d)]),
             "pl_mlp_blob_size": (ctypes.c_int, []),
+            "pl_mlp_blob_size_for": (ctypes.c_int, [ctypes.c_int32]),
             "pl_set_mlp_weights": (ctypes.c_int, [vp, P(ctypes.c_float), sz]),
             "pl_step": (ctypes.c_int, [vp, i32]),
             "pl_apply_correction": (ctypes.c_int, [vp]),
@@ -204,6 +206,12 @@ def pl_mlp_blob_size() -> int:
     return _L().pl_mlp_blob_size()
 
 
+def pl_mlp_blob_size_for(mlp_in: int) -> int:
+    n = _L().pl_mlp_blob_size_for(mlp_in)
+    _chk("pl_mlp_blob_size_for", min(n, 0))
+    return n
+
+
 def pl_set_mlp_weights(h, blob: np.ndarray):
     b = np.ascontiguousarray(blob, dtype=np.float32)
     return _chk("pl_set_mlp_weights", _L().pl_set_mlp_weights(
@@ -296,9 +304,7 @@ class Lattice:
     @classmethod
     def from_workload(cls, job, device="cuda", stream=None):
         """Build, initialise and load weights for a ``workloads.Lattice`` description."""
-        p = pl_params_default(job.nx, job.ny, storage=job.storage, mlp=job.mlp, G=job.G, tau=job.tau,
-                              rho0=job.rho0, rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u)
-        lat = cls(p, device=device, stream=stream)
+        lat = cls(job_params(job), device=device, stream=stream)
         lat.init_droplets(job.droplets, job.rho_in, job.rho_out, job.width, job.noise_amp, job.seed)
         if job.K > 0:
             lat.set_weights(job.weights())
@@ -444,7 +450,8 @@ def pl_batch_destroy(h):
 def job_params(job) -> pl_params:
     """C parameters of a ``workloads.Lattice`` description."""
     return pl_params_default(job.nx, job.ny, storage=job.storage, mlp=job.mlp, G=job.G, tau=job.tau, rho0=job.rho0,
-                             rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u)
+                             rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u,
+                             mlp_in=getattr(job, "mlp_in", 2))
 
 
 class Batch:

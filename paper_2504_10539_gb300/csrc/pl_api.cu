@@ -36,6 +36,7 @@ int check_params(const pl_params* p) {
     if (!std::isfinite(p->rho_ref) || !std::isfinite(p->beta_rho) || !std::isfinite(p->beta_u) ||
         !std::isfinite(p->threshold))
         return PL_ERR_INVALID_ARG;
+    if (p->mlp_in != 2 && p->mlp_in != 11) return PL_ERR_INVALID_ARG;
     return PL_OK;
 }
 
@@ -178,7 +179,7 @@ SingleLayout single_layout(const pl_params* p) {
     S.table = o;
     o = align_up(o + Table::bytes(1));
     S.w32 = o;
-    o = align_up(o + (size_t)MLP_BLOB * sizeof(float));
+    o = align_up(o + (size_t)MLP_BLOB_MAX * sizeof(float));
     S.wbf16 = o;
     o = align_up(o + bf16_weight_elems() * sizeof(uint16_t));
     S.droplets = o;
@@ -260,10 +261,16 @@ int pl_params_default(pl_params* p, int32_t nx, int32_t ny) {
     p->beta_rho = 0.1;
     p->beta_u = 0.01;
     p->threshold = 0.01;
+    p->mlp_in = 2;
     return PL_OK;
 }
 
 int pl_mlp_blob_size(void) { return MLP_BLOB; }
+
+int pl_mlp_blob_size_for(int32_t mlp_in) {
+    if (mlp_in != 2 && mlp_in != 11) return PL_ERR_INVALID_ARG;
+    return mlp_blob(mlp_in);
+}
 
 int pl_lattice_bytes(const pl_params* p, size_t* bytes_out) {
     int st = check_params(p);
@@ -367,12 +374,12 @@ int pl_lattice_init_rho(pl_lattice* L, const double* host_rho) {
 }
 
 int pl_set_mlp_weights(pl_lattice* L, const float* blob, size_t n) {
-    if (!L || !blob || n != (size_t)MLP_BLOB) return PL_ERR_INVALID_ARG;
+    if (!L || !blob || n != (size_t)mlp_blob(L->p.mlp_in)) return PL_ERR_INVALID_ARG;
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(blob[k])) return PL_ERR_INVALID_ARG;
     L->h_weights.assign(blob, blob + n);
     PL_CUDA(cudaMemcpyAsync(L->w32, L->h_weights.data(), n * sizeof(float), cudaMemcpyHostToDevice, L->stream));
-    PL_CUDA(launch_convert_weights_bf16(L->w32, L->wbf16, L->stream));
+    PL_CUDA(launch_convert_weights_bf16(L->w32, L->wbf16, L->p.mlp_in, L->stream));
     L->weights_set = 1;
     return PL_OK;
 }
@@ -395,7 +402,7 @@ int pl_step(pl_lattice* L, int32_t n) {
 int pl_apply_correction(pl_lattice* L) {
     if (!L) return PL_ERR_INVALID_ARG;
     if (!L->initialised || !L->weights_set) return PL_ERR_STATE;
-    PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, L->cur, L->p.mlp, L->w32, L->wbf16, L->stream));
+    PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, L->cur, L->p.mlp, L->p.mlp_in, L->w32, L->wbf16, L->stream));
     return PL_OK;
 }
 
@@ -407,7 +414,7 @@ static int enqueue_run(pl_lattice* L, int nsteps, int K, long long step0, int pa
         PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, cur, L->stream));
         cur ^= 1;
         if (K > 0 && ((step0 + s) % K) == 0)
-            PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, cur, L->p.mlp, L->w32, L->wbf16, L->stream));
+            PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, cur, L->p.mlp, L->p.mlp_in, L->w32, L->wbf16, L->stream));
     }
     return PL_OK;
 }
@@ -543,7 +550,8 @@ int pl_get_mlp_field(pl_lattice* L, double* host_out3) {
     if (!L || !host_out3) return PL_ERR_INVALID_ARG;
     if (!L->weights_set || !L->initialised) return PL_ERR_STATE;
     const size_t N3 = 3 * (size_t)L->p.nx * L->p.ny;
-    PL_CUDA(launch_mlp_tab(L->tab.view, L->p.storage, L->p.mlp, L->w32, L->wbf16, L->stream));
+    if (L->p.mlp_in == 11) PL_CUDA(launch_moments_tab(L->tab.view, L->p.storage, L->cur, L->stream));
+    PL_CUDA(launch_mlp_tab(L->tab.view, L->p.storage, L->p.mlp, L->p.mlp_in, L->w32, L->wbf16, L->stream));
     const void* out3 = L->tab.d[0].out3;
     if (L->p.storage == PL_F64) {
         PL_CUDA(cudaMemcpyAsync(host_out3, out3, N3 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));

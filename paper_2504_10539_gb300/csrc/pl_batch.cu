@@ -106,7 +106,7 @@ Head head_layout(int max_jobs) {
     Head h;
     size_t o = 0;
     h.w32 = o;
-    o = align_up(o + (size_t)MLP_BLOB * sizeof(float));
+    o = align_up(o + (size_t)MLP_BLOB_MAX * sizeof(float));
     h.wbf16 = o;
     o = align_up(o + bf16_weight_elems() * sizeof(uint16_t));
     h.table = o;
@@ -149,6 +149,7 @@ struct pl_batch {
         int laplace;
     };
     std::vector<Pending> pending;
+    int mlp_in;                 // network inputs of every job (0 until weights or a job fix it)
     float* h_weights;           // pinned staging of the FP32 weight blob
     cudaEvent_t ev_w;           // its last upload (the buffer is rewritten only after it)
     std::vector<pl_droplet> h_drops;
@@ -258,7 +259,8 @@ static int enqueue_interval(pl_batch* b, int parity, bool captured) {
         cur ^= 1;
     }
     PL_CUDA(cudaEventRecordWithFlags(b->ev[1], b->stream, flags));
-    PL_CUDA(launch_correction_tab(b->tab.view, b->storage, cur, b->mlp, reinterpret_cast<const float*>(b->base + b->H.w32),
+    PL_CUDA(launch_correction_tab(b->tab.view, b->storage, cur, b->mlp, b->mlp_in,
+                                  reinterpret_cast<const float*>(b->base + b->H.w32),
                                   reinterpret_cast<const uint16_t*>(b->base + b->H.wbf16), b->stream));
     PL_CUDA(launch_metrics_tab(b->tab.view, b->storage, cur, 0, 1, b->stream));
     PL_CUDA(cudaEventRecordWithFlags(b->ev[2], b->stream, flags));
@@ -313,12 +315,13 @@ PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_
     b->h_live = nullptr;
     b->h_weights = nullptr;
     b->ev_w = nullptr;
+    b->mlp_in = 0;
     b->ev[0] = b->ev[1] = b->ev[2] = nullptr;
     // pinned host slots for records and the weight upload (host allocations; no device
     // memory is allocated)
     cudaError_t e = cudaMallocHost(&b->h_records, sizeof(DevRecord) * (size_t)max_jobs);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_live, sizeof(DevRecord) * (size_t)max_jobs);
-    if (e == cudaSuccess) e = cudaMallocHost(&b->h_weights, sizeof(float) * (size_t)MLP_BLOB);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_weights, sizeof(float) * (size_t)MLP_BLOB_MAX);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_w, cudaEventDisableTiming);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&b->ev[k]);
     for (int s = max_jobs - 1; s >= 0; --s) b->free_slots.push_back(s);
@@ -343,7 +346,10 @@ PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_
 }
 
 PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* blob, size_t n) {
-    if (!b || !blob || n != (size_t)MLP_BLOB) return PL_ERR_INVALID_ARG;
+    if (!b || !blob) return PL_ERR_INVALID_ARG;
+    // the blob's length gives the network's input count, which all jobs of a batch share
+    const int n_in = n == (size_t)mlp_blob(2) ? 2 : (n == (size_t)mlp_blob(11) ? 11 : 0);
+    if (n_in == 0 || (b->mlp_in != 0 && b->mlp_in != n_in)) return PL_ERR_INVALID_ARG;
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(blob[k])) return PL_ERR_INVALID_ARG;
     // the pinned staging buffer may still feed the previous upload: wait for that one
@@ -352,7 +358,8 @@ PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* blob, size_t n) {
     float* w32 = reinterpret_cast<float*>(b->base + b->H.w32);
     PL_CUDA(cudaMemcpyAsync(w32, b->h_weights, n * sizeof(float), cudaMemcpyHostToDevice, b->stream));
     PL_CUDA(cudaEventRecord(b->ev_w, b->stream));
-    PL_CUDA(launch_convert_weights_bf16(w32, reinterpret_cast<uint16_t*>(b->base + b->H.wbf16), b->stream));
+    PL_CUDA(launch_convert_weights_bf16(w32, reinterpret_cast<uint16_t*>(b->base + b->H.wbf16), n_in, b->stream));
+    b->mlp_in = n_in;
     b->weights_set = 1;
     return PL_OK;
 }
@@ -363,6 +370,7 @@ PL_API int pl_batch_submit(pl_batch* b, const pl_params* p, const pl_droplet* d,
     int st = check_params(p);
     if (st) return st;
     if (p->storage != b->storage) return PL_ERR_INVALID_ARG;
+    if (b->mlp_in != 0 && p->mlp_in != b->mlp_in) return PL_ERR_INVALID_ARG;  // one network per batch
     if (n < 0 || n > PL_MAX_DROPLETS || (n > 0 && !d) || !(width > 0.0) || !std::isfinite(rho_in) ||
         !std::isfinite(rho_out) || !std::isfinite(noise_amp))
         return PL_ERR_INVALID_ARG;
@@ -418,6 +426,7 @@ PL_API int pl_batch_submit(pl_batch* b, const pl_params* p, const pl_droplet* d,
     if (e != cudaSuccess) return fail(e);
     b->jobs.push_back(j);
     b->mass0_pending = 1;
+    if (b->mlp_in == 0) b->mlp_in = p->mlp_in;
     rebuild_table(b);
     *job_id = j.id;
     return PL_OK;

@@ -37,7 +37,12 @@ inline size_t scratch_elem_bytes(int storage) { return storage == PL_F64 ? 8 : 4
 // even column pair, is aligned for vector access.
 inline int row_pitch(int nx) { return (nx + 7) / 8 * 8; }
 
-constexpr int MLP_BLOB = 64 * 2 + 64 + 128 * 64 + 128 + 128 * 128 + 128 + 64 * 128 + 64 + 3 * 64 + 3;
+// FP32 weight blob: W1[64 x n_in] b1 W2 b2 W3 b3 W4 b4 W5 b5 (n_in = 2 or 11)
+constexpr int mlp_blob(int n_in) {
+    return 64 * n_in + 64 + 128 * 64 + 128 + 128 * 128 + 128 + 64 * 128 + 64 + 3 * 64 + 3;
+}
+constexpr int MLP_BLOB = mlp_blob(2);
+constexpr int MLP_BLOB_MAX = mlp_blob(11);  // the size every weight buffer is laid out for
 
 int check_params(const pl_params* p);
 

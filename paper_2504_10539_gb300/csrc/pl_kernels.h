@@ -106,13 +106,16 @@ cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStr
 // Metrics of every lattice: moments, Eq. 16 gradient, Eqs. 9-15 sums (+ Laplace where defined).
 cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
                                cudaStream_t s);
-// Network field of every lattice (BF16 tensor cores or SIMT), then the correction.
-cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, const float* w32, const uint16_t* wbf16,
-                           cudaStream_t s);
-cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, const float* w32,
-                                  const uint16_t* wbf16, cudaStream_t s);
+// Density and momentum fields of every lattice (the network's stencil input reads rho).
+cudaError_t launch_moments_tab(const TableView& t, int storage, int parity, cudaStream_t s);
+// Network field of every lattice (BF16 tensor cores or SIMT) on n_in = 2 or 11 inputs (11
+// reads the density field, which must be current), then the correction.
+cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, int n_in, const float* w32,
+                           const uint16_t* wbf16, cudaStream_t s);
+cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, int n_in,
+                                  const float* w32, const uint16_t* wbf16, cudaStream_t s);
 
-cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, cudaStream_t s);
+cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, int n_in, cudaStream_t s);
 cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t s);
 size_t bf16_weight_elems();
 

@@ -736,12 +736,12 @@ __global__ void __launch_bounds__(RB_THREADS) k_fix_apply(TableView t, int parit
 }
 
 template <int MODE>
-static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, const float* w32, const uint16_t* wbf16,
-                                cudaStream_t s) {
+static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, int n_in, const float* w32,
+                                const uint16_t* wbf16, cudaStream_t s) {
     using R = typename Traits<MODE>::R;
-    cudaError_t e = launch_mlp_tab(t, MODE, mlp_mode, w32, wbf16, s);
+    k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);  // rho, j (and the stencil input)
+    cudaError_t e = launch_mlp_tab(t, MODE, mlp_mode, n_in, w32, wbf16, s);
     if (e != cudaSuccess) return e;
-    k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
     k_grad_tab<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_final_metrics_tab<<<RED_GRID, RB_THREADS, 0, s>>>(t, 0);
     k_corr_sums1<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
@@ -758,14 +758,25 @@ static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, const float* w32,
-                                  const uint16_t* wbf16, cudaStream_t s) {
+cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, int n_in,
+                                  const float* w32, const uint16_t* wbf16, cudaStream_t s) {
     switch (storage) {
-        case PL_F64: return correction_t<PL_F64>(t, parity, mlp_mode, w32, wbf16, s);
-        case PL_F32: return correction_t<PL_F32>(t, parity, mlp_mode, w32, wbf16, s);
-        case PL_F16_OFFSET: return correction_t<PL_F16_OFFSET>(t, parity, mlp_mode, w32, wbf16, s);
+        case PL_F64: return correction_t<PL_F64>(t, parity, mlp_mode, n_in, w32, wbf16, s);
+        case PL_F32: return correction_t<PL_F32>(t, parity, mlp_mode, n_in, w32, wbf16, s);
+        case PL_F16_OFFSET: return correction_t<PL_F16_OFFSET>(t, parity, mlp_mode, n_in, w32, wbf16, s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_moments_tab(const TableView& t, int storage, int parity, cudaStream_t s) {
+    switch (storage) {
+        case PL_F64: k_moments<PL_F64><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity); break;
+        case PL_F32: k_moments<PL_F32><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity); break;
+        case PL_F16_OFFSET: k_moments<PL_F16_OFFSET><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity); break;
+        default: return cudaErrorInvalidValue;
+    }
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------

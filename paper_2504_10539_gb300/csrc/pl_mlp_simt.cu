@@ -1,7 +1,8 @@
 // Correction network on CUDA cores (FP64 or FP32), arXiv 2504.10539 Sec. II-B
 // Eq. 2 and Sec. III-B: N(x, y) = (rho^, u^_x, u^_y), 2 -> 64 -> 128 -> 128 -> 64 -> 3,
 // tanh on the hidden layers, linear output.  Input: the cell centre mapped to
-// [-1, 1] (x^ = 2 (x + 0.5) / nx - 1).
+// [-1, 1] (x^ = 2 (x + 0.5) / nx - 1); with n_in = 11 (a stencil variant the paper does
+// not have) also the density of the cell and its 8 neighbours, velocity order, periodic.
 //
 // One thread per cell, 64 cells per block, persistent over the table's half tiles
 // (a 128-cell tile of lattice j is two 64-cell halves).  Activations live in shared
@@ -13,7 +14,7 @@
 
 namespace pl {
 
-cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s);
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, cudaStream_t s);
 
 constexpr int MLP_THREADS = 64;
 constexpr int MLP_CHUNK = 16;
@@ -57,7 +58,7 @@ __device__ __forceinline__ int find_tile_s(const long long* __restrict__ pre, in
 }
 
 template <typename R>
-__global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restrict__ w, TableView tab) {
+__global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restrict__ w, TableView tab, int n_in) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* bufA = reinterpret_cast<R*>(smem_raw);     // [128][MLP_THREADS]
     R* bufB = bufA + 128 * MLP_THREADS;            // [128][MLP_THREADS]
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
     const long long halves = 2 * tab.hdr->total_tiles;
     // blob offsets
     const float* W1 = w;
-    const float* b1 = W1 + 64 * 2;
+    const float* b1 = W1 + 64 * n_in;
     const float* W2 = b1 + 64;
     const float* b2 = W2 + 128 * 64;
     const float* W3 = b2 + 128;
@@ -87,7 +88,17 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
         const int x = (int)(cc % nx), y = (int)(cc / nx);
         bufA[0 * MLP_THREADS + t] = R(2) * (R(x) + R(0.5)) / R(nx) - R(1);
         bufA[1 * MLP_THREADS + t] = R(2) * (R(y) + R(0.5)) / R(ny) - R(1);
-        dense<R, true>(W1, b1, 2, 64, bufA, bufB, t);
+        if (n_in == 11) {
+            const R* rho = static_cast<const R*>(d.rho);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                int xn = x + cx(i), yn = y + cy(i);
+                xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
+                yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
+                bufA[(2 + i) * MLP_THREADS + t] = rho[(long long)yn * nx + xn];
+            }
+        }
+        dense<R, true>(W1, b1, n_in, 64, bufA, bufB, t);
         dense<R, true>(W2, b2, 64, 128, bufB, bufA, t);
         dense<R, true>(W3, b3, 128, 128, bufA, bufB, t);
         dense<R, true>(W4, b4, 128, 64, bufB, bufA, t);
@@ -101,7 +112,7 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
 }
 
 template <typename R>
-static cudaError_t mlp_simt_t(const TableView& t, const float* w32, cudaStream_t s) {
+static cudaError_t mlp_simt_t(const TableView& t, const float* w32, int n_in, cudaStream_t s) {
     const size_t smem = 2 * 128 * MLP_THREADS * sizeof(R);
     static bool attr_set = false;  // per process and instantiation (one device)
     if (!attr_set) {
@@ -109,21 +120,22 @@ static cudaError_t mlp_simt_t(const TableView& t, const float* w32, cudaStream_t
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_mlp_simt<R><<<MLP_GRID, MLP_THREADS, smem, s>>>(w32, t);
+    k_mlp_simt<R><<<MLP_GRID, MLP_THREADS, smem, s>>>(w32, t, n_in);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, const float* w32, const uint16_t* wbf16,
-                           cudaStream_t s) {
+cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, int n_in, const float* w32,
+                           const uint16_t* wbf16, cudaStream_t s) {
+    if (n_in != 2 && n_in != 11) return cudaErrorInvalidValue;
     // The output element type follows the lattice's scratch type: double for FP64 storage.
     if (storage == PL_F64) {
         if (mlp_mode != PL_MLP_F64) return cudaErrorInvalidValue;
-        return mlp_simt_t<double>(t, w32, s);
+        return mlp_simt_t<double>(t, w32, n_in, s);
     }
-    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(t, w32, wbf16, s);
+    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(t, w32, wbf16, n_in, s);
     if (mlp_mode != PL_MLP_F32) return cudaErrorInvalidValue;
-    return mlp_simt_t<float>(t, w32, s);
+    return mlp_simt_t<float>(t, w32, n_in, s);
 }
 
 }  // namespace pl

@@ -53,7 +53,9 @@ constexpr int WB_ELEMS = (128 + 128 + 64) * 16;      // bias blocks of layers 2-
 constexpr int OFF_WB = OFF_W4 + 64 * 128 * 2;        // (bias split hi + lo in K columns 0 and 1)
 constexpr int OFF_ONES = OFF_WB + WB_ELEMS * 2;      // 128 x 16 BF16 A operand: columns 0, 1 = 1
 constexpr int OFF_P = OFF_ONES + M * 16 * 2;         // FP32 parameters
-constexpr int P_W1 = 0, P_B1 = 128, P_W5 = 192, P_B5 = 384, P_N = 388;  // layers 2-4 biases: in the MMA
+// FP32 parameters of layers 1 and 5 (the biases of layers 2-4 are in the MMA): W1 as 64 rows of
+// n_in inputs, packed (n_in = 2) or padded to 12 (n_in = 11, 16-byte rows); b1; W5; b5
+constexpr int P_W1 = 0, P_B1 = 768, P_W5 = 832, P_B5 = 1024, P_N = 1028;
 constexpr int OFF_BAR = (OFF_P + P_N * 4 + 15) / 16 * 16;
 constexpr int OFF_TMEM_SLOT = OFF_BAR + 8 * (1 + NWG);
 constexpr int SMEM_USED = OFF_TMEM_SLOT + 16;
@@ -65,8 +67,21 @@ constexpr int W_IMG_ELEMS = 128 * 64 + 128 * 128 + 64 * 128 + WB_ELEMS;   // BF1
 constexpr long long WAIT_NS = 2000000000ll;                       // 2 s per wait
 
 // Blob offsets (FP32 master weights, row-major W[out][in]).
-constexpr int B_W1 = 0, B_B1 = 128, B_W2 = 192, B_B2 = B_W2 + 8192, B_W3 = B_B2 + 128, B_B3 = B_W3 + 16384,
-              B_W4 = B_B3 + 128, B_B4 = B_W4 + 8192, B_W5 = B_B4 + 64, B_B5 = B_W5 + 192;
+struct BlobOff {
+    int W1, B1, W2, B2, W3, B3, W4, B4, W5, B5;
+};
+__host__ __device__ constexpr BlobOff blob_off(int n_in) {
+    return BlobOff{0,
+                   64 * n_in,
+                   64 * n_in + 64,
+                   64 * n_in + 64 + 8192,
+                   64 * n_in + 64 + 8192 + 128,
+                   64 * n_in + 64 + 8192 + 128 + 16384,
+                   64 * n_in + 64 + 8192 + 128 + 16384 + 128,
+                   64 * n_in + 64 + 8192 + 128 + 16384 + 128 + 8192,
+                   64 * n_in + 64 + 8192 + 128 + 16384 + 128 + 8192 + 64,
+                   64 * n_in + 64 + 8192 + 128 + 16384 + 128 + 8192 + 64 + 192};
+}
 
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
     // kind::f16 instruction descriptor: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
@@ -198,23 +213,24 @@ size_t bf16_weight_elems() { return tc::W_IMG_ELEMS; }
 // layout above: element (n, k) of an N x K matrix at ((k/8) * N/8 + n/8) * 64 + (n%8) * 8 + k%8;
 // then the bias blocks of layers 2, 3, 4 (N x 16, same layout): column 0 = bf16(b),
 // column 1 = bf16(b - bf16(b)), the other columns 0.
-__global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* __restrict__ img) {
+__global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* __restrict__ img, int n_in) {
     constexpr int NW = 8192 + 16384 + 8192;
+    const tc::BlobOff bo = tc::blob_off(n_in);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tc::W_IMG_ELEMS; e += gridDim.x * blockDim.x) {
         int N, K, base, loc;
         float v;
         if (e < NW) {
             int src;
-            if (e < 8192) { N = 128; K = 64; src = tc::B_W2; base = 0; loc = e; }
-            else if (e < 8192 + 16384) { N = 128; K = 128; src = tc::B_W3; base = 8192; loc = e - 8192; }
-            else { N = 64; K = 128; src = tc::B_W4; base = 8192 + 16384; loc = e - 8192 - 16384; }
+            if (e < 8192) { N = 128; K = 64; src = bo.W2; base = 0; loc = e; }
+            else if (e < 8192 + 16384) { N = 128; K = 128; src = bo.W3; base = 8192; loc = e - 8192; }
+            else { N = 64; K = 128; src = bo.W4; base = 8192 + 16384; loc = e - 8192 - 16384; }
             v = w32[src + (loc / K) * K + loc % K];
         } else {
             int src;
             K = 16;
-            if (e < NW + 2048) { N = 128; src = tc::B_B2; base = NW; loc = e - NW; }
-            else if (e < NW + 4096) { N = 128; src = tc::B_B3; base = NW + 2048; loc = e - NW - 2048; }
-            else { N = 64; src = tc::B_B4; base = NW + 4096; loc = e - NW - 4096; }
+            if (e < NW + 2048) { N = 128; src = bo.B2; base = NW; loc = e - NW; }
+            else if (e < NW + 4096) { N = 128; src = bo.B3; base = NW + 2048; loc = e - NW - 2048; }
+            else { N = 64; src = bo.B4; base = NW + 4096; loc = e - NW - 4096; }
             const float b = w32[src + loc / 16], hi = __bfloat162float(__float2bfloat16_rn(b));
             v = loc % 16 == 0 ? b : (loc % 16 == 1 ? b - hi : 0.0f);
         }
@@ -224,8 +240,9 @@ __global__ void k_convert_weights_bf16(const float* __restrict__ w32, uint16_t* 
     }
 }
 
-cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, cudaStream_t s) {
-    k_convert_weights_bf16<<<32, 256, 0, s>>>(w32, wbf16);
+cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, int n_in, cudaStream_t s) {
+    if (n_in != 2 && n_in != 11) return cudaErrorInvalidValue;
+    k_convert_weights_bf16<<<32, 256, 0, s>>>(w32, wbf16, n_in);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -242,8 +259,12 @@ __device__ __forceinline__ int find_tile(const long long* __restrict__ pre, int 
 
 // Persistent over the table's 128-cell tiles (tile v of the table belongs to the lattice j
 // with tile_pre[j] <= v < tile_pre[j+1]; tiles never straddle lattices).
+// NIN = 2 (the paper's inputs) or 11 (with the density stencil): one instantiation each, so
+// that the paper's form keeps its own register allocation.
+template <int NIN>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, TableView tab) {
+    constexpr int n_in = NIN;
     using namespace tc;
     extern __shared__ __align__(1024) uint8_t sm[];
     const int tid = threadIdx.x, wg = tid >> 7, t = tid & 127, warp = tid >> 5;
@@ -267,10 +288,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // small FP32 parameters
-    for (int k = tid; k < 128; k += THREADS) P[P_W1 + k] = w32[B_W1 + k];
-    for (int k = tid; k < 64; k += THREADS) P[P_B1 + k] = w32[B_B1 + k];
-    for (int k = tid; k < 192; k += THREADS) P[P_W5 + k] = w32[B_W5 + k];
-    for (int k = tid; k < 3; k += THREADS) P[P_B5 + k] = w32[B_B5 + k];
+    const BlobOff bo = blob_off(n_in);
+    if constexpr (NIN == 2) {
+        for (int k = tid; k < 128; k += THREADS) P[P_W1 + k] = w32[bo.W1 + k];
+    } else {
+        for (int k = tid; k < 64 * 12; k += THREADS) P[P_W1 + k] = k % 12 < 11 ? w32[bo.W1 + (k / 12) * 11 + k % 12] : 0.0f;
+    }
+    for (int k = tid; k < 64; k += THREADS) P[P_B1 + k] = w32[bo.B1 + k];
+    for (int k = tid; k < 192; k += THREADS) P[P_W5 + k] = w32[bo.W5 + k];
+    for (int k = tid; k < 3; k += THREADS) P[P_B5 + k] = w32[bo.B5 + k];
     // the ones block (A operand of the bias step): element (m, k) at
     // ((k/8) * M/8 + m/8) * 64 + (m%8) * 8 + k%8, 1 in columns 0 and 1
     {
@@ -325,6 +351,46 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const float yh = 2.0f * ((float)y + 0.5f) / (float)ny - 1.0f;
 
         // ---- layer 1 on FMA: A1 (128 x 64) into AX
+        if constexpr (NIN == 11) {
+            // the density of the cell and its 8 neighbours (periodic), velocity order
+            const float* rho = static_cast<const float*>(ld.rho);
+            float in[11];
+            in[0] = xh;
+            in[1] = yh;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                int xn = x + cx(i), yn = y + cy(i);
+                xn = xn < 0 ? xn + nx : (xn >= nx ? xn - nx : xn);
+                yn = yn < 0 ? yn + ny : (yn >= ny ? yn - ny : yn);
+                in[2 + i] = rho[(long long)yn * nx + xn];
+            }
+#pragma unroll 1
+            for (int k0 = 0; k0 < 64; k0 += 8) {
+                const float4* b4 = reinterpret_cast<const float4*>(P + P_B1 + k0);
+                const float4 bA = b4[0], bB = b4[1];
+                const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
+                float h[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4* w4 = reinterpret_cast<const float4*>(P + P_W1 + (k0 + j) * 12);
+                    const float4 a = w4[0], b = w4[1], c = w4[2];
+                    float z = bias[j];
+                    z = fmaf(a.x, in[0], z);
+                    z = fmaf(a.y, in[1], z);
+                    z = fmaf(a.z, in[2], z);
+                    z = fmaf(a.w, in[3], z);
+                    z = fmaf(b.x, in[4], z);
+                    z = fmaf(b.y, in[5], z);
+                    z = fmaf(b.z, in[6], z);
+                    z = fmaf(b.w, in[7], z);
+                    z = fmaf(c.x, in[8], z);
+                    z = fmaf(c.y, in[9], z);
+                    z = fmaf(c.z, in[10], z);
+                    h[j] = tanh_fast(z);
+                }
+                store8(AX, t, k0, h);
+            }
+        } else
 #pragma unroll
         for (int k0 = 0; k0 < 64; k0 += 8) {
             // parameters as 16-byte shared loads: W1 rows (o, o+1) and biases (o..o+3)
@@ -422,10 +488,12 @@ cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s) {
+template <int NIN>
+static cudaError_t launch_mlp_tc_t(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s) {
     static int sms = 0;
     if (!sms) {
-        cudaError_t e = cudaFuncSetAttribute(k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_ALLOC);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_mlp_tc<NIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_ALLOC);
         if (e != cudaSuccess) return e;
         int dev = 0;
         cudaGetDevice(&dev);
@@ -433,9 +501,14 @@ cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* 
         if (sms < 1) sms = 1;
     }
     // persistent: one CTA per SM (CTAs without a tile return before any set-up)
-    k_mlp_tc<<<sms, tc::THREADS, tc::SMEM_ALLOC, s>>>(wbf16, w32, t);
+    k_mlp_tc<NIN><<<sms, tc::THREADS, tc::SMEM_ALLOC, s>>>(wbf16, w32, t);
     note_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, cudaStream_t s) {
+    if (n_in == 11) return launch_mlp_tc_t<11>(t, w32, wbf16, s);
+    return launch_mlp_tc_t<2>(t, w32, wbf16, s);
 }
 
 }  // namespace pl

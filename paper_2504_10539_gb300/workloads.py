@@ -79,13 +79,14 @@ class Lattice:
     weight_seed: int = 11
     beta_rho: float = 0.1
     beta_u: float = 0.01
+    mlp_in: int = 2                   # network inputs: 2 = (x^, y^); 11 = with the density stencil
 
     @property
     def cells(self) -> int:
         return self.nx * self.ny
 
     def weights(self) -> np.ndarray:
-        return mlp_weights(self.weight_seed)
+        return mlp_weights(self.weight_seed, dims=(self.mlp_in,) + MLP_DIMS[1:])
 
 
 def single_64(seed: int = 1) -> Lattice:
