@@ -3,9 +3,10 @@
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  The product library never does.
 
-Thin ctypes marshalling over ``pinnlbm_oracle.c``; every number is computed
-there.  Arrays are numpy float64 in the layout f[i, y, x] (direction-major,
-x fastest).
+Thin ctypes marshalling over ``pinnlbm_oracle.c``; every number of the lattice,
+the metrics, the network and the correction is computed there.  The network's
+training (Eqs. 3-8) is the numpy module ``oracle.train``.  Arrays are numpy
+float64 in the layout f[i, y, x] (direction-major, x fastest).
 """
 import ctypes
 import os
