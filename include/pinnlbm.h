@@ -216,6 +216,72 @@ PL_API int pl_lattice_status(pl_lattice* lat);
 /* Free the handle; the caller's device memory is not touched. */
 PL_API int pl_destroy(pl_lattice* lat);
 
+/* Network weights currently on the device (the FP32 blob, n = pl_mlp_blob_size_for(
+ * params.mlp_in)); after pl_train these are the trained weights.  Synchronises. */
+PL_API int pl_get_mlp_weights(pl_lattice* lat, float* host_blob, size_t n);
+
+/* ---------------------------------------------------------------------------------
+ * Network training on the lattice state (Sec. II-C step 2; loss Eqs. 3-8; Sec. III-B:
+ * learning rate 3e-4, 300 epochs per coupling step), for the paper's 2-input network
+ * (params.mlp_in = 2).  The paper leaves the following open; the library's reading:
+ *   - samples: every cell, input (x^, y^) as for the correction; one epoch = one
+ *     gradient step on the loss over all cells;
+ *   - targets: rho = sum f_i and u = j / rho of the state when pl_train is called;
+ *   - L_data (Eq. 4): mean over the cells of |N - (rho, u_x, u_y)|^2;
+ *   - L_phys (Eqs. 5-7): mean over the cells of r_c^2 + |r_m|^2, r_c = div(rho u),
+ *     r_m = div(rho u u) + grad p, on the network's fields and their spatial derivatives
+ *     (lattice units, d/dx = (2/nx) d/dx^); no time derivative (N has no time input),
+ *     p = rho/3 + G psi^2/6, stress taken as zero;
+ *   - L_int (Eq. 8): mean over the cells with |grad rho| (Eq. 16) above params.threshold
+ *     of -alpha1 q + alpha2 q^2, q = |grad rho_N|^2 (the signs the text describes);
+ *   - optimizer: Adam with bias correction, no weight decay; its moments and step count
+ *     live in the trainer and persist across pl_train calls;
+ *   - between calls the network is the lattice's FP32 blob (the correction's weights):
+ *     each call starts from it and writes the trained weights back to it (and to the
+ *     tensor-core operand image).
+ * Arithmetic: FP64 for FP64 lattices, FP32 otherwise (CUDA cores).
+ * --------------------------------------------------------------------------------- */
+typedef struct pl_train_params {
+    double lr;          /* Adam step size (default 3e-4, Sec. III-B)          */
+    double beta1;       /* Adam first-moment decay (0.9)                      */
+    double beta2;       /* Adam second-moment decay (0.999)                   */
+    double eps;         /* Adam denominator guard (1e-8)                      */
+    double lambda_phys; /* Eq. 3 weight of L_phys (1)                         */
+    double lambda_int;  /* Eq. 3 weight of L_int (1)                          */
+    double alpha1;      /* Eq. 8 weight of q = |grad rho_N|^2 (1)             */
+    double alpha2;      /* Eq. 8 weight of q^2 (1)                            */
+} pl_train_params;
+
+typedef struct pl_trainer pl_trainer;
+
+PL_API int pl_train_params_default(pl_train_params* tp);
+/* Bytes of caller device memory a trainer for lattices of this storage type needs with a
+ * loss history of max_epochs >= 1 entries (depends on the current device's SM count). */
+PL_API int pl_trainer_bytes(const pl_params* p, int32_t max_epochs, size_t* bytes_out);
+/* Trainer of lattice `lat` over caller memory dev_mem[0, bytes) (256-byte aligned, valid
+ * until pl_trainer_destroy); enqueues on the lattice's stream.  Adam's moments start at
+ * zero.  PL_ERR_INVALID_ARG for a lattice with mlp_in != 2 or invalid hyper-parameters
+ * (lr > 0, 0 <= beta < 1, eps > 0, lambdas and alphas finite and >= 0). */
+PL_API int pl_trainer_create(pl_lattice* lat, const pl_train_params* tp, int32_t max_epochs, void* dev_mem,
+                             size_t bytes, pl_trainer** out);
+/* epochs (1..max_epochs) training epochs on the lattice's current state; the loss
+ * history of the call is kept for pl_train_losses.  Requires weights and a state
+ * (PL_ERR_STATE otherwise).  No host synchronisation. */
+PL_API int pl_train(pl_trainer* tr, int32_t epochs);
+/* Loss history of the last pl_train call, host_loss[epochs][4] = (L, L_data, L_phys,
+ * L_int), each evaluated at the weights its epoch started from.  Synchronises. */
+PL_API int pl_train_losses(pl_trainer* tr, double* host_loss, int32_t epochs);
+/* The gradient of Eq. 3 with respect to the blob (host_grad[pl_mlp_blob_size()], FP64)
+ * and the loss terms (host_loss4[4] as above) at the lattice's current weights and state;
+ * nothing is updated.  Synchronises. */
+PL_API int pl_train_gradient(pl_trainer* tr, double* host_grad, double* host_loss4);
+/* Coupled run with training (Sec. II-C): nsteps time steps; after every step whose count
+ * is a multiple of K (K > 0), `epochs` training epochs on the state, then one correction
+ * with the trained network. */
+PL_API int pl_run_trained(pl_trainer* tr, int32_t nsteps, int32_t K, int32_t epochs);
+/* Free the handle; the caller's device memory is not touched. */
+PL_API int pl_trainer_destroy(pl_trainer* tr);
+
 /* Self-test of the device-side failure detection: one thread waits, with the bounded
  * mbarrier wait used by the tensor-core kernel, on a barrier that nothing arrives on;
  * after limit_ns (<= 5 s) the wait gives up and the kernel writes PL_ERR_TIMEOUT to the

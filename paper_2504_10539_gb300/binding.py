@@ -68,6 +68,12 @@ class pl_job_result(ctypes.Structure):
         return d
 
 
+class pl_train_params(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("lambda_phys", ctypes.c_double), ("lambda_int", ctypes.c_double),
+                ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double)]
+
+
 class PLError(RuntimeError):
     def __init__(self, fn, status):
         self.status = status
@@ -128,6 +134,15 @@ def _L():
             "pl_batch_destroy": (ctypes.c_int, [vp]),
             "pl_destroy": (ctypes.c_int, [vp]),
             "pl_selftest_wait_timeout": (ctypes.c_int, [vp, i64, vp]),
+            "pl_get_mlp_weights": (ctypes.c_int, [vp, P(ctypes.c_float), sz]),
+            "pl_train_params_default": (ctypes.c_int, [P(pl_train_params)]),
+            "pl_trainer_bytes": (ctypes.c_int, [P(pl_params), i32, P(sz)]),
+            "pl_trainer_create": (ctypes.c_int, [vp, P(pl_train_params), i32, vp, sz, P(vp)]),
+            "pl_train": (ctypes.c_int, [vp, i32]),
+            "pl_train_losses": (ctypes.c_int, [vp, P(d), i32]),
+            "pl_train_gradient": (ctypes.c_int, [vp, P(d), P(d)]),
+            "pl_run_trained": (ctypes.c_int, [vp, i32, i32, i32]),
+            "pl_trainer_destroy": (ctypes.c_int, [vp]),
         }
         for name, (res, args) in sigs.items():
             if hasattr(L, name):
@@ -282,6 +297,57 @@ def pl_selftest_wait_timeout(dev_status_ptr: int, limit_ns: int, stream: int = 0
     return _L().pl_selftest_wait_timeout(ctypes.c_void_p(dev_status_ptr), int(limit_ns), ctypes.c_void_p(stream))
 
 
+def pl_get_mlp_weights(h, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float32)
+    _chk("pl_get_mlp_weights", _L().pl_get_mlp_weights(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n))
+    return out
+
+
+def pl_train_params_default(**kw) -> pl_train_params:
+    tp = pl_train_params()
+    _chk("pl_train_params_default", _L().pl_train_params_default(ctypes.byref(tp)))
+    for k, v in kw.items():
+        setattr(tp, k, v)
+    return tp
+
+
+def pl_trainer_bytes(p: pl_params, max_epochs: int) -> int:
+    out = ctypes.c_size_t(0)
+    _chk("pl_trainer_bytes", _L().pl_trainer_bytes(ctypes.byref(p), int(max_epochs), ctypes.byref(out)))
+    return out.value
+
+
+def pl_trainer_create(lat_h, tp: pl_train_params, max_epochs: int, dev_ptr: int, nbytes: int) -> int:
+    h = ctypes.c_void_p()
+    _chk("pl_trainer_create", _L().pl_trainer_create(lat_h, ctypes.byref(tp), int(max_epochs), ctypes.c_void_p(dev_ptr),
+                                                     nbytes, ctypes.byref(h)))
+    return h.value
+
+
+def pl_train(h, epochs: int):
+    _chk("pl_train", _L().pl_train(h, int(epochs)))
+
+
+def pl_train_losses(h, epochs: int) -> np.ndarray:
+    out = np.zeros((epochs, 4))
+    _chk("pl_train_losses", _L().pl_train_losses(h, _dptr(out), int(epochs)))
+    return out
+
+
+def pl_train_gradient(h, n: int):
+    g, loss = np.zeros(n), np.zeros(4)
+    _chk("pl_train_gradient", _L().pl_train_gradient(h, _dptr(g), _dptr(loss)))
+    return g, loss
+
+
+def pl_run_trained(h, nsteps: int, K: int, epochs: int):
+    _chk("pl_run_trained", _L().pl_run_trained(h, int(nsteps), int(K), int(epochs)))
+
+
+def pl_trainer_destroy(h):
+    _chk("pl_trainer_destroy", _L().pl_trainer_destroy(h))
+
+
 # ----------------------------------------------------------------------------- owner of one lattice
 
 class Lattice:
@@ -346,9 +412,51 @@ class Lattice:
     def status(self):
         return pl_lattice_status(self.h)
 
+    def weights(self):
+        return pl_get_mlp_weights(self.h, pl_mlp_blob_size_for(self.params.mlp_in))
+
     def close(self):
         if getattr(self, "h", None):
             pl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Trainer:
+    """Network training on a Lattice's state (Eqs. 3-8) over a torch-allocated device buffer;
+    enqueues on the lattice's stream.  Keeps a reference to the lattice, so the lattice
+    outlives it."""
+
+    def __init__(self, lattice: Lattice, max_epochs: int = 300, **hyper):
+        import torch
+        self.lattice = lattice
+        self.tp = pl_train_params_default(**hyper)
+        self.max_epochs = max_epochs
+        self.nbytes = pl_trainer_bytes(lattice.params, max_epochs)
+        self.mem = torch.empty(self.nbytes, dtype=torch.uint8, device=lattice.mem.device)
+        lattice.stream.wait_stream(torch.cuda.current_stream(self.mem.device))
+        self.h = pl_trainer_create(lattice.h, self.tp, max_epochs, self.mem.data_ptr(), self.nbytes)
+
+    def train(self, epochs):
+        pl_train(self.h, epochs)
+
+    def losses(self, epochs):
+        return pl_train_losses(self.h, epochs)
+
+    def gradient(self):
+        return pl_train_gradient(self.h, pl_mlp_blob_size())
+
+    def run(self, nsteps, K, epochs):
+        pl_run_trained(self.h, nsteps, K, epochs)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pl_trainer_destroy(self.h)
             self.h = None
 
     def __del__(self):

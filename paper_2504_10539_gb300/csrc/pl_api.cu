@@ -620,6 +620,215 @@ int pl_destroy(pl_lattice* L) {
     return PL_OK;
 }
 
+int pl_get_mlp_weights(pl_lattice* L, float* host_blob, size_t n) {
+    if (!L || !host_blob || n != (size_t)mlp_blob(L->p.mlp_in)) return PL_ERR_INVALID_ARG;
+    if (!L->weights_set) return PL_ERR_STATE;
+    PL_CUDA(cudaMemcpyAsync(host_blob, L->w32, n * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
+    PL_CUDA(cudaStreamSynchronize(L->stream));
+    return PL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Network training (Eqs. 3-8).  Trainer memory (caller's): master weights, Adam moments and
+// the last gradient (4 x blob, element type of the lattice's arithmetic), the per-CTA
+// gradient slices of the training kernel, per-CTA loss sums, the loss history and the
+// interface-cell count.
+
+struct pl_trainer {
+    pl_lattice* lat;
+    TrainHyper hp;
+    TrainBufs b;
+    double* hist;
+    int max_epochs;
+    int fp64;
+    long long t;         // Adam steps taken
+    int last_epochs;     // epochs of the last pl_train call
+};
+
+namespace {
+
+struct TrainerLayout {
+    size_t master, m, v, grad, part, loss_part, hist, ni, total;
+    int grid;
+};
+
+int trainer_layout(int storage, int max_epochs, TrainerLayout* T) {
+    const int fp64 = storage == PL_F64;
+    cudaError_t e = train_grid(fp64, &T->grid);
+    if (e != cudaSuccess) {
+        g_last_cuda_error = (int)e;
+        (void)cudaGetLastError();
+        return PL_ERR_CUDA;
+    }
+    const size_t es = fp64 ? 8 : 4, P = (size_t)train_params_count();
+    size_t o = 0;
+    T->master = o; o = align_up(o + P * es);
+    T->m = o;      o = align_up(o + P * es);
+    T->v = o;      o = align_up(o + P * es);
+    T->grad = o;   o = align_up(o + P * es);
+    T->part = o;   o = align_up(o + (size_t)T->grid * (size_t)train_part_stride() * es);
+    T->loss_part = o; o = align_up(o + (size_t)T->grid * 4 * sizeof(double));
+    T->hist = o;   o = align_up(o + (size_t)max_epochs * 4 * sizeof(double));
+    T->ni = o;     o = align_up(o + sizeof(unsigned long long));
+    T->total = o;
+    return PL_OK;
+}
+
+TrainLat train_lat(pl_lattice* L) {
+    const LatDesc& d = L->tab.d[0];
+    return TrainLat{d.rho, d.jx, d.jy, d.g, d.nx, d.ny, d.G, d.rho0, d.threshold};
+}
+
+bool hyper_ok(const pl_train_params* tp) {
+    auto fin = [](double v) { return std::isfinite(v); };
+    return tp && fin(tp->lr) && tp->lr > 0 && fin(tp->beta1) && tp->beta1 >= 0 && tp->beta1 < 1 && fin(tp->beta2) &&
+           tp->beta2 >= 0 && tp->beta2 < 1 && fin(tp->eps) && tp->eps > 0 && fin(tp->lambda_phys) &&
+           tp->lambda_phys >= 0 && fin(tp->lambda_int) && tp->lambda_int >= 0 && fin(tp->alpha1) && tp->alpha1 >= 0 &&
+           fin(tp->alpha2) && tp->alpha2 >= 0;
+}
+
+// Targets of the current state, master weights from the blob, interface count.
+int train_begin(pl_trainer* T) {
+    pl_lattice* L = T->lat;
+    PL_CUDA(launch_train_fields_tab(L->tab.view, L->p.storage, L->cur, L->stream));
+    PL_CUDA(launch_train_begin(train_lat(L), T->b, T->fp64, L->w32, L->stream));
+    return PL_OK;
+}
+
+int train_epochs(pl_trainer* T, int epochs) {
+    pl_lattice* L = T->lat;
+    int st = train_begin(T);
+    if (st) return st;
+    const TrainLat tl = train_lat(L);
+    for (int e = 0; e < epochs; ++e) {
+        PL_CUDA(launch_train_epoch(tl, T->b, T->fp64, T->hp, T->t + 1, 1, T->hist + 4 * e, L->stream));
+        ++T->t;
+    }
+    PL_CUDA(launch_train_end(T->b, T->fp64, L->w32, L->wbf16, L->stream));
+    T->last_epochs = epochs;
+    return PL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pl_train_params_default(pl_train_params* tp) {
+    if (!tp) return PL_ERR_INVALID_ARG;
+    *tp = pl_train_params{3e-4, 0.9, 0.999, 1e-8, 1.0, 1.0, 1.0, 1.0};
+    return PL_OK;
+}
+
+int pl_trainer_bytes(const pl_params* p, int32_t max_epochs, size_t* bytes_out) {
+    int st = check_params(p);
+    if (st) return st;
+    if (!bytes_out || max_epochs < 1 || p->mlp_in != 2) return PL_ERR_INVALID_ARG;
+    TrainerLayout T;
+    st = trainer_layout(p->storage, max_epochs, &T);
+    if (st) return st;
+    *bytes_out = T.total;
+    return PL_OK;
+}
+
+int pl_trainer_create(pl_lattice* L, const pl_train_params* tp, int32_t max_epochs, void* dev_mem, size_t bytes,
+                      pl_trainer** out) {
+    if (!L || !out || !dev_mem || ((uintptr_t)dev_mem % ALIGN) != 0 || max_epochs < 1 || !hyper_ok(tp) ||
+        L->p.mlp_in != 2)
+        return PL_ERR_INVALID_ARG;
+    TrainerLayout TL;
+    int st = trainer_layout(L->p.storage, max_epochs, &TL);
+    if (st) return st;
+    if (bytes < TL.total) return PL_ERR_BUDGET;
+    pl_trainer* T = new (std::nothrow) pl_trainer();
+    if (!T) return PL_ERR_BUDGET;
+    char* base = static_cast<char*>(dev_mem);
+    T->lat = L;
+    T->hp = TrainHyper{tp->lr, tp->beta1, tp->beta2, tp->eps, tp->lambda_phys, tp->lambda_int, tp->alpha1, tp->alpha2};
+    T->b = TrainBufs{base + TL.master, base + TL.m, base + TL.v, base + TL.grad, base + TL.part,
+                     reinterpret_cast<double*>(base + TL.loss_part), reinterpret_cast<unsigned long long*>(base + TL.ni),
+                     TL.grid};
+    T->hist = reinterpret_cast<double*>(base + TL.hist);
+    T->max_epochs = max_epochs;
+    T->fp64 = L->p.storage == PL_F64;
+    T->t = 0;
+    T->last_epochs = 0;
+    const size_t moments = TL.grad - TL.m;  // m and v, adjacent
+    cudaError_t e = cudaMemsetAsync(base + TL.m, 0, moments, L->stream);
+    if (e != cudaSuccess) {
+        delete T;
+        g_last_cuda_error = (int)e;
+        (void)cudaGetLastError();
+        return PL_ERR_CUDA;
+    }
+    *out = T;
+    return PL_OK;
+}
+
+int pl_train(pl_trainer* T, int32_t epochs) {
+    if (!T || epochs < 1 || epochs > T->max_epochs) return PL_ERR_INVALID_ARG;
+    if (!T->lat->initialised || !T->lat->weights_set) return PL_ERR_STATE;
+    return train_epochs(T, epochs);
+}
+
+int pl_train_losses(pl_trainer* T, double* host_loss, int32_t epochs) {
+    if (!T || !host_loss || epochs < 1 || epochs > T->last_epochs) return PL_ERR_INVALID_ARG;
+    PL_CUDA(cudaMemcpyAsync(host_loss, T->hist, (size_t)epochs * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                            T->lat->stream));
+    PL_CUDA(cudaStreamSynchronize(T->lat->stream));
+    return PL_OK;
+}
+
+int pl_train_gradient(pl_trainer* T, double* host_grad, double* host_loss4) {
+    if (!T || !host_grad || !host_loss4) return PL_ERR_INVALID_ARG;
+    pl_lattice* L = T->lat;
+    if (!L->initialised || !L->weights_set) return PL_ERR_STATE;
+    int st = train_begin(T);
+    if (st) return st;
+    PL_CUDA(launch_train_epoch(train_lat(L), T->b, T->fp64, T->hp, 0, 0, T->hist, L->stream));
+    const size_t P = (size_t)train_params_count();
+    if (T->fp64) {
+        PL_CUDA(cudaMemcpyAsync(host_grad, T->b.grad, P * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    } else {
+        std::vector<float> tmp(P);
+        PL_CUDA(cudaMemcpyAsync(tmp.data(), T->b.grad, P * sizeof(float), cudaMemcpyDeviceToHost, L->stream));
+        PL_CUDA(cudaStreamSynchronize(L->stream));
+        for (size_t p = 0; p < P; ++p) host_grad[p] = tmp[p];
+    }
+    PL_CUDA(cudaMemcpyAsync(host_loss4, T->hist, 4 * sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    PL_CUDA(cudaStreamSynchronize(L->stream));
+    T->last_epochs = 0;
+    return PL_OK;
+}
+
+int pl_run_trained(pl_trainer* T, int32_t nsteps, int32_t K, int32_t epochs) {
+    if (!T || nsteps < 0 || K < 1 || epochs < 1 || epochs > T->max_epochs) return PL_ERR_INVALID_ARG;
+    pl_lattice* L = T->lat;
+    if (!L->initialised || !L->weights_set) return PL_ERR_STATE;
+    long long left = nsteps;
+    while (left > 0) {
+        const long long to_boundary = K - (L->step % K);
+        const int n = (int)(left < to_boundary ? left : to_boundary);
+        int st = do_steps(L, n);
+        if (st) return st;
+        left -= n;
+        if (L->step % K == 0) {
+            st = train_epochs(T, epochs);
+            if (st) return st;
+            PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, L->cur, L->p.mlp, L->p.mlp_in, L->w32, L->wbf16,
+                                          L->stream));
+        }
+    }
+    return PL_OK;
+}
+
+int pl_trainer_destroy(pl_trainer* T) {
+    if (!T) return PL_ERR_INVALID_ARG;
+    delete T;
+    return PL_OK;
+}
+
 int pl_selftest_wait_timeout(void* dev_status, int64_t limit_ns, void* stream) {
     if (!dev_status || ((uintptr_t)dev_status % sizeof(int)) || limit_ns < 0 || limit_ns > 5000000000ll)
         return PL_ERR_INVALID_ARG;

@@ -116,6 +116,42 @@ cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, i
                                   const float* w32, const uint16_t* wbf16, cudaStream_t s);
 
 cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, int n_in, cudaStream_t s);
+
+// Network training (Eqs. 3-8, the 2-input network): the lattice fields it reads (element type
+// double for FP64 lattices, float otherwise), its hyper-parameters and its device buffers.
+struct TrainLat {
+    const void* rho;
+    const void* jx;
+    const void* jy;
+    const void* g;
+    int nx, ny;
+    double G, rho0, threshold;
+};
+struct TrainHyper {
+    double lr, beta1, beta2, eps, lambda_phys, lambda_int, alpha1, alpha2;
+};
+struct TrainBufs {
+    void* master;              // weights being trained [train_params_count()]
+    void* m;                   // Adam first moments
+    void* v;                   // Adam second moments
+    void* grad;                // gradient of the last epoch
+    void* part;                // per-CTA gradient slices [grid][train_part_stride()]
+    double* loss_part;         // per-CTA loss sums [grid][4]
+    unsigned long long* ni;    // interface-cell count
+    int grid;                  // CTAs the partial buffers hold
+};
+int train_params_count();
+long long train_part_stride();
+cudaError_t train_grid(int fp64, int* grid);
+// Density, momentum and Eq. 16 gradient fields of every lattice (the training targets).
+cudaError_t launch_train_fields_tab(const TableView& t, int storage, int parity, cudaStream_t s);
+cudaError_t launch_train_begin(const TrainLat& L, const TrainBufs& b, int fp64, const float* w32, cudaStream_t s);
+// One epoch: gradient over all cells, then (apply = 1) the Adam step number t; writes the
+// loss terms at the weights the epoch started from to hist_row[4].
+cudaError_t launch_train_epoch(const TrainLat& L, const TrainBufs& b, int fp64, const TrainHyper& hp, long long t,
+                               int apply, double* hist_row, cudaStream_t s);
+// Trained weights -> the FP32 blob and its BF16 image.
+cudaError_t launch_train_end(const TrainBufs& b, int fp64, float* w32, uint16_t* wbf16, cudaStream_t s);
 cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t s);
 size_t bf16_weight_elems();
 

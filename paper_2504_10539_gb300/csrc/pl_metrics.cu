@@ -768,6 +768,26 @@ cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, i
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_train_fields_tab(const TableView& t, int storage, int parity, cudaStream_t s) {
+    switch (storage) {
+        case PL_F64:
+            k_moments<PL_F64><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+            k_grad_tab<double><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+            break;
+        case PL_F32:
+            k_moments<PL_F32><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+            k_grad_tab<float><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+            break;
+        case PL_F16_OFFSET:
+            k_moments<PL_F16_OFFSET><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+            k_grad_tab<float><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    note_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments_tab(const TableView& t, int storage, int parity, cudaStream_t s) {
     switch (storage) {
         case PL_F64: k_moments<PL_F64><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity); break;

@@ -1,0 +1,598 @@
+// Training of the correction network on the lattice state, arXiv 2504.10539 Sec. II-C step 2
+// with the composite loss of Eqs. 3-8 and the hyper-parameters of Sec. III-B, on CUDA cores:
+// FP32 for FP32 / FP16-offset lattices, FP64 for FP64 lattices.
+//
+// What one epoch computes (the readings of the paper's open points are fixed here):
+//   samples  every cell, input (x^, y^) = the cell centre mapped to [-1, 1]; one epoch is one
+//            gradient step on the loss over all cells;
+//   targets  rho = sum f_i, u = j / rho of the state when training starts;
+//   L_data   (Eq. 4) mean over the cells of |N - (rho, u_x, u_y)|^2;
+//   L_phys   (Eqs. 5-7) mean of r_c^2 + |r_m|^2 with r_c = div(rho u), r_m = div(rho u u) +
+//            grad p, on the network's own fields and their spatial derivatives; no time
+//            derivative (N has no time input), p = rho/3 + G psi^2/6, stress taken as zero;
+//   L_int    (Eq. 8) mean over the interface cells (lattice |grad rho| above the Eq. 9
+//            threshold) of -alpha1 q + alpha2 q^2, q = |grad rho_N|^2: the signs the text
+//            describes (Eq. 8 as printed is unbounded below);
+//   d/dx     in lattice units, (2 / nx) d/dx^;
+//   update   Adam (lr 3e-4 in Sec. III-B), moments kept across calls.
+//
+// The spatial derivatives of the network are forward tangents: every layer carries three
+// rows per sample, its value and its derivatives along x^ and y^ (z_d = W a_d, a_d =
+// tanh'(z) z_d).  The reverse pass runs through all three rows; the only coupling between
+// them is tanh's second derivative:  dL/dz = s dL/da - 2 a sum_d a_d dL/da_d, s = 1 - a^2.
+//
+// Kernel layout.  A CTA of 256 threads takes tiles of T samples (T = 16 in FP32, 8 in FP64),
+// i.e. 3T rows, and keeps every hidden layer's rows of the tile in shared memory for the
+// reverse pass.  The dense layers are register-tiled loops over shared memory: each warp
+// owns 3T/8 rows and each lane 32-strided columns, operand rows are broadcast and weight
+// columns are conflict-free (FP32 weights are staged per layer with rows padded by 4).  The
+// weight gradient of a tile is added into a per-CTA slice of a partial buffer that each
+// thread owns element-wise, so no atomics are needed and the sums are deterministic for a
+// given grid.  The update kernel folds the slices in CTA order and applies Adam.
+#include <cmath>
+
+#include "pl_device.cuh"
+#include "pl_kernels.h"
+
+namespace pl {
+
+namespace {
+
+constexpr int TR_THREADS = 256;
+constexpr int NIN = 2;
+// Blob offsets of the 2-input network: W1[64x2] b1 W2[128x64] b2 W3[128x128] b3 W4[64x128] b4 W5[3x64] b5.
+constexpr int OW1 = 0, OB1 = OW1 + 64 * NIN, OW2 = OB1 + 64, OB2 = OW2 + 128 * 64, OW3 = OB2 + 128,
+              OB3 = OW3 + 128 * 128, OW4 = OB3 + 128, OB4 = OW4 + 64 * 128, OW5 = OB4 + 64, OB5 = OW5 + 3 * 64,
+              NPARAM = OB5 + 3;
+static_assert(NPARAM == 33475, "blob of the 2-input network");
+constexpr long long PSTRIDE = (NPARAM + 63) / 64 * 64;  // elements per CTA slice of the partials
+
+template <typename R> struct TileOf;
+template <> struct TileOf<float> { static constexpr int T = 16; static constexpr bool STAGE = true; };
+template <> struct TileOf<double> { static constexpr int T = 8; static constexpr bool STAGE = false; };
+
+// Shared-memory plan (elements of R): activations of the 4 hidden layers [3][T][N_l], two
+// reverse-pass buffers [3T][128], the staged weight matrix [128][128 + 4] (FP32 only), and
+// the per-sample scalars.
+template <typename R>
+struct Smem {
+    static constexpr int T = TileOf<R>::T, RT = 3 * T;
+    static constexpr int A1 = 0, A2 = A1 + RT * 64, A3 = A2 + RT * 128, A4 = A3 + RT * 128, D0 = A4 + RT * 64,
+                         D1 = D0 + RT * 128, WS = D1 + RT * 128, WS_N = TileOf<R>::STAGE ? 128 * 132 : 0,
+                         X = WS + WS_N, TG = X + 2 * T, O5 = TG + 3 * T, D5 = O5 + RT * 3, IF = D5 + RT * 3,
+                         TOTAL = IF + T;
+    static constexpr size_t bytes = (size_t)TOTAL * sizeof(R);
+};
+
+template <typename R>
+__device__ __forceinline__ void ld4(const R* p, R (&v)[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+template <typename R> __device__ __forceinline__ R tanh_r(R z);
+template <> __device__ __forceinline__ float tanh_r<float>(float z) { return tanhf(z); }
+template <> __device__ __forceinline__ double tanh_r<double>(double z) { return tanh(z); }
+template <typename R> __device__ __forceinline__ R exp_r(R z);
+template <> __device__ __forceinline__ float exp_r<float>(float z) { return expf(z); }
+template <> __device__ __forceinline__ double exp_r<double>(double z) { return exp(z); }
+
+// "g > threshold" with the decision an FP64 comparison gives (FP32 g: compare with the
+// largest FP32 number not above the threshold).
+__device__ __forceinline__ bool above(float g, double thr) { return g > __double2float_rd(thr); }
+__device__ __forceinline__ bool above(double g, double thr) { return g > thr; }
+
+// out[r][n] = sum_k in[r][k] W[n][k] (+ b[n] on the value rows r < T); rows of `in` have KIN
+// elements, rows of W have ldw.
+template <typename R, int KIN, int NOUT>
+__device__ __forceinline__ void dense_fwd(const R* in, const R* W, int ldw, const R* __restrict__ b, R* out) {
+    constexpr int T = TileOf<R>::T, RW = 3 * T / 8, NJ = NOUT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * RW;
+    R acc[RW][NJ];
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) acc[i][j] = R(0);
+#pragma unroll 2
+    for (int k = 0; k < KIN; k += 4) {
+        R a[RW][4], w[NJ][4];
+#pragma unroll
+        for (int i = 0; i < RW; ++i) ld4<R>(in + (r0 + i) * KIN + k, a[i]);
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) ld4<R>(W + (lane + 32 * j) * ldw + k, w[j]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < RW; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i][q], w[j][q], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < NJ; ++j) {
+            const int r = r0 + i, n = lane + 32 * j;
+            out[r * NOUT + n] = r < T ? acc[i][j] + b[n] : acc[i][j];
+        }
+}
+
+// out[r][k] = sum_n dz[r][n] W[n][k] (reverse pass of a dense layer, k < KIN).
+template <typename R, int KIN, int NOUT>
+__device__ __forceinline__ void dense_bwd(const R* dz, const R* W, int ldw, R* out) {
+    constexpr int T = TileOf<R>::T, RW = 3 * T / 8, KJ = KIN / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * RW;
+    R acc[RW][KJ];
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) acc[i][j] = R(0);
+#pragma unroll 2
+    for (int n = 0; n < NOUT; n += 4) {
+        R a[RW][4];
+#pragma unroll
+        for (int i = 0; i < RW; ++i) ld4<R>(dz + (r0 + i) * NOUT + n, a[i]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            R w[KJ];
+#pragma unroll
+            for (int j = 0; j < KJ; ++j) w[j] = W[(n + q) * ldw + lane + 32 * j];
+#pragma unroll
+            for (int i = 0; i < RW; ++i)
+#pragma unroll
+                for (int j = 0; j < KJ; ++j) acc[i][j] = fma(a[i][q], w[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < KJ; ++j) out[(r0 + i) * KIN + lane + 32 * j] = acc[i][j];
+}
+
+template <typename R>
+__device__ __forceinline__ void acc_store(R* p, R v, bool first) { *p = first ? v : *p + v; }
+
+// Weight and bias gradient of a dense layer over the tile's rows, added to this CTA's slice:
+// pw[n][k] += sum_r dz[r][n] in[r][k],  pb[n] += sum_{s < T} dz[s][n].
+template <typename R, int KIN, int NOUT>
+__device__ __forceinline__ void dense_wgrad(const R* dz, const R* in, R* pw, R* pb, bool first) {
+    constexpr int T = TileOf<R>::T, RT = 3 * T, NW = NOUT / 8, KJ = KIN / 32, NB = 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int n0 = warp * NW; n0 < (warp + 1) * NW; n0 += NB) {
+        R acc[NB][KJ];
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int j = 0; j < KJ; ++j) acc[i][j] = R(0);
+#pragma unroll 2
+        for (int r = 0; r < RT; ++r) {
+            R d[2][4], a[KJ];
+            ld4<R>(dz + r * NOUT + n0, d[0]);
+            ld4<R>(dz + r * NOUT + n0 + 4, d[1]);
+#pragma unroll
+            for (int j = 0; j < KJ; ++j) a[j] = in[r * KIN + lane + 32 * j];
+#pragma unroll
+            for (int i = 0; i < NB; ++i)
+#pragma unroll
+                for (int j = 0; j < KJ; ++j) acc[i][j] = fma(d[i >> 2][i & 3], a[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int j = 0; j < KJ; ++j) acc_store(pw + (n0 + i) * KIN + lane + 32 * j, acc[i][j], first);
+    }
+    if (threadIdx.x < NOUT) {
+        R s = R(0);
+        for (int q = 0; q < T; ++q) s += dz[q * NOUT + threadIdx.x];
+        acc_store(pb + threadIdx.x, s, first);
+    }
+}
+
+// Hidden activation in place: value rows z -> tanh(z), tangent rows z_d -> (1 - a^2) z_d.
+template <typename R, int N>
+__device__ __forceinline__ void tanh_fwd(R* A) {
+    constexpr int T = TileOf<R>::T, TN = T * N;
+    for (int idx = threadIdx.x; idx < TN; idx += TR_THREADS) {
+        const R a = tanh_r<R>(A[idx]), s = R(1) - a * a;
+        A[idx] = a;
+        A[TN + idx] *= s;
+        A[2 * TN + idx] *= s;
+    }
+}
+
+// Reverse pass through a hidden activation: D holds dL/d(a, a_x, a_y), replaced by
+// dL/d(z, z_x, z_y); A holds (a, a_x, a_y).
+template <typename R, int N>
+__device__ __forceinline__ void tanh_bwd(const R* A, R* D) {
+    constexpr int T = TileOf<R>::T, TN = T * N;
+    for (int idx = threadIdx.x; idx < TN; idx += TR_THREADS) {
+        const R a = A[idx], ax = A[TN + idx], ay = A[2 * TN + idx], s = R(1) - a * a;
+        const R d0 = D[idx], d1 = D[TN + idx], d2 = D[2 * TN + idx];
+        D[idx] = s * d0 - R(2) * a * (ax * d1 + ay * d2);
+        D[TN + idx] = s * d1;
+        D[2 * TN + idx] = s * d2;
+    }
+}
+
+// Weight matrix W[N][K] of the master weights for the dense loops: FP32 copies it into the
+// padded staging rows of shared memory, FP64 reads it where it is.
+template <typename R, int N, int K>
+__device__ __forceinline__ const R* stage(const R* __restrict__ w, R* ws, int& ldw) {
+    if constexpr (TileOf<R>::STAGE) {
+        for (int i = threadIdx.x; i < N * K / 4; i += TR_THREADS) {
+            const int n = i / (K / 4), k4 = i % (K / 4);
+            *reinterpret_cast<float4*>(ws + n * (K + 4) + 4 * k4) = *reinterpret_cast<const float4*>(w + n * K + 4 * k4);
+        }
+        ldw = K + 4;
+        return ws;
+    } else {
+        ldw = K;
+        return w;
+    }
+}
+
+// Loss terms of one sample and dL/d(outputs) for its value and tangent rows.
+template <typename R>
+struct SampleLoss {
+    R g[3], gx[3], gy[3];
+    double ld, lp, li;
+};
+
+template <typename R>
+__device__ __forceinline__ SampleLoss<R> sample_loss(const R (&o)[3], const R (&ox)[3], const R (&oy)[3],
+                                                     const R (&t)[3], bool iface, R sx, R sy, R inv_n, R c_phys,
+                                                     R c_int, const TrainLat& L, const TrainHyper& hp) {
+    SampleLoss<R> q;
+    const R r = o[0], u = o[1], v = o[2];
+    const R rx = sx * ox[0], ux = sx * ox[1], vx = sx * ox[2];
+    const R ry = sy * oy[0], uy = sy * oy[1], vy = sy * oy[2];
+    // Eq. 4
+    R e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        e[k] = o[k] - t[k];
+        q.g[k] = R(2) * e[k] * inv_n;
+    }
+    q.ld = (double)e[0] * e[0] + (double)e[1] * e[1] + (double)e[2] * e[2];
+    // Eqs. 5-7: p' and p'' of p = rho/3 + G psi^2/6
+    const R rho0 = R(L.rho0), G = R(L.G);
+    const R ex = exp_r<R>(-r / rho0), psi = rho0 * (R(1) - ex);
+    const R P = R(1) / R(3) + G * psi * ex / R(3);
+    const R dP = G * (ex * ex - psi * ex / rho0) / R(3);
+    const R rc = u * rx + r * ux + v * ry + r * vy;
+    const R rmx = u * u * rx + R(2) * r * u * ux + u * v * ry + r * v * uy + r * u * vy + P * rx;
+    const R rmy = u * v * rx + r * v * ux + r * u * vx + v * v * ry + R(2) * r * v * vy + P * ry;
+    q.lp = (double)rc * rc + (double)rmx * rmx + (double)rmy * rmy;
+    const R A = c_phys * rc, B = c_phys * rmx, C = c_phys * rmy;
+    const R dr = A * (ux + vy) + B * (R(2) * u * ux + v * uy + u * vy + dP * rx) +
+                 C * (v * ux + u * vx + R(2) * v * vy + dP * ry);
+    const R du = A * rx + B * (R(2) * u * rx + R(2) * r * ux + v * ry + r * vy) + C * (v * rx + r * vx);
+    const R dv = A * ry + B * (u * ry + r * uy) + C * (u * rx + r * ux + R(2) * v * ry + R(2) * r * vy);
+    R drx = A * u + B * (u * u + P) + C * (u * v);
+    R dry = A * v + B * (u * v) + C * (v * v + P);
+    const R dux = A * r + B * (R(2) * r * u) + C * (r * v);
+    const R duy = B * (r * v);
+    const R dvx = C * (r * u);
+    const R dvy = A * r + B * (r * u) + C * (R(2) * r * v);
+    // Eq. 8 (signs of the text)
+    q.li = 0.0;
+    if (iface) {
+        const R qq = rx * rx + ry * ry;
+        const R a1 = R(hp.alpha1), a2 = R(hp.alpha2);
+        q.li = (double)(-a1 * qq + a2 * qq * qq);
+        const R dq = c_int * (-a1 + R(2) * a2 * qq);
+        drx += R(2) * dq * rx;
+        dry += R(2) * dq * ry;
+    }
+    q.g[0] += dr;
+    q.g[1] += du;
+    q.g[2] += dv;
+    q.gx[0] = sx * drx; q.gx[1] = sx * dux; q.gx[2] = sx * dvx;
+    q.gy[0] = sy * dry; q.gy[1] = sy * duy; q.gy[2] = sy * dvy;
+    return q;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TR_THREADS, 1)
+k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* __restrict__ loss_part,
+             const unsigned long long* __restrict__ ni_dev, TrainHyper hp, long long ntiles) {
+    using SM = Smem<R>;
+    constexpr int T = SM::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    R *A1 = sm + SM::A1, *A2 = sm + SM::A2, *A3 = sm + SM::A3, *A4 = sm + SM::A4;
+    R *D0 = sm + SM::D0, *D1 = sm + SM::D1, *WS = sm + SM::WS, *X = sm + SM::X, *TG = sm + SM::TG;
+    R *O5 = sm + SM::O5, *D5 = sm + SM::D5, *IF = sm + SM::IF;
+    const int tid = threadIdx.x;
+    const long long N = (long long)L.nx * L.ny;
+    const unsigned long long ni = *ni_dev;
+    const R sx = R(2.0 / L.nx), sy = R(2.0 / L.ny), inv_n = R(1.0 / (double)N);
+    const R c_phys = R(2.0 * hp.lambda_phys / (double)N);
+    const R c_int = ni ? R(hp.lambda_int / (double)ni) : R(0);
+    const R* rho = static_cast<const R*>(L.rho);
+    const R* jx = static_cast<const R*>(L.jx);
+    const R* jy = static_cast<const R*>(L.jy);
+    const R* gf = static_cast<const R*>(L.g);
+    R* P = part + (long long)blockIdx.x * PSTRIDE;
+    double ld = 0.0, lp = 0.0, li = 0.0;
+    int staged = 0, ldw = 0;
+    const R* Wst = nullptr;
+
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const bool first = tile == blockIdx.x;
+        if (tid < T) {
+            const long long c = tile * T + tid;
+            const bool valid = c < N;
+            const long long cc = valid ? c : N - 1;
+            const int x = (int)(cc % L.nx), y = (int)(cc / L.nx);
+            X[2 * tid] = R(2) * (R(x) + R(0.5)) / R(L.nx) - R(1);
+            X[2 * tid + 1] = R(2) * (R(y) + R(0.5)) / R(L.ny) - R(1);
+            const R r = rho[cc];
+            TG[3 * tid] = r;
+            TG[3 * tid + 1] = jx[cc] / r;
+            TG[3 * tid + 2] = jy[cc] / r;
+            IF[tid] = valid ? (above(gf[cc], L.threshold) ? R(1) : R(0)) : R(-1);  // -1: padding sample
+        }
+        __syncthreads();
+        // layer 1 (2 -> 64): value rows from (x^, y^), tangent rows are W1's columns
+        for (int idx = tid; idx < 3 * T * 64; idx += TR_THREADS) {
+            const int r = idx / 64, n = idx % 64, ch = r / T, s = r % T;
+            const R w0 = w[OW1 + 2 * n], w1 = w[OW1 + 2 * n + 1];
+            A1[idx] = ch == 0 ? X[2 * s] * w0 + X[2 * s + 1] * w1 + w[OB1 + n] : (ch == 1 ? w0 : w1);
+        }
+        __syncthreads();
+        tanh_fwd<R, 64>(A1);
+        if (staged != 2) { Wst = stage<R, 128, 64>(w + OW2, WS, ldw); staged = 2; }
+        __syncthreads();
+        dense_fwd<R, 64, 128>(A1, Wst, ldw, w + OB2, A2);
+        __syncthreads();
+        tanh_fwd<R, 128>(A2);
+        Wst = stage<R, 128, 128>(w + OW3, WS, ldw);
+        __syncthreads();
+        dense_fwd<R, 128, 128>(A2, Wst, ldw, w + OB3, A3);
+        __syncthreads();
+        tanh_fwd<R, 128>(A3);
+        Wst = stage<R, 64, 128>(w + OW4, WS, ldw);
+        __syncthreads();
+        dense_fwd<R, 128, 64>(A3, Wst, ldw, w + OB4, A4);
+        __syncthreads();
+        tanh_fwd<R, 64>(A4);
+        __syncthreads();
+        // layer 5 (64 -> 3, linear)
+        for (int idx = tid; idx < 3 * T * 3; idx += TR_THREADS) {
+            const int r = idx / 3, o = idx % 3;
+            R acc = R(0);
+            for (int k = 0; k < 64; ++k) acc = fma(A4[r * 64 + k], w[OW5 + o * 64 + k], acc);
+            O5[idx] = r < T ? acc + w[OB5 + o] : acc;
+        }
+        __syncthreads();
+        // loss and dL/d(outputs), rows s, T + s, 2T + s
+        if (tid < T) {
+            const int s = tid;
+            if (IF[s] >= R(0)) {
+                const R o[3] = {O5[3 * s], O5[3 * s + 1], O5[3 * s + 2]};
+                const R ox[3] = {O5[3 * (T + s)], O5[3 * (T + s) + 1], O5[3 * (T + s) + 2]};
+                const R oy[3] = {O5[3 * (2 * T + s)], O5[3 * (2 * T + s) + 1], O5[3 * (2 * T + s) + 2]};
+                const R t[3] = {TG[3 * s], TG[3 * s + 1], TG[3 * s + 2]};
+                const SampleLoss<R> q = sample_loss<R>(o, ox, oy, t, IF[s] > R(0), sx, sy, inv_n, c_phys, c_int, L, hp);
+                ld += q.ld;
+                lp += q.lp;
+                li += q.li;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    D5[3 * s + k] = q.g[k];
+                    D5[3 * (T + s) + k] = q.gx[k];
+                    D5[3 * (2 * T + s) + k] = q.gy[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) D5[3 * s + k] = D5[3 * (T + s) + k] = D5[3 * (2 * T + s) + k] = R(0);
+            }
+        }
+        __syncthreads();
+        // layer 5 reverse: dW5, db5 and dL/dA4 -> D0 [3T][64]
+        for (int idx = tid; idx < 3 * 64; idx += TR_THREADS) {
+            const int o = idx / 64, k = idx % 64;
+            R acc = R(0);
+            for (int r = 0; r < 3 * T; ++r) acc = fma(D5[3 * r + o], A4[r * 64 + k], acc);
+            acc_store(P + OW5 + idx, acc, first);
+        }
+        if (tid >= 192 && tid < 195) {
+            const int o = tid - 192;
+            R acc = R(0);
+            for (int s = 0; s < T; ++s) acc += D5[3 * s + o];
+            acc_store(P + OB5 + o, acc, first);
+        }
+        for (int idx = tid; idx < 3 * T * 64; idx += TR_THREADS) {
+            const int r = idx / 64, k = idx % 64;
+            D0[idx] = D5[3 * r] * w[OW5 + k] + D5[3 * r + 1] * w[OW5 + 64 + k] + D5[3 * r + 2] * w[OW5 + 128 + k];
+        }
+        __syncthreads();
+        tanh_bwd<R, 64>(A4, D0);
+        __syncthreads();
+        // layer 4 (128 -> 64): W4 is still staged
+        dense_wgrad<R, 128, 64>(D0, A3, P + OW4, P + OB4, first);
+        dense_bwd<R, 128, 64>(D0, Wst, ldw, D1);
+        __syncthreads();
+        tanh_bwd<R, 128>(A3, D1);
+        Wst = stage<R, 128, 128>(w + OW3, WS, ldw);
+        __syncthreads();
+        // layer 3 (128 -> 128)
+        dense_wgrad<R, 128, 128>(D1, A2, P + OW3, P + OB3, first);
+        dense_bwd<R, 128, 128>(D1, Wst, ldw, D0);
+        __syncthreads();
+        tanh_bwd<R, 128>(A2, D0);
+        Wst = stage<R, 128, 64>(w + OW2, WS, ldw);
+        staged = 2;
+        __syncthreads();
+        // layer 2 (64 -> 128)
+        dense_wgrad<R, 64, 128>(D0, A1, P + OW2, P + OB2, first);
+        dense_bwd<R, 64, 128>(D0, Wst, ldw, D1);
+        __syncthreads();
+        tanh_bwd<R, 64>(A1, D1);
+        __syncthreads();
+        // layer 1 (2 -> 64): inputs (x^, y^) on the value rows, unit vectors on the tangent rows
+        if (tid < 64) {
+            R s0 = R(0), s1 = R(0), sb = R(0);
+            for (int s = 0; s < T; ++s) {
+                const R d0 = D1[s * 64 + tid], d1 = D1[(T + s) * 64 + tid], d2 = D1[(2 * T + s) * 64 + tid];
+                s0 += d0 * X[2 * s] + d1;
+                s1 += d0 * X[2 * s + 1] + d2;
+                sb += d0;
+            }
+            acc_store(P + OW1 + 2 * tid, s0, first);
+            acc_store(P + OW1 + 2 * tid + 1, s1, first);
+            acc_store(P + OB1 + tid, sb, first);
+        }
+        __syncthreads();
+    }
+    if ((long long)blockIdx.x < ntiles) {
+        __shared__ double red[3 * 32];
+        double v[3] = {ld, lp, li};
+        const int op[3] = {0, 0, 0};
+        block_reduce<3>(v, op, red);
+        if (tid == 0)
+            for (int k = 0; k < 3; ++k) loss_part[blockIdx.x * 4 + k] = v[k];
+    }
+}
+
+// Interface-cell count (exact integer sum) and the master weights from the FP32 blob.
+template <typename R>
+__global__ void k_train_prep(TrainLat L, const float* __restrict__ w32, R* __restrict__ master,
+                             unsigned long long* __restrict__ ni) {
+    const long long N = (long long)L.nx * L.ny;
+    const R* g = static_cast<const R*>(L.g);
+    unsigned cnt = 0;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        cnt += above(g[c], L.threshold) ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(ni, (unsigned long long)cnt);
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NPARAM; p += gridDim.x * blockDim.x) master[p] = R(w32[p]);
+}
+
+// Fold the CTA slices (CTA order), keep the gradient, apply Adam if `apply`; block 0 also
+// folds the loss terms into hist_row = (L, L_data, L_phys, L_int).
+template <typename R>
+__global__ void k_train_update(R* __restrict__ master, R* __restrict__ m, R* __restrict__ v, R* __restrict__ grad,
+                               const R* __restrict__ part, const double* __restrict__ loss_part,
+                               const unsigned long long* __restrict__ ni, int nact, long long ncells,
+                               TrainHyper hp, double bc1, double bc2, int apply, double* __restrict__ hist_row) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NPARAM; p += gridDim.x * blockDim.x) {
+        SumAcc<R> acc;
+        for (int b = 0; b < nact; ++b) acc.add(part[(long long)b * PSTRIDE + p]);
+        const R g = R(acc.value());
+        grad[p] = g;
+        if (apply) {
+            const R mm = R(hp.beta1) * m[p] + R(1.0 - hp.beta1) * g;
+            const R vv = R(hp.beta2) * v[p] + R(1.0 - hp.beta2) * g * g;
+            m[p] = mm;
+            v[p] = vv;
+            master[p] -= R(hp.lr) * (mm * R(bc1)) / (sqrt(vv * R(bc2)) + R(hp.eps));
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        double s[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; b < nact; ++b)
+            for (int k = 0; k < 3; ++k) s[k] += loss_part[b * 4 + k];
+        const double Ld = s[0] / (double)ncells, Lp = s[1] / (double)ncells;
+        const double Li = *ni ? s[2] / (double)*ni : 0.0;
+        hist_row[0] = Ld + hp.lambda_phys * Lp + hp.lambda_int * Li;
+        hist_row[1] = Ld;
+        hist_row[2] = Lp;
+        hist_row[3] = Li;
+    }
+}
+
+template <typename R>
+__global__ void k_train_finish(const R* __restrict__ master, float* __restrict__ w32) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NPARAM; p += gridDim.x * blockDim.x)
+        w32[p] = (float)master[p];
+}
+
+constexpr int UPD_GRID = 132, UPD_THREADS = 256;  // 33,792 threads >= one per parameter
+
+template <typename R>
+cudaError_t grad_setup(int* grid) {
+    static int g_grid = 0;  // per process and instantiation (one device)
+    if (!g_grid) {
+        cudaError_t e = cudaFuncSetAttribute(k_train_grad<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Smem<R>::bytes);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, occ = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_train_grad<R>, TR_THREADS, Smem<R>::bytes)) !=
+            cudaSuccess)
+            return e;
+        if (occ < 1) return cudaErrorInvalidConfiguration;
+        g_grid = sms * occ;
+    }
+    *grid = g_grid;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+int train_params_count() { return NPARAM; }
+long long train_part_stride() { return PSTRIDE; }
+
+cudaError_t train_grid(int fp64, int* grid) { return fp64 ? grad_setup<double>(grid) : grad_setup<float>(grid); }
+
+template <typename R>
+static cudaError_t begin_t(const TrainLat& L, const TrainBufs& b, const float* w32, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.ni, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_train_prep<R><<<UPD_GRID * 4, 256, 0, s>>>(L, w32, static_cast<R*>(b.master), b.ni);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_begin(const TrainLat& L, const TrainBufs& b, int fp64, const float* w32, cudaStream_t s) {
+    return fp64 ? begin_t<double>(L, b, w32, s) : begin_t<float>(L, b, w32, s);
+}
+
+template <typename R>
+static cudaError_t epoch_t(const TrainLat& L, const TrainBufs& b, const TrainHyper& hp, long long t, int apply,
+                           double* hist_row, cudaStream_t s) {
+    int grid = 0;
+    cudaError_t e = grad_setup<R>(&grid);
+    if (e != cudaSuccess) return e;
+    if (grid > b.grid) return cudaErrorInvalidValue;  // partial buffer sized for fewer CTAs
+    const long long N = (long long)L.nx * L.ny;
+    const long long ntiles = (N + TileOf<R>::T - 1) / TileOf<R>::T;
+    k_train_grad<R><<<grid, TR_THREADS, Smem<R>::bytes, s>>>(L, static_cast<const R*>(b.master),
+                                                             static_cast<R*>(b.part), b.loss_part, b.ni, hp, ntiles);
+    const int nact = (int)(ntiles < grid ? ntiles : grid);
+    const double bc1 = apply ? 1.0 / (1.0 - std::pow(hp.beta1, (double)t)) : 1.0;
+    const double bc2 = apply ? 1.0 / (1.0 - std::pow(hp.beta2, (double)t)) : 1.0;
+    k_train_update<R><<<UPD_GRID, UPD_THREADS, 0, s>>>(static_cast<R*>(b.master), static_cast<R*>(b.m),
+                                                       static_cast<R*>(b.v), static_cast<R*>(b.grad),
+                                                       static_cast<const R*>(b.part), b.loss_part, b.ni, nact, N, hp,
+                                                       bc1, bc2, apply, hist_row);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_train_epoch(const TrainLat& L, const TrainBufs& b, int fp64, const TrainHyper& hp, long long t,
+                               int apply, double* hist_row, cudaStream_t s) {
+    return fp64 ? epoch_t<double>(L, b, hp, t, apply, hist_row, s) : epoch_t<float>(L, b, hp, t, apply, hist_row, s);
+}
+
+cudaError_t launch_train_end(const TrainBufs& b, int fp64, float* w32, uint16_t* wbf16, cudaStream_t s) {
+    if (fp64) k_train_finish<double><<<UPD_GRID, UPD_THREADS, 0, s>>>(static_cast<const double*>(b.master), w32);
+    else k_train_finish<float><<<UPD_GRID, UPD_THREADS, 0, s>>>(static_cast<const float*>(b.master), w32);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_convert_weights_bf16(w32, wbf16, NIN, s);
+}
+
+}  // namespace pl

@@ -98,3 +98,20 @@ def test_null_handle_rejected(lib):
         fn = getattr(lib, name)
         args = [None] + ([1] if name == "pl_step" else [])
         assert fn(*args) == B.PL_ERR_INVALID_ARG
+
+
+def test_train_params_default_and_argument_checks(lib):
+    tp = B.pl_train_params_default()
+    assert (tp.lr, tp.beta1, tp.beta2, tp.eps) == (3e-4, 0.9, 0.999, 1e-8)     # Sec. III-B learning rate
+    assert (tp.lambda_phys, tp.lambda_int, tp.alpha1, tp.alpha2) == (1.0, 1.0, 1.0, 1.0)
+    h = ctypes.c_void_p()
+    # no lattice: refused before any device work
+    assert lib.pl_trainer_create(None, ctypes.byref(tp), 10, ctypes.c_void_p(256), 1 << 20,
+                                 ctypes.byref(h)) == B.PL_ERR_INVALID_ARG
+    out = ctypes.c_size_t(0)
+    p = B.pl_params_default(16, 16, mlp_in=11)
+    assert lib.pl_trainer_bytes(ctypes.byref(p), 10, ctypes.byref(out)) == B.PL_ERR_INVALID_ARG   # 2-input network only
+    p = B.pl_params_default(16, 16)
+    assert lib.pl_trainer_bytes(ctypes.byref(p), 0, ctypes.byref(out)) == B.PL_ERR_INVALID_ARG
+    assert lib.pl_train(None, 1) == B.PL_ERR_INVALID_ARG
+    assert lib.pl_trainer_destroy(None) == B.PL_ERR_INVALID_ARG
