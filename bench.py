@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-field", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--train-side", type=int, default=512)
+    ap.add_argument("--train-epochs", type=int, default=300)
     return ap.parse_args()
 
 
@@ -227,6 +230,66 @@ def run_reference(args):
 
 # ----------------------------------------------------------------------------- GB300 arm
 
+# Training: algorithmic FLOPs per sample and epoch.  Three rows per sample (value and the two
+# input tangents), each through the forward pass (33,088 multiply-adds), the reverse pass to
+# the layer inputs (32,960: none into the 2 coordinates) and the weight gradient (33,088).
+TRAIN_FLOP_PER_SAMPLE = 2 * 3 * (33088 + 32960 + 33088)
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz (maximum SM clock).
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def train_measurement(args, B, wl, torch):
+    """Sec. II-C step 2 at the paper's settings (lr 3e-4, 300 epochs per coupling round) on the
+    single-droplet lattice of side --train-side (FP32 storage): epochs timed with CUDA events on
+    the lattice's stream, then one full coupling round (K = 100 steps, training, correction)."""
+    side, E, K = args.train_side, args.train_epochs, 100
+    job = wl.Lattice(side, side, storage=wl.F32, droplets=[(side / 2, side / 2, side * 80.0 / 512)], seed=2,
+                     K=K, mlp=wl.MLP_BF16, weight_seed=12)
+    lat = B.Lattice.from_workload(job)
+    lat.step(K)
+    tr = B.Trainer(lat, max_epochs=E)
+    tr.train(min(3, E))                                     # warm-up (kernel set-up, first touch)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record(lat.stream)
+    tr.train(E)
+    ev[1].record(lat.stream)
+    ev[1].synchronize()
+    hist = tr.losses(E)
+    ev[2].record(lat.stream)
+    tr.run(K, K, E)                                         # one coupling round: steps, training, correction
+    ev[3].record(lat.stream)
+    ev[3].synchronize()
+    ms_epoch = ev[0].elapsed_time(ev[1]) / E
+    round_ms = ev[2].elapsed_time(ev[3])
+    tflops = job.cells * TRAIN_FLOP_PER_SAMPLE / (ms_epoch / 1e3) / 1e12
+    m = lat.metrics()
+    out = {"workload": "%dx%d single droplet (R=%g), FP32 storage, FP32 training, %d epochs per round, lr 3e-4"
+                       % (side, side, side * 80.0 / 512, E),
+           "ms_per_epoch": ms_epoch, "samples_per_s": job.cells / (ms_epoch / 1e3),
+           "roofline": {"bound": "alu", "kernel": "k_train_grad<float> + k_train_update<float>",
+                        "achieved": tflops, "peak": FP32_ALU_PEAK_TFLOPS, "peak_kind": "derived (152 SMs x 128 "
+                        "FP32 lanes x 2 x 2.07 GHz)", "unit": "TFLOP/s", "frac": tflops / FP32_ALU_PEAK_TFLOPS,
+                        "flop_per_sample": TRAIN_FLOP_PER_SAMPLE},
+           "round_ms": round_ms, "training_share_of_round": E * ms_epoch / round_ms,
+           "loss_first_last": [hist[0, 0], hist[-1, 0]], "status_after_round": m["status"]}
+    tr.close()
+    lat.close()
+    torch.cuda.empty_cache()
+    if not args.no_cpu:
+        import numpy as np
+        import oracle as O
+        import oracle.train as OT
+        n = 128
+        f = O.init_equilibrium(O.init_rho(n, n, [(n / 2, n / 2, n * 80.0 / 512)], 2.0, 0.15, 2.0, 0.01, 2))
+        t0 = time.perf_counter()
+        OT.train(job.weights(), f, 3, job.G)
+        dt = (time.perf_counter() - t0) / 3
+        out["cpu_baseline"] = {"value": n * n / dt, "unit": "samples/s", "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": "FP64 numpy training oracle, 3 epochs on a 128x128 lattice, %.2f s per epoch"
+                                         % dt}
+    return out
+
+
 def run_gb300(args):
     import numpy as np
     import torch
@@ -385,6 +448,11 @@ def run_gb300(args):
             del lat
             torch.cuda.empty_cache()
 
+    # --------------------------------------------------------------- network training (Eqs. 3-8)
+    training = None
+    if not args.no_train and rank == 0:
+        training = train_measurement(args, B, wl, torch)
+
     # --------------------------------------------------------------- CPU baseline
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -412,6 +480,7 @@ def run_gb300(args):
             "fp32_plain": fp32,
             "serving": serving,
             "field_4096": field,
+            "training": training,
             "cpu_baseline": cpu,
             "batch_checks": {"statuses": statuses, "max_mass_drift_post_correction": drift},
         }
