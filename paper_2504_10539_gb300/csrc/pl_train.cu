@@ -21,14 +21,18 @@
 // tanh'(z) z_d).  The reverse pass runs through all three rows; the only coupling between
 // them is tanh's second derivative:  dL/dz = s dL/da - 2 a sum_d a_d dL/da_d, s = 1 - a^2.
 //
-// Kernel layout.  A CTA of 256 threads takes tiles of T samples (T = 16 in FP32, 8 in FP64),
-// i.e. 3T rows, and keeps every hidden layer's rows of the tile in shared memory for the
-// reverse pass.  The dense layers are register-tiled loops over shared memory: each warp
-// owns 3T/8 rows and each lane 32-strided columns, operand rows are broadcast and weight
-// columns are conflict-free (FP32 weights are staged per layer with rows padded by 4).  The
-// weight gradient of a tile is added into a per-CTA slice of a partial buffer that each
-// thread owns element-wise, so no atomics are needed and the sums are deterministic for a
-// given grid.  The update kernel folds the slices in CTA order and applies Adam.
+// Kernel layout.  A CTA of 256 threads (one per SM) takes tiles of T samples (T = 16 in FP32,
+// 8 in FP64), i.e. 3T rows, and keeps every hidden layer's rows of the tile in shared memory
+// for the reverse pass.  The dense layers are register-tiled loops over shared memory: lane
+// (rg, cg) of a warp holds rows rg, rg + 8, ... and a group of columns, so operand rows come
+// as broadcast 16-byte loads; every row is padded by 4 elements, which puts the 8 row groups
+// on distinct banks.  In FP32, W3 stays in shared memory for the whole launch and W2 / W4 share
+// a second buffer that is refilled by cp.async while the other layers compute.  The weight
+// gradient of a tile is added into this CTA's slice of a partial buffer: the first tile
+// stores, later tiles add with vector reductions (red.global.add) that the thread does not
+// wait for.  Each element of a slice is written by one thread only, whose operations on it
+// are applied in program order, so the sums are deterministic for a given grid.  The update
+// kernel folds the slices in CTA order and applies Adam.
 #include <cmath>
 
 #include "pl_device.cuh"
@@ -51,30 +55,49 @@ template <typename R> struct TileOf;
 template <> struct TileOf<float> { static constexpr int T = 16; static constexpr bool STAGE = true; };
 template <> struct TileOf<double> { static constexpr int T = 8; static constexpr bool STAGE = false; };
 
-// Shared-memory plan (elements of R): activations of the 4 hidden layers [3][T][N_l], two
-// reverse-pass buffers [3T][128], the staged weight matrix [128][128 + 4] (FP32 only), and
-// the per-sample scalars.
+constexpr int L64 = 64 + 4, L128 = 128 + 4;  // padded lengths of 64- and 128-wide rows
+template <int K> struct Ld { static constexpr int v = K + 4; };
+
+// Shared-memory plan (elements of R): activations of the 4 hidden layers [3T][N_l + 4], two
+// reverse-pass buffers [3T][128 + 4], in FP32 the resident W3 [128][128 + 4] and the W2 / W4
+// buffer [128][64 + 4] >= [64][128 + 4], and the per-sample scalars.
 template <typename R>
 struct Smem {
+    static constexpr bool ST = TileOf<R>::STAGE;
     static constexpr int T = TileOf<R>::T, RT = 3 * T;
-    static constexpr int A1 = 0, A2 = A1 + RT * 64, A3 = A2 + RT * 128, A4 = A3 + RT * 128, D0 = A4 + RT * 64,
-                         D1 = D0 + RT * 128, WS = D1 + RT * 128, WS_N = TileOf<R>::STAGE ? 128 * 132 : 0,
-                         X = WS + WS_N, TG = X + 2 * T, O5 = TG + 3 * T, D5 = O5 + RT * 3, IF = D5 + RT * 3,
-                         TOTAL = IF + T;
+    static constexpr int A1 = 0, A2 = A1 + RT * L64, A3 = A2 + RT * L128, A4 = A3 + RT * L128, D0 = A4 + RT * L64,
+                         D1 = D0 + RT * L128, WA = D1 + RT * L128, WB = WA + (ST ? 128 * L128 : 0),
+                         X = WB + (ST ? 128 * L64 : 0), TG = X + 2 * T, O5 = TG + 3 * T, D5 = O5 + RT * 3,
+                         IF = D5 + RT * 3, TOTAL = IF + T;
     static constexpr size_t bytes = (size_t)TOTAL * sizeof(R);
+    static_assert(128 * L64 >= 64 * L128, "W2 / W4 buffer");
+    static_assert(A2 % 4 == 0 && A3 % 4 == 0 && A4 % 4 == 0 && D0 % 4 == 0 && D1 % 4 == 0 && WA % 4 == 0 &&
+                      WB % 4 == 0 && X % 4 == 0,
+                  "16-byte aligned regions");
 };
+static_assert(Smem<float>::bytes <= 227 * 1024, "shared memory of one CTA");
 
-template <typename R>
-__device__ __forceinline__ void ld4(const R* p, R (&v)[4]);
+template <typename R, int N>
+__device__ __forceinline__ void ldv(const R* p, R (&v)[N]);
 template <>
-__device__ __forceinline__ void ld4<float>(const float* p, float (&v)[4]) {
+__device__ __forceinline__ void ldv<float, 4>(const float* p, float (&v)[4]) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
 template <>
-__device__ __forceinline__ void ld4<double>(const double* p, double (&v)[4]) {
+__device__ __forceinline__ void ldv<float, 2>(const float* p, float (&v)[2]) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+}
+template <>
+__device__ __forceinline__ void ldv<double, 4>(const double* p, double (&v)[4]) {
     const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <>
+__device__ __forceinline__ void ldv<double, 2>(const double* p, double (&v)[2]) {
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    v[0] = a.x; v[1] = a.y;
 }
 
 template <typename R> __device__ __forceinline__ R tanh_r(R z);
@@ -89,121 +112,148 @@ template <> __device__ __forceinline__ double exp_r<double>(double z) { return e
 __device__ __forceinline__ bool above(float g, double thr) { return g > __double2float_rd(thr); }
 __device__ __forceinline__ bool above(double g, double thr) { return g > thr; }
 
-// out[r][n] = sum_k in[r][k] W[n][k] (+ b[n] on the value rows r < T); rows of `in` have KIN
-// elements, rows of W have ldw.
+// Partial-slice updates: the first tile stores, later tiles add.  FP32 adds are reductions
+// the thread does not wait for; FP64 (the parity path) reads and writes.
+__device__ __forceinline__ void acc1(float* p, float v, bool first) {
+    if (first) *p = v;
+    else asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void acc1(double* p, double v, bool first) { *p = first ? v : *p + v; }
+__device__ __forceinline__ void acc4(float* p, const float (&v)[4], bool first) {
+    if (first) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(__cvta_generic_to_global(p)), "f"(v[0]),
+                     "f"(v[1]), "f"(v[2]),
+                     "f"(v[3])
+                     : "memory");
+}
+__device__ __forceinline__ void acc4(double* p, const double (&v)[4], bool first) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) p[e] = first ? v[e] : p[e] + v[e];
+}
+
+// out[r][n] = sum_k in[r][k] W[n][k] (+ b[n] on the value rows r < T), n < NOUT.  Lane
+// (rg, cg) = (lane / 4, lane % 4) of warp w computes rows rg + 8 i and columns
+// w NOUT/8 + cg + 4 c.  Rows of `in` / `out` are padded (KIN + 4, NOUT + 4); rows of W have ldw.
 template <typename R, int KIN, int NOUT>
 __device__ __forceinline__ void dense_fwd(const R* in, const R* W, int ldw, const R* __restrict__ b, R* out) {
-    constexpr int T = TileOf<R>::T, RW = 3 * T / 8, NJ = NOUT / 32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * RW;
-    R acc[RW][NJ];
+    constexpr int T = TileOf<R>::T, RPL = 3 * T / 8, CPL = NOUT / 32, LI = Ld<KIN>::v, LO = Ld<NOUT>::v;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, rg = lane >> 2, cg = lane & 3;
+    const int nb = warp * (NOUT / 8) + cg;
+    R acc[RPL][CPL];
 #pragma unroll
-    for (int i = 0; i < RW; ++i)
+    for (int i = 0; i < RPL; ++i)
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) acc[i][j] = R(0);
+        for (int c = 0; c < CPL; ++c) acc[i][c] = R(0);
 #pragma unroll 2
     for (int k = 0; k < KIN; k += 4) {
-        R a[RW][4], w[NJ][4];
+        R a[RPL][4], w[CPL][4];
 #pragma unroll
-        for (int i = 0; i < RW; ++i) ld4<R>(in + (r0 + i) * KIN + k, a[i]);
+        for (int i = 0; i < RPL; ++i) ldv<R, 4>(in + (rg + 8 * i) * LI + k, a[i]);
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) ld4<R>(W + (lane + 32 * j) * ldw + k, w[j]);
+        for (int c = 0; c < CPL; ++c) ldv<R, 4>(W + (nb + 4 * c) * ldw + k, w[c]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int i = 0; i < RW; ++i)
+            for (int i = 0; i < RPL; ++i)
 #pragma unroll
-                for (int j = 0; j < NJ; ++j) acc[i][j] = fma(a[i][q], w[j][q], acc[i][j]);
+                for (int c = 0; c < CPL; ++c) acc[i][c] = fma(a[i][q], w[c][q], acc[i][c]);
     }
 #pragma unroll
-    for (int i = 0; i < RW; ++i)
+    for (int i = 0; i < RPL; ++i)
 #pragma unroll
-        for (int j = 0; j < NJ; ++j) {
-            const int r = r0 + i, n = lane + 32 * j;
-            out[r * NOUT + n] = r < T ? acc[i][j] + b[n] : acc[i][j];
+        for (int c = 0; c < CPL; ++c) {
+            const int r = rg + 8 * i, n = nb + 4 * c;
+            out[r * LO + n] = r < T ? acc[i][c] + b[n] : acc[i][c];
         }
 }
 
-// out[r][k] = sum_n dz[r][n] W[n][k] (reverse pass of a dense layer, k < KIN).
+// out[r][k] = sum_n dz[r][n] W[n][k], k < KIN (reverse pass of a dense layer).  Lane (rg, cg)
+// of warp w computes rows rg + 8 i and the CPL = KIN/32 adjacent columns from
+// w KIN/8 + cg CPL.
 template <typename R, int KIN, int NOUT>
 __device__ __forceinline__ void dense_bwd(const R* dz, const R* W, int ldw, R* out) {
-    constexpr int T = TileOf<R>::T, RW = 3 * T / 8, KJ = KIN / 32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, r0 = warp * RW;
-    R acc[RW][KJ];
+    constexpr int T = TileOf<R>::T, RPL = 3 * T / 8, CPL = KIN / 32, LZ = Ld<NOUT>::v, LO = Ld<KIN>::v;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, rg = lane >> 2, cg = lane & 3;
+    const int k0 = warp * (KIN / 8) + cg * CPL;
+    R acc[RPL][CPL];
 #pragma unroll
-    for (int i = 0; i < RW; ++i)
+    for (int i = 0; i < RPL; ++i)
 #pragma unroll
-        for (int j = 0; j < KJ; ++j) acc[i][j] = R(0);
+        for (int c = 0; c < CPL; ++c) acc[i][c] = R(0);
 #pragma unroll 2
     for (int n = 0; n < NOUT; n += 4) {
-        R a[RW][4];
+        R a[RPL][4];
 #pragma unroll
-        for (int i = 0; i < RW; ++i) ld4<R>(dz + (r0 + i) * NOUT + n, a[i]);
+        for (int i = 0; i < RPL; ++i) ldv<R, 4>(dz + (rg + 8 * i) * LZ + n, a[i]);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            R w[KJ];
+            R w[CPL];
+            ldv<R, CPL>(W + (n + q) * ldw + k0, w);
 #pragma unroll
-            for (int j = 0; j < KJ; ++j) w[j] = W[(n + q) * ldw + lane + 32 * j];
+            for (int i = 0; i < RPL; ++i)
 #pragma unroll
-            for (int i = 0; i < RW; ++i)
-#pragma unroll
-                for (int j = 0; j < KJ; ++j) acc[i][j] = fma(a[i][q], w[j], acc[i][j]);
+                for (int c = 0; c < CPL; ++c) acc[i][c] = fma(a[i][q], w[c], acc[i][c]);
         }
     }
 #pragma unroll
-    for (int i = 0; i < RW; ++i)
+    for (int i = 0; i < RPL; ++i)
 #pragma unroll
-        for (int j = 0; j < KJ; ++j) out[(r0 + i) * KIN + lane + 32 * j] = acc[i][j];
+        for (int c = 0; c < CPL; ++c) out[(rg + 8 * i) * LO + k0 + c] = acc[i][c];
 }
 
-template <typename R>
-__device__ __forceinline__ void acc_store(R* p, R v, bool first) { *p = first ? v : *p + v; }
-
 // Weight and bias gradient of a dense layer over the tile's rows, added to this CTA's slice:
-// pw[n][k] += sum_r dz[r][n] in[r][k],  pb[n] += sum_{s < T} dz[s][n].
+// pw[n][k] += sum_r dz[r][n] in[r][k],  pb[n] += sum_{s < T} dz[s][n].  Warp w owns rows
+// n of W in [w NOUT/8, (w+1) NOUT/8); lane = ng KG + kg holds 4 adjacent n and the column
+// quads kg + KG j.
 template <typename R, int KIN, int NOUT>
 __device__ __forceinline__ void dense_wgrad(const R* dz, const R* in, R* pw, R* pb, bool first) {
-    constexpr int T = TileOf<R>::T, RT = 3 * T, NW = NOUT / 8, KJ = KIN / 32, NB = 8;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll 1
-    for (int n0 = warp * NW; n0 < (warp + 1) * NW; n0 += NB) {
-        R acc[NB][KJ];
+    constexpr int T = TileOf<R>::T, RT = 3 * T, LZ = Ld<NOUT>::v, LI = Ld<KIN>::v;
+    constexpr int NW = NOUT / 8, NG = NW / 4, KG = 32 / NG, KQ = KIN / (4 * KG);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, ng = lane / KG, kg = lane % KG;
+    const int n0 = warp * NW + 4 * ng;
+    R acc[4][KQ][4];
 #pragma unroll
-        for (int i = 0; i < NB; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < KJ; ++j) acc[i][j] = R(0);
+        for (int j = 0; j < KQ; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = R(0);
 #pragma unroll 2
-        for (int r = 0; r < RT; ++r) {
-            R d[2][4], a[KJ];
-            ld4<R>(dz + r * NOUT + n0, d[0]);
-            ld4<R>(dz + r * NOUT + n0 + 4, d[1]);
+    for (int r = 0; r < RT; ++r) {
+        R d[4];
+        ldv<R, 4>(dz + r * LZ + n0, d);
 #pragma unroll
-            for (int j = 0; j < KJ; ++j) a[j] = in[r * KIN + lane + 32 * j];
+        for (int j = 0; j < KQ; ++j) {
+            R a[4];
+            ldv<R, 4>(in + r * LI + 4 * (kg + KG * j), a);
 #pragma unroll
-            for (int i = 0; i < NB; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < KJ; ++j) acc[i][j] = fma(d[i >> 2][i & 3], a[j], acc[i][j]);
+                for (int e = 0; e < 4; ++e) acc[i][j][e] = fma(d[i], a[e], acc[i][j][e]);
         }
-#pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int j = 0; j < KJ; ++j) acc_store(pw + (n0 + i) * KIN + lane + 32 * j, acc[i][j], first);
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < KQ; ++j) acc4(pw + (n0 + i) * KIN + 4 * (kg + KG * j), acc[i][j], first);
     if (threadIdx.x < NOUT) {
         R s = R(0);
-        for (int q = 0; q < T; ++q) s += dz[q * NOUT + threadIdx.x];
-        acc_store(pb + threadIdx.x, s, first);
+        for (int q = 0; q < T; ++q) s += dz[q * LZ + threadIdx.x];
+        acc1(pb + threadIdx.x, s, first);
     }
 }
 
 // Hidden activation in place: value rows z -> tanh(z), tangent rows z_d -> (1 - a^2) z_d.
 template <typename R, int N>
 __device__ __forceinline__ void tanh_fwd(R* A) {
-    constexpr int T = TileOf<R>::T, TN = T * N;
-    for (int idx = threadIdx.x; idx < TN; idx += TR_THREADS) {
-        const R a = tanh_r<R>(A[idx]), s = R(1) - a * a;
-        A[idx] = a;
-        A[TN + idx] *= s;
-        A[2 * TN + idx] *= s;
+    constexpr int T = TileOf<R>::T, L = Ld<N>::v, TL = T * L;
+    for (int idx = threadIdx.x; idx < T * N; idx += TR_THREADS) {
+        const int o = (idx / N) * L + idx % N;
+        const R a = tanh_r<R>(A[o]), s = R(1) - a * a;
+        A[o] = a;
+        A[TL + o] *= s;
+        A[2 * TL + o] *= s;
     }
 }
 
@@ -211,32 +261,30 @@ __device__ __forceinline__ void tanh_fwd(R* A) {
 // dL/d(z, z_x, z_y); A holds (a, a_x, a_y).
 template <typename R, int N>
 __device__ __forceinline__ void tanh_bwd(const R* A, R* D) {
-    constexpr int T = TileOf<R>::T, TN = T * N;
-    for (int idx = threadIdx.x; idx < TN; idx += TR_THREADS) {
-        const R a = A[idx], ax = A[TN + idx], ay = A[2 * TN + idx], s = R(1) - a * a;
-        const R d0 = D[idx], d1 = D[TN + idx], d2 = D[2 * TN + idx];
-        D[idx] = s * d0 - R(2) * a * (ax * d1 + ay * d2);
-        D[TN + idx] = s * d1;
-        D[2 * TN + idx] = s * d2;
+    constexpr int T = TileOf<R>::T, L = Ld<N>::v, TL = T * L;
+    for (int idx = threadIdx.x; idx < T * N; idx += TR_THREADS) {
+        const int o = (idx / N) * L + idx % N;
+        const R a = A[o], ax = A[TL + o], ay = A[2 * TL + o], s = R(1) - a * a;
+        const R d0 = D[o], d1 = D[TL + o], d2 = D[2 * TL + o];
+        D[o] = s * d0 - R(2) * a * (ax * d1 + ay * d2);
+        D[TL + o] = s * d1;
+        D[2 * TL + o] = s * d2;
     }
 }
 
-// Weight matrix W[N][K] of the master weights for the dense loops: FP32 copies it into the
-// padded staging rows of shared memory, FP64 reads it where it is.
-template <typename R, int N, int K>
-__device__ __forceinline__ const R* stage(const R* __restrict__ w, R* ws, int& ldw) {
-    if constexpr (TileOf<R>::STAGE) {
-        for (int i = threadIdx.x; i < N * K / 4; i += TR_THREADS) {
-            const int n = i / (K / 4), k4 = i % (K / 4);
-            *reinterpret_cast<float4*>(ws + n * (K + 4) + 4 * k4) = *reinterpret_cast<const float4*>(w + n * K + 4 * k4);
-        }
-        ldw = K + 4;
-        return ws;
-    } else {
-        ldw = K;
-        return w;
+// Asynchronous copy of W[N][K] (FP32 master weights) into padded shared rows (K + 4); the
+// caller waits with stage_wait() and a barrier before reading.
+template <int N, int K>
+__device__ __forceinline__ void stage_async(const float* __restrict__ w, float* ws) {
+    for (int i = threadIdx.x; i < N * K / 4; i += TR_THREADS) {
+        const int n = i / (K / 4), k4 = i % (K / 4);
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(ws + n * (K + 4) + 4 * k4);
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(__cvta_generic_to_global(w + n * K + 4 * k4))
+                     : "memory");
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Loss terms of one sample and dL/d(outputs) for its value and tangent rows.
 template <typename R>
@@ -304,13 +352,15 @@ __global__ void __launch_bounds__(TR_THREADS, 1)
 k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* __restrict__ loss_part,
              const unsigned long long* __restrict__ ni_dev, TrainHyper hp, long long ntiles) {
     using SM = Smem<R>;
-    constexpr int T = SM::T;
+    constexpr int T = SM::T, RT = SM::RT;
+    constexpr bool ST = TileOf<R>::STAGE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     R *A1 = sm + SM::A1, *A2 = sm + SM::A2, *A3 = sm + SM::A3, *A4 = sm + SM::A4;
-    R *D0 = sm + SM::D0, *D1 = sm + SM::D1, *WS = sm + SM::WS, *X = sm + SM::X, *TG = sm + SM::TG;
+    R *D0 = sm + SM::D0, *D1 = sm + SM::D1, *X = sm + SM::X, *TG = sm + SM::TG;
     R *O5 = sm + SM::O5, *D5 = sm + SM::D5, *IF = sm + SM::IF;
     const int tid = threadIdx.x;
+    if ((long long)blockIdx.x >= ntiles) return;   // no tile, no slice (the fold skips it)
     const long long N = (long long)L.nx * L.ny;
     const unsigned long long ni = *ni_dev;
     const R sx = R(2.0 / L.nx), sy = R(2.0 / L.ny), inv_n = R(1.0 / (double)N);
@@ -322,8 +372,22 @@ k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* 
     const R* gf = static_cast<const R*>(L.g);
     R* P = part + (long long)blockIdx.x * PSTRIDE;
     double ld = 0.0, lp = 0.0, li = 0.0;
-    int staged = 0, ldw = 0;
-    const R* Wst = nullptr;
+    // Weight operands: FP32 reads W3 from its resident copy and W2 / W4 from the shared buffer
+    // WB (W2 on entry to every tile); FP64 reads the master weights in place.
+    const R* W2 = w + OW2;
+    const R* W3 = w + OW3;
+    const R* W4 = w + OW4;
+    int ld2 = 64, ld3 = 128, ld4 = 128;
+    if constexpr (ST) {
+        R* WA = sm + SM::WA;
+        R* WB = sm + SM::WB;
+        stage_async<128, 128>(w + OW3, WA);
+        stage_async<128, 64>(w + OW2, WB);
+        stage_wait();
+        W2 = WB; W3 = WA; W4 = WB;
+        ld2 = L64; ld3 = L128; ld4 = L128;
+    }
+    __syncthreads();
 
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const bool first = tile == blockIdx.x;
@@ -342,34 +406,33 @@ k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* 
         }
         __syncthreads();
         // layer 1 (2 -> 64): value rows from (x^, y^), tangent rows are W1's columns
-        for (int idx = tid; idx < 3 * T * 64; idx += TR_THREADS) {
+        for (int idx = tid; idx < RT * 64; idx += TR_THREADS) {
             const int r = idx / 64, n = idx % 64, ch = r / T, s = r % T;
             const R w0 = w[OW1 + 2 * n], w1 = w[OW1 + 2 * n + 1];
-            A1[idx] = ch == 0 ? X[2 * s] * w0 + X[2 * s + 1] * w1 + w[OB1 + n] : (ch == 1 ? w0 : w1);
+            A1[r * L64 + n] = ch == 0 ? X[2 * s] * w0 + X[2 * s + 1] * w1 + w[OB1 + n] : (ch == 1 ? w0 : w1);
         }
         __syncthreads();
         tanh_fwd<R, 64>(A1);
-        if (staged != 2) { Wst = stage<R, 128, 64>(w + OW2, WS, ldw); staged = 2; }
         __syncthreads();
-        dense_fwd<R, 64, 128>(A1, Wst, ldw, w + OB2, A2);
+        dense_fwd<R, 64, 128>(A1, W2, ld2, w + OB2, A2);               // layer 2 (W2 in WB)
         __syncthreads();
+        if constexpr (ST) stage_async<64, 128>(w + OW4, sm + SM::WB);   // W4 -> WB behind layer 3
         tanh_fwd<R, 128>(A2);
-        Wst = stage<R, 128, 128>(w + OW3, WS, ldw);
         __syncthreads();
-        dense_fwd<R, 128, 128>(A2, Wst, ldw, w + OB3, A3);
+        dense_fwd<R, 128, 128>(A2, W3, ld3, w + OB3, A3);              // layer 3
+        if constexpr (ST) stage_wait();
         __syncthreads();
         tanh_fwd<R, 128>(A3);
-        Wst = stage<R, 64, 128>(w + OW4, WS, ldw);
         __syncthreads();
-        dense_fwd<R, 128, 64>(A3, Wst, ldw, w + OB4, A4);
+        dense_fwd<R, 128, 64>(A3, W4, ld4, w + OB4, A4);               // layer 4 (W4 in WB)
         __syncthreads();
         tanh_fwd<R, 64>(A4);
         __syncthreads();
         // layer 5 (64 -> 3, linear)
-        for (int idx = tid; idx < 3 * T * 3; idx += TR_THREADS) {
+        for (int idx = tid; idx < RT * 3; idx += TR_THREADS) {
             const int r = idx / 3, o = idx % 3;
             R acc = R(0);
-            for (int k = 0; k < 64; ++k) acc = fma(A4[r * 64 + k], w[OW5 + o * 64 + k], acc);
+            for (int k = 0; k < 64; ++k) acc = fma(A4[r * L64 + k], w[OW5 + o * 64 + k], acc);
             O5[idx] = r < T ? acc + w[OB5 + o] : acc;
         }
         __syncthreads();
@@ -401,40 +464,40 @@ k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* 
         for (int idx = tid; idx < 3 * 64; idx += TR_THREADS) {
             const int o = idx / 64, k = idx % 64;
             R acc = R(0);
-            for (int r = 0; r < 3 * T; ++r) acc = fma(D5[3 * r + o], A4[r * 64 + k], acc);
-            acc_store(P + OW5 + idx, acc, first);
+            for (int r = 0; r < RT; ++r) acc = fma(D5[3 * r + o], A4[r * L64 + k], acc);
+            acc1(P + OW5 + idx, acc, first);
         }
         if (tid >= 192 && tid < 195) {
             const int o = tid - 192;
             R acc = R(0);
             for (int s = 0; s < T; ++s) acc += D5[3 * s + o];
-            acc_store(P + OB5 + o, acc, first);
+            acc1(P + OB5 + o, acc, first);
         }
-        for (int idx = tid; idx < 3 * T * 64; idx += TR_THREADS) {
+        for (int idx = tid; idx < RT * 64; idx += TR_THREADS) {
             const int r = idx / 64, k = idx % 64;
-            D0[idx] = D5[3 * r] * w[OW5 + k] + D5[3 * r + 1] * w[OW5 + 64 + k] + D5[3 * r + 2] * w[OW5 + 128 + k];
+            D0[r * L64 + k] =
+                D5[3 * r] * w[OW5 + k] + D5[3 * r + 1] * w[OW5 + 64 + k] + D5[3 * r + 2] * w[OW5 + 128 + k];
         }
         __syncthreads();
         tanh_bwd<R, 64>(A4, D0);
         __syncthreads();
-        // layer 4 (128 -> 64): W4 is still staged
+        // layer 4 (128 -> 64), W4 in WB
         dense_wgrad<R, 128, 64>(D0, A3, P + OW4, P + OB4, first);
-        dense_bwd<R, 128, 64>(D0, Wst, ldw, D1);
+        dense_bwd<R, 128, 64>(D0, W4, ld4, D1);
         __syncthreads();
+        if constexpr (ST) stage_async<128, 64>(w + OW2, sm + SM::WB);   // W2 -> WB behind layer 3
         tanh_bwd<R, 128>(A3, D1);
-        Wst = stage<R, 128, 128>(w + OW3, WS, ldw);
         __syncthreads();
         // layer 3 (128 -> 128)
         dense_wgrad<R, 128, 128>(D1, A2, P + OW3, P + OB3, first);
-        dense_bwd<R, 128, 128>(D1, Wst, ldw, D0);
+        dense_bwd<R, 128, 128>(D1, W3, ld3, D0);
+        if constexpr (ST) stage_wait();
         __syncthreads();
         tanh_bwd<R, 128>(A2, D0);
-        Wst = stage<R, 128, 64>(w + OW2, WS, ldw);
-        staged = 2;
         __syncthreads();
-        // layer 2 (64 -> 128)
+        // layer 2 (64 -> 128), W2 in WB (and for the next tile's forward pass)
         dense_wgrad<R, 64, 128>(D0, A1, P + OW2, P + OB2, first);
-        dense_bwd<R, 64, 128>(D0, Wst, ldw, D1);
+        dense_bwd<R, 64, 128>(D0, W2, ld2, D1);
         __syncthreads();
         tanh_bwd<R, 64>(A1, D1);
         __syncthreads();
@@ -442,25 +505,22 @@ k_train_grad(TrainLat L, const R* __restrict__ w, R* __restrict__ part, double* 
         if (tid < 64) {
             R s0 = R(0), s1 = R(0), sb = R(0);
             for (int s = 0; s < T; ++s) {
-                const R d0 = D1[s * 64 + tid], d1 = D1[(T + s) * 64 + tid], d2 = D1[(2 * T + s) * 64 + tid];
+                const R d0 = D1[s * L64 + tid], d1 = D1[(T + s) * L64 + tid], d2 = D1[(2 * T + s) * L64 + tid];
                 s0 += d0 * X[2 * s] + d1;
                 s1 += d0 * X[2 * s + 1] + d2;
                 sb += d0;
             }
-            acc_store(P + OW1 + 2 * tid, s0, first);
-            acc_store(P + OW1 + 2 * tid + 1, s1, first);
-            acc_store(P + OB1 + tid, sb, first);
+            acc1(P + OW1 + 2 * tid, s0, first);
+            acc1(P + OW1 + 2 * tid + 1, s1, first);
+            acc1(P + OB1 + tid, sb, first);
         }
         __syncthreads();
     }
-    if ((long long)blockIdx.x < ntiles) {
-        __shared__ double red[3 * 32];
-        double v[3] = {ld, lp, li};
-        const int op[3] = {0, 0, 0};
-        block_reduce<3>(v, op, red);
-        if (tid == 0)
-            for (int k = 0; k < 3; ++k) loss_part[blockIdx.x * 4 + k] = v[k];
-    }
+    double v[3] = {ld, lp, li};
+    const int op[3] = {0, 0, 0};
+    block_reduce<3>(v, op, reinterpret_cast<double*>(D0));   // D0 is free here
+    if (tid == 0)
+        for (int k = 0; k < 3; ++k) loss_part[blockIdx.x * 4 + k] = v[k];
 }
 
 // Interface-cell count (exact integer sum) and the master weights from the FP32 blob.
