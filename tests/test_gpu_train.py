@@ -170,3 +170,38 @@ def test_full_size_512_gradient_matches_oracle():
     tr.train(2)
     h = tr.losses(2)
     assert h[1, 0] < h[0, 0]
+
+
+def test_protocol_series_match_oracle():
+    """Sec. III-C protocol on a 48 x 48 FP64 droplet (shortened: 60 initial steps recorded
+    every 20, rounds of 20 steps with 4, 3, 2 epochs): every recorded metric of the initial,
+    PINN-LBM and pure-LBM series against the oracle running the same sequence."""
+    from paper_2504_10539_gb300 import protocol
+    job = wl.Lattice(48, 48, storage=B.PL_F64, mlp=B.PL_MLP_F64, droplets=[(24.0, 24.0, 10.0)], seed=6, K=20,
+                     weight_seed=42)
+    out = protocol.run(job, init_steps=60, K=20, epochs=(4, 3, 2), record_every=20)
+    assert out["status"] == {"pinn": 0, "pure": 0}
+    fo = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
+                                       job.noise_amp, job.seed))
+    M0 = O.mass(fo)
+
+    def close(gpu, f):
+        ref = O.metrics_rho(O.density(f))
+        for k in protocol.METRICS:
+            assert gpu[k] == pytest.approx(ref[k], rel=1e-9, abs=1e-12), k
+
+    close(out["init"][0][1], fo)
+    for step, m in out["init"][1:]:
+        O.step(fo, 20, job.G, job.tau)
+        close(m, fo)
+    fp = fo.copy()
+    blob, st = job.weights(), None
+    for (step, e, m, losses), (step2, mp) in zip(out["pinn"], out["pure"]):
+        O.step(fo, 20, job.G, job.tau)
+        blob, hist, st = T.train(blob, fo, e, job.G, state=st)
+        assert O.correct(fo, blob, job.beta_rho, job.beta_u, M0, O.MLP_F64) == 0
+        O.step(fp, 20, job.G, job.tau)
+        close(m, fo)
+        close(mp, fp)
+        assert losses[0] == pytest.approx(hist[0, 0], rel=1e-10) and losses[1] == pytest.approx(hist[-1, 0], rel=1e-10)
+    assert [e for _, e, _, _ in out["pinn"]] == [4, 3, 2] and out["pinn"][-1][0] == 120
