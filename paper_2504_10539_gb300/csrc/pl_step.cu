@@ -382,26 +382,28 @@ __device__ __forceinline__ void collide_pair(const float2 (&h)[9], float2 rho, f
     const float2 uy = fma2(bc2(k.tau), fy, jy) * inv;
     const float2 usq = fma2(ux, ux, uy * uy);
     const float2 Ap = fma2(rho, fma2(bc2(-1.5f), usq, bc2(1.0f)), bc2(-k.rho_ref));
-    const float2 t3 = bc2(3.0f) * rho, t45 = bc2(4.5f) * rho;
+    // o_i = h_i + omega (f_i^eq - h_i) = (1 - omega) h_i + omega f_i^eq, with omega w_i folded
+    // into the equilibrium's parts: omega f_i^eq = a_i (Ap + 4.5 rho (c_i.u)^2) +- 3 a_i rho (c_i.u),
+    // a_i = omega w_i, so each population costs one add and one FMA
+    const float a0 = k.omega * (4.0f / 9.0f), a1 = k.omega * (1.0f / 9.0f), a2 = k.omega * (1.0f / 36.0f);
+    const float2 keep = bc2(1.0f - k.omega);
+    const float2 A1 = bc2(a1) * Ap, A2 = bc2(a2) * Ap;
+    const float2 q1 = bc2(4.5f * a1) * rho, q2 = bc2(4.5f * a2) * rho;
+    const float2 d1 = bc2(3.0f * a1) * rho, d2 = bc2(3.0f * a2) * rho;
     const float2 pp = ux + uy, pm = ux - uy;
-    const float2 Sx = fma2(t45 * ux, ux, Ap), Dx = t3 * ux;
-    const float2 Sy = fma2(t45 * uy, uy, Ap), Dy = t3 * uy;
-    const float2 Sp = fma2(t45 * pp, pp, Ap), Dp = t3 * pp;
-    const float2 Sm = fma2(t45 * pm, pm, Ap), Dm = t3 * pm;
-    const float2 w0 = bc2(4.0f / 9.0f), w1 = bc2(1.0f / 9.0f), w2 = bc2(1.0f / 36.0f);
-    float2 fe[9];
-    fe[0] = w0 * Ap;
-    fe[1] = w1 * (Sx + Dx);
-    fe[3] = w1 * (Sx - Dx);
-    fe[2] = w1 * (Sy + Dy);
-    fe[4] = w1 * (Sy - Dy);
-    fe[5] = w2 * (Sp + Dp);
-    fe[7] = w2 * (Sp - Dp);
-    fe[8] = w2 * (Sm + Dm);
-    fe[6] = w2 * (Sm - Dm);
-    const float2 om = bc2(k.omega);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) o[i] = fma2(om, fe[i] - h[i], h[i]);
+    const float2 Sx = fma2(q1 * ux, ux, A1), Dx = d1 * ux;
+    const float2 Sy = fma2(q1 * uy, uy, A1), Dy = d1 * uy;
+    const float2 Sp = fma2(q2 * pp, pp, A2), Dp = d2 * pp;
+    const float2 Sm = fma2(q2 * pm, pm, A2), Dm = d2 * pm;
+    o[0] = fma2(keep, h[0], bc2(a0) * Ap);
+    o[1] = fma2(keep, h[1], Sx + Dx);
+    o[3] = fma2(keep, h[3], Sx - Dx);
+    o[2] = fma2(keep, h[2], Sy + Dy);
+    o[4] = fma2(keep, h[4], Sy - Dy);
+    o[5] = fma2(keep, h[5], Sp + Dp);
+    o[7] = fma2(keep, h[7], Sp - Dp);
+    o[8] = fma2(keep, h[8], Sm + Dm);
+    o[6] = fma2(keep, h[6], Sm - Dm);
 }
 
 // Store of a lane's pair.  `split` lanes (a pair that wraps around the lattice edge, is
@@ -502,13 +504,18 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
                 // nearest; the rest population takes the cell's stored mass minus their
                 // rounded values, and is rounded stochastically (unbiased), so the stored
                 // mass changes by one zero-mean rounding per cell and step.
-                float2 q[9];
+                // sum of the rounded values, each half added to an FP32 accumulator directly
+                // (sm_100 mixed-precision add: no separate conversion)
+                float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     out[i] = __floats2half2_rn(o[i].x, o[i].y);
-                    q[i] = __half22float2(out[i]);
+                    unsigned short lo, hi;
+                    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(*reinterpret_cast<const uint32_t*>(&out[i])));
+                    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s0) : "h"(lo));
+                    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s1) : "h"(hi));
                 }
-                const float2 rest = sh_p - (((q[1] + q[2]) + (q[3] + q[4])) + ((q[5] + q[6]) + (q[7] + q[8])));
+                const float2 rest = sh_p - make_float2(s0, s1);
                 // dither: a hash of the cell pair's position and the lattice's step count
                 const uint32_t rnd =
                     fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
