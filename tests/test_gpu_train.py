@@ -69,12 +69,21 @@ def test_fp32_gradient_matches_oracle(nx, ny, which, storage):
     lat, job = droplet_lattice(nx, ny, storage)
     tr = B.Trainer(lat, max_epochs=4, **HP[which])
     g, loss = tr.gradient()
-    f, L, terms, go = oracle_gradient(lat, job, HP[which])
-    # the interface set is decided in FP32 on the GPU: keep clear of the threshold
-    gm = O.grad_mag(O.density(f))
-    assert np.abs(gm - 0.01).min() > 2e-6
-    assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
-    assert loss[0] == pytest.approx(L, rel=1e-5)
+    f, _ = lat.state()
+    t, iface = T.targets_from_state(f, 0.01)
+    # The GPU decides the interface set (Eq. 16 gradient > 0.01) from an FP32 density: a cell
+    # whose FP64 gradient lies within FP32 rounding of the threshold may fall on either side,
+    # and both results are correct.  Accept the oracle gradient of any such assignment.
+    gm = O.grad_mag(O.density(f)).ravel()
+    amb = np.flatnonzero(np.abs(gm - 0.01) < 2e-6)
+    assert amb.size <= 3
+    ok = []
+    for bits in range(1 << amb.size):
+        m = iface.copy()
+        m[amb] = [(bits >> q) & 1 == 1 for q in range(amb.size)]
+        L, _, go = T.loss_and_grad(job.weights(), job.nx, job.ny, t, m, job.G, 1.0, T.TrainParams(**HP[which]))
+        ok.append(np.abs(g - go).max() <= 1e-4 * np.abs(go).max() and abs(loss[0] - L) <= 1e-5 * abs(L))
+    assert any(ok)
 
 
 def test_fp64_training_matches_oracle_and_persists_adam_state():
