@@ -279,7 +279,8 @@ PL_API int pl_train_gradient(pl_trainer* tr, double* host_grad, double* host_los
  * is a multiple of K (K > 0), `epochs` training epochs on the state, then one correction
  * with the trained network. */
 PL_API int pl_run_trained(pl_trainer* tr, int32_t nsteps, int32_t K, int32_t epochs);
-/* Free the handle; the caller's device memory is not touched. */
+/* Free the handle; the caller's device memory is not touched.  A trainer refers to its
+ * lattice: destroy it before the lattice (pl_destroy). */
 PL_API int pl_trainer_destroy(pl_trainer* tr);
 
 /* Self-test of the device-side failure detection: one thread waits, with the bounded

@@ -214,3 +214,29 @@ def test_protocol_series_match_oracle():
         close(mp, fp)
         assert losses[0] == pytest.approx(hist[0, 0], rel=1e-10) and losses[1] == pytest.approx(hist[-1, 0], rel=1e-10)
     assert [e for _, e, _, _ in out["pinn"]] == [4, 3, 2] and out["pinn"][-1][0] == 120
+
+
+@pytest.mark.parametrize("storage,mlp,mode,tol", [(B.PL_F32, B.PL_MLP_F32, O.MLP_F64, 1e-4),
+                                                   (B.PL_F16_OFFSET, B.PL_MLP_BF16, O.MLP_BF16, 1e-2)])
+def test_coupled_run_with_training_fp32_arithmetic(storage, mlp, mode, tol):
+    """FP32 / FP16-offset lattices with FP32 training, two coupled rounds against the FP64
+    oracle (FP32 storage with the FP32 network; FP16 storage with the BF16 tensor-core network
+    and the oracle's BF16 emulation); the relative L-inf bounds on rho are the ones the storage
+    types are held to (1e-4 FP32, 1e-2 FP16)."""
+    job = wl.Lattice(64, 64, storage=storage, mlp=mlp, droplets=[(32.0, 32.0, 12.0)], seed=7, K=25,
+                     weight_seed=43)
+    lat = B.Lattice.from_workload(job)
+    tr = B.Trainer(lat, max_epochs=4, eps=1e-2)
+    tr.run(50, 25, 4)
+    f, _ = lat.state()
+    m = lat.metrics()
+    fo = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
+                                       job.noise_amp, job.seed))
+    M0 = O.mass(fo)
+    st, blob, _ = T.run_trained(fo, 50, job.G, job.tau, 25, job.weights(), 4, hp=T.TrainParams(eps=1e-2), mode=mode,
+                                M0=M0)
+    assert st == 0 and m["status"] == 0 and m["corrections"] == 2
+    ro = O.density(fo)
+    assert np.abs(O.density(f) - ro).max() <= tol * np.abs(ro).max()
+    # the correction restores the lattice's own M0 (the mass of its stored initial state)
+    assert abs(m["mass"] - m["mass0"]) <= 1e-6 * m["mass0"]
