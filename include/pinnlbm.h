@@ -241,6 +241,12 @@ PL_API int pl_get_mlp_weights(pl_lattice* lat, float* host_blob, size_t n);
  *     tensor-core operand image).
  * Arithmetic: FP64 for FP64 lattices, FP32 otherwise (CUDA cores).
  * --------------------------------------------------------------------------------- */
+/* Training arithmetic (pl_train_params.mode). */
+#define PL_TRAIN_SIMT 0 /* CUDA cores: FP64 for FP64 lattices, FP32 otherwise (default)        */
+#define PL_TRAIN_TC 1   /* tcgen05 tensor cores for layers 2-4: BF16 operands, FP32 accumulation,
+                           layers 1 and 5, the loss and the tanh terms in FP32; FP32 and
+                           FP16-offset lattices only                                           */
+
 typedef struct pl_train_params {
     double lr;          /* Adam step size (default 3e-4, Sec. III-B)          */
     double beta1;       /* Adam first-moment decay (0.9)                      */
@@ -250,6 +256,8 @@ typedef struct pl_train_params {
     double lambda_int;  /* Eq. 3 weight of L_int (1)                          */
     double alpha1;      /* Eq. 8 weight of q = |grad rho_N|^2 (1)             */
     double alpha2;      /* Eq. 8 weight of q^2 (1)                            */
+    int32_t mode;       /* PL_TRAIN_SIMT (default) or PL_TRAIN_TC             */
+    int32_t reserved;   /* 0                                                  */
 } pl_train_params;
 
 typedef struct pl_trainer pl_trainer;
@@ -260,8 +268,9 @@ PL_API int pl_train_params_default(pl_train_params* tp);
 PL_API int pl_trainer_bytes(const pl_params* p, int32_t max_epochs, size_t* bytes_out);
 /* Trainer of lattice `lat` over caller memory dev_mem[0, bytes) (256-byte aligned, valid
  * until pl_trainer_destroy); enqueues on the lattice's stream.  Adam's moments start at
- * zero.  PL_ERR_INVALID_ARG for a lattice with mlp_in != 2 or invalid hyper-parameters
- * (lr > 0, 0 <= beta < 1, eps > 0, lambdas and alphas finite and >= 0). */
+ * zero.  PL_ERR_INVALID_ARG for a lattice with mlp_in != 2, invalid hyper-parameters
+ * (lr > 0, 0 <= beta < 1, eps > 0, lambdas and alphas finite and >= 0) or PL_TRAIN_TC on an
+ * FP64 lattice. */
 PL_API int pl_trainer_create(pl_lattice* lat, const pl_train_params* tp, int32_t max_epochs, void* dev_mem,
                              size_t bytes, pl_trainer** out);
 /* epochs (1..max_epochs) training epochs on the lattice's current state; the loss
@@ -269,7 +278,9 @@ PL_API int pl_trainer_create(pl_lattice* lat, const pl_train_params* tp, int32_t
  * (PL_ERR_STATE otherwise).  No host synchronisation. */
 PL_API int pl_train(pl_trainer* tr, int32_t epochs);
 /* Loss history of the last pl_train call, host_loss[epochs][4] = (L, L_data, L_phys,
- * L_int), each evaluated at the weights its epoch started from.  Synchronises. */
+ * L_int), each evaluated at the weights its epoch started from.  Synchronises.  Returns
+ * PL_ERR_TIMEOUT if a bounded device wait of the tensor-core kernel gave up during the call
+ * (the losses of the affected epochs are NaN). */
 PL_API int pl_train_losses(pl_trainer* tr, double* host_loss, int32_t epochs);
 /* The gradient of Eq. 3 with respect to the blob (host_grad[pl_mlp_blob_size()], FP64)
  * and the loss terms (host_loss4[4] as above) at the lattice's current weights and state;

@@ -29,6 +29,7 @@ PL_ERR_TIMEOUT = -5
 PL_ERR_STATE = -6
 
 PL_F64, PL_F32, PL_F16_OFFSET = 0, 1, 2
+PL_TRAIN_SIMT, PL_TRAIN_TC = 0, 1
 PL_MLP_F64, PL_MLP_F32, PL_MLP_BF16 = 0, 1, 2
 PL_MAX_DROPLETS = 4096
 
@@ -71,7 +72,8 @@ class pl_job_result(ctypes.Structure):
 class pl_train_params(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double), ("lambda_phys", ctypes.c_double), ("lambda_int", ctypes.c_double),
-                ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double)]
+                ("alpha1", ctypes.c_double), ("alpha2", ctypes.c_double), ("mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class PLError(RuntimeError):

@@ -650,7 +650,7 @@ struct pl_trainer {
 namespace {
 
 struct TrainerLayout {
-    size_t master, m, v, grad, part, loss_part, hist, ni, total;
+    size_t master, m, v, grad, part, loss_part, hist, ni, err, wimg, total;
     int grid;
 };
 
@@ -672,6 +672,8 @@ int trainer_layout(int storage, int max_epochs, TrainerLayout* T) {
     T->loss_part = o; o = align_up(o + (size_t)T->grid * 4 * sizeof(double));
     T->hist = o;   o = align_up(o + (size_t)max_epochs * 4 * sizeof(double));
     T->ni = o;     o = align_up(o + sizeof(unsigned long long));
+    T->err = o;    o = align_up(o + sizeof(unsigned));
+    T->wimg = o;   o = align_up(o + bf16_weight_elems() * sizeof(uint16_t));
     T->total = o;
     return PL_OK;
 }
@@ -683,7 +685,7 @@ TrainLat train_lat(pl_lattice* L) {
 
 bool hyper_ok(const pl_train_params* tp) {
     auto fin = [](double v) { return std::isfinite(v); };
-    return tp && fin(tp->lr) && tp->lr > 0 && fin(tp->beta1) && tp->beta1 >= 0 && tp->beta1 < 1 && fin(tp->beta2) &&
+    return tp && (tp->mode == PL_TRAIN_SIMT || tp->mode == PL_TRAIN_TC) && fin(tp->lr) && tp->lr > 0 && fin(tp->beta1) && tp->beta1 >= 0 && tp->beta1 < 1 && fin(tp->beta2) &&
            tp->beta2 >= 0 && tp->beta2 < 1 && fin(tp->eps) && tp->eps > 0 && fin(tp->lambda_phys) &&
            tp->lambda_phys >= 0 && fin(tp->lambda_int) && tp->lambda_int >= 0 && fin(tp->alpha1) && tp->alpha1 >= 0 &&
            fin(tp->alpha2) && tp->alpha2 >= 0;
@@ -717,7 +719,7 @@ extern "C" {
 
 int pl_train_params_default(pl_train_params* tp) {
     if (!tp) return PL_ERR_INVALID_ARG;
-    *tp = pl_train_params{3e-4, 0.9, 0.999, 1e-8, 1.0, 1.0, 1.0, 1.0};
+    *tp = pl_train_params{3e-4, 0.9, 0.999, 1e-8, 1.0, 1.0, 1.0, 1.0, PL_TRAIN_SIMT, 0};
     return PL_OK;
 }
 
@@ -735,7 +737,7 @@ int pl_trainer_bytes(const pl_params* p, int32_t max_epochs, size_t* bytes_out) 
 int pl_trainer_create(pl_lattice* L, const pl_train_params* tp, int32_t max_epochs, void* dev_mem, size_t bytes,
                       pl_trainer** out) {
     if (!L || !out || !dev_mem || ((uintptr_t)dev_mem % ALIGN) != 0 || max_epochs < 1 || !hyper_ok(tp) ||
-        L->p.mlp_in != 2)
+        L->p.mlp_in != 2 || (tp->mode == PL_TRAIN_TC && L->p.storage == PL_F64))
         return PL_ERR_INVALID_ARG;
     TrainerLayout TL;
     int st = trainer_layout(L->p.storage, max_epochs, &TL);
@@ -745,10 +747,18 @@ int pl_trainer_create(pl_lattice* L, const pl_train_params* tp, int32_t max_epoc
     if (!T) return PL_ERR_BUDGET;
     char* base = static_cast<char*>(dev_mem);
     T->lat = L;
-    T->hp = TrainHyper{tp->lr, tp->beta1, tp->beta2, tp->eps, tp->lambda_phys, tp->lambda_int, tp->alpha1, tp->alpha2};
-    T->b = TrainBufs{base + TL.master, base + TL.m, base + TL.v, base + TL.grad, base + TL.part,
-                     reinterpret_cast<double*>(base + TL.loss_part), reinterpret_cast<unsigned long long*>(base + TL.ni),
-                     TL.grid};
+    T->hp = TrainHyper{tp->lr,          tp->beta1,      tp->beta2,  tp->eps, tp->lambda_phys,
+                       tp->lambda_int, tp->alpha1,     tp->alpha2, tp->mode};
+    T->b = TrainBufs{base + TL.master,
+                     base + TL.m,
+                     base + TL.v,
+                     base + TL.grad,
+                     base + TL.part,
+                     reinterpret_cast<double*>(base + TL.loss_part),
+                     reinterpret_cast<unsigned long long*>(base + TL.ni),
+                     TL.grid,
+                     reinterpret_cast<uint16_t*>(base + TL.wimg),
+                     reinterpret_cast<unsigned*>(base + TL.err)};
     T->hist = reinterpret_cast<double*>(base + TL.hist);
     T->max_epochs = max_epochs;
     T->fp64 = L->p.storage == PL_F64;
@@ -774,10 +784,12 @@ int pl_train(pl_trainer* T, int32_t epochs) {
 
 int pl_train_losses(pl_trainer* T, double* host_loss, int32_t epochs) {
     if (!T || !host_loss || epochs < 1 || epochs > T->last_epochs) return PL_ERR_INVALID_ARG;
+    unsigned err = 0;
     PL_CUDA(cudaMemcpyAsync(host_loss, T->hist, (size_t)epochs * 4 * sizeof(double), cudaMemcpyDeviceToHost,
                             T->lat->stream));
+    PL_CUDA(cudaMemcpyAsync(&err, T->b.err, sizeof(unsigned), cudaMemcpyDeviceToHost, T->lat->stream));
     PL_CUDA(cudaStreamSynchronize(T->lat->stream));
-    return PL_OK;
+    return err ? PL_ERR_TIMEOUT : PL_OK;
 }
 
 int pl_train_gradient(pl_trainer* T, double* host_grad, double* host_loss4) {

@@ -129,6 +129,7 @@ struct TrainLat {
 };
 struct TrainHyper {
     double lr, beta1, beta2, eps, lambda_phys, lambda_int, alpha1, alpha2;
+    int mode;                  // PL_TRAIN_SIMT or PL_TRAIN_TC
 };
 struct TrainBufs {
     void* master;              // weights being trained [train_params_count()]
@@ -139,6 +140,8 @@ struct TrainBufs {
     double* loss_part;         // per-CTA loss sums [grid][4]
     unsigned long long* ni;    // interface-cell count
     int grid;                  // CTAs the partial buffers hold
+    uint16_t* wimg;            // BF16 operand image of the weights (tensor-core mode)
+    unsigned* err;             // nonzero: a bounded device wait gave up
 };
 int train_params_count();
 long long train_part_stride();

@@ -37,6 +37,7 @@
 
 #include "pl_device.cuh"
 #include "pl_kernels.h"
+#include "pl_tcgen05.cuh"
 
 namespace pl {
 
@@ -599,6 +600,451 @@ cudaError_t grad_setup(int* grid) {
     return cudaSuccess;
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// Tensor-core form: the dense layers 2-4 of the forward pass, of the reverse pass and of the
+// weight gradient as tcgen05 MMAs (BF16 operands in shared memory, FP32 accumulators in TMEM);
+// layers 1 and 5, the loss and the tanh terms on CUDA cores in FP32.
+//
+// One warpgroup per CTA (one CTA per SM: all of TMEM).  A tile is 40 samples as 128 operand
+// rows: row 32 w + 3 q + c is channel c (value, d/dx^, d/dy^) of sample 10 w + q; lanes 30
+// and 31 of each warp are padding (zero rows).  Thread r owns row r, i.e. TMEM lane r, and the
+// three rows of a sample are neighbouring lanes of one warp, so the tanh terms that couple them
+// (s = 1 - a^2 for the tangent rows, the second-derivative term of the value row) move by warp
+// shuffles.  Every activation is stored once, K-major over its features: it is the A operand
+// of the next forward MMA and, read MN-major (K = rows), an operand of the weight-gradient MMAs;
+// the weight images serve the forward MMAs K-major and the reverse MMAs MN-major (K = outputs).
+//   forward   Z_l = A_{l-1} W_l^T                 M = 128 rows, N = out_l, K = in_l
+//   reverse   dA_{l-1} = dZ_l W_l                  M = 128 rows, N = in_l,  K = out_l
+//   gradient  dW_l += dZ_l^T A_{l-1} (l = 2, 3)    M = out_l,    N = in_l,  K = 128 rows
+//             dW_4^T += A_3^T dZ_4                  M = in_4,     N = out_4, K = 128 rows
+// The three weight gradients accumulate in TMEM over all tiles of the CTA and are written once;
+// layers 1 and 5 and the biases go to the CTA's partial slice per tile, as in the FP32 kernel.
+namespace ttc {
+constexpr int THREADS = 128;
+constexpr int SPT = 40;                            // samples per tile
+constexpr int OFF_A1 = 0, OFF_A2 = OFF_A1 + 128 * 64 * 2, OFF_A3 = OFF_A2 + 128 * 128 * 2,
+              OFF_A4 = OFF_A3 + 128 * 128 * 2, OFF_W2 = OFF_A4 + 128 * 64 * 2, OFF_W3 = OFF_W2 + 128 * 64 * 2,
+              OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_DP = OFF_W4 + 64 * 128 * 2, OFF_DQ = OFF_DP + 128 * 128 * 2,
+              OFF_S5 = OFF_DQ + 128 * 128 * 2, OFF_BAR = OFF_S5 + 4 * 128 * 4, OFF_SLOT = OFF_BAR + 16,
+              SMEM = OFF_SLOT + 16;
+static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+constexpr int WIMG_BYTES = (128 * 64 + 128 * 128 + 64 * 128) * 2;   // W2, W3, W4 at the head of the image
+constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 192, TM_DW4T = 320, TM_COLS = 512;
+constexpr uint32_t KLBO = 2048;                    // K-major 128-row operand: core matrices along K
+
+// D (+)= A B over K in steps of 16 (each operand: base address, leading and stride byte
+// offsets, byte step per K step, major).
+__device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t alb, uint32_t asb, uint32_t ast,
+                                          bool amn, uint32_t b, uint32_t blb, uint32_t bsb, uint32_t bst, bool bmn,
+                                          int N, int K, bool acc) {
+    const uint32_t idesc = tc::idesc_bf16(128, N, amn, bmn);
+    for (int ks = 0; ks < K / 16; ++ks)
+        tc::mma_bf16(d, tc::smem_desc(a + ks * ast, alb, asb), tc::smem_desc(b + ks * bst, blb, bsb), idesc,
+                     (acc || ks > 0) ? 1u : 0u);
+}
+
+// 8 BF16 values of row r, features k0..k0+7, of a K-major 128-row operand -> FP32.
+__device__ __forceinline__ void load8(const uint8_t* A, int r, int k0, float (&v)[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(A + ((k0 >> 3) * 16 + (r >> 3)) * 128 + (r & 7) * 16);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[q]));
+        v[2 * q] = f.x;
+        v[2 * q + 1] = f.y;
+    }
+}
+__device__ __forceinline__ float bf16_at(const uint8_t* A, int r, int k) {
+    return __bfloat162float(
+        *reinterpret_cast<const __nv_bfloat16*>(A + ((k >> 3) * 16 + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2));
+}
+
+// Sum of v over the value lanes of the warp (the caller zeroes the other lanes); every lane
+// gets the sum (butterfly, fixed order).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Row roles of thread r.
+struct Row {
+    int r, lane, warp, c;
+    bool pad;
+};
+
+// Forward epilogue of a hidden layer from 16 pre-activations z (bias added on value rows):
+// value rows a = tanh(z), tangent rows (1 - a^2) z with a of their sample; out = FP32 values.
+__device__ __forceinline__ void act16(const Row& R, const float* __restrict__ b, int c0, float (&z)[16],
+                                      float (&out)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float zz = R.c == 0 ? z[j] + __ldg(b + c0 + j) : z[j];
+        const float a = tc::tanh_fast(zz);
+        const float sv = __shfl_sync(0xffffffffu, 1.0f - a * a, R.lane - R.c);
+        out[j] = R.pad ? 0.0f : (R.c == 0 ? a : sv * zz);
+    }
+}
+
+// Reverse pass through a hidden activation for 16 features k0..: dA (this row's dL/d act) ->
+// dL/dz; act = this row's stored activation (a or a_d).  Value rows: s dA - 2 a (a_x dA_x +
+// a_y dA_y); tangent rows: s dA_d, s = 1 - a^2 of their sample.
+__device__ __forceinline__ void dact16(const Row& R, const float (&dA)[16], const float (&act)[16],
+                                       float (&dz)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float a = __shfl_sync(0xffffffffu, act[j], R.lane - R.c);
+        const float ax = __shfl_sync(0xffffffffu, act[j], R.lane + 1);
+        const float ay = __shfl_sync(0xffffffffu, act[j], R.lane + 2);
+        const float dx = __shfl_sync(0xffffffffu, dA[j], R.lane + 1);
+        const float dy = __shfl_sync(0xffffffffu, dA[j], R.lane + 2);
+        const float sg = 1.0f - a * a;
+        dz[j] = R.pad ? 0.0f : (R.c == 0 ? sg * dA[j] - 2.0f * a * (ax * dx + ay * dy) : sg * dA[j]);
+    }
+}
+
+__device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (&v)[16]) {
+    tc::store8(A, r, c0, v);
+    tc::store8(A, r, c0 + 8, v + 8);
+}
+
+// Adds this chunk's value-row sums of v (16 features from c0) into per-warp slots red[warp][c0 + j].
+__device__ __forceinline__ void bias_chunk(const Row& R, const float (&v)[16], int c0, float* red) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const float t = warp_sum(R.c == 0 && !R.pad ? v[j] : 0.0f);
+        if (R.lane == j) red[R.warp * 128 + c0 + j] = t;
+    }
+}
+
+// Folds red[4][n] in warp order into the slice entries p[0..n).
+__device__ __forceinline__ void bias_fold(const float* red, int n, float* p, bool first) {
+    if (threadIdx.x < n) {
+        const int k = threadIdx.x;
+        acc1(p + k, ((red[k] + red[128 + k]) + red[256 + k]) + red[384 + k], first);
+    }
+}
+}  // namespace ttc
+
+__global__ void __launch_bounds__(ttc::THREADS, 1)
+k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restrict__ wimg, float* __restrict__ part,
+                double* __restrict__ loss_part, const unsigned long long* __restrict__ ni_dev, TrainHyper hp,
+                long long ntiles, unsigned* __restrict__ err) {
+    using namespace ttc;
+    extern __shared__ __align__(1024) uint8_t sm[];
+    if ((long long)blockIdx.x >= ntiles) return;
+    const int tid = threadIdx.x;
+    Row R;
+    R.r = tid;
+    R.lane = tid & 31;
+    R.warp = tid >> 5;
+    R.c = R.lane % 3;
+    R.pad = R.lane >= 30;
+    const int q = R.lane / 3;
+    uint8_t *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
+    uint8_t *DP = sm + OFF_DP, *DQ = sm + OFF_DQ;
+    float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
+    const uint32_t bar_w = tc::saddr(sm + OFF_BAR), bar_mma = tc::saddr(sm + OFF_BAR + 8);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(sm + OFF_SLOT);
+    if (tid == 0) {
+        tc::mbar_init(bar_w, 1);
+        tc::mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (R.warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(slot)),
+                     "r"(TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::tc_before_sync();
+    __syncthreads();
+    tc::tc_after_sync();
+    const uint32_t tmem = *slot;
+    const uint32_t lane_off = (uint32_t)(32 * R.warp) << 16;
+    if (tid == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_w), "r"(WIMG_BYTES) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         tc::saddr(sm + OFF_W2)),
+                     "l"(wimg), "r"(WIMG_BYTES), "r"(bar_w)
+                     : "memory");
+    }
+    bool ok = tc::wg_all(0, tc::mbar_wait(bar_w, 0));
+    uint32_t phase = 0;
+    bool pending = false;
+    const long long N = (long long)L.nx * L.ny;
+    const unsigned long long ni = *ni_dev;
+    const float sx = 2.0f / (float)L.nx, sy = 2.0f / (float)L.ny, inv_n = (float)(1.0 / (double)N);
+    const float c_phys = (float)(2.0 * hp.lambda_phys / (double)N);
+    const float c_int = ni ? (float)(hp.lambda_int / (double)ni) : 0.0f;
+    const float* rho = static_cast<const float*>(L.rho);
+    const float* jx = static_cast<const float*>(L.jx);
+    const float* jy = static_cast<const float*>(L.jy);
+    const float* gf = static_cast<const float*>(L.g);
+    float* P = part + (long long)blockIdx.x * PSTRIDE;
+    double ld = 0.0, lp = 0.0, li = 0.0;
+    const uint32_t sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3), sW2 = tc::saddr(sm + OFF_W2),
+                   sW3 = tc::saddr(sm + OFF_W3), sW4 = tc::saddr(sm + OFF_W4), sDP = tc::saddr(DP), sDQ = tc::saddr(DQ);
+
+    // issue (thread 0) and wait (all) for one batch of MMAs; false on timeout
+    auto sync_to_mma = [&]() {
+        tc::fence_async_smem();
+        tc::tc_before_sync();
+        tc::wg_bar(0);
+        tc::tc_after_sync();
+    };
+    auto wait_mma = [&]() {
+        if (tid == 0) tc::mma_commit(bar_mma);
+        pending = true;
+        ok = tc::wg_all(0, tc::mbar_wait(bar_mma, phase));
+        if (ok) {
+            pending = false;
+            phase ^= 1;
+        }
+        tc::tc_after_sync();
+        return ok;
+    };
+
+    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        const bool first = tile == blockIdx.x;
+        const long long smp = tile * SPT + R.warp * 10 + q;
+        const bool valid = !R.pad && smp < N;
+        const long long cc = valid ? smp : 0;
+        const int x = (int)(cc % L.nx), y = (int)(cc / L.nx);
+        const float xh = 2.0f * ((float)x + 0.5f) / (float)L.nx - 1.0f;
+        const float yh = 2.0f * ((float)y + 0.5f) / (float)L.ny - 1.0f;
+
+        // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float z[16], out[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float w0 = __ldg(w + OW1 + 2 * (c0 + j)), w1 = __ldg(w + OW1 + 2 * (c0 + j) + 1);
+                z[j] = R.c == 0 ? fmaf(xh, w0, yh * w1) : (R.c == 1 ? w0 : w1);
+            }
+            act16(R, w + OB1, c0, z, out);
+            store16(A1, R.r, c0, out);
+        }
+        // ---- layers 2-4: MMA, then the activation epilogue (layer 4 also feeds layer 5)
+        float o[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll 1
+        for (int layer = 2; layer <= 4 && ok; ++layer) {
+            sync_to_mma();
+            const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
+            const uint32_t a = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);
+            const uint32_t b = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
+            if (tid == 0)
+                mma_chain(tmem + TM_WORK, a, KLBO, 128, 2 * KLBO, false, b, (uint32_t)(Nout / 8) * 128, 128,
+                          2 * (uint32_t)(Nout / 8) * 128, false, Nout, Kin, false);
+            if (!wait_mma()) break;
+            uint8_t* dst = layer == 2 ? A2 : (layer == 3 ? A3 : A4);
+            const float* bias = w + (layer == 2 ? OB2 : (layer == 3 ? OB3 : OB4));
+#pragma unroll 1
+            for (int c0 = 0; c0 < Nout; c0 += 16) {
+                float z[16], out[16];
+                tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, z);
+                act16(R, bias, c0, z, out);
+                store16(dst, R.r, c0, out);
+                if (layer == 4) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        o[0] = fmaf(__ldg(w + OW5 + c0 + j), out[j], o[0]);
+                        o[1] = fmaf(__ldg(w + OW5 + 64 + c0 + j), out[j], o[1]);
+                        o[2] = fmaf(__ldg(w + OW5 + 128 + c0 + j), out[j], o[2]);
+                    }
+                }
+            }
+        }
+        if (!ok) break;
+        // ---- layer 5 output and the loss (value lane of each sample), dL/d(outputs) per row
+        float d5[3];
+        {
+            float ov[3], oxv[3], oyv[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                ov[k] = o[k] + (R.c == 0 ? __ldg(w + OB5 + k) : 0.0f);
+                oxv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 1);
+                oyv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 2);
+            }
+            float g[3] = {0.0f, 0.0f, 0.0f}, gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f};
+            if (valid && R.c == 0) {
+                const float rr = rho[cc];
+                const float t[3] = {rr, jx[cc] / rr, jy[cc] / rr};
+                const bool iface = above(gf[cc], L.threshold);
+                const SampleLoss<float> sl = sample_loss<float>(ov, oxv, oyv, t, iface, sx, sy, inv_n, c_phys, c_int, L, hp);
+                ld += sl.ld;
+                lp += sl.lp;
+                li += sl.li;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    g[k] = sl.g[k];
+                    gx[k] = sl.gx[k];
+                    gy[k] = sl.gy[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float t1 = __shfl_sync(0xffffffffu, gx[k], R.lane - R.c);
+                const float t2 = __shfl_sync(0xffffffffu, gy[k], R.lane - R.c);
+                d5[k] = R.pad ? 0.0f : (R.c == 0 ? g[k] : (R.c == 1 ? t1 : t2));
+                S5[R.r * 4 + k] = d5[k];
+            }
+        }
+        tc::wg_bar(0);
+        // ---- layer 5 gradient (rows summed in order) and dL/dA4 -> layer-4 reverse epilogue
+        for (int e = tid; e < 192; e += THREADS) {
+            const int oo = e / 64, k = e % 64;
+            float acc = 0.0f;
+            for (int rr = 0; rr < 128; ++rr) acc = fmaf(S5[rr * 4 + oo], bf16_at(A4, rr, k), acc);
+            acc1(P + OW5 + e, acc, first);
+        }
+        if (tid < 3) {   // value rows: lanes 0, 3, ..., 27 of each warp
+            float acc = 0.0f;
+            for (int rr = 0; rr < 128; ++rr)
+                if ((rr & 31) < 30 && (rr & 31) % 3 == 0) acc += S5[rr * 4 + tid];
+            acc1(P + OB5 + tid, acc, first);
+        }
+        tc::wg_bar(0);
+        float* red = S5;   // per-warp bias partials [4][128] (S5 is free again)
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float dA[16], act[16], dz[16], t8[8];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                dA[j] = d5[0] * __ldg(w + OW5 + c0 + j) + d5[1] * __ldg(w + OW5 + 64 + c0 + j) +
+                        d5[2] * __ldg(w + OW5 + 128 + c0 + j);
+            load8(A4, R.r, c0, t8);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) act[j] = t8[j];
+            load8(A4, R.r, c0 + 8, t8);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
+            dact16(R, dA, act, dz);
+            store16(DP, R.r, c0, dz);
+            bias_chunk(R, dz, c0, red);
+        }
+        tc::wg_bar(0);
+        bias_fold(red, 64, P + OB4, first);
+        // ---- reverse MMAs of layers 4, 3, 2 and their epilogues
+#pragma unroll 1
+        for (int layer = 4; layer >= 2 && ok; --layer) {
+            sync_to_mma();   // also orders bias_fold's reads of red before the next writes
+            const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
+            const uint32_t dz = layer == 3 ? sDQ : sDP;          // dZ_l
+            const uint32_t wl = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
+            const uint32_t ain = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);   // A_{l-1}
+            if (tid == 0) {
+                // dA_{l-1} = dZ_l W_l: A = dZ_l K-major (K = out), B = W_l MN-major (K = out, N = in)
+                mma_chain(tmem + TM_WORK, dz, KLBO, 128, 2 * KLBO, false, wl, 128, (uint32_t)(Nout / 8) * 128, 256,
+                          true, Kin, Nout, false);
+                if (layer == 4)   // dW4^T += A3^T dZ4: A = A3 MN-major (M = in), B = dZ4 MN-major (N = out)
+                    mma_chain(tmem + TM_DW4T, ain, 128, KLBO, 256, true, dz, 128, KLBO, 256, true, 64, 128, !first);
+                else              // dW_l += dZ_l^T A_{l-1}: A = dZ_l MN-major (M = out), B = A_{l-1} MN-major (N = in)
+                    mma_chain(tmem + (layer == 3 ? TM_DW3 : TM_DW2), dz, 128, KLBO, 256, true, ain, 128, KLBO, 256,
+                              true, Kin, 128, !first);
+            }
+            if (!wait_mma()) break;
+            const uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
+            if (layer > 2) {
+                uint8_t* dnext = layer == 4 ? DQ : DP;           // dZ_{l-1}
+#pragma unroll 1
+                for (int c0 = 0; c0 < Kin; c0 += 16) {
+                    float dA[16], act[16], dzv[16], t8[8];
+                    tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
+                    load8(Aact, R.r, c0, t8);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) act[j] = t8[j];
+                    load8(Aact, R.r, c0 + 8, t8);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
+                    dact16(R, dA, act, dzv);
+                    store16(dnext, R.r, c0, dzv);
+                    bias_chunk(R, dzv, c0, red);
+                }
+                tc::wg_bar(0);
+                bias_fold(red, 128, P + (layer == 4 ? OB3 : OB2), first);
+            } else {
+                // layer 1 reverse: dz1 -> dW1 (value rows x^, y^; tangent rows the unit vectors), db1
+                float* red3 = reinterpret_cast<float*>(DQ);   // [3][4][64] per-warp partials (DQ is free)
+#pragma unroll 1
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    float dA[16], act[16], dzv[16], t8[8];
+                    tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
+                    load8(A1, R.r, c0, t8);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) act[j] = t8[j];
+                    load8(A1, R.r, c0 + 8, t8);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
+                    dact16(R, dA, act, dzv);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float zx = __shfl_sync(0xffffffffu, dzv[j], R.lane + 1);
+                        const float zy = __shfl_sync(0xffffffffu, dzv[j], R.lane + 2);
+                        const bool v = R.c == 0 && !R.pad;
+                        const float s0 = warp_sum(v ? fmaf(dzv[j], xh, zx) : 0.0f);
+                        const float s1 = warp_sum(v ? fmaf(dzv[j], yh, zy) : 0.0f);
+                        const float sb = warp_sum(v ? dzv[j] : 0.0f);
+                        if (R.lane == j) {
+                            red3[0 * 256 + R.warp * 64 + c0 + j] = s0;
+                            red3[1 * 256 + R.warp * 64 + c0 + j] = s1;
+                            red3[2 * 256 + R.warp * 64 + c0 + j] = sb;
+                        }
+                    }
+                }
+                tc::wg_bar(0);
+                if (tid < 64) {
+                    float t3[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        t3[k] = ((red3[k * 256 + tid] + red3[k * 256 + 64 + tid]) + red3[k * 256 + 128 + tid]) +
+                                red3[k * 256 + 192 + tid];
+                    acc1(P + OW1 + 2 * tid, t3[0], first);
+                    acc1(P + OW1 + 2 * tid + 1, t3[1], first);
+                    acc1(P + OB1 + tid, t3[2], first);
+                }
+            }
+        }
+        tc::wg_bar(0);
+    }
+    if (ok) {
+        // the weight gradients accumulated in TMEM: row r of dW2, dW3 and of dW4^T
+        tc::tc_after_sync();
+#pragma unroll 1
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_off + TM_DW2 + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) P[OW2 + R.r * 64 + c0 + j] = v[j];
+            tc::tmem_ld16(tmem + lane_off + TM_DW4T + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) P[OW4 + (c0 + j) * 128 + R.r] = v[j];
+        }
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_off + TM_DW3 + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) P[OW3 + R.r * 128 + c0 + j] = v[j];
+        }
+    } else {
+        if (tid == 0) atomicOr(err, 1u);
+        if (pending) (void)tc::mbar_wait(bar_mma, phase);   // MMAs in flight finish before TMEM is freed
+    }
+    tc::tc_before_sync();
+    __syncthreads();
+    tc::tc_after_sync();
+    if (R.warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+    double v[3] = {ld, lp, li};
+    const int op[3] = {0, 0, 0};
+    block_reduce<3>(v, op, reinterpret_cast<double*>(sm + OFF_DP));
+    if (tid == 0)
+        for (int k = 0; k < 3; ++k) loss_part[blockIdx.x * 4 + k] = ok ? v[k] : NAN;
+}
+
 }  // namespace
 
 int train_params_count() { return NPARAM; }
@@ -610,6 +1056,7 @@ template <typename R>
 static cudaError_t begin_t(const TrainLat& L, const TrainBufs& b, const float* w32, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(b.ni, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.err, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
     k_train_prep<R><<<UPD_GRID * 4, 256, 0, s>>>(L, w32, static_cast<R*>(b.master), b.ni);
     note_launches(1);
     return cudaGetLastError();
@@ -641,8 +1088,41 @@ static cudaError_t epoch_t(const TrainLat& L, const TrainBufs& b, const TrainHyp
     return cudaGetLastError();
 }
 
+static cudaError_t epoch_tc(const TrainLat& L, const TrainBufs& b, const TrainHyper& hp, long long t, int apply,
+                            double* hist_row, cudaStream_t s) {
+    static int sms = 0;  // per process (one device)
+    if (!sms) {
+        cudaError_t e = cudaFuncSetAttribute(k_train_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, ttc::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    if (sms > b.grid) return cudaErrorInvalidValue;
+    // BF16 operand image of the weights this epoch starts from
+    cudaError_t e = launch_convert_weights_bf16(static_cast<const float*>(b.master), b.wimg, NIN, s);
+    if (e != cudaSuccess) return e;
+    const long long N = (long long)L.nx * L.ny;
+    const long long ntiles = (N + ttc::SPT - 1) / ttc::SPT;
+    k_train_grad_tc<<<sms, ttc::THREADS, ttc::SMEM, s>>>(L, static_cast<const float*>(b.master), b.wimg,
+                                                        static_cast<float*>(b.part), b.loss_part, b.ni, hp, ntiles, b.err);
+    const int nact = (int)(ntiles < sms ? ntiles : sms);
+    const double bc1 = apply ? 1.0 / (1.0 - std::pow(hp.beta1, (double)t)) : 1.0;
+    const double bc2 = apply ? 1.0 / (1.0 - std::pow(hp.beta2, (double)t)) : 1.0;
+    k_train_update<float><<<UPD_GRID, UPD_THREADS, 0, s>>>(static_cast<float*>(b.master), static_cast<float*>(b.m),
+                                                           static_cast<float*>(b.v), static_cast<float*>(b.grad),
+                                                           static_cast<const float*>(b.part), b.loss_part, b.ni, nact,
+                                                           N, hp, bc1, bc2, apply, hist_row);
+    note_launches(2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_train_epoch(const TrainLat& L, const TrainBufs& b, int fp64, const TrainHyper& hp, long long t,
                                int apply, double* hist_row, cudaStream_t s) {
+    if (hp.mode == PL_TRAIN_TC) {
+        if (fp64) return cudaErrorInvalidValue;
+        return epoch_tc(L, b, hp, t, apply, hist_row, s);
+    }
     return fp64 ? epoch_t<double>(L, b, hp, t, apply, hist_row, s) : epoch_t<float>(L, b, hp, t, apply, hist_row, s);
 }
 

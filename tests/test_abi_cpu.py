@@ -104,6 +104,7 @@ def test_train_params_default_and_argument_checks(lib):
     tp = B.pl_train_params_default()
     assert (tp.lr, tp.beta1, tp.beta2, tp.eps) == (3e-4, 0.9, 0.999, 1e-8)     # Sec. III-B learning rate
     assert (tp.lambda_phys, tp.lambda_int, tp.alpha1, tp.alpha2) == (1.0, 1.0, 1.0, 1.0)
+    assert tp.mode == B.PL_TRAIN_SIMT
     h = ctypes.c_void_p()
     # no lattice: refused before any device work
     assert lib.pl_trainer_create(None, ctypes.byref(tp), 10, ctypes.c_void_p(256), 1 << 20,

@@ -1,0 +1,110 @@
+"""Tensor-core training (PL_TRAIN_TC) against the FP64 training oracle.
+
+Layers 2-4 of the forward pass, of the reverse pass and of the weight gradient run as BF16
+tcgen05 MMAs with FP32 accumulation: the activations, their tangents, the back-propagated
+gradients and the weights enter each MMA rounded to BF16 (2^-9 relative).  A gradient entry
+sums one product of two such operands per sample and row, so its error is a few 2^-9 of the
+magnitudes it sums; the bound used is 2e-2 of the largest gradient component, and the loss
+(whose forward pass has three BF16 layers) is held to 1e-2 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import oracle.train as T
+from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+HP = {
+    "default": {},
+    "phys": dict(lambda_phys=3e3, lambda_int=0.0),
+    "int": dict(lambda_phys=0.0, lambda_int=1e3, alpha2=50.0),
+}
+
+
+def droplet_lattice(nx, ny, storage=B.PL_F32, steps=40, seed=3):
+    job = wl.Lattice(nx, ny, storage=storage, mlp=B.PL_MLP_BF16, droplets=[(nx / 2, ny / 2, min(nx, ny) / 4)],
+                     seed=seed, K=1, weight_seed=30 + seed)
+    lat = B.Lattice.from_workload(job)
+    lat.step(steps)
+    return lat, job
+
+
+def oracle_gradient(f, job, hp, iface=None):
+    t, m = T.targets_from_state(f, 0.01)
+    return T.loss_and_grad(job.weights(), job.nx, job.ny, t, m if iface is None else iface, job.G, 1.0,
+                           T.TrainParams(**hp))
+
+
+@pytest.mark.parametrize("which", sorted(HP))
+@pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (41, 7)])
+def test_tc_gradient_matches_oracle(nx, ny, which):
+    lat, job = droplet_lattice(nx, ny)
+    tr = B.Trainer(lat, max_epochs=2, mode=B.PL_TRAIN_TC, **HP[which])
+    g, loss = tr.gradient()
+    f, _ = lat.state()
+    L, terms, go = oracle_gradient(f, job, HP[which])
+    assert np.isfinite(g).all()
+    err = np.abs(g - go).max() / np.abs(go).max()
+    assert err <= 2e-2, err
+    assert loss[0] == pytest.approx(L, rel=1e-2)
+
+
+def test_tc_gradient_per_layer_blocks():
+    """Each layer's block of the gradient on its own (a wrong operand layout in one MMA shows
+    up as a block far from the oracle even when the whole vector's maximum is dominated by
+    another layer)."""
+    lat, job = droplet_lattice(96, 80)
+    tr = B.Trainer(lat, max_epochs=1, mode=B.PL_TRAIN_TC)
+    g, _ = tr.gradient()
+    f, _ = lat.state()
+    _, _, go = oracle_gradient(f, job, {})
+    sizes = [(64, 2), (64,), (128, 64), (128,), (128, 128), (128,), (64, 128), (64,), (3, 64), (3,)]
+    o = 0
+    for shp in sizes:
+        n = int(np.prod(shp))
+        blk, ref = g[o:o + n], go[o:o + n]
+        assert np.abs(blk - ref).max() <= 3e-2 * np.abs(ref).max() + 1e-12, (shp, o)
+        o += n
+    assert o == g.size
+
+
+def test_tc_training_follows_oracle_and_full_size():
+    lat, job = droplet_lattice(64, 48)
+    f, _ = lat.state()
+    tr = B.Trainer(lat, max_epochs=10, mode=B.PL_TRAIN_TC)
+    tr.train(10)
+    h = tr.losses(10)
+    _, hist, _ = T.train(job.weights(), f, 10, job.G)
+    assert np.abs(h[:, 0] - hist[:, 0]).max() <= 2e-2 * hist[0, 0]
+    assert h[-1, 0] < h[0, 0]
+    # the 512 x 512 single droplet: one gradient over all 262,144 cells
+    big = wl.single_512()
+    lat2 = B.Lattice.from_workload(big)
+    lat2.step(100)
+    tr2 = B.Trainer(lat2, max_epochs=1, mode=B.PL_TRAIN_TC)
+    g, loss = tr2.gradient()
+    f2, _ = lat2.state()
+    L, _, go = oracle_gradient(f2, big, {})
+    assert np.abs(g - go).max() <= 2e-2 * np.abs(go).max()
+    assert loss[0] == pytest.approx(L, rel=1e-2)
+
+
+def test_tc_coupled_run_and_mode_checks():
+    job = wl.Lattice(64, 64, storage=B.PL_F16_OFFSET, mlp=B.PL_MLP_BF16, droplets=[(32.0, 32.0, 12.0)], seed=7, K=25,
+                     weight_seed=43)
+    lat = B.Lattice.from_workload(job)
+    tr = B.Trainer(lat, max_epochs=4, mode=B.PL_TRAIN_TC)
+    tr.run(50, 25, 4)
+    m = lat.metrics()
+    assert m["status"] == 0 and m["corrections"] == 2
+    assert abs(m["mass"] - m["mass0"]) <= 1e-6 * m["mass0"]
+    lat64 = B.Lattice(B.pl_params_default(16, 16, storage=B.PL_F64, mlp=B.PL_MLP_F64))
+    with pytest.raises(B.PLError):
+        B.Trainer(lat64, mode=B.PL_TRAIN_TC)
