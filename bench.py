@@ -134,6 +134,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def measured_peaks_bf16():
+    """Dense BF16 tensor peak (burst) from MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
 def step_kernel_hash():
     h = hashlib.sha1()
     for f in ("pl_step.cu", "pl_device.cuh", "pl_kernels.h"):
@@ -238,16 +247,17 @@ TRAIN_FLOP_PER_SAMPLE = 2 * 3 * (33088 + 32960 + 33088)
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def train_measurement(args, B, wl, torch):
+def train_measurement(args, B, wl, torch, mode=0, cpu=True):
     """Sec. II-C step 2 at the paper's settings (lr 3e-4, 300 epochs per coupling round) on the
     single-droplet lattice of side --train-side (FP32 storage): epochs timed with CUDA events on
-    the lattice's stream, then one full coupling round (K = 100 steps, training, correction)."""
+    the lattice's stream, then one full coupling round (K = 100 steps, training, correction).
+    mode: PL_TRAIN_SIMT (FP32 CUDA cores) or PL_TRAIN_TC (BF16 tcgen05 layers 2-4)."""
     side, E, K = args.train_side, args.train_epochs, 100
     job = wl.Lattice(side, side, storage=wl.F32, droplets=[(side / 2, side / 2, side * 80.0 / 512)], seed=2,
                      K=K, mlp=wl.MLP_BF16, weight_seed=12)
     lat = B.Lattice.from_workload(job)
     lat.step(K)
-    tr = B.Trainer(lat, max_epochs=E)
+    tr = B.Trainer(lat, max_epochs=E, mode=mode)
     tr.train(min(3, E))                                     # warm-up (kernel set-up, first touch)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     ev[0].record(lat.stream)
@@ -263,19 +273,27 @@ def train_measurement(args, B, wl, torch):
     round_ms = ev[2].elapsed_time(ev[3])
     tflops = job.cells * TRAIN_FLOP_PER_SAMPLE / (ms_epoch / 1e3) / 1e12
     m = lat.metrics()
-    out = {"workload": "%dx%d single droplet (R=%g), FP32 storage, FP32 training, %d epochs per round, lr 3e-4"
-                       % (side, side, side * 80.0 / 512, E),
+    if mode == B.PL_TRAIN_TC:
+        peak, kind = measured_peaks_bf16()
+        roof = {"bound": "tensor", "kernel": "k_train_grad_tc + k_train_update<float>", "achieved": tflops,
+                "peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "frac": tflops / peak,
+                "flop_per_sample": TRAIN_FLOP_PER_SAMPLE}
+        arith = "BF16 tcgen05 layers 2-4, FP32 elsewhere"
+    else:
+        roof = {"bound": "alu", "kernel": "k_train_grad<float> + k_train_update<float>", "achieved": tflops,
+                "peak": FP32_ALU_PEAK_TFLOPS, "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
+                "unit": "TFLOP/s", "frac": tflops / FP32_ALU_PEAK_TFLOPS, "flop_per_sample": TRAIN_FLOP_PER_SAMPLE}
+        arith = "FP32 training"
+    out = {"workload": "%dx%d single droplet (R=%g), FP32 storage, %s, %d epochs per round, lr 3e-4"
+                       % (side, side, side * 80.0 / 512, arith, E),
            "ms_per_epoch": ms_epoch, "samples_per_s": job.cells / (ms_epoch / 1e3),
-           "roofline": {"bound": "alu", "kernel": "k_train_grad<float> + k_train_update<float>",
-                        "achieved": tflops, "peak": FP32_ALU_PEAK_TFLOPS, "peak_kind": "derived (152 SMs x 128 "
-                        "FP32 lanes x 2 x 2.07 GHz)", "unit": "TFLOP/s", "frac": tflops / FP32_ALU_PEAK_TFLOPS,
-                        "flop_per_sample": TRAIN_FLOP_PER_SAMPLE},
+           "roofline": roof,
            "round_ms": round_ms, "training_share_of_round": E * ms_epoch / round_ms,
            "loss_first_last": [hist[0, 0], hist[-1, 0]], "status_after_round": m["status"]}
     tr.close()
     lat.close()
     torch.cuda.empty_cache()
-    if not args.no_cpu:
+    if cpu and not args.no_cpu:
         import numpy as np
         import oracle as O
         import oracle.train as OT
@@ -449,9 +467,10 @@ def run_gb300(args):
             torch.cuda.empty_cache()
 
     # --------------------------------------------------------------- network training (Eqs. 3-8)
-    training = None
+    training = training_tc = None
     if not args.no_train and rank == 0:
-        training = train_measurement(args, B, wl, torch)
+        training = train_measurement(args, B, wl, torch, B.PL_TRAIN_SIMT)
+        training_tc = train_measurement(args, B, wl, torch, B.PL_TRAIN_TC, cpu=False)
 
     # --------------------------------------------------------------- CPU baseline
     cpu = None
@@ -481,6 +500,7 @@ def run_gb300(args):
             "serving": serving,
             "field_4096": field,
             "training": training,
+            "training_tc": training_tc,
             "cpu_baseline": cpu,
             "batch_checks": {"statuses": statuses, "max_mass_drift_post_correction": drift},
         }

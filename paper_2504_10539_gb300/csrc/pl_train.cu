@@ -621,7 +621,7 @@ cudaError_t grad_setup(int* grid) {
 // The three weight gradients accumulate in TMEM over all tiles of the CTA and are written once;
 // layers 1 and 5 and the biases go to the CTA's partial slice per tile, as in the FP32 kernel.
 namespace ttc {
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;   // two warps per TMEM lane quadrant
 constexpr int SPT = 40;                            // samples per tile
 constexpr int OFF_A1 = 0, OFF_A2 = OFF_A1 + 128 * 64 * 2, OFF_A3 = OFF_A2 + 128 * 128 * 2,
               OFF_A4 = OFF_A3 + 128 * 128 * 2, OFF_W2 = OFF_A4 + 128 * 64 * 2, OFF_W3 = OFF_W2 + 128 * 64 * 2,
@@ -687,21 +687,40 @@ __device__ __forceinline__ void act16(const Row& R, const float* __restrict__ b,
     }
 }
 
-// Reverse pass through a hidden activation for 16 features k0..: dA (this row's dL/d act) ->
-// dL/dz; act = this row's stored activation (a or a_d).  Value rows: s dA - 2 a (a_x dA_x +
-// a_y dA_y); tangent rows: s dA_d, s = 1 - a^2 of their sample.
-__device__ __forceinline__ void dact16(const Row& R, const float (&dA)[16], const float (&act)[16],
-                                       float (&dz)[16]) {
+// Reverse pass through a hidden activation for 16 features: dA (this row's dL/d act) -> dL/dz.
+// act / av / ax / ay: the stored activations of this row, of its sample's value row and of the
+// sample's two tangent rows (read from shared memory).  Value rows: s dA - 2 a (a_x dA_x +
+// a_y dA_y); tangent rows: s dA_d, s = 1 - a^2 of their sample; dA_x, dA_y come from the
+// neighbouring lanes.
+__device__ __forceinline__ void dact16(const Row& R, const float (&dA)[16], const float (&av)[16],
+                                       const float (&ax)[16], const float (&ay)[16], float (&dz)[16]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const float a = __shfl_sync(0xffffffffu, act[j], R.lane - R.c);
-        const float ax = __shfl_sync(0xffffffffu, act[j], R.lane + 1);
-        const float ay = __shfl_sync(0xffffffffu, act[j], R.lane + 2);
         const float dx = __shfl_sync(0xffffffffu, dA[j], R.lane + 1);
         const float dy = __shfl_sync(0xffffffffu, dA[j], R.lane + 2);
-        const float sg = 1.0f - a * a;
-        dz[j] = R.pad ? 0.0f : (R.c == 0 ? sg * dA[j] - 2.0f * a * (ax * dx + ay * dy) : sg * dA[j]);
+        const float a = av[j], sg = 1.0f - a * a;
+        dz[j] = R.pad ? 0.0f : (R.c == 0 ? sg * dA[j] - 2.0f * a * (ax[j] * dx + ay[j] * dy) : sg * dA[j]);
     }
+}
+
+// 16 stored activations (features c0..c0+15) of row r.
+__device__ __forceinline__ void load16(const uint8_t* A, int r, int c0, float (&v)[16]) {
+    float t[8];
+    load8(A, r, c0, t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = t[j];
+    load8(A, r, c0 + 8, t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[8 + j] = t[j];
+}
+
+// The value-row and tangent-row activations of this row's sample.
+__device__ __forceinline__ void sample_acts(const Row& R, const uint8_t* A, int c0, float (&av)[16], float (&ax)[16],
+                                            float (&ay)[16]) {
+    const int rv = R.r - R.c;
+    load16(A, rv, c0, av);
+    load16(A, rv + 1 < 128 ? rv + 1 : 127, c0, ax);
+    load16(A, rv + 2 < 128 ? rv + 2 : 127, c0, ay);
 }
 
 __device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (&v)[16]) {
@@ -709,20 +728,15 @@ __device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (
     tc::store8(A, r, c0 + 8, v + 8);
 }
 
-// Adds this chunk's value-row sums of v (16 features from c0) into per-warp slots red[warp][c0 + j].
-__device__ __forceinline__ void bias_chunk(const Row& R, const float (&v)[16], int c0, float* red) {
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const float t = warp_sum(R.c == 0 && !R.pad ? v[j] : 0.0f);
-        if (R.lane == j) red[R.warp * 128 + c0 + j] = t;
-    }
-}
-
-// Folds red[4][n] in warp order into the slice entries p[0..n).
-__device__ __forceinline__ void bias_fold(const float* red, int n, float* p, bool first) {
-    if (threadIdx.x < n) {
+// Bias gradient of a layer: the column sums of its stored dZ over the value rows (lanes 0, 3,
+// ..., 27 of each warp), in row order, added to the slice entries p[0..n).
+__device__ __forceinline__ void bias_cols(const uint8_t* D, int n, float* p, bool first) {
+    if ((int)threadIdx.x < n) {
         const int k = threadIdx.x;
-        acc1(p + k, ((red[k] + red[128 + k]) + red[256 + k]) + red[384 + k], first);
+        float sum = 0.0f;
+        for (int w = 0; w < 4; ++w)
+            for (int q = 0; q < 10; ++q) sum += bf16_at(D, 32 * w + 3 * q, k);
+        acc1(p + k, sum, first);
     }
 }
 }  // namespace ttc
@@ -734,17 +748,19 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     using namespace ttc;
     extern __shared__ __align__(1024) uint8_t sm[];
     if ((long long)blockIdx.x >= ntiles) return;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int h = warp >> 2;   // column half: this warp takes the 16-column chunks 16 h, 16 h + 32, ...
     Row R;
-    R.r = tid;
     R.lane = tid & 31;
-    R.warp = tid >> 5;
+    R.warp = warp & 3;         // TMEM lane quadrant
+    R.r = 32 * R.warp + R.lane;
     R.c = R.lane % 3;
     R.pad = R.lane >= 30;
     const int q = R.lane / 3;
     uint8_t *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
     uint8_t *DP = sm + OFF_DP, *DQ = sm + OFF_DQ;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
+    float* X = reinterpret_cast<float*>(DQ);   // exchange scratch while DQ holds no operand
     const uint32_t bar_w = tc::saddr(sm + OFF_BAR), bar_mma = tc::saddr(sm + OFF_BAR + 8);
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + OFF_SLOT);
     if (tid == 0) {
@@ -752,7 +768,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         tc::mbar_init(bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (R.warp == 0) {
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::saddr(slot)),
                      "r"(TM_COLS)
                      : "memory");
@@ -770,7 +786,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                      "l"(wimg), "r"(WIMG_BYTES), "r"(bar_w)
                      : "memory");
     }
-    bool ok = tc::wg_all(0, tc::mbar_wait(bar_w, 0));
+    bool ok = __syncthreads_and(tc::mbar_wait(bar_w, 0)) != 0;
     uint32_t phase = 0;
     bool pending = false;
     const long long N = (long long)L.nx * L.ny;
@@ -787,17 +803,18 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     const uint32_t sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3), sW2 = tc::saddr(sm + OFF_W2),
                    sW3 = tc::saddr(sm + OFF_W3), sW4 = tc::saddr(sm + OFF_W4), sDP = tc::saddr(DP), sDQ = tc::saddr(DQ);
 
-    // issue (thread 0) and wait (all) for one batch of MMAs; false on timeout
+    // operands written by the threads -> visible to the tensor core, then thread 0 issues
     auto sync_to_mma = [&]() {
         tc::fence_async_smem();
         tc::tc_before_sync();
-        tc::wg_bar(0);
+        __syncthreads();
         tc::tc_after_sync();
     };
+    // commit the issued MMAs and wait (bounded) for them; false on timeout
     auto wait_mma = [&]() {
         if (tid == 0) tc::mma_commit(bar_mma);
         pending = true;
-        ok = tc::wg_all(0, tc::mbar_wait(bar_mma, phase));
+        ok = __syncthreads_and(tc::mbar_wait(bar_mma, phase)) != 0;
         if (ok) {
             pending = false;
             phase ^= 1;
@@ -817,7 +834,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
 
         // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
 #pragma unroll 1
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
             float z[16], out[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -842,7 +859,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             uint8_t* dst = layer == 2 ? A2 : (layer == 3 ? A3 : A4);
             const float* bias = w + (layer == 2 ? OB2 : (layer == 3 ? OB3 : OB4));
 #pragma unroll 1
-            for (int c0 = 0; c0 < Nout; c0 += 16) {
+            for (int c0 = 16 * h; c0 < Nout; c0 += 32) {
                 float z[16], out[16];
                 tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, z);
                 act16(R, bias, c0, z, out);
@@ -858,12 +875,17 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             }
         }
         if (!ok) break;
-        // ---- layer 5 output and the loss (value lane of each sample), dL/d(outputs) per row
-        float d5[3];
-        {
+        // ---- layer 5: the two halves' partial sums, the output and the loss (value lanes of
+        // half 0), dL/d(outputs) per row into S5
+        if (h == 1)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) X[R.r * 4 + k] = o[k];
+        __syncthreads();
+        if (h == 0) {
             float ov[3], oxv[3], oyv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
+                o[k] += X[R.r * 4 + k];
                 ov[k] = o[k] + (R.c == 0 ? __ldg(w + OB5 + k) : 0.0f);
                 oxv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 1);
                 oyv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 2);
@@ -888,49 +910,53 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             for (int k = 0; k < 3; ++k) {
                 const float t1 = __shfl_sync(0xffffffffu, gx[k], R.lane - R.c);
                 const float t2 = __shfl_sync(0xffffffffu, gy[k], R.lane - R.c);
-                d5[k] = R.pad ? 0.0f : (R.c == 0 ? g[k] : (R.c == 1 ? t1 : t2));
-                S5[R.r * 4 + k] = d5[k];
+                S5[R.r * 4 + k] = R.pad ? 0.0f : (R.c == 0 ? g[k] : (R.c == 1 ? t1 : t2));
             }
         }
-        tc::wg_bar(0);
-        // ---- layer 5 gradient (rows summed in order) and dL/dA4 -> layer-4 reverse epilogue
-        for (int e = tid; e < 192; e += THREADS) {
-            const int oo = e / 64, k = e % 64;
-            float acc = 0.0f;
-            for (int rr = 0; rr < 128; ++rr) acc = fmaf(S5[rr * 4 + oo], bf16_at(A4, rr, k), acc);
-            acc1(P + OW5 + e, acc, first);
+        __syncthreads();
+        const float d5[3] = {S5[R.r * 4], S5[R.r * 4 + 1], S5[R.r * 4 + 2]};
+        // ---- layer 5 gradient: 24 groups (output o, 8 features) x 8 row blocks of 16, folded in order
+        if (tid < 192) {
+            const int gi = tid % 24, rb = tid / 24, oo = gi / 8, k0 = (gi % 8) * 8;
+            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, t8[8];
+            for (int rr = 16 * rb; rr < 16 * rb + 16; ++rr) {
+                const float d = S5[rr * 4 + oo];
+                load8(A4, rr, k0, t8);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[e] = fmaf(d, t8[e], acc[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) X[rb * 192 + oo * 64 + k0 + e] = acc[e];
         }
-        if (tid < 3) {   // value rows: lanes 0, 3, ..., 27 of each warp
+        __syncthreads();
+        if (tid < 192) {
             float acc = 0.0f;
-            for (int rr = 0; rr < 128; ++rr)
-                if ((rr & 31) < 30 && (rr & 31) % 3 == 0) acc += S5[rr * 4 + tid];
-            acc1(P + OB5 + tid, acc, first);
+            for (int rb = 0; rb < 8; ++rb) acc += X[rb * 192 + tid];
+            acc1(P + OW5 + tid, acc, first);
+        } else if (tid < 195) {   // value rows: lanes 0, 3, ..., 27 of each quadrant
+            const int oo = tid - 192;
+            float acc = 0.0f;
+            for (int wq = 0; wq < 40; ++wq) acc += S5[(32 * (wq / 10) + 3 * (wq % 10)) * 4 + oo];
+            acc1(P + OB5 + oo, acc, first);
         }
-        tc::wg_bar(0);
-        float* red = S5;   // per-warp bias partials [4][128] (S5 is free again)
+        // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 (DP)
 #pragma unroll 1
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            float dA[16], act[16], dz[16], t8[8];
+        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
+            float dA[16], av[16], ax[16], ay[16], dz[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
                 dA[j] = d5[0] * __ldg(w + OW5 + c0 + j) + d5[1] * __ldg(w + OW5 + 64 + c0 + j) +
                         d5[2] * __ldg(w + OW5 + 128 + c0 + j);
-            load8(A4, R.r, c0, t8);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) act[j] = t8[j];
-            load8(A4, R.r, c0 + 8, t8);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
-            dact16(R, dA, act, dz);
+            sample_acts(R, A4, c0, av, ax, ay);
+            dact16(R, dA, av, ax, ay, dz);
             store16(DP, R.r, c0, dz);
-            bias_chunk(R, dz, c0, red);
         }
-        tc::wg_bar(0);
-        bias_fold(red, 64, P + OB4, first);
+        __syncthreads();
+        bias_cols(DP, 64, P + OB4, first);
         // ---- reverse MMAs of layers 4, 3, 2 and their epilogues
 #pragma unroll 1
         for (int layer = 4; layer >= 2 && ok; --layer) {
-            sync_to_mma();   // also orders bias_fold's reads of red before the next writes
+            sync_to_mma();   // also orders the reads of the previous step before the next writes
             const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
             const uint32_t dz = layer == 3 ? sDQ : sDP;          // dZ_l
             const uint32_t wl = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
@@ -950,70 +976,55 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             if (layer > 2) {
                 uint8_t* dnext = layer == 4 ? DQ : DP;           // dZ_{l-1}
 #pragma unroll 1
-                for (int c0 = 0; c0 < Kin; c0 += 16) {
-                    float dA[16], act[16], dzv[16], t8[8];
+                for (int c0 = 16 * h; c0 < Kin; c0 += 32) {
+                    float dA[16], av[16], ax[16], ay[16], dzv[16];
                     tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
-                    load8(Aact, R.r, c0, t8);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) act[j] = t8[j];
-                    load8(Aact, R.r, c0 + 8, t8);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
-                    dact16(R, dA, act, dzv);
+                    sample_acts(R, Aact, c0, av, ax, ay);
+                    dact16(R, dA, av, ax, ay, dzv);
                     store16(dnext, R.r, c0, dzv);
-                    bias_chunk(R, dzv, c0, red);
                 }
-                tc::wg_bar(0);
-                bias_fold(red, 128, P + (layer == 4 ? OB3 : OB2), first);
+                __syncthreads();
+                bias_cols(dnext, 128, P + (layer == 4 ? OB3 : OB2), first);
             } else {
-                // layer 1 reverse: dz1 -> dW1 (value rows x^, y^; tangent rows the unit vectors), db1
-                float* red3 = reinterpret_cast<float*>(DQ);   // [3][4][64] per-warp partials (DQ is free)
+                // layer 1 reverse: dz1 (FP32, all rows) into a scratch, then per feature the sums
+                // over the samples of dz_v x^ + dz_x, dz_v y^ + dz_y and dz_v (dW1 and db1)
+                float* zs = X;   // [128][64] (DQ is free)
 #pragma unroll 1
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    float dA[16], act[16], dzv[16], t8[8];
+                for (int c0 = 16 * h; c0 < 64; c0 += 32) {
+                    float dA[16], av[16], ax[16], ay[16], dzv[16];
                     tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
-                    load8(A1, R.r, c0, t8);
+                    sample_acts(R, A1, c0, av, ax, ay);
+                    dact16(R, dA, av, ax, ay, dzv);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) act[j] = t8[j];
-                    load8(A1, R.r, c0 + 8, t8);
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) act[8 + j] = t8[j];
-                    dact16(R, dA, act, dzv);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const float zx = __shfl_sync(0xffffffffu, dzv[j], R.lane + 1);
-                        const float zy = __shfl_sync(0xffffffffu, dzv[j], R.lane + 2);
-                        const bool v = R.c == 0 && !R.pad;
-                        const float s0 = warp_sum(v ? fmaf(dzv[j], xh, zx) : 0.0f);
-                        const float s1 = warp_sum(v ? fmaf(dzv[j], yh, zy) : 0.0f);
-                        const float sb = warp_sum(v ? dzv[j] : 0.0f);
-                        if (R.lane == j) {
-                            red3[0 * 256 + R.warp * 64 + c0 + j] = s0;
-                            red3[1 * 256 + R.warp * 64 + c0 + j] = s1;
-                            red3[2 * 256 + R.warp * 64 + c0 + j] = sb;
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j) zs[R.r * 64 + c0 + j] = dzv[j];
                 }
-                tc::wg_bar(0);
+                __syncthreads();
                 if (tid < 64) {
-                    float t3[3];
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        t3[k] = ((red3[k * 256 + tid] + red3[k * 256 + 64 + tid]) + red3[k * 256 + 128 + tid]) +
-                                red3[k * 256 + 192 + tid];
-                    acc1(P + OW1 + 2 * tid, t3[0], first);
-                    acc1(P + OW1 + 2 * tid + 1, t3[1], first);
-                    acc1(P + OB1 + tid, t3[2], first);
+                    float s0 = 0.0f, s1 = 0.0f, sb = 0.0f;
+                    for (int wq = 0; wq < 40; ++wq) {
+                        const int rv = 32 * (wq / 10) + 3 * (wq % 10);
+                        const long long sp = tile * SPT + wq;
+                        const long long c2 = sp < N ? sp : 0;
+                        const float xq = 2.0f * ((float)(c2 % L.nx) + 0.5f) / (float)L.nx - 1.0f;
+                        const float yq = 2.0f * ((float)(c2 / L.nx) + 0.5f) / (float)L.ny - 1.0f;
+                        const float zv = zs[rv * 64 + tid];
+                        s0 += fmaf(zv, xq, zs[(rv + 1) * 64 + tid]);
+                        s1 += fmaf(zv, yq, zs[(rv + 2) * 64 + tid]);
+                        sb += zv;
+                    }
+                    acc1(P + OW1 + 2 * tid, s0, first);
+                    acc1(P + OW1 + 2 * tid + 1, s1, first);
+                    acc1(P + OB1 + tid, sb, first);
                 }
             }
         }
-        tc::wg_bar(0);
+        __syncthreads();
     }
     if (ok) {
         // the weight gradients accumulated in TMEM: row r of dW2, dW3 and of dW4^T
         tc::tc_after_sync();
 #pragma unroll 1
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
             float v[16];
             tc::tmem_ld16(tmem + lane_off + TM_DW2 + c0, v);
 #pragma unroll
@@ -1023,7 +1034,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             for (int j = 0; j < 16; ++j) P[OW4 + (c0 + j) * 128 + R.r] = v[j];
         }
 #pragma unroll 1
-        for (int c0 = 0; c0 < 128; c0 += 16) {
+        for (int c0 = 16 * h; c0 < 128; c0 += 32) {
             float v[16];
             tc::tmem_ld16(tmem + lane_off + TM_DW3 + c0, v);
 #pragma unroll
@@ -1036,7 +1047,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     tc::tc_before_sync();
     __syncthreads();
     tc::tc_after_sync();
-    if (R.warp == 0)
+    if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
     double v[3] = {ld, lp, li};
     const int op[3] = {0, 0, 0};
