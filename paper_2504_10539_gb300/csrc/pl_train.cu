@@ -639,9 +639,14 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t alb, 
                                           bool amn, uint32_t b, uint32_t blb, uint32_t bsb, uint32_t bst, bool bmn,
                                           int N, int K, bool acc) {
     const uint32_t idesc = tc::idesc_bf16(128, N, amn, bmn);
-    for (int ks = 0; ks < K / 16; ++ks)
-        tc::mma_bf16(d, tc::smem_desc(a + ks * ast, alb, asb), tc::smem_desc(b + ks * bst, blb, bsb), idesc,
-                     (acc || ks > 0) ? 1u : 0u);
+    // the start address is the descriptor's low field (address >> 4; every operand lies below
+    // 256 KB, so the field never carries): a K step adds step >> 4
+    uint64_t da = tc::smem_desc(a, alb, asb), db = tc::smem_desc(b, blb, bsb);
+    for (int ks = 0; ks < K / 16; ++ks) {
+        tc::mma_bf16(d, da, db, idesc, (acc || ks > 0) ? 1u : 0u);
+        da += ast >> 4;
+        db += bst >> 4;
+    }
 }
 
 // 8 BF16 values of row r, features k0..k0+7, of a K-major 128-row operand -> FP32.
@@ -728,15 +733,19 @@ __device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (
     tc::store8(A, r, c0 + 8, v + 8);
 }
 
-// Bias gradient of a layer: the column sums of its stored dZ over the value rows (lanes 0, 3,
-// ..., 27 of each warp), in row order, added to the slice entries p[0..n).
-__device__ __forceinline__ void bias_cols(const uint8_t* D, int n, float* p, bool first) {
+// Bias gradient of a layer: the column sums of its stored dZ over the 40 value rows (lanes 0,
+// 3, ..., 27 of each quadrant), added to the slice entries p[0..n).  The 256 threads take
+// 256 / n interleaved row groups of each column; the partial sums are folded in group order.
+__device__ __forceinline__ void bias_cols(const uint8_t* D, int n, float* p, bool first, float* scratch) {
+    const int k = threadIdx.x % n, grp = threadIdx.x / n, ng = THREADS / n;
+    float sum = 0.0f;
+    for (int v = grp; v < 40; v += ng) sum += bf16_at(D, 32 * (v / 10) + 3 * (v % 10), k);
+    scratch[grp * n + k] = sum;
+    __syncthreads();
     if ((int)threadIdx.x < n) {
-        const int k = threadIdx.x;
-        float sum = 0.0f;
-        for (int w = 0; w < 4; ++w)
-            for (int q = 0; q < 10; ++q) sum += bf16_at(D, 32 * w + 3 * q, k);
-        acc1(p + k, sum, first);
+        float t = 0.0f;
+        for (int g = 0; g < ng; ++g) t += scratch[g * n + k];
+        acc1(p + k, t, first);
     }
 }
 }  // namespace ttc
@@ -761,6 +770,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     uint8_t *DP = sm + OFF_DP, *DQ = sm + OFF_DQ;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
     float* X = reinterpret_cast<float*>(DQ);   // exchange scratch while DQ holds no operand
+    float* BS = reinterpret_cast<float*>(A4);  // bias partials in the reverse pass (A4 is read by then)
     const uint32_t bar_w = tc::saddr(sm + OFF_BAR), bar_mma = tc::saddr(sm + OFF_BAR + 8);
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + OFF_SLOT);
     if (tid == 0) {
@@ -810,9 +820,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         __syncthreads();
         tc::tc_after_sync();
     };
-    // commit the issued MMAs and wait (bounded) for them; false on timeout
-    auto wait_mma = [&]() {
-        if (tid == 0) tc::mma_commit(bar_mma);
+    // wait (bounded) for the last commit; false on timeout
+    auto wait_issued = [&]() {
         pending = true;
         ok = __syncthreads_and(tc::mbar_wait(bar_mma, phase)) != 0;
         if (ok) {
@@ -821,6 +830,11 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         }
         tc::tc_after_sync();
         return ok;
+    };
+    // commit the issued MMAs and wait for them
+    auto wait_mma = [&]() {
+        if (tid == 0) tc::mma_commit(bar_mma);
+        return wait_issued();
     };
 
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -832,6 +846,10 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         const float xh = 2.0f * ((float)x + 0.5f) / (float)L.nx - 1.0f;
         const float yh = 2.0f * ((float)y + 0.5f) / (float)L.ny - 1.0f;
 
+        if (h == 0 && R.c == 0 && !R.pad) {   // the sample's (x^, y^) for the layer-1 weight gradient
+            S5[R.r * 4 + 3] = xh;
+            S5[(R.r + 1) * 4 + 3] = yh;
+        }
         // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 64; c0 += 32) {
@@ -952,7 +970,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             store16(DP, R.r, c0, dz);
         }
         __syncthreads();
-        bias_cols(DP, 64, P + OB4, first);
+        bias_cols(DP, 64, P + OB4, first, BS);
         // ---- reverse MMAs of layers 4, 3, 2 and their epilogues
 #pragma unroll 1
         for (int layer = 4; layer >= 2 && ok; --layer) {
@@ -965,13 +983,18 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 // dA_{l-1} = dZ_l W_l: A = dZ_l K-major (K = out), B = W_l MN-major (K = out, N = in)
                 mma_chain(tmem + TM_WORK, dz, KLBO, 128, 2 * KLBO, false, wl, 128, (uint32_t)(Nout / 8) * 128, 256,
                           true, Kin, Nout, false);
+                // layers 4 and 3: the epilogue waits for dA only; the weight-gradient MMAs below
+                // run during it (they read dZ_l and A_{l-1}, which the epilogue does not write, and
+                // the next layer's wait covers them).  Layer 2 waits for both: the next tile
+                // rewrites A1 before its first wait.
+                if (layer > 2) tc::mma_commit(bar_mma);
                 if (layer == 4)   // dW4^T += A3^T dZ4: A = A3 MN-major (M = in), B = dZ4 MN-major (N = out)
                     mma_chain(tmem + TM_DW4T, ain, 128, KLBO, 256, true, dz, 128, KLBO, 256, true, 64, 128, !first);
                 else              // dW_l += dZ_l^T A_{l-1}: A = dZ_l MN-major (M = out), B = A_{l-1} MN-major (N = in)
                     mma_chain(tmem + (layer == 3 ? TM_DW3 : TM_DW2), dz, 128, KLBO, 256, true, ain, 128, KLBO, 256,
                               true, Kin, 128, !first);
             }
-            if (!wait_mma()) break;
+            if (!(layer > 2 ? wait_issued() : wait_mma())) break;
             const uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
             if (layer > 2) {
                 uint8_t* dnext = layer == 4 ? DQ : DP;           // dZ_{l-1}
@@ -984,7 +1007,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                     store16(dnext, R.r, c0, dzv);
                 }
                 __syncthreads();
-                bias_cols(dnext, 128, P + (layer == 4 ? OB3 : OB2), first);
+                bias_cols(dnext, 128, P + (layer == 4 ? OB3 : OB2), first, BS);
             } else {
                 // layer 1 reverse: dz1 (FP32, all rows) into a scratch, then per feature the sums
                 // over the samples of dz_v x^ + dz_x, dz_v y^ + dz_y and dz_v (dW1 and db1)
@@ -999,22 +1022,31 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                     for (int j = 0; j < 16; ++j) zs[R.r * 64 + c0 + j] = dzv[j];
                 }
                 __syncthreads();
-                if (tid < 64) {
+                {   // 4 interleaved groups of the 40 samples per feature, folded in group order
+                    const int k = tid % 64, grp = tid / 64;
                     float s0 = 0.0f, s1 = 0.0f, sb = 0.0f;
-                    for (int wq = 0; wq < 40; ++wq) {
+                    for (int wq = grp; wq < 40; wq += 4) {
                         const int rv = 32 * (wq / 10) + 3 * (wq % 10);
-                        const long long sp = tile * SPT + wq;
-                        const long long c2 = sp < N ? sp : 0;
-                        const float xq = 2.0f * ((float)(c2 % L.nx) + 0.5f) / (float)L.nx - 1.0f;
-                        const float yq = 2.0f * ((float)(c2 / L.nx) + 0.5f) / (float)L.ny - 1.0f;
-                        const float zv = zs[rv * 64 + tid];
-                        s0 += fmaf(zv, xq, zs[(rv + 1) * 64 + tid]);
-                        s1 += fmaf(zv, yq, zs[(rv + 2) * 64 + tid]);
+                        const float xq = S5[rv * 4 + 3], yq = S5[(rv + 1) * 4 + 3];
+                        const float zv = zs[rv * 64 + k];
+                        s0 += fmaf(zv, xq, zs[(rv + 1) * 64 + k]);
+                        s1 += fmaf(zv, yq, zs[(rv + 2) * 64 + k]);
                         sb += zv;
                     }
-                    acc1(P + OW1 + 2 * tid, s0, first);
-                    acc1(P + OW1 + 2 * tid + 1, s1, first);
-                    acc1(P + OB1 + tid, sb, first);
+                    BS[grp * 64 + k] = s0;
+                    BS[256 + grp * 64 + k] = s1;
+                    BS[512 + grp * 64 + k] = sb;
+                    __syncthreads();
+                    if (tid < 64) {
+                        float t3[3];
+#pragma unroll
+                        for (int m = 0; m < 3; ++m)
+                            t3[m] = ((BS[m * 256 + tid] + BS[m * 256 + 64 + tid]) + BS[m * 256 + 128 + tid]) +
+                                    BS[m * 256 + 192 + tid];
+                        acc1(P + OW1 + 2 * tid, t3[0], first);
+                        acc1(P + OW1 + 2 * tid + 1, t3[1], first);
+                        acc1(P + OB1 + tid, t3[2], first);
+                    }
                 }
             }
         }
