@@ -626,8 +626,12 @@ constexpr int SPT = 40;                            // samples per tile
 constexpr int OFF_A1 = 0, OFF_A2 = OFF_A1 + 128 * 64 * 2, OFF_A3 = OFF_A2 + 128 * 128 * 2,
               OFF_A4 = OFF_A3 + 128 * 128 * 2, OFF_W2 = OFF_A4 + 128 * 64 * 2, OFF_W3 = OFF_W2 + 128 * 64 * 2,
               OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_DP = OFF_W4 + 64 * 128 * 2, OFF_DQ = OFF_DP + 128 * 128 * 2,
-              OFF_S5 = OFF_DQ + 128 * 128 * 2, OFF_BAR = OFF_S5 + 4 * 128 * 4, OFF_SLOT = OFF_BAR + 16,
+              OFF_PAR = OFF_DQ + 128 * 128 * 2, OFF_BAR = OFF_PAR + 656 * 4, OFF_SLOT = OFF_BAR + 16,
               SMEM = OFF_SLOT + 16;
+// FP32 parameters kept in shared memory for the epilogues (floats from OFF_PAR): b1, b2, b3, b4, W5,
+// then the tile's sample coordinates (x^, y^) x 40
+constexpr int PB1 = 0, PB2 = 64, PB3 = 192, PB4 = 320, PW5 = 384, PXY = 576;
+constexpr int OFF_S5 = OFF_DQ + 8192;   // dL/d(outputs) per row [128][4], inside DQ (free at that point)
 static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 constexpr int WIMG_BYTES = (128 * 64 + 128 * 128 + 64 * 128) * 2;   // W2, W3, W4 at the head of the image
 constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 192, TM_DW4T = 320, TM_COLS = 512;
@@ -685,7 +689,7 @@ __device__ __forceinline__ void act16(const Row& R, const float* __restrict__ b,
                                       float (&out)[16]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
-        const float zz = R.c == 0 ? z[j] + __ldg(b + c0 + j) : z[j];
+        const float zz = R.c == 0 ? z[j] + b[c0 + j] : z[j];
         const float a = tc::tanh_fast(zz);
         const float sv = __shfl_sync(0xffffffffu, 1.0f - a * a, R.lane - R.c);
         out[j] = R.pad ? 0.0f : (R.c == 0 ? a : sv * zz);
@@ -769,7 +773,11 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     uint8_t *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
     uint8_t *DP = sm + OFF_DP, *DQ = sm + OFF_DQ;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
-    float* X = reinterpret_cast<float*>(DQ);   // exchange scratch while DQ holds no operand
+    float* X = reinterpret_cast<float*>(DQ);   // exchange scratch [0, 6 KB) while DQ holds no operand
+    float* PAR = reinterpret_cast<float*>(sm + OFF_PAR);
+    for (int i = tid; i < 576; i += THREADS)
+        PAR[i] = i < PB2 ? w[OB1 + i] : (i < PB3 ? w[OB2 + i - PB2] : (i < PB4 ? w[OB3 + i - PB3] :
+                 (i < PW5 ? w[OB4 + i - PB4] : w[OW5 + i - PW5])));
     float* BS = reinterpret_cast<float*>(A4);  // bias partials in the reverse pass (A4 is read by then)
     const uint32_t bar_w = tc::saddr(sm + OFF_BAR), bar_mma = tc::saddr(sm + OFF_BAR + 8);
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + OFF_SLOT);
@@ -847,8 +855,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         const float yh = 2.0f * ((float)y + 0.5f) / (float)L.ny - 1.0f;
 
         if (h == 0 && R.c == 0 && !R.pad) {   // the sample's (x^, y^) for the layer-1 weight gradient
-            S5[R.r * 4 + 3] = xh;
-            S5[(R.r + 1) * 4 + 3] = yh;
+            PAR[PXY + 2 * (R.warp * 10 + q)] = xh;
+            PAR[PXY + 2 * (R.warp * 10 + q) + 1] = yh;
         }
         // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
 #pragma unroll 1
@@ -859,7 +867,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 const float w0 = __ldg(w + OW1 + 2 * (c0 + j)), w1 = __ldg(w + OW1 + 2 * (c0 + j) + 1);
                 z[j] = R.c == 0 ? fmaf(xh, w0, yh * w1) : (R.c == 1 ? w0 : w1);
             }
-            act16(R, w + OB1, c0, z, out);
+            act16(R, PAR + PB1, c0, z, out);
             store16(A1, R.r, c0, out);
         }
         // ---- layers 2-4: MMA, then the activation epilogue (layer 4 also feeds layer 5)
@@ -875,7 +883,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                           2 * (uint32_t)(Nout / 8) * 128, false, Nout, Kin, false);
             if (!wait_mma()) break;
             uint8_t* dst = layer == 2 ? A2 : (layer == 3 ? A3 : A4);
-            const float* bias = w + (layer == 2 ? OB2 : (layer == 3 ? OB3 : OB4));
+            const float* bias = PAR + (layer == 2 ? PB2 : (layer == 3 ? PB3 : PB4));
 #pragma unroll 1
             for (int c0 = 16 * h; c0 < Nout; c0 += 32) {
                 float z[16], out[16];
@@ -885,9 +893,9 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 if (layer == 4) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        o[0] = fmaf(__ldg(w + OW5 + c0 + j), out[j], o[0]);
-                        o[1] = fmaf(__ldg(w + OW5 + 64 + c0 + j), out[j], o[1]);
-                        o[2] = fmaf(__ldg(w + OW5 + 128 + c0 + j), out[j], o[2]);
+                        o[0] = fmaf(PAR[PW5 + c0 + j], out[j], o[0]);
+                        o[1] = fmaf(PAR[PW5 + 64 + c0 + j], out[j], o[1]);
+                        o[2] = fmaf(PAR[PW5 + 128 + c0 + j], out[j], o[2]);
                     }
                 }
             }
@@ -963,8 +971,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             float dA[16], av[16], ax[16], ay[16], dz[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-                dA[j] = d5[0] * __ldg(w + OW5 + c0 + j) + d5[1] * __ldg(w + OW5 + 64 + c0 + j) +
-                        d5[2] * __ldg(w + OW5 + 128 + c0 + j);
+                dA[j] = d5[0] * PAR[PW5 + c0 + j] + d5[1] * PAR[PW5 + 64 + c0 + j] + d5[2] * PAR[PW5 + 128 + c0 + j];
             sample_acts(R, A4, c0, av, ax, ay);
             dact16(R, dA, av, ax, ay, dz);
             store16(DP, R.r, c0, dz);
@@ -1027,7 +1034,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                     float s0 = 0.0f, s1 = 0.0f, sb = 0.0f;
                     for (int wq = grp; wq < 40; wq += 4) {
                         const int rv = 32 * (wq / 10) + 3 * (wq % 10);
-                        const float xq = S5[rv * 4 + 3], yq = S5[(rv + 1) * 4 + 3];
+                        const float xq = PAR[PXY + 2 * wq], yq = PAR[PXY + 2 * wq + 1];
                         const float zv = zs[rv * 64 + k];
                         s0 += fmaf(zv, xq, zs[(rv + 1) * 64 + k]);
                         s1 += fmaf(zv, yq, zs[(rv + 2) * 64 + k]);
