@@ -7,8 +7,8 @@
  *     psi = rho0 (1 - exp(-rho/rho0)), Shan-Chen force, force-shifted
  *     equilibrium, BGK collision, periodic streaming);
  *   - network N(x, y) -> (rho, u_x, u_y): Sec. II-B Eq. 2, architecture Sec. III-B;
- *   - coupling / correction: Sec. II-C (correct "with emphasis on interface
- *     regions", at an adaptive, not per-step, frequency);
+ *   - coupling / correction: Sec. II-C (a correction weighted toward the
+ *     interface regions, applied every few steps rather than every step);
  *   - metrics: Sec. II-D Eqs. 9-13, discretised in Sec. IV-E Eqs. 14-16;
  *   - droplet set-up: Sec. III-A.
  *

@@ -503,7 +503,7 @@ void orc_mlp_field(int nx, int ny, const float* blob, int mode, double* out3) {
 
 /* ---------------------------------------------------------------------------
  * Interface correction (Sec. II-C step 3: the network's prediction corrects the
- * lattice state "with emphasis on interface regions"; the paper gives no
+ * lattice state, weighted toward the interface regions; the paper gives no
  * formula, so the operator below is the reading used):
  *   g = |grad rho| (Eq. 16), G_max = max g, m = g / G_max (0 everywhere if G_max = 0)
  *   (rho^, u^) = N(x^, y^)

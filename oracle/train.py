@@ -11,7 +11,7 @@ takes:
 
 T1 Samples: every cell of the lattice, input (x^, y^) = the cell centre mapped to [-1, 1]
    as for the correction.  One epoch is one gradient step on the loss over all cells
-   (Sec. III-B counts "epochs per coupling step" and names no batch size).
+   (Sec. III-B counts training epochs per coupling step and names no batch size).
 T2 Targets: the lattice state when training starts: rho = sum_i f_i and u = j / rho with
    j = sum_i f_i c_i.
 T3 L_data (Eq. 4): mean over the cells of |N - (rho, u_x, u_y)|^2 (the three outputs

@@ -4,17 +4,17 @@
   2. coupling: `K` steps, then training with epochs[0] (300, Sec. III-B) epochs, then the
      interface correction;
   3. evolution: len(epochs) - 1 further rounds of K steps + training + correction, with the
-     epoch counts epochs[1:] (the paper says "decreasing" without values; the default
+     epoch counts epochs[1:] (the paper gives no values, only that they decrease; the default
      250, 200, 150, 100, 50 decreases linearly);
   4. comparison: a pure LBM copy of the lattice, taken after the initialisation, advances the
      same number of steps;
   5. evaluation: the interface metrics (Eqs. 9-15) of both lattices after every round, and of
      the initialisation every `record_every` steps (the series of Figs. 1 and 3).
 
-The steps per round (K = 100) are the reading of "a small number of steps" (Sec. II-C) used
-by the single-droplet workloads.  Every number comes from the library's kernels (C ABI
-``pl_step``, ``pl_train``, ``pl_apply_correction``, ``pl_metrics``); this module only orders the
-calls.
+The steps per round (K = 100) are this library's reading of the few LBM steps between
+corrections that Sec. II-C calls for, as in the single-droplet workloads.  Every number comes
+from the library's kernels (C ABI ``pl_step``, ``pl_train``, ``pl_apply_correction``,
+``pl_metrics``); this module only orders the calls.
 """
 from __future__ import annotations
 
