@@ -108,3 +108,21 @@ def test_tc_coupled_run_and_mode_checks():
     lat64 = B.Lattice(B.pl_params_default(16, 16, storage=B.PL_F64, mlp=B.PL_MLP_F64))
     with pytest.raises(B.PLError):
         B.Trainer(lat64, mode=B.PL_TRAIN_TC)
+
+
+def test_protocol_with_tensor_core_training_follows_fp32_training():
+    """The Sec. III-C protocol (shortened) with either training form: the BF16 tensor-core
+    training moves the weights by steps that differ from the FP32 ones only through the BF16
+    rounding of the gradient, so every recorded interface metric agrees closely."""
+    from paper_2504_10539_gb300 import protocol
+    job = wl.Lattice(96, 96, storage=B.PL_F32, mlp=B.PL_MLP_F32, droplets=[(48.0, 48.0, 16.0)], seed=8, K=20,
+                     weight_seed=44)
+    a = protocol.run(job, init_steps=60, K=20, epochs=(20, 10), record_every=30)
+    b = protocol.run(job, init_steps=60, K=20, epochs=(20, 10), record_every=30, hyper=dict(mode=B.PL_TRAIN_TC))
+    assert a["status"] == b["status"] == {"pinn": 0, "pure": 0}
+    for (s1, e1, m1, l1), (s2, e2, m2, l2) in zip(a["pinn"], b["pinn"]):
+        assert (s1, e1) == (s2, e2)
+        for k in protocol.METRICS:
+            assert m2[k] == pytest.approx(m1[k], rel=1e-3, abs=1e-9), k
+        assert l2[0] == pytest.approx(l1[0], rel=1e-2) and l2[1] == pytest.approx(l1[1], rel=2e-2)
+    assert a["pure"] == b["pure"]
