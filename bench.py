@@ -251,7 +251,7 @@ def train_measurement(args, B, wl, torch, mode=0, cpu=True):
     """Sec. II-C step 2 at the paper's settings (lr 3e-4, 300 epochs per coupling round) on the
     single-droplet lattice of side --train-side (FP32 storage): epochs timed with CUDA events on
     the lattice's stream, then one full coupling round (K = 100 steps, training, correction).
-    mode: PL_TRAIN_SIMT (FP32 CUDA cores) or PL_TRAIN_TC (BF16 tcgen05 layers 2-4)."""
+    mode: PL_TRAIN_SIMT (FP32 CUDA cores) or PL_TRAIN_TC (BF16 tcgen05 layers 2-4 and gradients)."""
     side, E, K = args.train_side, args.train_epochs, 100
     job = wl.Lattice(side, side, storage=wl.F32, droplets=[(side / 2, side / 2, side * 80.0 / 512)], seed=2,
                      K=K, mlp=wl.MLP_BF16, weight_seed=12)
@@ -278,7 +278,7 @@ def train_measurement(args, B, wl, torch, mode=0, cpu=True):
         roof = {"bound": "tensor", "kernel": "k_train_grad_tc + k_train_update<float>", "achieved": tflops,
                 "peak": peak, "peak_kind": kind, "unit": "TFLOP/s", "frac": tflops / peak,
                 "flop_per_sample": TRAIN_FLOP_PER_SAMPLE}
-        arith = "BF16 tcgen05 layers 2-4, FP32 elsewhere"
+        arith = "BF16 tcgen05 layers 2-4 and the gradient sums, FP32 elsewhere"
     else:
         roof = {"bound": "alu", "kernel": "k_train_grad<float> + k_train_update<float>", "achieved": tflops,
                 "peak": FP32_ALU_PEAK_TFLOPS, "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",

@@ -243,9 +243,10 @@ PL_API int pl_get_mlp_weights(pl_lattice* lat, float* host_blob, size_t n);
  * --------------------------------------------------------------------------------- */
 /* Training arithmetic (pl_train_params.mode). */
 #define PL_TRAIN_SIMT 0 /* CUDA cores: FP64 for FP64 lattices, FP32 otherwise (default)        */
-#define PL_TRAIN_TC 1   /* tcgen05 tensor cores for layers 2-4: BF16 operands, FP32 accumulation,
-                           layers 1 and 5, the loss and the tanh terms in FP32; FP32 and
-                           FP16-offset lattices only                                           */
+#define PL_TRAIN_TC 1   /* tcgen05 tensor cores for layers 2-4 (forward, reverse, weight
+                           gradient) and for the bias and layer-1 gradients: BF16 operands,
+                           FP32 accumulation; the layer-1 forward pass, layer 5, the loss and
+                           the tanh terms in FP32; FP32 and FP16-offset lattices only          */
 
 typedef struct pl_train_params {
     double lr;          /* Adam step size (default 3e-4, Sec. III-B)          */

@@ -603,38 +603,62 @@ cudaError_t grad_setup(int* grid) {
 
 // ---------------------------------------------------------------------------------------------
 // Tensor-core form: the dense layers 2-4 of the forward pass, of the reverse pass and of the
-// weight gradient as tcgen05 MMAs (BF16 operands in shared memory, FP32 accumulators in TMEM);
-// layers 1 and 5, the loss and the tanh terms on CUDA cores in FP32.
+// weight gradient, and the bias and layer-1 gradients, as tcgen05 MMAs (BF16 operands in shared
+// memory, FP32 accumulators in TMEM); the layer-1 forward pass, layer 5, the loss and the tanh
+// terms on CUDA cores in FP32.
 //
-// One warpgroup per CTA (one CTA per SM: all of TMEM).  A tile is 40 samples as 128 operand
-// rows: row 32 w + 3 q + c is channel c (value, d/dx^, d/dy^) of sample 10 w + q; lanes 30
-// and 31 of each warp are padding (zero rows).  Thread r owns row r, i.e. TMEM lane r, and the
-// three rows of a sample are neighbouring lanes of one warp, so the tanh terms that couple them
-// (s = 1 - a^2 for the tangent rows, the second-derivative term of the value row) move by warp
-// shuffles.  Every activation is stored once, K-major over its features: it is the A operand
-// of the next forward MMA and, read MN-major (K = rows), an operand of the weight-gradient MMAs;
-// the weight images serve the forward MMAs K-major and the reverse MMAs MN-major (K = outputs).
-//   forward   Z_l = A_{l-1} W_l^T                 M = 128 rows, N = out_l, K = in_l
-//   reverse   dA_{l-1} = dZ_l W_l                  M = 128 rows, N = in_l,  K = out_l
-//   gradient  dW_l += dZ_l^T A_{l-1} (l = 2, 3)    M = out_l,    N = in_l,  K = 128 rows
-//             dW_4^T += A_3^T dZ_4                  M = in_4,     N = out_4, K = 128 rows
-// The three weight gradients accumulate in TMEM over all tiles of the CTA and are written once;
-// layers 1 and 5 and the biases go to the CTA's partial slice per tile, as in the FP32 kernel.
+// Sixteen warps per CTA (one CTA per SM: all of TMEM).  A tile is 40 samples as 128 operand
+// rows: row 32 u + 3 q + c is channel c (value, d/dx^, d/dy^) of sample 10 u + q; lanes 30 and
+// 31 of each warp are padding (zero rows).  Warp w serves TMEM lane quadrant u = w mod 4 (thread
+// r owns row r, i.e. TMEM lane r) and the 16-column chunks 16 (w / 4) + 64 i.  The three rows of
+// a sample are neighbouring lanes of one warp, so the tanh terms that couple them (s = 1 - a^2 for
+// the tangent rows, the second-derivative term of the value row) move by warp shuffles.  Every
+// activation is stored once, K-major over its features: it is the A operand of the next forward
+// MMA and, read MN-major (K = rows), an operand of the gradient MMAs; the weight images serve the
+// forward MMAs K-major and the reverse MMAs MN-major (K = outputs).  In the reverse pass dZ_l
+// overwrites A_l once the MMAs that read A_l are complete.
+//   forward   Z_l = A_{l-1} W_l^T                               M = 128 rows, N = out_l, K = in_l
+//   reverse   dA_{l-1} = dZ_l W_l                                M = 128 rows, N = in_l,  K = out_l
+//   gradient  [dW_l | . . db_l] += dZ_l^T [A_{l-1} | E_{l-1}]    M = out_l, N = in_l + 16, K = 128 rows
+//             (l = 2, 3);  dW_4^T += A_3^T dZ_4                   M = in_4,  N = out_4,     K = 128 rows
+//             [. . db_4] += dZ_4^T E_1                            M = 64,    N = 16,        K = 128 rows
+//             [dW_1 | db_1] += dZ_1^T E_1                         M = 64,    N = 16,        K = 128 rows
+// E_1, the 16 columns after A1's features, holds per row (x^, y^, 1) on value rows, (1, 0, 0) on
+// d/dx^ rows and (0, 1, 0) on d/dy^ rows, zeros elsewhere, so that dZ_1^T E_1 gives the layer-1
+// gradient (columns 0 and 1: the sums of dz_v x^ + dz_x and dz_v y^ + dz_y; column 2: of dz_v);
+// its column 2, the value-row indicator, gives the bias gradients of the layers above.  E_2, the 16
+// columns after A2's features, holds the indicator in its column 2 as well.  The last two rows
+// take M = 128 MMAs whose A operand runs on past the 64 rows that matter into the next buffer's
+// bytes; those rows of D are never read.  Everything accumulates in TMEM over the
+// CTA's tiles and is written once; layer 5 goes to the CTA's partial slice per tile, as in the
+// FP32 kernel.
 namespace ttc {
-constexpr int THREADS = 256;   // two warps per TMEM lane quadrant
+constexpr int THREADS = 512;                       // four warps per TMEM lane quadrant
+constexpr int NH = THREADS / 128;                  // warps per quadrant: warp w takes the column
+constexpr int CS = 16 * NH;                        // chunks 16 (w / 4) + CS i of 16 columns
 constexpr int SPT = 40;                            // samples per tile
-constexpr int OFF_A1 = 0, OFF_A2 = OFF_A1 + 128 * 64 * 2, OFF_A3 = OFF_A2 + 128 * 128 * 2,
-              OFF_A4 = OFF_A3 + 128 * 128 * 2, OFF_W2 = OFF_A4 + 128 * 64 * 2, OFF_W3 = OFF_W2 + 128 * 64 * 2,
-              OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_DP = OFF_W4 + 64 * 128 * 2, OFF_DQ = OFF_DP + 128 * 128 * 2,
-              OFF_PAR = OFF_DQ + 128 * 128 * 2, OFF_BAR = OFF_PAR + 656 * 4, OFF_SLOT = OFF_BAR + 16,
+constexpr int COLB = 128 * 2;                      // bytes of one feature of a 128-row BF16 operand
+constexpr int OFF_A1 = 0, OFF_E1 = OFF_A1 + 64 * COLB, OFF_A2 = OFF_E1 + 16 * COLB, OFF_E2 = OFF_A2 + 128 * COLB,
+              OFF_A3 = OFF_E2 + 16 * COLB, OFF_A4 = OFF_A3 + 128 * COLB, OFF_W2 = OFF_A4 + 64 * COLB,
+              OFF_W3 = OFF_W2 + 128 * 64 * 2, OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_SC = OFF_W4 + 64 * 128 * 2;
+// FP32 scratch: dL/d(outputs) per row [128][4]; the layer-5 partial sums of the warps with
+// w / 4 > 0 [NH - 1][128][4]; the layer-5 gradient partials [8][GP_LD] (lane l's 24 at l * 25)
+constexpr int GP_LD = 32 * 25 + 8;                 // 808 = 8 mod 32: the fold reads distinct banks
+constexpr int OFF_S5 = OFF_SC, OFF_X = OFF_S5 + 128 * 4 * 4, OFF_GP = OFF_X + (NH - 1) * 128 * 4 * 4,
+              OFF_PAR = OFF_GP + 8 * GP_LD * 4, OFF_BAR = OFF_PAR + 704 * 4, OFF_SLOT = OFF_BAR + 16,
               SMEM = OFF_SLOT + 16;
-// FP32 parameters kept in shared memory for the epilogues (floats from OFF_PAR): b1, b2, b3, b4, W5,
-// then the tile's sample coordinates (x^, y^) x 40
-constexpr int PB1 = 0, PB2 = 64, PB3 = 192, PB4 = 320, PW5 = 384, PXY = 576;
-constexpr int OFF_S5 = OFF_DQ + 8192;   // dL/d(outputs) per row [128][4], inside DQ (free at that point)
+// FP32 parameters kept in shared memory (floats from OFF_PAR): b1, b2, b3, b4, W5, W1
+constexpr int PB1 = 0, PB2 = 64, PB3 = 192, PB4 = 320, PW5 = 384, PW1 = 576, NPAR = 704;
 static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
+static_assert(OFF_PAR % 16 == 0 && OFF_W2 % 16 == 0, "16-byte aligned regions");
+static_assert(OFF_A1 + 16 * 2048 <= OFF_E2 && OFF_A4 + 16 * 2048 <= OFF_SC,
+              "the M = 128 operands read from A1 and A4 stay inside the operand regions");
 constexpr int WIMG_BYTES = (128 * 64 + 128 * 128 + 64 * 128) * 2;   // W2, W3, W4 at the head of the image
-constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 192, TM_DW4T = 320, TM_COLS = 512;
+// TMEM columns (each accumulator 32-column aligned): work 128, [dW2 | db2] 80, [dW3 | db3] 144,
+// dW4^T 64, [dW1 | db1] 16, db4 16
+constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 224, TM_DW4T = 384, TM_D1 = 448, TM_B4 = 480, TM_COLS = 512;
+static_assert(TM_DW2 + 80 <= TM_DW3 && TM_DW3 + 144 <= TM_DW4T && TM_DW4T + 64 <= TM_D1 && TM_D1 + 16 <= TM_B4 &&
+              TM_B4 + 16 <= TM_COLS, "TMEM columns");
 constexpr uint32_t KLBO = 2048;                    // K-major 128-row operand: core matrices along K
 
 // D (+)= A B over K in steps of 16 (each operand: base address, leading and stride byte
@@ -652,6 +676,10 @@ __device__ __forceinline__ void mma_chain(uint32_t d, uint32_t a, uint32_t alb, 
         db += bst >> 4;
     }
 }
+// D (+)= A^T B with both operands 128-row activation buffers read MN-major (K = the 128 rows)
+__device__ __forceinline__ void mma_rows(uint32_t d, uint32_t a, uint32_t b, int N, bool acc) {
+    mma_chain(d, a, 128, KLBO, 256, true, b, 128, KLBO, 256, true, N, 128, acc);
+}
 
 // 8 BF16 values of row r, features k0..k0+7, of a K-major 128-row operand -> FP32.
 __device__ __forceinline__ void load8(const uint8_t* A, int r, int k0, float (&v)[8]) {
@@ -663,18 +691,6 @@ __device__ __forceinline__ void load8(const uint8_t* A, int r, int k0, float (&v
         v[2 * q] = f.x;
         v[2 * q + 1] = f.y;
     }
-}
-__device__ __forceinline__ float bf16_at(const uint8_t* A, int r, int k) {
-    return __bfloat162float(
-        *reinterpret_cast<const __nv_bfloat16*>(A + ((k >> 3) * 16 + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2));
-}
-
-// Sum of v over the value lanes of the warp (the caller zeroes the other lanes); every lane
-// gets the sum (butterfly, fixed order).
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // Row roles of thread r.
@@ -723,34 +739,20 @@ __device__ __forceinline__ void load16(const uint8_t* A, int r, int c0, float (&
     for (int j = 0; j < 8; ++j) v[8 + j] = t[j];
 }
 
-// The value-row and tangent-row activations of this row's sample.
+// The value-row and tangent-row activations of this row's sample.  Every row read lies in the
+// warp's own quadrant (the padding lanes' reads are clamped to it), so that a warp may overwrite
+// its rows' chunk in place.
 __device__ __forceinline__ void sample_acts(const Row& R, const uint8_t* A, int c0, float (&av)[16], float (&ax)[16],
                                             float (&ay)[16]) {
-    const int rv = R.r - R.c;
+    const int rv = R.r - R.c, top = R.r | 31;
     load16(A, rv, c0, av);
-    load16(A, rv + 1 < 128 ? rv + 1 : 127, c0, ax);
-    load16(A, rv + 2 < 128 ? rv + 2 : 127, c0, ay);
+    load16(A, rv + 1 < top ? rv + 1 : top, c0, ax);
+    load16(A, rv + 2 < top ? rv + 2 : top, c0, ay);
 }
 
 __device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (&v)[16]) {
     tc::store8(A, r, c0, v);
     tc::store8(A, r, c0 + 8, v + 8);
-}
-
-// Bias gradient of a layer: the column sums of its stored dZ over the 40 value rows (lanes 0,
-// 3, ..., 27 of each quadrant), added to the slice entries p[0..n).  The 256 threads take
-// 256 / n interleaved row groups of each column; the partial sums are folded in group order.
-__device__ __forceinline__ void bias_cols(const uint8_t* D, int n, float* p, bool first, float* scratch) {
-    const int k = threadIdx.x % n, grp = threadIdx.x / n, ng = THREADS / n;
-    float sum = 0.0f;
-    for (int v = grp; v < 40; v += ng) sum += bf16_at(D, 32 * (v / 10) + 3 * (v % 10), k);
-    scratch[grp * n + k] = sum;
-    __syncthreads();
-    if ((int)threadIdx.x < n) {
-        float t = 0.0f;
-        for (int g = 0; g < ng; ++g) t += scratch[g * n + k];
-        acc1(p + k, t, first);
-    }
 }
 }  // namespace ttc
 
@@ -762,7 +764,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     extern __shared__ __align__(1024) uint8_t sm[];
     if ((long long)blockIdx.x >= ntiles) return;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int h = warp >> 2;   // column half: this warp takes the 16-column chunks 16 h, 16 h + 32, ...
+    const int h = warp >> 2;   // column group: this warp takes the 16-column chunks 16 h, 16 h + CS, ...
     Row R;
     R.lane = tid & 31;
     R.warp = warp & 3;         // TMEM lane quadrant
@@ -771,14 +773,20 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     R.pad = R.lane >= 30;
     const int q = R.lane / 3;
     uint8_t *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
-    uint8_t *DP = sm + OFF_DP, *DQ = sm + OFF_DQ;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
-    float* X = reinterpret_cast<float*>(DQ);   // exchange scratch [0, 6 KB) while DQ holds no operand
+    float* X = reinterpret_cast<float*>(sm + OFF_X);
+    float* GP = reinterpret_cast<float*>(sm + OFF_GP);
     float* PAR = reinterpret_cast<float*>(sm + OFF_PAR);
-    for (int i = tid; i < 576; i += THREADS)
+    for (int i = tid; i < NPAR; i += THREADS)
         PAR[i] = i < PB2 ? w[OB1 + i] : (i < PB3 ? w[OB2 + i - PB2] : (i < PB4 ? w[OB3 + i - PB3] :
-                 (i < PW5 ? w[OB4 + i - PB4] : w[OW5 + i - PW5])));
-    float* BS = reinterpret_cast<float*>(A4);  // bias partials in the reverse pass (A4 is read by then)
+                 (i < PW5 ? w[OB4 + i - PB4] : (i < PW1 ? w[OW5 + i - PW5] : w[OW1 + i - PW1]))));
+    if (h == 0) {   // E2: the value-row indicator in column 2 (the same for every tile)
+        float e[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) e[j] = 0.0f;
+        e[2] = (R.c == 0 && !R.pad) ? 1.0f : 0.0f;
+        store16(A2, R.r, 128, e);
+    }
     const uint32_t bar_w = tc::saddr(sm + OFF_BAR), bar_mma = tc::saddr(sm + OFF_BAR + 8);
     uint32_t* slot = reinterpret_cast<uint32_t*>(sm + OFF_SLOT);
     if (tid == 0) {
@@ -818,8 +826,9 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     const float* gf = static_cast<const float*>(L.g);
     float* P = part + (long long)blockIdx.x * PSTRIDE;
     double ld = 0.0, lp = 0.0, li = 0.0;
-    const uint32_t sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3), sW2 = tc::saddr(sm + OFF_W2),
-                   sW3 = tc::saddr(sm + OFF_W3), sW4 = tc::saddr(sm + OFF_W4), sDP = tc::saddr(DP), sDQ = tc::saddr(DQ);
+    const uint32_t sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3), sA4 = tc::saddr(A4),
+                   sE1 = tc::saddr(sm + OFF_E1), sW2 = tc::saddr(sm + OFF_W2), sW3 = tc::saddr(sm + OFF_W3),
+                   sW4 = tc::saddr(sm + OFF_W4);
 
     // operands written by the threads -> visible to the tensor core, then thread 0 issues
     auto sync_to_mma = [&]() {
@@ -828,8 +837,9 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         __syncthreads();
         tc::tc_after_sync();
     };
-    // wait (bounded) for the last commit; false on timeout
-    auto wait_issued = [&]() {
+    // commit the issued MMAs and wait (bounded) for them; false on timeout
+    auto wait_mma = [&]() {
+        if (tid == 0) tc::mma_commit(bar_mma);
         pending = true;
         ok = __syncthreads_and(tc::mbar_wait(bar_mma, phase)) != 0;
         if (ok) {
@@ -839,32 +849,51 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         tc::tc_after_sync();
         return ok;
     };
-    // commit the issued MMAs and wait for them
-    auto wait_mma = [&]() {
-        if (tid == 0) tc::mma_commit(bar_mma);
-        return wait_issued();
-    };
 
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         const bool first = tile == blockIdx.x;
         const long long smp = tile * SPT + R.warp * 10 + q;
         const bool valid = !R.pad && smp < N;
         const long long cc = valid ? smp : 0;
-        const int x = (int)(cc % L.nx), y = (int)(cc / L.nx);
+        int x, y;
+        if (N <= 0xffffffffLL) {   // 32-bit division (every lattice of practical size)
+            const unsigned c32 = (unsigned)cc, q32 = c32 / (unsigned)L.nx;
+            x = (int)(c32 - q32 * (unsigned)L.nx);
+            y = (int)q32;
+        } else {
+            x = (int)(cc % L.nx);
+            y = (int)(cc / L.nx);
+        }
+        // the loss targets of the value rows, loaded now so that their latency is hidden by the
+        // forward pass
+        float t_rho = 1.0f, t_jx = 0.0f, t_jy = 0.0f, t_g = 0.0f;
+        if (h == 0 && valid && R.c == 0) {
+            t_rho = rho[cc];
+            t_jx = jx[cc];
+            t_jy = jy[cc];
+            t_g = gf[cc];
+        }
         const float xh = 2.0f * ((float)x + 0.5f) / (float)L.nx - 1.0f;
         const float yh = 2.0f * ((float)y + 0.5f) / (float)L.ny - 1.0f;
 
-        if (h == 0 && R.c == 0 && !R.pad) {   // the sample's (x^, y^) for the layer-1 weight gradient
-            PAR[PXY + 2 * (R.warp * 10 + q)] = xh;
-            PAR[PXY + 2 * (R.warp * 10 + q) + 1] = yh;
+        if (h == 0) {   // E1 of this row (samples past the lattice end have dZ = 0: any finite entry)
+            float e[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) e[j] = 0.0f;
+            if (!R.pad) {
+                e[0] = R.c == 0 ? xh : (R.c == 1 ? 1.0f : 0.0f);
+                e[1] = R.c == 0 ? yh : (R.c == 2 ? 1.0f : 0.0f);
+                e[2] = R.c == 0 ? 1.0f : 0.0f;
+            }
+            store16(A1, R.r, 64, e);
         }
         // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
 #pragma unroll 1
-        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
+        for (int c0 = 16 * h; c0 < 64; c0 += CS) {
             float z[16], out[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const float w0 = __ldg(w + OW1 + 2 * (c0 + j)), w1 = __ldg(w + OW1 + 2 * (c0 + j) + 1);
+                const float w0 = PAR[PW1 + 2 * (c0 + j)], w1 = PAR[PW1 + 2 * (c0 + j) + 1];
                 z[j] = R.c == 0 ? fmaf(xh, w0, yh * w1) : (R.c == 1 ? w0 : w1);
             }
             act16(R, PAR + PB1, c0, z, out);
@@ -885,7 +914,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             uint8_t* dst = layer == 2 ? A2 : (layer == 3 ? A3 : A4);
             const float* bias = PAR + (layer == 2 ? PB2 : (layer == 3 ? PB3 : PB4));
 #pragma unroll 1
-            for (int c0 = 16 * h; c0 < Nout; c0 += 32) {
+            for (int c0 = 16 * h; c0 < Nout; c0 += CS) {
                 float z[16], out[16];
                 tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, z);
                 act16(R, bias, c0, z, out);
@@ -901,26 +930,26 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             }
         }
         if (!ok) break;
-        // ---- layer 5: the two halves' partial sums, the output and the loss (value lanes of
-        // half 0), dL/d(outputs) per row into S5
-        if (h == 1)
+        // ---- layer 5: the column groups' partial sums (added in group order), the output and
+        // the loss (value lanes of group 0), dL/d(outputs) per row into S5
+        if (h > 0)
 #pragma unroll
-            for (int k = 0; k < 3; ++k) X[R.r * 4 + k] = o[k];
+            for (int k = 0; k < 3; ++k) X[((h - 1) * 128 + R.r) * 4 + k] = o[k];
         __syncthreads();
         if (h == 0) {
             float ov[3], oxv[3], oyv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                o[k] += X[R.r * 4 + k];
+#pragma unroll
+                for (int hh = 1; hh < NH; ++hh) o[k] += X[((hh - 1) * 128 + R.r) * 4 + k];
                 ov[k] = o[k] + (R.c == 0 ? __ldg(w + OB5 + k) : 0.0f);
                 oxv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 1);
                 oyv[k] = __shfl_sync(0xffffffffu, o[k], R.lane + 2);
             }
             float g[3] = {0.0f, 0.0f, 0.0f}, gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f};
             if (valid && R.c == 0) {
-                const float rr = rho[cc];
-                const float t[3] = {rr, jx[cc] / rr, jy[cc] / rr};
-                const bool iface = above(gf[cc], L.threshold);
+                const float t[3] = {t_rho, t_jx / t_rho, t_jy / t_rho};
+                const bool iface = above(t_g, L.threshold);
                 const SampleLoss<float> sl = sample_loss<float>(ov, oxv, oyv, t, iface, sx, sy, inv_n, c_phys, c_int, L, hp);
                 ld += sl.ld;
                 lp += sl.lp;
@@ -941,143 +970,132 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         }
         __syncthreads();
         const float d5[3] = {S5[R.r * 4], S5[R.r * 4 + 1], S5[R.r * 4 + 2]};
-        // ---- layer 5 gradient: 24 groups (output o, 8 features) x 8 row blocks of 16, folded in order
-        if (tid < 192) {
-            const int gi = tid % 24, rb = tid / 24, oo = gi / 8, k0 = (gi % 8) * 8;
-            float acc[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, t8[8];
-            for (int rr = 16 * rb; rr < 16 * rb + 16; ++rr) {
-                const float d = S5[rr * 4 + oo];
-                load8(A4, rr, k0, t8);
+        // ---- layer 5 gradient: warp g < 8 takes features 8 g .. 8 g + 7, lane l the rows l + 32 i
+        // (a warp reads 32 consecutive rows of one feature group: no bank conflicts); the 32
+        // lanes' partials are folded in lane order (four chains)
+        if (warp < 8) {
+            float acc[3][8], t8[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) acc[e] = fmaf(d, t8[e], acc[e]);
+            for (int oo = 0; oo < 3; ++oo)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) acc[oo][e] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int rr = R.lane + 32 * i;
+                load8(A4, rr, 8 * warp, t8);
+#pragma unroll
+                for (int oo = 0; oo < 3; ++oo) {
+                    const float d = S5[rr * 4 + oo];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) acc[oo][e] = fmaf(d, t8[e], acc[oo][e]);
+                }
             }
 #pragma unroll
-            for (int e = 0; e < 8; ++e) X[rb * 192 + oo * 64 + k0 + e] = acc[e];
+            for (int oo = 0; oo < 3; ++oo)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) GP[warp * GP_LD + R.lane * 25 + oo * 8 + e] = acc[oo][e];
         }
         __syncthreads();
         if (tid < 192) {
-            float acc = 0.0f;
-            for (int rb = 0; rb < 8; ++rb) acc += X[rb * 192 + tid];
-            acc1(P + OW5 + tid, acc, first);
+            const int oo = tid / 64, k = tid % 64;
+            const float* g = GP + (k / 8) * GP_LD + oo * 8 + k % 8;
+            float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int l = 0; l < 32; ++l) a4[l & 3] += g[l * 25];
+            acc1(P + OW5 + tid, (a4[0] + a4[1]) + (a4[2] + a4[3]), first);
         } else if (tid < 195) {   // value rows: lanes 0, 3, ..., 27 of each quadrant
             const int oo = tid - 192;
             float acc = 0.0f;
             for (int wq = 0; wq < 40; ++wq) acc += S5[(32 * (wq / 10) + 3 * (wq % 10)) * 4 + oo];
             acc1(P + OB5 + oo, acc, first);
         }
-        // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 (DP)
+        // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 over A4
 #pragma unroll 1
-        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
+        for (int c0 = 16 * h; c0 < 64; c0 += CS) {
             float dA[16], av[16], ax[16], ay[16], dz[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j)
                 dA[j] = d5[0] * PAR[PW5 + c0 + j] + d5[1] * PAR[PW5 + 64 + c0 + j] + d5[2] * PAR[PW5 + 128 + c0 + j];
             sample_acts(R, A4, c0, av, ax, ay);
             dact16(R, dA, av, ax, ay, dz);
-            store16(DP, R.r, c0, dz);
+            store16(A4, R.r, c0, dz);
         }
-        __syncthreads();
-        bias_cols(DP, 64, P + OB4, first, BS);
-        // ---- reverse MMAs of layers 4, 3, 2 and their epilogues
+        // ---- reverse MMAs of layers 4, 3, 2 (with the gradients) and their epilogues
 #pragma unroll 1
         for (int layer = 4; layer >= 2 && ok; --layer) {
-            sync_to_mma();   // also orders the reads of the previous step before the next writes
+            sync_to_mma();
             const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
-            const uint32_t dz = layer == 3 ? sDQ : sDP;          // dZ_l
+            const uint32_t dz = layer == 4 ? sA4 : (layer == 3 ? sA3 : sA2);   // dZ_l, over A_l
             const uint32_t wl = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
-            const uint32_t ain = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);   // A_{l-1}
+            const uint32_t ain = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);   // A_{l-1} (and E_{l-1})
             if (tid == 0) {
+                if (layer == 4) {
+                    mma_rows(tmem + TM_DW4T, sA3, dz, 64, !first);   // dW4^T += A3^T dZ4
+                    mma_rows(tmem + TM_B4, dz, sE1, 16, !first);     // column 2: db4 += dZ4^T 1_v
+                } else {                                              // [dW_l | db_l] += dZ_l^T [A_{l-1} | E_{l-1}]
+                    mma_rows(tmem + (layer == 3 ? TM_DW3 : TM_DW2), dz, ain, Kin + 16, !first);
+                }
                 // dA_{l-1} = dZ_l W_l: A = dZ_l K-major (K = out), B = W_l MN-major (K = out, N = in)
                 mma_chain(tmem + TM_WORK, dz, KLBO, 128, 2 * KLBO, false, wl, 128, (uint32_t)(Nout / 8) * 128, 256,
                           true, Kin, Nout, false);
-                // layers 4 and 3: the epilogue waits for dA only; the weight-gradient MMAs below
-                // run during it (they read dZ_l and A_{l-1}, which the epilogue does not write, and
-                // the next layer's wait covers them).  Layer 2 waits for both: the next tile
-                // rewrites A1 before its first wait.
-                if (layer > 2) tc::mma_commit(bar_mma);
-                if (layer == 4)   // dW4^T += A3^T dZ4: A = A3 MN-major (M = in), B = dZ4 MN-major (N = out)
-                    mma_chain(tmem + TM_DW4T, ain, 128, KLBO, 256, true, dz, 128, KLBO, 256, true, 64, 128, !first);
-                else              // dW_l += dZ_l^T A_{l-1}: A = dZ_l MN-major (M = out), B = A_{l-1} MN-major (N = in)
-                    mma_chain(tmem + (layer == 3 ? TM_DW3 : TM_DW2), dz, 128, KLBO, 256, true, ain, 128, KLBO, 256,
-                              true, Kin, 128, !first);
             }
-            if (!(layer > 2 ? wait_issued() : wait_mma())) break;
-            const uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
-            if (layer > 2) {
-                uint8_t* dnext = layer == 4 ? DQ : DP;           // dZ_{l-1}
+            if (!wait_mma()) break;   // all of them: the epilogue overwrites A_{l-1}
+            uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
 #pragma unroll 1
-                for (int c0 = 16 * h; c0 < Kin; c0 += 32) {
-                    float dA[16], av[16], ax[16], ay[16], dzv[16];
-                    tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
-                    sample_acts(R, Aact, c0, av, ax, ay);
-                    dact16(R, dA, av, ax, ay, dzv);
-                    store16(dnext, R.r, c0, dzv);
-                }
-                __syncthreads();
-                bias_cols(dnext, 128, P + (layer == 4 ? OB3 : OB2), first, BS);
-            } else {
-                // layer 1 reverse: dz1 (FP32, all rows) into a scratch, then per feature the sums
-                // over the samples of dz_v x^ + dz_x, dz_v y^ + dz_y and dz_v (dW1 and db1)
-                float* zs = X;   // [128][64] (DQ is free)
-#pragma unroll 1
-                for (int c0 = 16 * h; c0 < 64; c0 += 32) {
-                    float dA[16], av[16], ax[16], ay[16], dzv[16];
-                    tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
-                    sample_acts(R, A1, c0, av, ax, ay);
-                    dact16(R, dA, av, ax, ay, dzv);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) zs[R.r * 64 + c0 + j] = dzv[j];
-                }
-                __syncthreads();
-                {   // 4 interleaved groups of the 40 samples per feature, folded in group order
-                    const int k = tid % 64, grp = tid / 64;
-                    float s0 = 0.0f, s1 = 0.0f, sb = 0.0f;
-                    for (int wq = grp; wq < 40; wq += 4) {
-                        const int rv = 32 * (wq / 10) + 3 * (wq % 10);
-                        const float xq = PAR[PXY + 2 * wq], yq = PAR[PXY + 2 * wq + 1];
-                        const float zv = zs[rv * 64 + k];
-                        s0 += fmaf(zv, xq, zs[(rv + 1) * 64 + k]);
-                        s1 += fmaf(zv, yq, zs[(rv + 2) * 64 + k]);
-                        sb += zv;
-                    }
-                    BS[grp * 64 + k] = s0;
-                    BS[256 + grp * 64 + k] = s1;
-                    BS[512 + grp * 64 + k] = sb;
-                    __syncthreads();
-                    if (tid < 64) {
-                        float t3[3];
-#pragma unroll
-                        for (int m = 0; m < 3; ++m)
-                            t3[m] = ((BS[m * 256 + tid] + BS[m * 256 + 64 + tid]) + BS[m * 256 + 128 + tid]) +
-                                    BS[m * 256 + 192 + tid];
-                        acc1(P + OW1 + 2 * tid, t3[0], first);
-                        acc1(P + OW1 + 2 * tid + 1, t3[1], first);
-                        acc1(P + OB1 + tid, t3[2], first);
-                    }
-                }
+            for (int c0 = 16 * h; c0 < Kin; c0 += CS) {
+                float dA[16], av[16], ax[16], ay[16], dzv[16];
+                sample_acts(R, Aact, c0, av, ax, ay);   // in flight during the TMEM load
+                tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
+                dact16(R, dA, av, ax, ay, dzv);
+                store16(Aact, R.r, c0, dzv);           // dZ_{l-1} over A_{l-1}
             }
         }
-        __syncthreads();
+        if (!ok) break;
+        // ---- layer-1 gradient: [dW1 | db1] += dZ1^T E1; complete before the next tile rewrites A1
+        sync_to_mma();
+        if (tid == 0) mma_rows(tmem + TM_D1, sA1, sE1, 16, !first);
+        if (!wait_mma()) break;
     }
     if (ok) {
-        // the weight gradients accumulated in TMEM: row r of dW2, dW3 and of dW4^T
+        // the gradients accumulated in TMEM: rows of [dW2 | db2], [dW3 | db3] and dW4^T; rows < 64
+        // of [dW1 | db1] and of db4 (column 2)
         tc::tc_after_sync();
+        float v[16];
 #pragma unroll 1
-        for (int c0 = 16 * h; c0 < 64; c0 += 32) {
-            float v[16];
+        for (int c0 = 16 * h; c0 < 80; c0 += CS) {
             tc::tmem_ld16(tmem + lane_off + TM_DW2 + c0, v);
+            if (c0 < 64) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) P[OW2 + R.r * 64 + c0 + j] = v[j];
+                for (int j = 0; j < 16; ++j) P[OW2 + R.r * 64 + c0 + j] = v[j];
+            } else {
+                P[OB2 + R.r] = v[2];
+            }
+        }
+#pragma unroll 1
+        for (int c0 = 16 * h; c0 < 144; c0 += CS) {
+            tc::tmem_ld16(tmem + lane_off + TM_DW3 + c0, v);
+            if (c0 < 128) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) P[OW3 + R.r * 128 + c0 + j] = v[j];
+            } else {
+                P[OB3 + R.r] = v[2];
+            }
+        }
+#pragma unroll 1
+        for (int c0 = 16 * h; c0 < 64; c0 += CS) {
             tc::tmem_ld16(tmem + lane_off + TM_DW4T + c0, v);
 #pragma unroll
             for (int j = 0; j < 16; ++j) P[OW4 + (c0 + j) * 128 + R.r] = v[j];
         }
-#pragma unroll 1
-        for (int c0 = 16 * h; c0 < 128; c0 += 32) {
-            float v[16];
-            tc::tmem_ld16(tmem + lane_off + TM_DW3 + c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) P[OW3 + R.r * 128 + c0 + j] = v[j];
+        if (h == 0) {
+            tc::tmem_ld16(tmem + lane_off + TM_D1, v);
+            if (R.r < 64) {
+                P[OW1 + 2 * R.r] = v[0];
+                P[OW1 + 2 * R.r + 1] = v[1];
+                P[OB1 + R.r] = v[2];
+            }
+            tc::tmem_ld16(tmem + lane_off + TM_B4, v);
+            if (R.r < 64) P[OB4 + R.r] = v[2];
         }
     } else {
         if (tid == 0) atomicOr(err, 1u);
@@ -1090,7 +1108,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
     double v[3] = {ld, lp, li};
     const int op[3] = {0, 0, 0};
-    block_reduce<3>(v, op, reinterpret_cast<double*>(sm + OFF_DP));
+    block_reduce<3>(v, op, reinterpret_cast<double*>(sm + OFF_SC));
     if (tid == 0)
         for (int k = 0; k < 3; ++k) loss_part[blockIdx.x * 4 + k] = ok ? v[k] : NAN;
 }

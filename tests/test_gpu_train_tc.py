@@ -1,8 +1,9 @@
 """Tensor-core training (PL_TRAIN_TC) against the FP64 training oracle.
 
-Layers 2-4 of the forward pass, of the reverse pass and of the weight gradient run as BF16
-tcgen05 MMAs with FP32 accumulation: the activations, their tangents, the back-propagated
-gradients and the weights enter each MMA rounded to BF16 (2^-9 relative).  A gradient entry
+Layers 2-4 of the forward pass, of the reverse pass and of the weight gradient, and the bias
+and layer-1 gradients, run as BF16 tcgen05 MMAs with FP32 accumulation: the activations, their
+tangents, the back-propagated gradients, the weights and the sample coordinates enter each MMA
+rounded to BF16 (2^-9 relative).  A gradient entry
 sums one product of two such operands per sample and row, so its error is a few 2^-9 of the
 magnitudes it sums; the bound used is 2e-2 of the largest gradient component, and the loss
 (whose forward pass has three BF16 layers) is held to 1e-2 relative.
