@@ -291,7 +291,7 @@ __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;"
 template <typename R>
 struct SampleLoss {
     R g[3], gx[3], gy[3];
-    double ld, lp, li;
+    R ld, lp, li;   // the sample's terms (squares summed in R)
 };
 
 template <typename R>
@@ -309,7 +309,7 @@ __device__ __forceinline__ SampleLoss<R> sample_loss(const R (&o)[3], const R (&
         e[k] = o[k] - t[k];
         q.g[k] = R(2) * e[k] * inv_n;
     }
-    q.ld = (double)e[0] * e[0] + (double)e[1] * e[1] + (double)e[2] * e[2];
+    q.ld = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
     // Eqs. 5-7: p' and p'' of p = rho/3 + G psi^2/6
     const R rho0 = R(L.rho0), G = R(L.G);
     const R ex = exp_r<R>(-r / rho0), psi = rho0 * (R(1) - ex);
@@ -318,7 +318,7 @@ __device__ __forceinline__ SampleLoss<R> sample_loss(const R (&o)[3], const R (&
     const R rc = u * rx + r * ux + v * ry + r * vy;
     const R rmx = u * u * rx + R(2) * r * u * ux + u * v * ry + r * v * uy + r * u * vy + P * rx;
     const R rmy = u * v * rx + r * v * ux + r * u * vx + v * v * ry + R(2) * r * v * vy + P * ry;
-    q.lp = (double)rc * rc + (double)rmx * rmx + (double)rmy * rmy;
+    q.lp = rc * rc + rmx * rmx + rmy * rmy;
     const R A = c_phys * rc, B = c_phys * rmx, C = c_phys * rmy;
     const R dr = A * (ux + vy) + B * (R(2) * u * ux + v * uy + u * vy + dP * rx) +
                  C * (v * ux + u * vx + R(2) * v * vy + dP * ry);
@@ -331,11 +331,11 @@ __device__ __forceinline__ SampleLoss<R> sample_loss(const R (&o)[3], const R (&
     const R dvx = C * (r * u);
     const R dvy = A * r + B * (r * u) + C * (R(2) * r * v);
     // Eq. 8 (signs of the text)
-    q.li = 0.0;
+    q.li = R(0);
     if (iface) {
         const R qq = rx * rx + ry * ry;
         const R a1 = R(hp.alpha1), a2 = R(hp.alpha2);
-        q.li = (double)(-a1 * qq + a2 * qq * qq);
+        q.li = -a1 * qq + a2 * qq * qq;
         const R dq = c_int * (-a1 + R(2) * a2 * qq);
         drx += R(2) * dq * rx;
         dry += R(2) * dq * ry;
@@ -619,27 +619,26 @@ cudaError_t grad_setup(int* grid) {
 // overwrites A_l once the MMAs that read A_l are complete.
 //   forward   Z_l = A_{l-1} W_l^T                               M = 128 rows, N = out_l, K = in_l
 //   reverse   dA_{l-1} = dZ_l W_l                                M = 128 rows, N = in_l,  K = out_l
-//   gradient  [dW_l | . . db_l] += dZ_l^T [A_{l-1} | E_{l-1}]    M = out_l, N = in_l + 16, K = 128 rows
-//             (l = 2, 3);  dW_4^T += A_3^T dZ_4                   M = in_4,  N = out_4,     K = 128 rows
-//             [. . db_4] += dZ_4^T E_1                            M = 64,    N = 16,        K = 128 rows
-//             [dW_1 | db_1] += dZ_1^T E_1                         M = 64,    N = 16,        K = 128 rows
-// E_1, the 16 columns after A1's features, holds per row (x^, y^, 1) on value rows, (1, 0, 0) on
+//   gradient  [. . db_2 | dW_2] += dZ_2^T [E_1 | A_1]            M = out_2, N = 16 + in_2, K = 128 rows
+//             [dW_3 | . . db_3] += dZ_3^T [A_2 | E_2]            M = out_3, N = in_3 + 16, K = 128 rows
+//             dW_4^T += A_3^T dZ_4                                M = in_4,  N = out_4,     K = 128 rows
+//             [dW_1 | db_1 ; . . db_4] += [dZ_1 | dZ_4]^T E_1     M = 64 + 64, N = 16,      K = 128 rows
+// E_1, 16 columns stored just before A1, holds per row (x^, y^, 1) on value rows, (1, 0, 0) on
 // d/dx^ rows and (0, 1, 0) on d/dy^ rows, zeros elsewhere, so that dZ_1^T E_1 gives the layer-1
 // gradient (columns 0 and 1: the sums of dz_v x^ + dz_x and dz_v y^ + dz_y; column 2: of dz_v);
 // its column 2, the value-row indicator, gives the bias gradients of the layers above.  E_2, the 16
-// columns after A2's features, holds the indicator in its column 2 as well.  The last two rows
-// take M = 128 MMAs whose A operand runs on past the 64 rows that matter into the next buffer's
-// bytes; those rows of D are never read.  Everything accumulates in TMEM over the
-// CTA's tiles and is written once; layer 5 goes to the CTA's partial slice per tile, as in the
-// FP32 kernel.
+// columns after A2's features, holds the indicator in its column 2 as well.  A4 (holding dZ_4 by
+// then) is stored right after A1, so that the last row is one M = 128 MMA.  Everything
+// accumulates in TMEM over the CTA's tiles and is written once; layer 5 goes to the CTA's
+// partial slice per tile, as in the FP32 kernel.
 namespace ttc {
 constexpr int THREADS = 512;                       // four warps per TMEM lane quadrant
 constexpr int NH = THREADS / 128;                  // warps per quadrant: warp w takes the column
 constexpr int CS = 16 * NH;                        // chunks 16 (w / 4) + CS i of 16 columns
 constexpr int SPT = 40;                            // samples per tile
 constexpr int COLB = 128 * 2;                      // bytes of one feature of a 128-row BF16 operand
-constexpr int OFF_A1 = 0, OFF_E1 = OFF_A1 + 64 * COLB, OFF_A2 = OFF_E1 + 16 * COLB, OFF_E2 = OFF_A2 + 128 * COLB,
-              OFF_A3 = OFF_E2 + 16 * COLB, OFF_A4 = OFF_A3 + 128 * COLB, OFF_W2 = OFF_A4 + 64 * COLB,
+constexpr int OFF_E1 = 0, OFF_A1 = OFF_E1 + 16 * COLB, OFF_A4 = OFF_A1 + 64 * COLB, OFF_A2 = OFF_A4 + 64 * COLB,
+              OFF_E2 = OFF_A2 + 128 * COLB, OFF_A3 = OFF_E2 + 16 * COLB, OFF_W2 = OFF_A3 + 128 * COLB,
               OFF_W3 = OFF_W2 + 128 * 64 * 2, OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_SC = OFF_W4 + 64 * 128 * 2;
 // FP32 scratch: dL/d(outputs) per row [128][4]; the layer-5 partial sums of the warps with
 // w / 4 > 0 [NH - 1][128][4]; the layer-5 gradient partials [8][GP_LD] (lane l's 24 at l * 25)
@@ -647,18 +646,19 @@ constexpr int GP_LD = 32 * 25 + 8;                 // 808 = 8 mod 32: the fold r
 constexpr int OFF_S5 = OFF_SC, OFF_X = OFF_S5 + 128 * 4 * 4, OFF_GP = OFF_X + (NH - 1) * 128 * 4 * 4,
               OFF_PAR = OFF_GP + 8 * GP_LD * 4, OFF_BAR = OFF_PAR + 704 * 4, OFF_SLOT = OFF_BAR + 16,
               SMEM = OFF_SLOT + 16;
-// FP32 parameters kept in shared memory (floats from OFF_PAR): b1, b2, b3, b4, W5, W1
+// FP32 parameters kept in shared memory (floats from OFF_PAR): b1, b2, b3, b4, W5, then W1 by
+// column (W1[k][0] at PW1 + k, W1[k][1] at PW1 + 64 + k)
 constexpr int PB1 = 0, PB2 = 64, PB3 = 192, PB4 = 320, PW5 = 384, PW1 = 576, NPAR = 704;
 static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 static_assert(OFF_PAR % 16 == 0 && OFF_W2 % 16 == 0, "16-byte aligned regions");
-static_assert(OFF_A1 + 16 * 2048 <= OFF_E2 && OFF_A4 + 16 * 2048 <= OFF_SC,
-              "the M = 128 operands read from A1 and A4 stay inside the operand regions");
+static_assert(OFF_A1 == OFF_E1 + 2 * 2048 && OFF_A4 == OFF_A1 + 8 * 2048 && OFF_E2 == OFF_A2 + 16 * 2048,
+              "operands read as one: [E1 | A1], [A1 | A4], [A2 | E2]");
 constexpr int WIMG_BYTES = (128 * 64 + 128 * 128 + 64 * 128) * 2;   // W2, W3, W4 at the head of the image
-// TMEM columns (each accumulator 32-column aligned): work 128, [dW2 | db2] 80, [dW3 | db3] 144,
-// dW4^T 64, [dW1 | db1] 16, db4 16
-constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 224, TM_DW4T = 384, TM_D1 = 448, TM_B4 = 480, TM_COLS = 512;
-static_assert(TM_DW2 + 80 <= TM_DW3 && TM_DW3 + 144 <= TM_DW4T && TM_DW4T + 64 <= TM_D1 && TM_D1 + 16 <= TM_B4 &&
-              TM_B4 + 16 <= TM_COLS, "TMEM columns");
+// TMEM columns (each accumulator 32-column aligned): work 128, [db2 | dW2] 80, [dW3 | db3] 144,
+// dW4^T 64, [dW1 | db1 ; db4] 16
+constexpr uint32_t TM_WORK = 0, TM_DW2 = 128, TM_DW3 = 224, TM_DW4T = 384, TM_D1 = 448, TM_COLS = 512;
+static_assert(TM_DW2 + 80 <= TM_DW3 && TM_DW3 + 144 <= TM_DW4T && TM_DW4T + 64 <= TM_D1 && TM_D1 + 16 <= TM_COLS,
+              "TMEM columns");
 constexpr uint32_t KLBO = 2048;                    // K-major 128-row operand: core matrices along K
 
 // D (+)= A B over K in steps of 16 (each operand: base address, leading and stride byte
@@ -693,38 +693,85 @@ __device__ __forceinline__ void load8(const uint8_t* A, int r, int k0, float (&v
     }
 }
 
-// Row roles of thread r.
+// Packed FP32 pairs: one sm_100-family f32x2 instruction per operation on both halves (the same
+// IEEE rounding as the scalar operation on each).
+__device__ __forceinline__ unsigned long long pk(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// Row roles of thread r; kv = 1 on value rows, kt = 1 on tangent rows (both 0 on padding rows).
 struct Row {
     int r, lane, warp, c;
     bool pad;
+    float kv, kt;
 };
 
 // Forward epilogue of a hidden layer from 16 pre-activations z (bias added on value rows):
 // value rows a = tanh(z), tangent rows (1 - a^2) z with a of their sample; out = FP32 values.
-__device__ __forceinline__ void act16(const Row& R, const float* __restrict__ b, int c0, float (&z)[16],
+__device__ __forceinline__ void act16(const Row& R, const float* __restrict__ b, int c0, const float (&z)[16],
                                       float (&out)[16]) {
+    const float2 kv = bc2(R.kv), kt = bc2(R.kt), one = bc2(1.0f);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const float zz = R.c == 0 ? z[j] + b[c0 + j] : z[j];
-        const float a = tc::tanh_fast(zz);
-        const float sv = __shfl_sync(0xffffffffu, 1.0f - a * a, R.lane - R.c);
-        out[j] = R.pad ? 0.0f : (R.c == 0 ? a : sv * zz);
+    for (int j = 0; j < 16; j += 2) {
+        const float2 zz = fma2(kv, ld2(b + c0 + j), make_float2(z[j], z[j + 1]));
+        const float2 a = make_float2(tc::tanh_fast(zz.x), tc::tanh_fast(zz.y));
+        const float2 sg = sub2(one, mul2(a, a));
+        const float2 sv = make_float2(__shfl_sync(0xffffffffu, sg.x, R.lane - R.c),
+                                      __shfl_sync(0xffffffffu, sg.y, R.lane - R.c));
+        const float2 o = fma2(kt, mul2(sv, zz), mul2(kv, a));
+        out[j] = o.x;
+        out[j + 1] = o.y;
     }
 }
 
 // Reverse pass through a hidden activation for 16 features: dA (this row's dL/d act) -> dL/dz.
-// act / av / ax / ay: the stored activations of this row, of its sample's value row and of the
-// sample's two tangent rows (read from shared memory).  Value rows: s dA - 2 a (a_x dA_x +
-// a_y dA_y); tangent rows: s dA_d, s = 1 - a^2 of their sample; dA_x, dA_y come from the
-// neighbouring lanes.
+// av / own: the stored activations of the sample's value row and of this row.  Value rows:
+// s dA - 2 a (a_x dA_x + a_y dA_y); tangent rows: s dA_d; s = 1 - a^2 of the sample.  Each
+// tangent row forms its product a_d dA_d, which the value row takes from the next two lanes.
 __device__ __forceinline__ void dact16(const Row& R, const float (&dA)[16], const float (&av)[16],
-                                       const float (&ax)[16], const float (&ay)[16], float (&dz)[16]) {
+                                       const float (&own)[16], float (&dz)[16]) {
+    const float2 m = bc2(-2.0f * R.kv), one = bc2(1.0f);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        const float dx = __shfl_sync(0xffffffffu, dA[j], R.lane + 1);
-        const float dy = __shfl_sync(0xffffffffu, dA[j], R.lane + 2);
-        const float a = av[j], sg = 1.0f - a * a;
-        dz[j] = R.pad ? 0.0f : (R.c == 0 ? sg * dA[j] - 2.0f * a * (ax[j] * dx + ay[j] * dy) : sg * dA[j]);
+    for (int j = 0; j < 16; j += 2) {
+        const float2 d = make_float2(dA[j], dA[j + 1]), a = make_float2(av[j], av[j + 1]);
+        const float2 p = mul2(make_float2(own[j], own[j + 1]), d);
+        const float2 px = make_float2(__shfl_sync(0xffffffffu, p.x, R.lane + 1),
+                                      __shfl_sync(0xffffffffu, p.y, R.lane + 1));
+        const float2 py = make_float2(__shfl_sync(0xffffffffu, p.x, R.lane + 2),
+                                      __shfl_sync(0xffffffffu, p.y, R.lane + 2));
+        const float2 sg = sub2(one, mul2(a, a));
+        const float2 o = fma2(mul2(m, a), add2(px, py), mul2(sg, d));
+        dz[j] = o.x;
+        dz[j + 1] = o.y;
     }
 }
 
@@ -739,15 +786,11 @@ __device__ __forceinline__ void load16(const uint8_t* A, int r, int c0, float (&
     for (int j = 0; j < 8; ++j) v[8 + j] = t[j];
 }
 
-// The value-row and tangent-row activations of this row's sample.  Every row read lies in the
-// warp's own quadrant (the padding lanes' reads are clamped to it), so that a warp may overwrite
-// its rows' chunk in place.
-__device__ __forceinline__ void sample_acts(const Row& R, const uint8_t* A, int c0, float (&av)[16], float (&ax)[16],
-                                            float (&ay)[16]) {
-    const int rv = R.r - R.c, top = R.r | 31;
-    load16(A, rv, c0, av);
-    load16(A, rv + 1 < top ? rv + 1 : top, c0, ax);
-    load16(A, rv + 2 < top ? rv + 2 : top, c0, ay);
+// The activations of this row's sample's value row and of this row (both in the warp's own
+// quadrant, so that a warp may overwrite its rows' chunk in place).
+__device__ __forceinline__ void sample_acts(const Row& R, const uint8_t* A, int c0, float (&av)[16], float (&own)[16]) {
+    load16(A, R.r - R.c, c0, av);
+    load16(A, R.r, c0, own);
 }
 
 __device__ __forceinline__ void store16(uint8_t* A, int r, int c0, const float (&v)[16]) {
@@ -771,15 +814,18 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     R.r = 32 * R.warp + R.lane;
     R.c = R.lane % 3;
     R.pad = R.lane >= 30;
+    R.kv = (!R.pad && R.c == 0) ? 1.0f : 0.0f;
+    R.kt = (!R.pad && R.c != 0) ? 1.0f : 0.0f;
     const int q = R.lane / 3;
-    uint8_t *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
+    uint8_t *E1 = sm + OFF_E1, *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
     float* X = reinterpret_cast<float*>(sm + OFF_X);
     float* GP = reinterpret_cast<float*>(sm + OFF_GP);
     float* PAR = reinterpret_cast<float*>(sm + OFF_PAR);
     for (int i = tid; i < NPAR; i += THREADS)
         PAR[i] = i < PB2 ? w[OB1 + i] : (i < PB3 ? w[OB2 + i - PB2] : (i < PB4 ? w[OB3 + i - PB3] :
-                 (i < PW5 ? w[OB4 + i - PB4] : (i < PW1 ? w[OW5 + i - PW5] : w[OW1 + i - PW1]))));
+                 (i < PW5 ? w[OB4 + i - PB4] : (i < PW1 ? w[OW5 + i - PW5] :
+                 w[OW1 + 2 * ((i - PW1) % 64) + (i - PW1) / 64]))));
     if (h == 0) {   // E2: the value-row indicator in column 2 (the same for every tile)
         float e[16];
 #pragma unroll
@@ -825,9 +871,11 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     const float* jy = static_cast<const float*>(L.jy);
     const float* gf = static_cast<const float*>(L.g);
     float* P = part + (long long)blockIdx.x * PSTRIDE;
-    double ld = 0.0, lp = 0.0, li = 0.0;
-    const uint32_t sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3), sA4 = tc::saddr(A4),
-                   sE1 = tc::saddr(sm + OFF_E1), sW2 = tc::saddr(sm + OFF_W2), sW3 = tc::saddr(sm + OFF_W3),
+    // loss terms: FP32 per thread (a few dozen samples each), FP64 from the CTA reduction on
+    float ld = 0.0f, lp = 0.0f, li = 0.0f;
+    const float thr = __double2float_rd(L.threshold);   // g > thr, as in above()
+    const uint32_t sE1 = tc::saddr(E1), sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3),
+                   sA4 = tc::saddr(A4), sW2 = tc::saddr(sm + OFF_W2), sW3 = tc::saddr(sm + OFF_W3),
                    sW4 = tc::saddr(sm + OFF_W4);
 
     // operands written by the threads -> visible to the tensor core, then thread 0 issues
@@ -836,10 +884,10 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         tc::tc_before_sync();
         __syncthreads();
         tc::tc_after_sync();
+        return ok;
     };
-    // commit the issued MMAs and wait (bounded) for them; false on timeout
-    auto wait_mma = [&]() {
-        if (tid == 0) tc::mma_commit(bar_mma);
+    // wait (bounded) for the last commit to bar_mma; false on timeout
+    auto wait_issued = [&]() {
         pending = true;
         ok = __syncthreads_and(tc::mbar_wait(bar_mma, phase)) != 0;
         if (ok) {
@@ -848,6 +896,11 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         }
         tc::tc_after_sync();
         return ok;
+    };
+    // commit the issued MMAs and wait for them
+    auto wait_mma = [&]() {
+        if (tid == 0) tc::mma_commit(bar_mma);
+        return wait_issued();
     };
 
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -885,25 +938,28 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 e[1] = R.c == 0 ? yh : (R.c == 2 ? 1.0f : 0.0f);
                 e[2] = R.c == 0 ? 1.0f : 0.0f;
             }
-            store16(A1, R.r, 64, e);
+            store16(E1, R.r, 0, e);
         }
         // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
+        const float2 cx = bc2(R.c == 0 ? xh : (R.c == 1 ? 1.0f : 0.0f));   // value rows (x^, y^), tangent
+        const float2 cy = bc2(R.c == 0 ? yh : (R.c == 2 ? 1.0f : 0.0f));   // rows the unit vectors
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 64; c0 += CS) {
             float z[16], out[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float w0 = PAR[PW1 + 2 * (c0 + j)], w1 = PAR[PW1 + 2 * (c0 + j) + 1];
-                z[j] = R.c == 0 ? fmaf(xh, w0, yh * w1) : (R.c == 1 ? w0 : w1);
+            for (int j = 0; j < 16; j += 2) {
+                const float2 zz = fma2(cx, ld2(PAR + PW1 + c0 + j), mul2(cy, ld2(PAR + PW1 + 64 + c0 + j)));
+                z[j] = zz.x;
+                z[j + 1] = zz.y;
             }
             act16(R, PAR + PB1, c0, z, out);
             store16(A1, R.r, c0, out);
         }
         // ---- layers 2-4: MMA, then the activation epilogue (layer 4 also feeds layer 5)
-        float o[3] = {0.0f, 0.0f, 0.0f};
+        float2 o2[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
 #pragma unroll 1
         for (int layer = 2; layer <= 4 && ok; ++layer) {
-            sync_to_mma();
+            if (!sync_to_mma()) break;
             const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
             const uint32_t a = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);
             const uint32_t b = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
@@ -921,15 +977,16 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 store16(dst, R.r, c0, out);
                 if (layer == 4) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        o[0] = fmaf(PAR[PW5 + c0 + j], out[j], o[0]);
-                        o[1] = fmaf(PAR[PW5 + 64 + c0 + j], out[j], o[1]);
-                        o[2] = fmaf(PAR[PW5 + 128 + c0 + j], out[j], o[2]);
+                    for (int j = 0; j < 16; j += 2) {
+                        const float2 v = make_float2(out[j], out[j + 1]);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) o2[k] = fma2(ld2(PAR + PW5 + 64 * k + c0 + j), v, o2[k]);
                     }
                 }
             }
         }
         if (!ok) break;
+        float o[3] = {o2[0].x + o2[0].y, o2[1].x + o2[1].y, o2[2].x + o2[2].y};
         // ---- layer 5: the column groups' partial sums (added in group order), the output and
         // the loss (value lanes of group 0), dL/d(outputs) per row into S5
         if (h > 0)
@@ -949,7 +1006,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             float g[3] = {0.0f, 0.0f, 0.0f}, gx[3] = {0.0f, 0.0f, 0.0f}, gy[3] = {0.0f, 0.0f, 0.0f};
             if (valid && R.c == 0) {
                 const float t[3] = {t_rho, t_jx / t_rho, t_jy / t_rho};
-                const bool iface = above(t_g, L.threshold);
+                const bool iface = t_g > thr;
                 const SampleLoss<float> sl = sample_loss<float>(ov, oxv, oyv, t, iface, sx, sy, inv_n, c_phys, c_int, L, hp);
                 ld += sl.ld;
                 lp += sl.lp;
@@ -1012,29 +1069,33 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 over A4
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 64; c0 += CS) {
-            float dA[16], av[16], ax[16], ay[16], dz[16];
+            float dA[16], av[16], own[16], dz[16];
+            sample_acts(R, A4, c0, av, own);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                dA[j] = d5[0] * PAR[PW5 + c0 + j] + d5[1] * PAR[PW5 + 64 + c0 + j] + d5[2] * PAR[PW5 + 128 + c0 + j];
-            sample_acts(R, A4, c0, av, ax, ay);
-            dact16(R, dA, av, ax, ay, dz);
+            for (int j = 0; j < 16; j += 2) {
+                const float2 t = fma2(bc2(d5[2]), ld2(PAR + PW5 + 128 + c0 + j),
+                                      fma2(bc2(d5[1]), ld2(PAR + PW5 + 64 + c0 + j),
+                                           mul2(bc2(d5[0]), ld2(PAR + PW5 + c0 + j))));
+                dA[j] = t.x;
+                dA[j + 1] = t.y;
+            }
+            dact16(R, dA, av, own, dz);
             store16(A4, R.r, c0, dz);
         }
         // ---- reverse MMAs of layers 4, 3, 2 (with the gradients) and their epilogues
 #pragma unroll 1
         for (int layer = 4; layer >= 2 && ok; --layer) {
-            sync_to_mma();
+            if (!sync_to_mma()) break;
             const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
             const uint32_t dz = layer == 4 ? sA4 : (layer == 3 ? sA3 : sA2);   // dZ_l, over A_l
             const uint32_t wl = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
-            const uint32_t ain = layer == 2 ? sA1 : (layer == 3 ? sA2 : sA3);   // A_{l-1} (and E_{l-1})
             if (tid == 0) {
-                if (layer == 4) {
-                    mma_rows(tmem + TM_DW4T, sA3, dz, 64, !first);   // dW4^T += A3^T dZ4
-                    mma_rows(tmem + TM_B4, dz, sE1, 16, !first);     // column 2: db4 += dZ4^T 1_v
-                } else {                                              // [dW_l | db_l] += dZ_l^T [A_{l-1} | E_{l-1}]
-                    mma_rows(tmem + (layer == 3 ? TM_DW3 : TM_DW2), dz, ain, Kin + 16, !first);
-                }
+                if (layer == 4)        // dW4^T += A3^T dZ4
+                    mma_rows(tmem + TM_DW4T, sA3, dz, 64, !first);
+                else if (layer == 3)   // [dW3 | db3] += dZ3^T [A2 | E2]
+                    mma_rows(tmem + TM_DW3, dz, sA2, 144, !first);
+                else                   // [db2 | dW2] += dZ2^T [E1 | A1]
+                    mma_rows(tmem + TM_DW2, dz, sE1, 80, !first);
                 // dA_{l-1} = dZ_l W_l: A = dZ_l K-major (K = out), B = W_l MN-major (K = out, N = in)
                 mma_chain(tmem + TM_WORK, dz, KLBO, 128, 2 * KLBO, false, wl, 128, (uint32_t)(Nout / 8) * 128, 256,
                           true, Kin, Nout, false);
@@ -1043,32 +1104,34 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
 #pragma unroll 1
             for (int c0 = 16 * h; c0 < Kin; c0 += CS) {
-                float dA[16], av[16], ax[16], ay[16], dzv[16];
-                sample_acts(R, Aact, c0, av, ax, ay);   // in flight during the TMEM load
+                float dA[16], av[16], own[16], dzv[16];
+                sample_acts(R, Aact, c0, av, own);   // in flight during the TMEM load
                 tc::tmem_ld16(tmem + lane_off + TM_WORK + c0, dA);
-                dact16(R, dA, av, ax, ay, dzv);
+                dact16(R, dA, av, own, dzv);
                 store16(Aact, R.r, c0, dzv);           // dZ_{l-1} over A_{l-1}
             }
         }
         if (!ok) break;
-        // ---- layer-1 gradient: [dW1 | db1] += dZ1^T E1; complete before the next tile rewrites A1
-        sync_to_mma();
+        // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1, complete
+        // before the next tile rewrites E1 and A1
+        if (!sync_to_mma()) break;
         if (tid == 0) mma_rows(tmem + TM_D1, sA1, sE1, 16, !first);
         if (!wait_mma()) break;
     }
     if (ok) {
-        // the gradients accumulated in TMEM: rows of [dW2 | db2], [dW3 | db3] and dW4^T; rows < 64
-        // of [dW1 | db1] and of db4 (column 2)
+        // the gradients accumulated in TMEM: rows of [db2 | dW2], [dW3 | db3] and dW4^T; rows < 64
+        // of [dW1 | db1], rows >= 64 of db4 (column 2)
         tc::tc_after_sync();
         float v[16];
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 80; c0 += CS) {
             tc::tmem_ld16(tmem + lane_off + TM_DW2 + c0, v);
-            if (c0 < 64) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) P[OW2 + R.r * 64 + c0 + j] = v[j];
-            } else {
+            if (c0 == 0) {
                 P[OB2 + R.r] = v[2];
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4*>(P + OW2 + R.r * 64 + c0 - 16 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             }
         }
 #pragma unroll 1
@@ -1076,7 +1139,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             tc::tmem_ld16(tmem + lane_off + TM_DW3 + c0, v);
             if (c0 < 128) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) P[OW3 + R.r * 128 + c0 + j] = v[j];
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4*>(P + OW3 + R.r * 128 + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             } else {
                 P[OB3 + R.r] = v[2];
             }
@@ -1093,20 +1157,29 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 P[OW1 + 2 * R.r] = v[0];
                 P[OW1 + 2 * R.r + 1] = v[1];
                 P[OB1 + R.r] = v[2];
+            } else {
+                P[OB4 + R.r - 64] = v[2];
             }
-            tc::tmem_ld16(tmem + lane_off + TM_B4, v);
-            if (R.r < 64) P[OB4 + R.r] = v[2];
         }
     } else {
-        if (tid == 0) atomicOr(err, 1u);
-        if (pending) (void)tc::mbar_wait(bar_mma, phase);   // MMAs in flight finish before TMEM is freed
+        // MMAs in flight finish before TMEM is freed (bounded waits, as everywhere): a fresh
+        // commit covers every MMA issued; an unobserved earlier commit completes the phase before
+        if (tid == 0) {
+            atomicOr(err, 1u);
+            tc::mma_commit(bar_mma);
+        }
+        if (pending) {
+            (void)tc::mbar_wait(bar_mma, phase);
+            phase ^= 1;
+        }
+        (void)tc::mbar_wait(bar_mma, phase);
     }
     tc::tc_before_sync();
     __syncthreads();
     tc::tc_after_sync();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
-    double v[3] = {ld, lp, li};
+    double v[3] = {(double)ld, (double)lp, (double)li};
     const int op[3] = {0, 0, 0};
     block_reduce<3>(v, op, reinterpret_cast<double*>(sm + OFF_SC));
     if (tid == 0)
