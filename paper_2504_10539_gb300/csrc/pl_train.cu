@@ -929,6 +929,25 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         const float xh = 2.0f * ((float)x + 0.5f) / (float)L.nx - 1.0f;
         const float yh = 2.0f * ((float)y + 0.5f) / (float)L.ny - 1.0f;
 
+        // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns;
+        // this warp's chunk (64 = CS columns: one) in registers first
+        static_assert(CS == 64, "layer 1: one 16-column chunk per warp");
+        const int c1 = 16 * h;
+        const float2 cx = bc2(R.c == 0 ? xh : (R.c == 1 ? 1.0f : 0.0f));   // value rows (x^, y^), tangent
+        const float2 cy = bc2(R.c == 0 ? yh : (R.c == 2 ? 1.0f : 0.0f));   // rows the unit vectors
+        float a1[16];
+        {
+            float z[16];
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+                const float2 zz = fma2(cx, ld2(PAR + PW1 + c1 + j), mul2(cy, ld2(PAR + PW1 + 64 + c1 + j)));
+                z[j] = zz.x;
+                z[j + 1] = zz.y;
+            }
+            act16(R, PAR + PB1, c1, z, a1);
+        }
+        // the previous tile's gradient MMA reads E1 and A1: complete before they are rewritten
+        if (pending && !wait_issued()) break;
         if (h == 0) {   // E1 of this row (samples past the lattice end have dZ = 0: any finite entry)
             float e[16];
 #pragma unroll
@@ -940,21 +959,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             }
             store16(E1, R.r, 0, e);
         }
-        // ---- layer 1 (2 -> 64) on CUDA cores: value rows from (x^, y^), tangent rows W1's columns
-        const float2 cx = bc2(R.c == 0 ? xh : (R.c == 1 ? 1.0f : 0.0f));   // value rows (x^, y^), tangent
-        const float2 cy = bc2(R.c == 0 ? yh : (R.c == 2 ? 1.0f : 0.0f));   // rows the unit vectors
-#pragma unroll 1
-        for (int c0 = 16 * h; c0 < 64; c0 += CS) {
-            float z[16], out[16];
-#pragma unroll
-            for (int j = 0; j < 16; j += 2) {
-                const float2 zz = fma2(cx, ld2(PAR + PW1 + c0 + j), mul2(cy, ld2(PAR + PW1 + 64 + c0 + j)));
-                z[j] = zz.x;
-                z[j + 1] = zz.y;
-            }
-            act16(R, PAR + PB1, c0, z, out);
-            store16(A1, R.r, c0, out);
-        }
+        store16(A1, R.r, c1, a1);
         // ---- layers 2-4: MMA, then the activation epilogue (layer 4 also feeds layer 5)
         float2 o2[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
 #pragma unroll 1
@@ -1052,20 +1057,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
 #pragma unroll
                 for (int e = 0; e < 8; ++e) GP[warp * GP_LD + R.lane * 25 + oo * 8 + e] = acc[oo][e];
         }
-        __syncthreads();
-        if (tid < 192) {
-            const int oo = tid / 64, k = tid % 64;
-            const float* g = GP + (k / 8) * GP_LD + oo * 8 + k % 8;
-            float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int l = 0; l < 32; ++l) a4[l & 3] += g[l * 25];
-            acc1(P + OW5 + tid, (a4[0] + a4[1]) + (a4[2] + a4[3]), first);
-        } else if (tid < 195) {   // value rows: lanes 0, 3, ..., 27 of each quadrant
-            const int oo = tid - 192;
-            float acc = 0.0f;
-            for (int wq = 0; wq < 40; ++wq) acc += S5[(32 * (wq / 10) + 3 * (wq % 10)) * 4 + oo];
-            acc1(P + OB5 + oo, acc, first);
-        }
+        __syncthreads();   // GP complete; folded during the reverse layer-4 MMAs
         // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 over A4
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 64; c0 += CS) {
@@ -1083,6 +1075,23 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             store16(A4, R.r, c0, dz);
         }
         // ---- reverse MMAs of layers 4, 3, 2 (with the gradients) and their epilogues
+        auto fold5 = [&]() {   // dW5 (GP, in lane order) and db5 (S5) into the slice
+            if (tid < 192) {
+                const int oo = tid / 64, k = tid % 64;
+                const float* g = GP + (k / 8) * GP_LD + oo * 8 + k % 8;
+                float a4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int l = 0; l < 32; ++l) a4[l & 3] += g[l * 25];
+                acc1(P + OW5 + tid, (a4[0] + a4[1]) + (a4[2] + a4[3]), first);
+            } else if (warp >= 8 && warp < 11) {   // db5[o], warp 8 + o: the 40 value rows (lanes 0,
+                const int oo = warp - 8;             // 3, ..., 27 of each quadrant), butterfly over lanes
+                float a = 0.0f;
+                for (int wq = R.lane; wq < 40; wq += 32) a += S5[(32 * (wq / 10) + 3 * (wq % 10)) * 4 + oo];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (R.lane == 0) acc1(P + OB5 + oo, a, first);
+            }
+        };
 #pragma unroll 1
         for (int layer = 4; layer >= 2 && ok; --layer) {
             if (!sync_to_mma()) break;
@@ -1100,6 +1109,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 mma_chain(tmem + TM_WORK, dz, KLBO, 128, 2 * KLBO, false, wl, 128, (uint32_t)(Nout / 8) * 128, 256,
                           true, Kin, Nout, false);
             }
+            if (layer == 4) fold5();  // CUDA-core work of the previous step, while the MMAs run
             if (!wait_mma()) break;   // all of them: the epilogue overwrites A_{l-1}
             uint8_t* Aact = layer == 2 ? A1 : (layer == 3 ? A2 : A3);
 #pragma unroll 1
@@ -1112,12 +1122,16 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             }
         }
         if (!ok) break;
-        // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1, complete
-        // before the next tile rewrites E1 and A1
+        // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1, committed
+        // here and waited for by the next tile before it rewrites E1 and A1
         if (!sync_to_mma()) break;
-        if (tid == 0) mma_rows(tmem + TM_D1, sA1, sE1, 16, !first);
-        if (!wait_mma()) break;
+        if (tid == 0) {
+            mma_rows(tmem + TM_D1, sA1, sE1, 16, !first);
+            tc::mma_commit(bar_mma);
+        }
+        pending = true;
     }
+    if (ok && pending) ok = wait_issued();   // the last tile's gradient MMA
     if (ok) {
         // the gradients accumulated in TMEM: rows of [db2 | dW2], [dW3 | db3] and dW4^T; rows < 64
         // of [dW1 | db1], rows >= 64 of db4 (column 2)
