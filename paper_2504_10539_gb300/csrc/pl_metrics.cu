@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "pl_device.cuh"
 #include "pl_kernels.h"
@@ -38,6 +39,56 @@ __device__ __forceinline__ int find_blk(const int* __restrict__ pre, int n, int 
         else hi = mid;
     }
     return lo;
+}
+
+// Block reduction of FP32 partials (FP32 and FP16-offset lattices).  The FP64 pipe of this part
+// runs at a small fraction of the FP32 rate, so the per-block tree stays in FP32: a sum as an
+// unevaluated pair hi + lo merged by an error-free TwoSum (about 2^-48 relative), an extremum or
+// a count (an integer below 2^24, so exact) directly; thread 0 converts the results to FP64.
+// Fixed tree, as in block_reduce: the result depends on the block's values alone.
+__device__ __forceinline__ void ff_merge(float& hi, float& lo, float bhi, float blo) {
+    const float s = __fadd_rn(hi, bhi);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bhi, bb));
+    hi = s;
+    lo = __fadd_rn(__fadd_rn(lo, blo), e);
+}
+template <int NV>
+__device__ __forceinline__ void ff_level(float (&hi)[NV], float (&lo)[NV], const int (&op)[NV], int o) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const float bh = __shfl_down_sync(0xffffffffu, hi[k], o);
+        const float bl = __shfl_down_sync(0xffffffffu, lo[k], o);
+        if (op[k] == 0) ff_merge(hi[k], lo[k], bh, bl);
+        else hi[k] = op[k] == 1 ? fmaxf(hi[k], bh) : fminf(hi[k], bh);
+    }
+}
+// op: 0 = sum, 1 = max, 2 = min (lo unused).  out valid in thread 0; smem: 2 NV x 32 floats.
+template <int NV>
+__device__ __forceinline__ void block_reduce_ff(float (&hi)[NV], float (&lo)[NV], const int (&op)[NV], float* smem,
+                                                double (&out)[NV]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ff_level<NV>(hi, lo, op, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < NV; ++k) {
+            smem[k * 32 + warp] = hi[k];
+            smem[(NV + k) * 32 + warp] = lo[k];
+        }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float init = op[k] == 0 ? 0.0f : (op[k] == 1 ? -INFINITY : INFINITY);
+            hi[k] = lane < nw ? smem[k * 32 + lane] : init;
+            lo[k] = lane < nw ? smem[(NV + k) * 32 + lane] : 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ff_level<NV>(hi, lo, op, o);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = op[k] == 0 ? (double)hi[k] + (double)lo[k] : (double)hi[k];
+    }
+    __syncthreads();
 }
 
 // Virtual block vb of the table -> lattice j, local block lb.
@@ -240,8 +291,14 @@ __global__ void __launch_bounds__(RB_THREADS) k_grad_tab(TableView t) {
             grad_accumulate(rho, d.nx, d.ny, it.c, it.x, it.y, static_cast<R*>(d.g), thr, a);
         double v[8];
         const int op[8] = {0, 1, 0, 0, 1, 2, 0, 0};
-        a.to(v);
-        block_reduce<8>(v, op, sm);
+        if constexpr (std::is_same<R, float>::value) {
+            float hi[8] = {a.mass.hi, a.gmax, a.sum_g.hi, a.sum_g2.hi, a.rmax, a.rmin, (float)a.count, (float)a.bad};
+            float lo[8] = {a.mass.lo, 0.0f, a.sum_g.lo, a.sum_g2.lo, 0.0f, 0.0f, 0.0f, 0.0f};
+            block_reduce_ff<8>(hi, lo, op, reinterpret_cast<float*>(sm), v);
+        } else {
+            a.to(v);
+            block_reduce<8>(v, op, sm);
+        }
         if (threadIdx.x == 0)
             for (int k = 0; k < 8; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
@@ -317,8 +374,16 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
                 ++out_n;
             }
         }
-        double v[6] = {in_rho.value(), in_p.value(), (double)in_n, out_rho.value(), out_p.value(), (double)out_n};
-        block_reduce<6>(v, op, sm);
+        double v[6];
+        if constexpr (std::is_same<R, float>::value) {
+            float hi[6] = {in_rho.hi, in_p.hi, (float)in_n, out_rho.hi, out_p.hi, (float)out_n};
+            float lo[6] = {in_rho.lo, in_p.lo, 0.0f, out_rho.lo, out_p.lo, 0.0f};
+            block_reduce_ff<6>(hi, lo, op, reinterpret_cast<float*>(sm), v);
+        } else {
+            v[0] = in_rho.value(), v[1] = in_p.value(), v[2] = (double)in_n;
+            v[3] = out_rho.value(), v[4] = out_p.value(), v[5] = (double)out_n;
+            block_reduce<6>(v, op, sm);
+        }
         if (threadIdx.x == 0)
             for (int k = 0; k < 6; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
@@ -403,8 +468,14 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
             sm_dr.add(beta_rho * mm * (out3[c] - r));
             sm_rho.add(r);
         }
-        double v[3] = {sm_m.value(), sm_dr.value(), sm_rho.value()};
-        block_reduce<3>(v, op, sm);
+        double v[3];
+        if constexpr (std::is_same<R, float>::value) {
+            float hi[3] = {sm_m.hi, sm_dr.hi, sm_rho.hi}, lo[3] = {sm_m.lo, sm_dr.lo, sm_rho.lo};
+            block_reduce_ff<3>(hi, lo, op, reinterpret_cast<float*>(sm), v);
+        } else {
+            v[0] = sm_m.value(), v[1] = sm_dr.value(), v[2] = sm_rho.value();
+            block_reduce<3>(v, op, sm);
+        }
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
@@ -499,8 +570,14 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(TableView t) {
                 reject = reject || !ok;
             }
         }
-        double v[3] = {s_jx.value(), s_jy.value(), reject ? 1.0 : 0.0};
-        block_reduce<3>(v, op, sm);
+        double v[3];
+        if constexpr (std::is_same<R, float>::value) {
+            float hi[3] = {s_jx.hi, s_jy.hi, reject ? 1.0f : 0.0f}, lo[3] = {s_jx.lo, s_jy.lo, 0.0f};
+            block_reduce_ff<3>(hi, lo, op, reinterpret_cast<float*>(sm), v);
+        } else {
+            v[0] = s_jx.value(), v[1] = s_jy.value(), v[2] = reject ? 1.0 : 0.0;
+            block_reduce<3>(v, op, sm);
+        }
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) d.partials[m.lb * PARTIAL_STRIDE + k] = v[k];
     }
@@ -559,7 +636,7 @@ __device__ __forceinline__ bool fix_candidate(__half h) {
 // error-free pair sums over cells) and the number of restoration candidates, into partial
 // slots 0 and 1, for the mass restoration that follows.
 template <int MODE>
-__global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 3 : 1) k_corr_apply(TableView t, int parity) {
+__global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_corr_apply(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
     const int n = t.hdr->n, total = t.hdr->total_blocks;
