@@ -293,15 +293,24 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const float bias[8] = {bA.x, bA.y, bA.z, bA.w, bB.x, bB.y, bB.z, bB.w};
             float h[8];
 #pragma unroll
-            for (int j = 0; j < 8; j += 2) {
+            for (int j = 0; j < 8; j += 2) {   // features j, j + 1 as one pair: W1 x^ + (W1 y^ + b)
                 const float4 w = w4[j >> 1];
-                h[j] = tanh_fast(fmaf(w.x, xh, fmaf(w.y, yh, bias[j])));
-                h[j + 1] = tanh_fast(fmaf(w.z, xh, fmaf(w.w, yh, bias[j + 1])));
+                const float2 z = fma2(make_float2(w.x, w.z), bc2(xh),
+                                      fma2(make_float2(w.y, w.w), bc2(yh), make_float2(bias[j], bias[j + 1])));
+                h[j] = tanh_fast(z.x);
+                h[j + 1] = tanh_fast(z.y);
             }
             store8(AX, t, k0, h);
         }
         // ---- layers 2..4: MMA, then epilogue
-        float o0 = P[P_B5 + 0], o1 = P[P_B5 + 1], o2 = P[P_B5 + 2];
+        // layer 5: per output two packed partial sums (features = 0 / 1 mod 2, and j mod 4 < 2 or
+        // not), added at the end: short dependency chains
+        float2 oa[3], ob[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            oa[k] = make_float2(P[P_B5 + k], 0.0f);
+            ob[k] = bc2(0.0f);
+        }
 #pragma unroll 1
         for (int layer = 2; layer <= 4 && ok; ++layer) {
             fence_async_smem();
@@ -333,25 +342,26 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
                     for (int q = 0; q < 2; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
                 } else {
-                    const float4* u0 = reinterpret_cast<const float4*>(P + P_W5 + 0 * 64 + c0);
-                    const float4* u1 = reinterpret_cast<const float4*>(P + P_W5 + 1 * 64 + c0);
-                    const float4* u2 = reinterpret_cast<const float4*>(P + P_W5 + 2 * 64 + c0);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        const float4 a0 = u0[q], a1 = u1[q], a2 = u2[q];
-                        const float* v4 = v + 4 * q;
-                        o0 = fmaf(a0.w, v4[3], fmaf(a0.z, v4[2], fmaf(a0.y, v4[1], fmaf(a0.x, v4[0], o0))));
-                        o1 = fmaf(a1.w, v4[3], fmaf(a1.z, v4[2], fmaf(a1.y, v4[1], fmaf(a1.x, v4[0], o1))));
-                        o2 = fmaf(a2.w, v4[3], fmaf(a2.z, v4[2], fmaf(a2.y, v4[1], fmaf(a2.x, v4[0], o2))));
+                        const float2 va = make_float2(v[4 * q], v[4 * q + 1]), vb = make_float2(v[4 * q + 2], v[4 * q + 3]);
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float4 a = reinterpret_cast<const float4*>(P + P_W5 + k * 64 + c0)[q];
+                            oa[k] = fma2(make_float2(a.x, a.y), va, oa[k]);
+                            ob[k] = fma2(make_float2(a.z, a.w), vb, ob[k]);
+                        }
                     }
                 }
             }
         }
         if (!ok) break;
         if (c < N) {
-            out3[c] = o0;
-            out3[N + c] = o1;
-            out3[2 * N + c] = o2;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float2 s2 = add2(oa[k], ob[k]);
+                out3[k * N + c] = s2.x + s2.y;
+            }
         }
     }
     if (!ok) {
