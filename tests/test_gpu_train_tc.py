@@ -97,6 +97,20 @@ def test_tc_training_follows_oracle_and_full_size():
     assert loss[0] == pytest.approx(L, rel=1e-2)
 
 
+def test_tc_gradient_is_reproducible():
+    """The gradient is a fixed-order sum: TMEM accumulation over a CTA's tiles in tile order, one
+    writer per element of a CTA's slice, the slices folded in CTA order; two calls on the same
+    state give the same bits (also for a lattice whose last tile is partial)."""
+    for nx, ny in [(96, 80), (67, 35)]:
+        lat, job = droplet_lattice(nx, ny)
+        tr = B.Trainer(lat, max_epochs=2, mode=B.PL_TRAIN_TC)
+        g1, l1 = tr.gradient()
+        g2, l2 = tr.gradient()
+        assert np.array_equal(g1, g2) and np.array_equal(l1, l2), (nx, ny)
+        tr.close()
+        lat.close()
+
+
 def test_tc_coupled_run_and_mode_checks():
     job = wl.Lattice(64, 64, storage=B.PL_F16_OFFSET, mlp=B.PL_MLP_BF16, droplets=[(32.0, 32.0, 12.0)], seed=7, K=25,
                      weight_seed=43)
