@@ -616,7 +616,7 @@ cudaError_t grad_setup(int* grid) {
 // activation is stored once, K-major over its features: it is the A operand of the next forward
 // MMA and, read MN-major (K = rows), an operand of the gradient MMAs; the weight images serve the
 // forward MMAs K-major and the reverse MMAs MN-major (K = outputs).  In the reverse pass dZ_l
-// overwrites A_l once the MMAs that read A_l are complete.
+// (l = 3, 2, 1) overwrites A_l once the MMAs that read A_l are complete.
 //   forward   Z_l = A_{l-1} W_l^T                               M = 128 rows, N = out_l, K = in_l
 //   reverse   dA_{l-1} = dZ_l W_l                                M = 128 rows, N = in_l,  K = out_l
 //   gradient  [. . db_2 | dW_2] += dZ_2^T [E_1 | A_1]            M = out_2, N = 16 + in_2, K = 128 rows
@@ -627,8 +627,9 @@ cudaError_t grad_setup(int* grid) {
 // d/dx^ rows and (0, 1, 0) on d/dy^ rows, zeros elsewhere, so that dZ_1^T E_1 gives the layer-1
 // gradient (columns 0 and 1: the sums of dz_v x^ + dz_x and dz_v y^ + dz_y; column 2: of dz_v);
 // its column 2, the value-row indicator, gives the bias gradients of the layers above.  E_2, the 16
-// columns after A2's features, holds the indicator in its column 2 as well.  A4 (holding dZ_4 by
-// then) is stored right after A1, so that the last row is one M = 128 MMA.  Everything
+// columns after A2's features, holds the indicator in its column 2 as well.  dZ_4 has a buffer of
+// its own right after A1 (A4 stays readable for the layer-5 gradient meanwhile), so that the
+// last row is one M = 128 MMA.  Everything
 // accumulates in TMEM over the CTA's tiles and is written once; layer 5 goes to the CTA's
 // partial slice per tile, as in the FP32 kernel.
 namespace ttc {
@@ -637,7 +638,8 @@ constexpr int NH = THREADS / 128;                  // warps per quadrant: warp w
 constexpr int CS = 16 * NH;                        // chunks 16 (w / 4) + CS i of 16 columns
 constexpr int SPT = 40;                            // samples per tile
 constexpr int COLB = 128 * 2;                      // bytes of one feature of a 128-row BF16 operand
-constexpr int OFF_E1 = 0, OFF_A1 = OFF_E1 + 16 * COLB, OFF_A4 = OFF_A1 + 64 * COLB, OFF_A2 = OFF_A4 + 64 * COLB,
+constexpr int OFF_E1 = 0, OFF_A1 = OFF_E1 + 16 * COLB, OFF_DZ4 = OFF_A1 + 64 * COLB, OFF_A4 = OFF_DZ4 + 64 * COLB,
+              OFF_A2 = OFF_A4 + 64 * COLB,
               OFF_E2 = OFF_A2 + 128 * COLB, OFF_A3 = OFF_E2 + 16 * COLB, OFF_W2 = OFF_A3 + 128 * COLB,
               OFF_W3 = OFF_W2 + 128 * 64 * 2, OFF_W4 = OFF_W3 + 128 * 128 * 2, OFF_SC = OFF_W4 + 64 * 128 * 2;
 // FP32 scratch: dL/d(outputs) per row [128][4]; the layer-5 partial sums of the warps with
@@ -651,8 +653,8 @@ constexpr int OFF_S5 = OFF_SC, OFF_X = OFF_S5 + 128 * 4 * 4, OFF_GP = OFF_X + (N
 constexpr int PB1 = 0, PB2 = 64, PB3 = 192, PB4 = 320, PW5 = 384, PW1 = 576, NPAR = 704;
 static_assert(SMEM <= 227 * 1024, "shared memory of one CTA");
 static_assert(OFF_PAR % 16 == 0 && OFF_W2 % 16 == 0, "16-byte aligned regions");
-static_assert(OFF_A1 == OFF_E1 + 2 * 2048 && OFF_A4 == OFF_A1 + 8 * 2048 && OFF_E2 == OFF_A2 + 16 * 2048,
-              "operands read as one: [E1 | A1], [A1 | A4], [A2 | E2]");
+static_assert(OFF_A1 == OFF_E1 + 2 * 2048 && OFF_DZ4 == OFF_A1 + 8 * 2048 && OFF_E2 == OFF_A2 + 16 * 2048,
+              "operands read as one: [E1 | A1], [A1 | DZ4], [A2 | E2]");
 constexpr int WIMG_BYTES = (128 * 64 + 128 * 128 + 64 * 128) * 2;   // W2, W3, W4 at the head of the image
 // TMEM columns (each accumulator 32-column aligned): work 128, [db2 | dW2] 80, [dW3 | db3] 144,
 // dW4^T 64, [dW1 | db1 ; db4] 16
@@ -789,7 +791,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     R.kv = (!R.pad && R.c == 0) ? 1.0f : 0.0f;
     R.kt = (!R.pad && R.c != 0) ? 1.0f : 0.0f;
     const int q = R.lane / 3;
-    uint8_t *E1 = sm + OFF_E1, *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4;
+    uint8_t *E1 = sm + OFF_E1, *A1 = sm + OFF_A1, *A2 = sm + OFF_A2, *A3 = sm + OFF_A3, *A4 = sm + OFF_A4,
+            *DZ4 = sm + OFF_DZ4;
     float* S5 = reinterpret_cast<float*>(sm + OFF_S5);
     float* X = reinterpret_cast<float*>(sm + OFF_X);
     float* GP = reinterpret_cast<float*>(sm + OFF_GP);
@@ -847,7 +850,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
     float ld = 0.0f, lp = 0.0f, li = 0.0f;
     const float thr = __double2float_rd(L.threshold);   // g > thr, as in above()
     const uint32_t sE1 = tc::saddr(E1), sA1 = tc::saddr(A1), sA2 = tc::saddr(A2), sA3 = tc::saddr(A3),
-                   sA4 = tc::saddr(A4), sW2 = tc::saddr(sm + OFF_W2), sW3 = tc::saddr(sm + OFF_W3),
+                   sDZ4 = tc::saddr(DZ4), sW2 = tc::saddr(sm + OFF_W2), sW3 = tc::saddr(sm + OFF_W3),
                    sW4 = tc::saddr(sm + OFF_W4);
 
     // operands written by the threads -> visible to the tensor core, then thread 0 issues
@@ -1029,8 +1032,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
 #pragma unroll
                 for (int e = 0; e < 8; ++e) GP[warp * GP_LD + R.lane * 25 + oo * 8 + e] = acc[oo][e];
         }
-        __syncthreads();   // GP complete; folded during the reverse layer-4 MMAs
-        // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 over A4
+        // ---- dL/dA4 and the layer-4 reverse epilogue -> dZ4 (its own buffer: A4 is read by the
+        // layer-5 gradient of warps 0-7 at the same time; GP is folded after the next barrier)
 #pragma unroll 1
         for (int c0 = 16 * h; c0 < 64; c0 += CS) {
             float dA[16], av[16], own[16], dz[16];
@@ -1044,7 +1047,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
                 dA[j + 1] = t.y;
             }
             dact16(R, dA, av, own, dz);
-            store16(A4, R.r, c0, dz);
+            store16(DZ4, R.r, c0, dz);
         }
         // ---- reverse MMAs of layers 4, 3, 2 (with the gradients) and their epilogues
         auto fold5 = [&]() {   // dW5 (GP, in lane order) and db5 (S5) into the slice
@@ -1068,7 +1071,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         for (int layer = 4; layer >= 2 && ok; --layer) {
             if (!sync_to_mma()) break;
             const int Nout = layer == 4 ? 64 : 128, Kin = layer == 2 ? 64 : 128;
-            const uint32_t dz = layer == 4 ? sA4 : (layer == 3 ? sA3 : sA2);   // dZ_l, over A_l
+            const uint32_t dz = layer == 4 ? sDZ4 : (layer == 3 ? sA3 : sA2);   // dZ_l (dZ3, dZ2 over A_l)
             const uint32_t wl = layer == 2 ? sW2 : (layer == 3 ? sW3 : sW4);
             if (tid == 0) {
                 if (layer == 4)        // dW4^T += A3^T dZ4
@@ -1094,7 +1097,8 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
             }
         }
         if (!ok) break;
-        // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1, committed
+        // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1 (A1 and DZ4
+        // adjacent), committed
         // here and waited for by the next tile before it rewrites E1 and A1
         if (!sync_to_mma()) break;
         if (tid == 0) {
