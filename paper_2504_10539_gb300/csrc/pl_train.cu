@@ -1098,8 +1098,7 @@ k_train_grad_tc(TrainLat L, const float* __restrict__ w, const uint16_t* __restr
         }
         if (!ok) break;
         // ---- layer-1 and layer-4 bias gradients: [dW1 | db1 ; db4] += [dZ1 | dZ4]^T E1 (A1 and DZ4
-        // adjacent), committed
-        // here and waited for by the next tile before it rewrites E1 and A1
+        // adjacent), committed here and waited for by the next tile before it rewrites E1 and A1
         if (!sync_to_mma()) break;
         if (tid == 0) {
             mma_rows(tmem + TM_D1, sA1, sE1, 16, !first);
