@@ -158,15 +158,28 @@ struct GradAcc {
 
 // Eq. 16 gradient magnitude (central differences, periodic, dx = dy = 1) of cell c = (x, y),
 // optionally stored to g, accumulated into a (a non-physical cell: rho <= 0 or not finite).
+// The five densities the Eq. 16 gradient magnitude of cell c = (x, y) reads (periodic).
 template <typename R>
-__device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int nx, int ny, long long c, int x, int y,
-                                                R* __restrict__ g, R thr, GradAcc<R>& a) {
+struct GradIn {
+    R xp, xm, yp, ym, r;
+};
+template <typename R>
+__device__ __forceinline__ GradIn<R> grad_load(const R* __restrict__ rho, int nx, int ny, long long c, int x, int y) {
     const long long row = c - x;
-    const R gx = (rho[row + (x == nx - 1 ? 0 : x + 1)] - rho[row + (x == 0 ? nx - 1 : x - 1)]) / R(2);
-    const R gy = (rho[(long long)(y == ny - 1 ? 0 : y + 1) * nx + x] - rho[(long long)(y == 0 ? ny - 1 : y - 1) * nx + x]) / R(2);
+    return GradIn<R>{rho[row + (x == nx - 1 ? 0 : x + 1)], rho[row + (x == 0 ? nx - 1 : x - 1)],
+                     rho[(long long)(y == ny - 1 ? 0 : y + 1) * nx + x], rho[(long long)(y == 0 ? ny - 1 : y - 1) * nx + x],
+                     rho[c]};
+}
+// Eq. 16 gradient magnitude (central differences, dx = dy = 1) of cell c from its loaded
+// densities, optionally stored to g, accumulated into a (a non-physical cell: rho <= 0 or not
+// finite).
+template <typename R>
+__device__ __forceinline__ void grad_apply(const GradIn<R>& in, long long c, R* __restrict__ g, R thr, GradAcc<R>& a) {
+    const R gx = (in.xp - in.xm) / R(2);
+    const R gy = (in.yp - in.ym) / R(2);
     const R gm = sqrt(gx * gx + gy * gy);
     if (g) g[c] = gm;
-    const R r = rho[c];
+    const R r = in.r;
     a.mass.add(r);
     a.gmax = fmax(a.gmax, gm);
     a.sum_g.add(gm);
@@ -176,6 +189,31 @@ __device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int n
     a.count += gm > thr ? 1u : 0u;
     a.bad += (r > R(0) && isfinite(r)) ? 0u : 1u;
 }
+template <typename R>
+__device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int nx, int ny, long long c, int x, int y,
+                                                R* __restrict__ g, R thr, GradAcc<R>& a) {
+    grad_apply(grad_load(rho, nx, ny, c, x, y), c, g, thr, a);
+}
+
+// A thread's cells, U at a time: the next U cells of the walk (valid while c < N) with their
+// loads issued together, then processed in walk order, so that the sums are the same as cell
+// by cell while U loads per thread are in flight.
+constexpr int CELL_BATCH = 4;
+struct CellBatch {
+    long long c[CELL_BATCH];
+    int x[CELL_BATCH], y[CELL_BATCH];
+    bool v[CELL_BATCH];
+    __device__ __forceinline__ void take(CellIt& it, long long N, int nx) {
+#pragma unroll
+        for (int u = 0; u < CELL_BATCH; ++u) {
+            v[u] = it.c < N;
+            c[u] = it.c;
+            x[u] = it.x;
+            y[u] = it.y;
+            if (v[u]) it.next(nx);
+        }
+    }
+};
 
 template <typename R>
 __global__ void __launch_bounds__(RB_THREADS) k_grad_reduce(const R* __restrict__ rho, int nx, int ny,
@@ -286,9 +324,18 @@ __global__ void __launch_bounds__(RB_THREADS) k_grad_tab(TableView t) {
         const R* rho = static_cast<const R*>(d.rho);
         const R thr = threshold_below<R>(d.threshold);
         GradAcc<R> a;
-        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
-             it.next(d.nx))
-            grad_accumulate(rho, d.nx, d.ny, it.c, it.x, it.y, static_cast<R*>(d.g), thr, a);
+        R* gout = static_cast<R*>(d.g);
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;) {
+            CellBatch b;
+            b.take(it, N, d.nx);
+            GradIn<R> in[CELL_BATCH];
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u)
+                if (b.v[u]) in[u] = grad_load(rho, d.nx, d.ny, b.c[u], b.x[u], b.y[u]);
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u)
+                if (b.v[u]) grad_apply(in[u], b.c[u], gout, thr, a);
+        }
         double v[8];
         const int op[8] = {0, 1, 0, 0, 1, 2, 0, 0};
         if constexpr (std::is_same<R, float>::value) {
@@ -351,27 +398,34 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_region(TableView t) {
         const R nxr = R(d.nx), nyr = R(d.ny), cxr = R(d.cx), cyr = R(d.cy), rho0 = R(d.rho0), G = R(d.G);
         const R inv_rho0 = R(1.0 / d.rho0), third = R(1.0 / 3.0), sixth = R(1.0 / 6.0);  // no divisions per cell
         const R inner = R(0.5 * Req), outer = R(Req + 4.0 * d.width);
-        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
-             it.next(d.nx)) {
-            const long long c = it.c;
-            R ax = fabs(R(it.x) - cxr), ay = fabs(R(it.y) - cyr);
-            if (ax >= nxr) ax = fmod(ax, nxr);
-            if (ay >= nyr) ay = fmod(ay, nyr);
-            if (ax > R(0.5) * nxr) ax = nxr - ax;  // minimum image
-            if (ay > R(0.5) * nyr) ay = nyr - ay;
-            const R dd = sqrt(ax * ax + ay * ay);
-            const R r = rho[c];
-            const R ps = -rho0 * expm1(-r * inv_rho0);
-            const R p = r * third + G * ps * ps * sixth;
-            if (dd < inner) {
-                in_rho.add(r);
-                in_p.add(p);
-                ++in_n;
-            }
-            if (dd > outer) {
-                out_rho.add(r);
-                out_p.add(p);
-                ++out_n;
+        for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;) {
+            CellBatch b;
+            b.take(it, N, d.nx);
+            R rr[CELL_BATCH];
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u) rr[u] = b.v[u] ? rho[b.c[u]] : R(0);
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u) {
+                if (!b.v[u]) continue;
+                R ax = fabs(R(b.x[u]) - cxr), ay = fabs(R(b.y[u]) - cyr);
+                if (ax >= nxr) ax = fmod(ax, nxr);
+                if (ay >= nyr) ay = fmod(ay, nyr);
+                if (ax > R(0.5) * nxr) ax = nxr - ax;  // minimum image
+                if (ay > R(0.5) * nyr) ay = nyr - ay;
+                const R dd = sqrt(ax * ax + ay * ay);
+                const R r = rr[u];
+                const R ps = -rho0 * expm1(-r * inv_rho0);
+                const R p = r * third + G * ps * ps * sixth;
+                if (dd < inner) {
+                    in_rho.add(r);
+                    in_p.add(p);
+                    ++in_n;
+                }
+                if (dd > outer) {
+                    out_rho.add(r);
+                    out_p.add(p);
+                    ++out_n;
+                }
             }
         }
         double v[6];
@@ -461,12 +515,26 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
         const R* out3 = static_cast<const R*>(d.out3);
         const R gmax = R(d.rec->gmax), beta_rho = R(d.beta_rho);
         SumAcc<R> sm_m, sm_dr, sm_rho;  // sum m, sum drho_raw, sum rho
-        for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
-            const R r = rho[c];
-            const R mm = gmax > R(0) ? g[c] / gmax : R(0);
-            sm_m.add(mm);
-            sm_dr.add(beta_rho * mm * (out3[c] - r));
-            sm_rho.add(r);
+        const long long step = (long long)d.red_blocks * RB_THREADS;
+        for (long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x; c0 < N; c0 += CELL_BATCH * step) {
+            R rr[CELL_BATCH], gg[CELL_BATCH], oo[CELL_BATCH];   // loads of U cells together
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u) {
+                const long long c = c0 + u * step;
+                const bool v = c < N;
+                rr[u] = v ? rho[c] : R(0);
+                gg[u] = v ? g[c] : R(0);
+                oo[u] = v ? out3[c] : R(0);
+            }
+#pragma unroll
+            for (int u = 0; u < CELL_BATCH; ++u) {
+                if (c0 + u * step >= N) break;
+                const R r = rr[u];
+                const R mm = gmax > R(0) ? gg[u] / gmax : R(0);
+                sm_m.add(mm);
+                sm_dr.add(beta_rho * mm * (oo[u] - r));
+                sm_rho.add(r);
+            }
         }
         double v[3];
         if constexpr (std::is_same<R, float>::value) {
@@ -560,14 +628,27 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(TableView t) {
         bool reject = false;
         if (d.rec->sum_m > 0.0) {
             const CorrK<R> k = corr_constants<R>(d.rec, d.beta_rho, d.beta_u);
-            for (long long c = (long long)m.lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
-                const CellCorr<R> q = cell_corr(c, static_cast<const R*>(d.rho), static_cast<const R*>(d.jx),
-                                                static_cast<const R*>(d.jy), static_cast<const R*>(d.g),
-                                                static_cast<const R*>(d.out3), N, k);
-                s_jx.add(q.djx_raw);
-                s_jy.add(q.djy_raw);
-                const bool ok = q.rhop > R(0) && isfinite(q.rhop) && isfinite(q.djx_raw) && isfinite(q.djy_raw);
-                reject = reject || !ok;
+            const long long step = (long long)d.red_blocks * RB_THREADS;
+            for (long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x; c0 < N; c0 += 2 * step) {
+                // two cells' loads together, then the cells in walk order
+                const bool v1 = c0 + step < N;
+                const CellIn<R> in0 = cell_in(c0, static_cast<const R*>(d.rho), static_cast<const R*>(d.jx),
+                                              static_cast<const R*>(d.jy), static_cast<const R*>(d.g),
+                                              static_cast<const R*>(d.out3), N);
+                CellIn<R> in1{};
+                if (v1)
+                    in1 = cell_in(c0 + step, static_cast<const R*>(d.rho), static_cast<const R*>(d.jx),
+                                  static_cast<const R*>(d.jy), static_cast<const R*>(d.g),
+                                  static_cast<const R*>(d.out3), N);
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    if (u == 1 && !v1) break;
+                    const CellCorr<R> q = cell_corr(u == 0 ? in0 : in1, k);
+                    s_jx.add(q.djx_raw);
+                    s_jy.add(q.djy_raw);
+                    const bool ok = q.rhop > R(0) && isfinite(q.rhop) && isfinite(q.djx_raw) && isfinite(q.djy_raw);
+                    reject = reject || !ok;
+                }
             }
         }
         double v[3];
