@@ -197,8 +197,9 @@ __device__ __forceinline__ void grad_accumulate(const R* __restrict__ rho, int n
 
 // A thread's cells, U at a time: the next U cells of the walk (valid while c < N) with their
 // loads issued together, then processed in walk order, so that the sums are the same as cell
-// by cell while U loads per thread are in flight.
-constexpr int CELL_BATCH = 4;
+// by cell while U times the loads per thread are in flight (U = 2 measured best of 1, 2, 4, 8:
+// more cells per thread cost resident warps through registers).
+constexpr int CELL_BATCH = 2;
 struct CellBatch {
     long long c[CELL_BATCH];
     int x[CELL_BATCH], y[CELL_BATCH];
