@@ -155,6 +155,14 @@ PL_API int pl_mlp_blob_size(void);
  * PL_ERR_INVALID_ARG for another input count. */
 PL_API int pl_mlp_blob_size_for(int32_t mlp_in);
 PL_API int pl_set_mlp_weights(pl_lattice* lat, const float* host_blob, size_t n);
+/* Seeded weights for the network of Sec. III-B (the configurations' "seed-initialised"
+ * network; the paper fixes no distribution, so the fan-in uniform is used): entry k of the
+ * blob above, in blob order, is (2 U - 1) / sqrt(fan_in) with U = top 53 bits of SplitMix64
+ * output k for `seed` (the generator of pl_lattice_init_droplets) divided by 2^53 and fan_in
+ * the input width of the entry's layer (params.mlp_in for layer 1), rounded to FP32.
+ * Written on the device on the lattice's stream (no host data); replaces any earlier
+ * weights.  Read them back with pl_get_mlp_weights. */
+PL_API int pl_init_mlp_weights(pl_lattice* lat, uint64_t seed);
 
 /* n >= 0 time steps of Eq. 1 on the device (no host synchronisation). */
 PL_API int pl_step(pl_lattice* lat, int32_t n);
@@ -191,22 +199,25 @@ PL_API int pl_get_mlp_field(pl_lattice* lat, double* host_out3);
 PL_API int pl_get_state(pl_lattice* lat, double* host_f, int64_t* step);
 PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
 
-/* Allocation-free metrics (the paper has no counterpart: this serves callers that
- * cannot allocate device memory - code running inside an allocator or pool callback,
- * or a host that must not grow its device footprint after start-up - and therefore
- * cannot hand the library the scratch buffer that pl_lattice_create carves up).
- * Computes the Eq. 9-15 metrics and the mass (no Laplace fields: NaN; mass0: NaN,
- * step: 0) of populations that the caller passes at dev_pops (device memory, element
- * type given by `storage`, 9 planes of ny rows of `pitch` >= nx elements, x fastest,
- * FP16-offset values h_i = f_i - w_i*rho_ref) and writes the record to host memory at
- * `out`.  Its scratch (density field, block partials, record) is a static device array
- * of 8.07 MB that every GPU loading the library keeps until the process exits; it calls
- * no cudaMalloc, cudaFree or allocating library routine.  Lattices above 1,048,576
- * cells are rejected with PL_ERR_BUDGET (and a message on stderr).  The first call on a
- * device looks up the array's device address with that device current; make that first
- * call before any stream capture.  All calls share the one array: calls whose work
- * overlaps on the GPU (different streams, or different host threads) race and must be
- * serialised by the caller.  Enqueues on `stream` and synchronises it. */
+/* Allocation-free metrics (the paper has no counterpart).  Some callers cannot allocate
+ * device memory: code running inside an allocator or a memory-pool callback (where a
+ * cudaMalloc would re-enter the allocator), or a host that must not grow its device
+ * footprint after start-up.  They cannot hand the library the scratch buffer that
+ * pl_lattice_create carves up, so this call keeps its scratch in a static device array.
+ * It fills the record fields mass, W, G_max, delta_rho, W_eff, E_int, rho_max, rho_min,
+ * sum_g, sum_g2 and count (threshold: the gradient threshold that W and count use), the
+ * same quantities pl_metrics returns, of populations that the caller passes at dev_pops
+ * (device memory, element type given by `storage`, 9 planes of ny rows of `pitch` >= nx
+ * elements, x fastest, FP16-offset values h_i = f_i - w_i*rho_ref).  The Laplace fields
+ * and mass0 are NaN, step, status and corrections 0.  The record is written to host memory
+ * at `out`.  Its scratch (density field, block partials, record) is a static device array
+ * of 8.07 MB that every GPU loading the library keeps until the process exits; the call
+ * makes no cudaMalloc, cudaFree or allocating library call.  Lattices above 1,048,576
+ * cells are rejected with PL_ERR_BUDGET (and a message on stderr).  Every call looks up the
+ * array's address on the calling thread's current device, which must be the device that
+ * holds dev_pops.  All calls share the one array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  Enqueues on `stream` and synchronises it. */
 PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32_t ny, int32_t pitch, int32_t storage,
                               double rho_ref, double threshold, void* stream, pl_metric_record* out);
 
@@ -339,6 +350,10 @@ PL_API int pl_batch_create(int32_t storage, int32_t mlp, int32_t K, int32_t max_
                            void* stream, pl_batch** out);
 /* Network weights shared by all jobs (layout of pl_set_mlp_weights). */
 PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* host_blob, size_t n);
+/* Seeded weights shared by all jobs, as pl_init_mlp_weights, for a network with mlp_in (2
+ * or 11) inputs; PL_ERR_INVALID_ARG if the batch already holds a network of another input
+ * count. */
+PL_API int pl_batch_init_mlp_weights(pl_batch* b, int32_t mlp_in, uint64_t seed);
 /* Admit one job: lattice parameters (storage must match the batch), initial droplets
  * (as pl_lattice_init_droplets) and the number of steps.  PL_ERR_BUDGET if its memory or
  * a job slot is not available now.  Writes the job id. */

@@ -71,6 +71,7 @@ def lib():
         L.orc_correct_n.argtypes = [i, i, _dp, _fp, i, i, vp, d, d, d]
         L.orc_run_n.restype = i
         L.orc_run_n.argtypes = [i, i, _dp, i, ctypes.c_long, i, d, d, d, _fp, i, i, d, d, d]
+        L.orc_mlp_init_weights.argtypes = [i, u64, _fp]
         L.orc_num_threads.restype = i
         L.orc_set_num_threads.argtypes = [i]
         L.orc_lattice_tables.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]
@@ -232,6 +233,13 @@ def mlp_blob_size(n_in=2):
     """Weight blob length for n_in network inputs (2: the paper's (x^, y^); 11: with the
     density stencil)."""
     return lib().orc_mlp_blob_size_n(int(n_in))
+
+
+def mlp_init_weights(seed, n_in=2):
+    """The seeded FP32 weight blob (fan-in uniform from SplitMix64, counter = blob index)."""
+    out = np.zeros(mlp_blob_size(n_in), dtype=np.float32)
+    lib().orc_mlp_init_weights(int(n_in), seed & (2**64 - 1), _f(out))
+    return out
 
 
 def mlp_forward(blob, xh, yh, mode=MLP_F64):

@@ -413,6 +413,24 @@ long orc_mlp_blob_size_n(int n_in) {
 
 long orc_mlp_blob_size(void) { return orc_mlp_blob_size_n(2); }
 
+/* Seeded weights (Sec. III-B gives the architecture; the configurations call the network
+ * "seed-initialised" without a distribution, so the reading used is the common fan-in
+ * uniform): entry k of the blob, in blob order (layer by layer, W[out][in] row-major, then
+ * b), is (2 U(seed, k) - 1) / sqrt(fan_in) with U the SplitMix64 uniform above and fan_in
+ * the input width of its layer, rounded to FP32 (nearest). */
+void orc_mlp_init_weights(int n_in, uint64_t seed, float* blob) {
+    long k = 0;
+    for (int l = 0; l < 5; ++l) {
+        int nin = mlp_dim(n_in, l), nout = MLP_HIDDEN[l];
+        double bound = 1.0 / sqrt((double)nin);
+        long count = (long)nout * nin + nout;
+        for (long e = 0; e < count; ++e, ++k) {
+            double t = 2.0 * orc_uniform01(seed, (uint64_t)k) - 1.0;
+            blob[k] = (float)(t * bound);
+        }
+    }
+}
+
 /* Round a double to the nearest BF16 value (8 significant bits), ties to even. */
 double orc_round_bf16(double v) {
     if (v == 0.0 || !isfinite(v)) return v;

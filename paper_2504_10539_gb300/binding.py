@@ -110,6 +110,8 @@ def _L():
             "pl_mlp_blob_size": (ctypes.c_int, []),
             "pl_mlp_blob_size_for": (ctypes.c_int, [ctypes.c_int32]),
             "pl_set_mlp_weights": (ctypes.c_int, [vp, P(ctypes.c_float), sz]),
+            "pl_init_mlp_weights": (ctypes.c_int, [vp, u64]),
+            "pl_batch_init_mlp_weights": (ctypes.c_int, [vp, i32, u64]),
             "pl_step": (ctypes.c_int, [vp, i32]),
             "pl_apply_correction": (ctypes.c_int, [vp]),
             "pl_run": (ctypes.c_int, [vp, i32, i32]),
@@ -233,6 +235,10 @@ def pl_set_mlp_weights(h, blob: np.ndarray):
     b = np.ascontiguousarray(blob, dtype=np.float32)
     return _chk("pl_set_mlp_weights", _L().pl_set_mlp_weights(
         ctypes.c_void_p(h), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
+
+
+def pl_init_mlp_weights(h, seed: int):
+    return _chk("pl_init_mlp_weights", _L().pl_init_mlp_weights(ctypes.c_void_p(h), seed & (2 ** 64 - 1)))
 
 
 def pl_step(h, n: int):
@@ -387,6 +393,9 @@ class Lattice:
     def set_weights(self, blob):
         pl_set_mlp_weights(self.h, blob)
 
+    def init_weights(self, seed):
+        pl_init_mlp_weights(self.h, seed)
+
     def step(self, n):
         pl_step(self.h, n)
 
@@ -495,6 +504,11 @@ def pl_batch_set_mlp_weights(h, blob: np.ndarray):
         ctypes.c_void_p(h), b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), b.size))
 
 
+def pl_batch_init_mlp_weights(h, mlp_in: int, seed: int):
+    return _chk("pl_batch_init_mlp_weights", _L().pl_batch_init_mlp_weights(ctypes.c_void_p(h), mlp_in,
+                                                                            seed & (2 ** 64 - 1)))
+
+
 def pl_batch_submit(h, p: pl_params, droplets, rho_in, rho_out, width, noise_amp, seed, steps):
     """Returns the job id, or None when the batch has no room for it now (PL_ERR_BUDGET)."""
     n = len(droplets)
@@ -583,6 +597,9 @@ class Batch:
     def set_weights(self, blob):
         pl_batch_set_mlp_weights(self.h, blob)
 
+    def init_weights(self, seed, mlp_in=2):
+        pl_batch_init_mlp_weights(self.h, mlp_in, seed)
+
     def submit(self, job, steps=None):
         jid = pl_batch_submit(self.h, job_params(job), job.droplets, job.rho_in, job.rho_out, job.width,
                               job.noise_amp, job.seed, int(steps if steps is not None else job.steps))
@@ -592,6 +609,14 @@ class Batch:
 
     def advance(self, intervals=1):
         pl_batch_advance(self.h, intervals)
+
+    def job_bytes(self, job) -> int:
+        """Arena bytes the job's lattice takes (pl_batch_job_bytes)."""
+        return pl_batch_job_bytes(job_params(job))
+
+    def arena_bytes(self) -> int:
+        """Size of the arena the jobs are carved from (the budget minus the batch's head)."""
+        return pl_batch_info(self.h)["arena_total"]
 
     def poll(self):
         return pl_batch_poll(self.h)

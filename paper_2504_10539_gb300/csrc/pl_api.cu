@@ -384,6 +384,14 @@ int pl_set_mlp_weights(pl_lattice* L, const float* blob, size_t n) {
     return PL_OK;
 }
 
+int pl_init_mlp_weights(pl_lattice* L, uint64_t seed) {
+    if (!L) return PL_ERR_INVALID_ARG;
+    PL_CUDA(launch_init_weights(L->w32, L->p.mlp_in, seed, L->stream));
+    PL_CUDA(launch_convert_weights_bf16(L->w32, L->wbf16, L->p.mlp_in, L->stream));
+    L->weights_set = 1;
+    return PL_OK;
+}
+
 static int do_steps(pl_lattice* L, int n) {
     for (int k = 0; k < n; ++k) {
         PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, L->cur, L->stream));

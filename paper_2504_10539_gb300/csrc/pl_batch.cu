@@ -364,6 +364,16 @@ PL_API int pl_batch_set_mlp_weights(pl_batch* b, const float* blob, size_t n) {
     return PL_OK;
 }
 
+PL_API int pl_batch_init_mlp_weights(pl_batch* b, int32_t mlp_in, uint64_t seed) {
+    if (!b || (mlp_in != 2 && mlp_in != 11) || (b->mlp_in != 0 && b->mlp_in != mlp_in)) return PL_ERR_INVALID_ARG;
+    float* w32 = reinterpret_cast<float*>(b->base + b->H.w32);
+    PL_CUDA(launch_init_weights(w32, mlp_in, seed, b->stream));
+    PL_CUDA(launch_convert_weights_bf16(w32, reinterpret_cast<uint16_t*>(b->base + b->H.wbf16), mlp_in, b->stream));
+    b->mlp_in = mlp_in;
+    b->weights_set = 1;
+    return PL_OK;
+}
+
 PL_API int pl_batch_submit(pl_batch* b, const pl_params* p, const pl_droplet* d, int n, double rho_in, double rho_out,
                            double width, double noise_amp, uint64_t seed, int64_t steps, int64_t* job_id) {
     if (!b || !job_id || steps < 1) return PL_ERR_INVALID_ARG;

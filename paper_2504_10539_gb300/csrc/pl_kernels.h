@@ -116,6 +116,8 @@ cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, i
                                   const float* w32, const uint16_t* wbf16, cudaStream_t s);
 
 cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, int n_in, cudaStream_t s);
+// Seeded FP32 weight blob (fan-in uniform from SplitMix64, counter = blob index) written on the device.
+cudaError_t launch_init_weights(float* w32, int n_in, uint64_t seed, cudaStream_t s);
 
 // Network training (Eqs. 3-8, the 2-input network): the lattice fields it reads (element type
 // double for FP64 lattices, float otherwise), its hyper-parameters and its device buffers.

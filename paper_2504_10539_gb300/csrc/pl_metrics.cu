@@ -13,7 +13,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <type_traits>
 
 #include "pl_device.cuh"
@@ -1017,12 +1016,6 @@ static_assert(sizeof(DevRecord) <= 256, "record slot of the static scratch");
 
 }  // namespace pl
 
-namespace {
-// Device address of g_noalloc_scratch, looked up once per device (with that device current).
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {nullptr};
-}  // namespace
-
 extern "C" PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32_t ny, int32_t pitch, int32_t storage,
                                          double rho_ref, double threshold, void* stream, pl_metric_record* out) {
     using namespace pl;
@@ -1036,26 +1029,16 @@ extern "C" PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32
                              "static scratch\n", (long long)nx * ny, NOALLOC_MAX_CELLS);
         return PL_ERR_BUDGET;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    // In host code g_noalloc_scratch names a host-side stand-in, not device memory: the
+    // array's address on the current device is looked up on every call (a cheap query), so
+    // no address outlives the context it belongs to (a cudaDeviceReset reloads the module).
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
         (void)cudaGetLastError();
         return PL_ERR_CUDA;
     }
-    unsigned char* scratch;
-    {
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p) {
-                (void)cudaGetLastError();
-                return PL_ERR_CUDA;
-            }
-            g_noalloc_ptr[dev] = p;
-        }
-        scratch = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
-    }
+    unsigned char* scratch = static_cast<unsigned char*>(p);
     DevRecord* rec = reinterpret_cast<DevRecord*>(scratch + NOALLOC_RHO_BYTES + NOALLOC_PART_BYTES);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     e = cudaMemsetAsync(rec, 0, sizeof(DevRecord), s);  // the record starts at zero on every call

@@ -138,4 +138,33 @@ cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, int n_
     return mlp_simt_t<float>(t, w32, n_in, s);
 }
 
+// Seeded weights (Sec. III-B gives the architecture; "seed-initialised" fixes no
+// distribution, so the fan-in uniform is used): entry k of the FP32 blob, in blob order
+// (layer by layer, W[out][in] row-major, then b), is (2 U(seed, k) - 1) / sqrt(fan_in), U the
+// SplitMix64 uniform of output k (top 53 bits), rounded to FP32 to nearest.  All arithmetic
+// in FP64 with correctly rounded sqrt and division, so the blob is the same bits on any host.
+__global__ void k_init_weights(float* __restrict__ w32, int n_in, uint64_t seed) {
+    const int dims[6] = {n_in, 64, 128, 128, 64, 3};
+    int ends[5];
+    int e = 0;
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        e += dims[l + 1] * dims[l] + dims[l + 1];
+        ends[l] = e;
+    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x) {
+        int l = 0;
+        while (k >= ends[l]) ++l;
+        const double t = 2.0 * uniform01_at(seed, (uint64_t)k) - 1.0;
+        w32[k] = __double2float_rn(t * (1.0 / sqrt((double)dims[l])));
+    }
+}
+
+cudaError_t launch_init_weights(float* w32, int n_in, uint64_t seed, cudaStream_t s) {
+    if (n_in != 2 && n_in != 11) return cudaErrorInvalidValue;
+    k_init_weights<<<64, 256, 0, s>>>(w32, n_in, seed);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 }  // namespace pl

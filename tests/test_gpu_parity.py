@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import seeded_states as S
 from paper_2504_10539_gb300 import binding as B
 from paper_2504_10539_gb300 import workloads as wl
 
@@ -33,14 +34,7 @@ def lattice(nx, ny, storage, mlp=None, **kw):
 
 def stored(f, storage):
     """The FP64 values a storage type actually holds for populations f."""
-    if storage == F64:
-        return f.copy()
-    if storage == F32:
-        return f.astype(np.float32).astype(np.float64)
-    _, _, w = O.lattice_tables()
-    off = (w * RHO_REF).astype(np.float32)[:, None, None]
-    h = (f.astype(np.float32) - off).astype(np.float16)        # encode: rn_half(float(f) - off)
-    return (h.astype(np.float32) + off).astype(np.float64)     # decode: float(h) + off
+    return S.stored(f, storage, RHO_REF)
 
 
 def rel_linf(a, b):
@@ -99,7 +93,7 @@ def test_single_64_fp64_coupled_run_matches_oracle():
                  beta_rho=job.beta_rho, beta_u=job.beta_u, M0=M0) == 0
     ro = O.density(fo)
     assert step == 2000 and m["corrections"] == 40 and m["status"] == 0
-    assert rel_linf(O.density(f_gpu), ro) < 1e-11
+    assert rel_linf(lat.rho(), ro) < 1e-11
     mo = O.metrics_rho(ro)
     lo = O.laplace(ro, 32.0, 32.0, job.width, job.G)
     assert abs(m["mass"] - M0) < 1e-12 * M0 and abs(mo["mass"] - M0) < 1e-12 * M0
@@ -121,33 +115,13 @@ def test_fp32_droplet_with_fp32_network_matches_oracle():
     fo = O.init_equilibrium(O.init_rho(n, n, job.droplets, 2.0, 0.15, 2.0, 0.01, 5))
     M0 = O.mass(fo)
     assert O.run(fo, job.steps, job.G, job.tau, K=job.K, blob=job.weights(), mode=O.MLP_F64, M0=M0) == 0
-    assert rel_linf(O.density(f_gpu), O.density(fo)) < 1e-4
+    assert rel_linf(lat.rho(), O.density(fo)) < 1e-4
     assert abs(m["mass"] - M0) < 1e-6 * M0
     mo = O.metrics_rho(O.density(fo))
     assert abs(m["W"] - mo["W"]) <= 0.02 * mo["W"]
 
 
 # ----------------------------------------------------------------------------- metrics, network, correction
-
-@pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (300, 33)])
-def test_metrics_match_oracle_on_same_state(nx, ny):
-    drops = [(nx / 2, ny / 2, min(nx, ny) / 4)]
-    lat = lattice(nx, ny, F64)
-    lat.init_droplets(drops, 2.0, 0.15, 2.0, 0.01, 3)
-    lat.step(50)
-    m = lat.metrics()
-    f, _ = lat.state()
-    r = O.density(f)
-    mo = O.metrics_rho(r)
-    lo = O.laplace(r, nx / 2, ny / 2, 2.0, -5.5)
-    assert m["count"] == mo["count"]
-    for k in ("mass", "G_max", "W", "W_eff", "E_int", "delta_rho", "rho_max", "rho_min"):
-        assert abs(m[k] - mo[k]) <= 1e-12 * max(abs(mo[k]), 1e-300), k
-    for k in ("R_eq", "rho_in", "rho_out", "p_in", "p_out"):
-        assert abs(m[k] - lo[k]) <= 1e-12 * abs(lo[k]), k
-    # same state; the GPU sums the 9 populations pairwise, the oracle in order
-    assert np.abs(lat.rho() - r).max() <= 4e-16 * np.abs(r).max() * 9
-
 
 @pytest.mark.parametrize("storage,mode,tol", [(F64, B.PL_MLP_F64, 1e-13), (F32, B.PL_MLP_F32, 2e-5)])
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35)])
@@ -165,16 +139,15 @@ def test_network_field_matches_oracle(storage, mode, tol, nx, ny):
 def test_single_correction_matches_oracle(storage, tol):
     n = 48
     lat = lattice(n, n, storage, beta_rho=0.3, beta_u=0.05)
-    lat.init_droplets([(24.0, 24.0, 10.0)], 2.0, 0.15, 2.0, 0.01, 9)
-    lat.step(40)
-    f0, _ = lat.state()
+    f0 = stored(S.oracle_droplet_state(n, n, [(24.0, 24.0, 10.0)], steps=40, seed=9), storage)
+    lat.set_state(f0, 40)
     m0 = lat.metrics()
     blob = wl.mlp_weights(42)
     lat.set_weights(blob)
     lat.correct()
     f1, _ = lat.state()
     fo = f0.copy()
-    assert O.correct(fo, blob, 0.3, 0.05, m0["mass0"], O.MLP_F64) == 0
+    assert O.correct(fo, blob, 0.3, 0.05, O.mass(f0), O.MLP_F64) == 0
     assert np.abs(f1 - fo).max() <= tol * np.abs(fo).max()
     m1 = lat.metrics()
     assert m1["corrections"] == 1 and m1["status"] == 0
@@ -188,16 +161,15 @@ def test_f16_correction_matches_oracle_and_restores_mass(nx, ny):
     the stored mass returns to M0 within 1e-6 even on small lattices (the stochastic
     rounding of the apply pass alone leaves ~ulp sqrt(N) / M ~ 1e-5 there)."""
     lat = lattice(nx, ny, F16, beta_rho=0.3, beta_u=0.05)
-    lat.init_droplets([(nx / 2, ny / 2, min(nx, ny) / 4)], 2.0, 0.15, 2.0, 0.01, 9)
-    lat.step(40)
-    f0, _ = lat.state()
+    f0 = stored(S.oracle_droplet_state(nx, ny, [(nx / 2, ny / 2, min(nx, ny) / 4)], steps=40, seed=9), F16)
+    lat.set_state(f0, 40)
     m0 = lat.metrics()
     blob = wl.mlp_weights(42)
     lat.set_weights(blob)
     lat.correct()
     f1, _ = lat.state()
     fo = f0.copy()
-    assert O.correct(fo, blob, 0.3, 0.05, m0["mass0"], O.MLP_F64) == 0
+    assert O.correct(fo, blob, 0.3, 0.05, O.mass(f0), O.MLP_F64) == 0
     # Per cell, in offset space h = f - w rho_ref: a moving population is rounded to nearest
     # (at most half its FP16 spacing); the rest population takes the cell's corrected mass
     # minus the rounded moving populations, so their eight rounding errors land in it, and
@@ -222,9 +194,8 @@ def test_f16_correction_matches_oracle_and_restores_mass(nx, ny):
 def test_nonphysical_correction_leaves_state_and_sets_status():
     n = 32
     lat = lattice(n, n, F64, beta_rho=1.0, beta_u=0.0)
-    lat.init_droplets([(16.0, 16.0, 6.0)], 2.0, 0.15, 2.0, 0.01, 1)
-    lat.step(20)
-    f0, _ = lat.state()
+    f0 = S.oracle_droplet_state(n, n, [(16.0, 16.0, 6.0)], steps=20, seed=1)
+    lat.set_state(f0, 20)
     blob = np.zeros(wl.mlp_blob_size(), dtype=np.float32)
     offs, o = [], 0
     dims = wl.MLP_DIMS

@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import seeded_states as S
 from paper_2504_10539_gb300 import binding as B
 from paper_2504_10539_gb300 import workloads as wl
 
@@ -50,10 +51,12 @@ def test_blob_size_and_input_count_are_checked():
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (300, 33)])
 def test_stencil_network_field_matches_oracle(storage, mlp, mode, tol, nx, ny):
     blob = wl.mlp_weights(71, dims=DIMS)
-    lat = droplet_lattice(nx, ny, storage, mlp)
+    lat = B.Lattice(B.pl_params_default(nx, ny, storage=storage, mlp=mlp, mlp_in=11))
+    drops = [(nx / 2, ny / 2, min(nx, ny) / 4), (0.2 * nx, 0.7 * ny, 3.0)]
+    f = S.stored(S.oracle_droplet_state(nx, ny, drops, steps=20, seed=4), storage, 1.075)
+    lat.set_state(f, 20)
     lat.set_weights(blob)
     out = lat.mlp_field()
-    f, _ = lat.state()
     ref = O.mlp_field(blob, nx, ny, mode, n_in=11, rho=O.density(f))
     assert np.isfinite(out).all()
     assert np.abs(out - ref).max() <= tol
@@ -71,7 +74,7 @@ def test_stencil_network_coupled_fp64_run_matches_oracle():
     M0 = O.mass(fo)
     assert O.run(fo, job.steps, job.G, job.tau, K=job.K, blob=job.weights(), mode=O.MLP_F64, M0=M0, n_in=11) == 0
     ro = O.density(fo)
-    assert np.abs(O.density(f) - ro).max() / np.abs(ro).max() < 1e-11
+    assert np.abs(lat.rho() - ro).max() / np.abs(ro).max() < 1e-11
     assert m["corrections"] == job.steps // job.K and abs(m["mass"] - M0) < 1e-12 * M0
 
 

@@ -16,6 +16,7 @@ import pytest
 
 import oracle as O
 import oracle.train as T
+import seeded_states as S
 from paper_2504_10539_gb300 import binding as B
 from paper_2504_10539_gb300 import workloads as wl
 
@@ -33,28 +34,32 @@ HP = {
 
 
 def droplet_lattice(nx, ny, storage, steps=40, seed=3):
+    """A lattice holding the oracle's droplet after `steps` of its steps (stored exactly in the
+    lattice's storage type); returns the lattice, its job and that state, which both sides read."""
     mlp = B.PL_MLP_F64 if storage == B.PL_F64 else B.PL_MLP_BF16
     job = wl.Lattice(nx, ny, storage=storage, mlp=mlp, droplets=[(nx / 2, ny / 2, min(nx, ny) / 4)], seed=seed,
                      K=1, weight_seed=30 + seed)
-    lat = B.Lattice.from_workload(job)
-    lat.step(steps)
-    return lat, job
+    f = S.stored(S.oracle_droplet_state(nx, ny, job.droplets, steps=steps, G=job.G, tau=job.tau, seed=seed), storage,
+                 job.rho_ref)
+    lat = B.Lattice(B.job_params(job))
+    lat.set_state(f, steps)
+    lat.set_weights(job.weights())
+    return lat, job, f
 
 
-def oracle_gradient(lat, job, hp):
-    f, _ = lat.state()
+def oracle_gradient(f, job, hp):
     t, iface = T.targets_from_state(f, 0.01)
     L, terms, g = T.loss_and_grad(job.weights(), job.nx, job.ny, t, iface, job.G, 1.0, T.TrainParams(**hp))
-    return f, L, terms, g
+    return L, terms, g
 
 
 @pytest.mark.parametrize("which", sorted(HP))
 @pytest.mark.parametrize("nx,ny", [(64, 64), (37, 23), (300, 33), (5, 3)])
 def test_fp64_gradient_matches_oracle(nx, ny, which):
-    lat, job = droplet_lattice(nx, ny, B.PL_F64)
+    lat, job, f = droplet_lattice(nx, ny, B.PL_F64)
     tr = B.Trainer(lat, max_epochs=4, **HP[which])
     g, loss = tr.gradient()
-    _, L, terms, go = oracle_gradient(lat, job, HP[which])
+    L, terms, go = oracle_gradient(f, job, HP[which])
     assert np.isfinite(g).all()
     assert np.abs(g - go).max() <= 1e-10 * np.abs(go).max()
     assert loss[0] == pytest.approx(L, rel=1e-11)
@@ -66,10 +71,9 @@ def test_fp64_gradient_matches_oracle(nx, ny, which):
 @pytest.mark.parametrize("which", sorted(HP))
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35)])
 def test_fp32_gradient_matches_oracle(nx, ny, which, storage):
-    lat, job = droplet_lattice(nx, ny, storage)
+    lat, job, f = droplet_lattice(nx, ny, storage)
     tr = B.Trainer(lat, max_epochs=4, **HP[which])
     g, loss = tr.gradient()
-    f, _ = lat.state()
     t, iface = T.targets_from_state(f, 0.01)
     # The GPU decides the interface set (Eq. 16 gradient > 0.01) from an FP32 density: a cell
     # whose FP64 gradient lies within FP32 rounding of the threshold may fall on either side,
@@ -87,9 +91,8 @@ def test_fp32_gradient_matches_oracle(nx, ny, which, storage):
 
 
 def test_fp64_training_matches_oracle_and_persists_adam_state():
-    lat, job = droplet_lattice(48, 40, B.PL_F64)
+    lat, job, f = droplet_lattice(48, 40, B.PL_F64)
     tr = B.Trainer(lat, max_epochs=8)
-    f, _ = lat.state()
     blob1, hist1, st = T.train(job.weights(), f, 5, job.G)
     tr.train(5)
     w1 = lat.weights().astype(np.float64)
@@ -104,8 +107,7 @@ def test_fp64_training_matches_oracle_and_persists_adam_state():
 
 @pytest.mark.parametrize("storage", [B.PL_F32, B.PL_F16_OFFSET])
 def test_fp32_training_matches_oracle(storage):
-    lat, job = droplet_lattice(64, 48, storage)
-    f, _ = lat.state()
+    lat, job, f = droplet_lattice(64, 48, storage)
     # well-conditioned Adam (eps = 1e-2): weights within 10 epochs x lr/eps x gradient error
     tr = B.Trainer(lat, max_epochs=10, eps=1e-2)
     tr.train(10)
@@ -113,7 +115,7 @@ def test_fp32_training_matches_oracle(storage):
     assert np.abs(lat.weights().astype(np.float64) - blob).max() <= 1e-6
     assert np.abs(tr.losses(10) - hist).max() <= 1e-5 * np.abs(hist).max()
     # default eps: the loss history follows the oracle's
-    lat2, _ = droplet_lattice(64, 48, storage)
+    lat2, _, _ = droplet_lattice(64, 48, storage)
     tr2 = B.Trainer(lat2, max_epochs=10)
     tr2.train(10)
     _, hist2, _ = T.train(job.weights(), f, 10, job.G)
@@ -134,7 +136,7 @@ def test_fp64_coupled_run_with_training_matches_oracle():
     st, blob, _ = T.run_trained(fo, 50, job.G, job.tau, 20, job.weights(), 3, M0=M0)
     assert st == 0 and step == 50
     ro = O.density(fo)
-    assert np.abs(O.density(f) - ro).max() <= 1e-10 * np.abs(ro).max()
+    assert np.abs(lat.rho() - ro).max() <= 1e-10 * np.abs(ro).max()
     assert np.abs(lat.weights().astype(np.float64) - blob).max() <= 2.0 ** -23 * np.abs(blob).max()
     assert m["corrections"] == 2 and abs(m["mass"] - M0) <= 1e-12 * M0
 
@@ -169,11 +171,14 @@ def test_full_size_512_gradient_matches_oracle():
     """The 512 x 512 single-droplet lattice (FP32 storage), after 200 steps: the full-batch
     gradient and loss terms against the oracle's over all 262,144 cells."""
     job = wl.single_512()
-    lat = B.Lattice.from_workload(job)
-    lat.step(200)
+    f = S.stored(S.oracle_droplet_state(job.nx, job.ny, job.droplets, steps=200, G=job.G, tau=job.tau, seed=job.seed),
+                 job.storage, job.rho_ref)
+    lat = B.Lattice(B.job_params(job))
+    lat.set_state(f, 200)
+    lat.set_weights(job.weights())
     tr = B.Trainer(lat, max_epochs=2)
     g, loss = tr.gradient()
-    f, L, terms, go = oracle_gradient(lat, job, {})
+    L, terms, go = oracle_gradient(f, job, {})
     assert np.abs(g - go).max() <= 1e-4 * np.abs(go).max()
     assert loss[0] == pytest.approx(L, rel=1e-5)
     tr.train(2)
@@ -237,6 +242,6 @@ def test_coupled_run_with_training_fp32_arithmetic(storage, mlp, mode, tol):
                                 M0=M0)
     assert st == 0 and m["status"] == 0 and m["corrections"] == 2
     ro = O.density(fo)
-    assert np.abs(O.density(f) - ro).max() <= tol * np.abs(ro).max()
+    assert np.abs(lat.rho() - ro).max() <= tol * np.abs(ro).max()
     # the correction restores the lattice's own M0 (the mass of its stored initial state)
     assert abs(m["mass"] - m["mass0"]) <= 1e-6 * m["mass0"]

@@ -13,6 +13,7 @@ import pytest
 
 import oracle as O
 import oracle.train as T
+import seeded_states as S
 from paper_2504_10539_gb300 import binding as B
 from paper_2504_10539_gb300 import workloads as wl
 
@@ -29,12 +30,22 @@ HP = {
 }
 
 
+def seeded_lattice(job, steps):
+    """A lattice holding the oracle's droplet of `job` after `steps` of its steps (stored exactly
+    in the lattice's storage type), with the job's weights; returns the lattice and the state."""
+    f = S.stored(S.oracle_droplet_state(job.nx, job.ny, job.droplets, steps=steps, G=job.G, tau=job.tau,
+                                        seed=job.seed), job.storage, job.rho_ref)
+    lat = B.Lattice(B.job_params(job))
+    lat.set_state(f, steps)
+    lat.set_weights(job.weights())
+    return lat, f
+
+
 def droplet_lattice(nx, ny, storage=B.PL_F32, steps=40, seed=3):
     job = wl.Lattice(nx, ny, storage=storage, mlp=B.PL_MLP_BF16, droplets=[(nx / 2, ny / 2, min(nx, ny) / 4)],
                      seed=seed, K=1, weight_seed=30 + seed)
-    lat = B.Lattice.from_workload(job)
-    lat.step(steps)
-    return lat, job
+    lat, f = seeded_lattice(job, steps)
+    return lat, job, f
 
 
 def oracle_gradient(f, job, hp, iface=None):
@@ -46,10 +57,9 @@ def oracle_gradient(f, job, hp, iface=None):
 @pytest.mark.parametrize("which", sorted(HP))
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (41, 7)])
 def test_tc_gradient_matches_oracle(nx, ny, which):
-    lat, job = droplet_lattice(nx, ny)
+    lat, job, f = droplet_lattice(nx, ny)
     tr = B.Trainer(lat, max_epochs=2, mode=B.PL_TRAIN_TC, **HP[which])
     g, loss = tr.gradient()
-    f, _ = lat.state()
     L, terms, go = oracle_gradient(f, job, HP[which])
     assert np.isfinite(g).all()
     err = np.abs(g - go).max() / np.abs(go).max()
@@ -61,10 +71,9 @@ def test_tc_gradient_per_layer_blocks():
     """Each layer's block of the gradient on its own (a wrong operand layout in one MMA shows
     up as a block far from the oracle even when the whole vector's maximum is dominated by
     another layer)."""
-    lat, job = droplet_lattice(96, 80)
+    lat, job, f = droplet_lattice(96, 80)
     tr = B.Trainer(lat, max_epochs=1, mode=B.PL_TRAIN_TC)
     g, _ = tr.gradient()
-    f, _ = lat.state()
     _, _, go = oracle_gradient(f, job, {})
     sizes = [(64, 2), (64,), (128, 64), (128,), (128, 128), (128,), (64, 128), (64,), (3, 64), (3,)]
     o = 0
@@ -77,8 +86,7 @@ def test_tc_gradient_per_layer_blocks():
 
 
 def test_tc_training_follows_oracle_and_full_size():
-    lat, job = droplet_lattice(64, 48)
-    f, _ = lat.state()
+    lat, job, f = droplet_lattice(64, 48)
     tr = B.Trainer(lat, max_epochs=10, mode=B.PL_TRAIN_TC)
     tr.train(10)
     h = tr.losses(10)
@@ -87,11 +95,9 @@ def test_tc_training_follows_oracle_and_full_size():
     assert h[-1, 0] < h[0, 0]
     # the 512 x 512 single droplet: one gradient over all 262,144 cells
     big = wl.single_512()
-    lat2 = B.Lattice.from_workload(big)
-    lat2.step(100)
+    lat2, f2 = seeded_lattice(big, 100)
     tr2 = B.Trainer(lat2, max_epochs=1, mode=B.PL_TRAIN_TC)
     g, loss = tr2.gradient()
-    f2, _ = lat2.state()
     L, _, go = oracle_gradient(f2, big, {})
     assert np.abs(g - go).max() <= 2e-2 * np.abs(go).max()
     assert loss[0] == pytest.approx(L, rel=1e-2)
@@ -102,7 +108,7 @@ def test_tc_gradient_is_reproducible():
     writer per element of a CTA's slice, the slices folded in CTA order; two calls on the same
     state give the same bits (also for a lattice whose last tile is partial)."""
     for nx, ny in [(96, 80), (67, 35)]:
-        lat, job = droplet_lattice(nx, ny)
+        lat, job, _ = droplet_lattice(nx, ny)
         tr = B.Trainer(lat, max_epochs=2, mode=B.PL_TRAIN_TC)
         g1, l1 = tr.gradient()
         g2, l2 = tr.gradient()
