@@ -35,7 +35,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-BYTES_PER_UPDATE = {0: 144, 1: 72, 2: 36}   # read + write of 9 populations (8 / 4 / 2 bytes)
+BYTES_PER_UPDATE = {0: 144, 1: 72, 2: 40}   # read + write of 9 populations (8 / 4 / 2 bytes); FP16-offset also its FP16 reference density
 STORAGE_NAME = {0: "f64", 1: "f32", 2: "f16_offset"}
 
 
@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--lattices", type=int, default=256)
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--serve-light-requests", type=int, default=60)
+    ap.add_argument("--serve-light-rate", type=float, default=3.0)
     ap.add_argument("--field-side", type=int, default=4096)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -54,6 +56,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-field", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     ap.add_argument("--train-side", type=int, default=512)
     ap.add_argument("--train-epochs", type=int, default=300)
     return ap.parse_args()
@@ -191,6 +194,95 @@ def cpu_sample(jobs, budget_s):
         if secs > budget_s:
             break
     return upd, secs, done, O.num_threads()
+
+
+def accuracy_record():
+    """The full-length accuracy results (rho rel L-inf, W, mass drift against the FP64 oracle)
+    as recorded by tests/test_gpu_accuracy.py on a GB300 (profiles/accuracy_full_length.json),
+    marked stale if the step kernel's source changed since."""
+    p = os.path.join(ROOT, "profiles", "accuracy_full_length.json")
+    if not os.path.exists(p):
+        return None
+    rec = json.load(open(p))
+    rec["stale"] = rec.get("kernel_sha1") != step_kernel_hash()
+    return rec
+
+
+def oracle_run_rate(job, steps, threads):
+    """MLUPS of the FP64 oracle on `steps` steps of `job` (with its corrections) on `threads`
+    host threads: a bounded sample of the configuration, extrapolated per cell update."""
+    import oracle as O
+    O.set_num_threads(threads)
+    f = O.init_equilibrium(O.init_rho(job.nx, job.ny, job.droplets, job.rho_in, job.rho_out, job.width,
+                                      job.noise_amp, job.seed))
+    M0 = O.mass(f)
+    mode = O.MLP_F64 if job.mlp == 0 else O.MLP_BF16
+    t0 = time.perf_counter()
+    O.run(f, steps, job.G, job.tau, K=job.K, blob=job.weights() if job.K else None, mode=mode,
+          beta_rho=job.beta_rho, beta_u=job.beta_u, M0=M0)
+    dt = time.perf_counter() - t0
+    return job.cells * steps / dt / 1e6, dt
+
+
+CONFIG_CASES = ("C1_single_64_fp64", "C2_single_512_fp32", "C3_field_4096_fp16", "C3_field_4096_fp32")
+
+
+def config_jobs(wl):
+    return {"C1_single_64_fp64": wl.single_64(), "C2_single_512_fp32": wl.single_512(),
+            "C3_field_4096_fp16": wl.field_4096(storage=wl.F16_OFFSET),
+            "C3_field_4096_fp32": wl.field_4096(storage=wl.F32)}
+
+
+def config_runs(B, wl, torch):
+    """Configurations 1-3 as configured, on the GPU: one run each through the single-lattice
+    API (the first interval, which captures the graph, untimed), CUDA events on the lattice's
+    stream."""
+    out = {}
+    jobs = config_jobs(wl)
+    for name in CONFIG_CASES:
+        job = jobs[name]
+        lat = B.Lattice.from_workload(job)
+        lat.run(job.K, job.K)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = job.steps - job.K
+        e0.record(lat.stream)
+        lat.run(steps, job.K)
+        e1.record(lat.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        m = lat.metrics()
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        out[name] = {"workload": "%dx%d %s, %d steps, correction every %d (%s network)"
+                                 % (job.nx, job.ny, STORAGE_NAME[job.storage], job.steps, job.K,
+                                    {0: "FP64", 1: "FP32", 2: "BF16 tcgen05"}[job.mlp]),
+                     "gpu_mlups": job.cells * steps / (ms / 1e3) / 1e6, "gpu_ms": ms, "status": m["status"]}
+    return out
+
+
+def config_oracle_rates(wl):
+    """The FP64 oracle on a bounded sample of each of configurations 1-3, on one host thread and
+    on all of them (per-cell-update rates extrapolated from the sample; the 4096^2 field is
+    sampled on a 512^2 crop of its droplet density)."""
+    jobs = config_jobs(wl)
+    out = {}
+    for name in CONFIG_CASES:
+        if name == "C3_field_4096_fp32":            # the same FP64 computation as the FP16 case
+            out[name] = out["C3_field_4096_fp16"]
+            continue
+        job, n = jobs[name], 100
+        if name.startswith("C1"):
+            n = 200
+        if name.startswith("C3"):
+            job = wl.field_4096(storage=job.storage, side=512, n_drop=6)
+        r1, t1 = oracle_run_rate(job, n, 1)
+        rn, tn = oracle_run_rate(job, n, os.cpu_count() or 1)
+        out[name] = {"oracle_1_thread_mlups": r1, "oracle_all_threads_mlups": rn, "threads": os.cpu_count(),
+                     "sample": "%dx%d, %d steps with its corrections (%.1f s on one thread, %.1f s on all), "
+                               "MLUPS extrapolated per cell update" % (job.nx, job.ny, n, t1, tn)}
+    return out
 
 
 def batch_config(n_lattices, cells, K, world):
@@ -423,25 +515,29 @@ def run_gb300(args):
                                                        "BF16 network, graph per interval",
                 "speedup_batched_f16_over_plain_f32": value / v32}
 
-    # --------------------------------------------------------------- served request stream
+    # --------------------------------------------------------------- served request streams
     serving = None
-    if not args.no_serve and rank == 0:
-        reqs = wl.serve_poisson(n_requests=args.serve_requests, seed=5)
-        srv = S.Server(wl.F16_OFFSET, wl.MLP_BF16, K, 150 * (1 << 30), reqs[0].job.weights(), max_jobs=1024)
-        out = srv.run(reqs, max_wall_s=240.0)
-        srv.close()
-        torch.cuda.empty_cache()
-        serving = {k: out[k] for k in ("jobs_done", "jobs_submitted", "p50_latency_s", "p99_latency_s",
-                                       "p50_queue_wait_s", "served_mlups", "offered_mlups", "elapsed_s",
-                                       "peak_active_jobs")}
-        serving["statuses"] = {str(k): v for k, v in out["statuses"].items()}
-        serving["workload"] = ("Poisson 200 req/s, side U{64..2048 step 32}, 1-8 droplets, G U[-6,-5], "
-                               "steps U[1000,20000] rounded up to K=100, 150 GB budget, %d requests"
-                               % args.serve_requests)
+    if not args.no_serve and rank == 0 and world == 1:
+        serving = {}
+        legs = [("saturated", args.serve_requests, 200.0), ("sub_capacity", args.serve_light_requests,
+                                                            args.serve_light_rate)]
+        for leg, n_req, rate in legs:
+            reqs = wl.serve_poisson(n_requests=n_req, rate_hz=rate, seed=5)
+            srv = S.Server(wl.F16_OFFSET, wl.MLP_BF16, K, 150 * (1 << 30), reqs[0].job.weights(), max_jobs=1024)
+            out = srv.run(reqs, max_wall_s=300.0)
+            srv.close()
+            torch.cuda.empty_cache()
+            rec = {k: out[k] for k in ("jobs_done", "jobs_submitted", "jobs_rejected", "p50_latency_s",
+                                       "p99_latency_s", "p50_queue_wait_s", "p99_queue_wait_s", "served_mlups",
+                                       "offered_mlups", "elapsed_s", "intervals", "peak_active_jobs")}
+            rec["statuses"] = {str(k): v for k, v in out["statuses"].items()}
+            rec["workload"] = ("Poisson %g req/s, side U{64..2048 step 32}, 1-8 droplets, G U[-6,-5], "
+                               "steps U[1000,20000] rounded up to K=100, 150 GB budget, %d requests" % (rate, n_req))
+            serving[leg] = rec
 
     # --------------------------------------------------------------- single 4096^2 field
     field = None
-    if not args.no_field:
+    if not args.no_field and world == 1:
         field = {}
         for st in (wl.F16_OFFSET, wl.F32):
             job = wl.field_4096(storage=st, side=args.field_side)
@@ -468,9 +564,14 @@ def run_gb300(args):
 
     # --------------------------------------------------------------- network training (Eqs. 3-8)
     training = training_tc = None
-    if not args.no_train and rank == 0:
+    if not args.no_train and rank == 0 and world == 1:
         training = train_measurement(args, B, wl, torch, B.PL_TRAIN_SIMT)
         training_tc = train_measurement(args, B, wl, torch, B.PL_TRAIN_TC, cpu=False)
+
+    # --------------------------------------------------------------- configurations 1-3
+    configs = None
+    if not args.no_configs and rank == 0 and world == 1:
+        configs = config_runs(B, wl, torch)
 
     # --------------------------------------------------------------- CPU baseline
     cpu = None
@@ -479,6 +580,8 @@ def run_gb300(args):
         cpu = {"value": upd / secs / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                "sample": "FP64 oracle, one coupling interval (K=100 steps + FP64 network correction + metrics) of "
                          "the %d smallest lattices of the batch (%s), %.1f s" % (len(done), ", ".join(done), secs)}
+        if not args.no_configs:
+            cpu["per_config"] = config_oracle_rates(wl)
 
     if rank == 0:
         line = {
@@ -501,6 +604,8 @@ def run_gb300(args):
             "field_4096": field,
             "training": training,
             "training_tc": training_tc,
+            "configs": configs,
+            "accuracy": accuracy_record(),
             "cpu_baseline": cpu,
             "batch_checks": {"statuses": statuses, "max_mass_drift_post_correction": drift},
         }

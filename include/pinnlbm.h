@@ -60,7 +60,19 @@ extern "C" {
 /* Population storage (bytes per population: 8, 4, 2). */
 #define PL_F64 0        /* FP64 storage, FP64 arithmetic                          */
 #define PL_F32 1        /* FP32 storage, FP32 arithmetic                          */
-#define PL_F16_OFFSET 2 /* FP16 storage of f_i - w_i*rho_ref, FP32 arithmetic     */
+#define PL_F16_OFFSET 2 /* FP16 offsets from each population's source reference,  */
+                        /* FP32 arithmetic (see below)                           */
+
+/* FP16-offset storage (PL_F16_OFFSET; the paper fixes no number format).  A population
+ * buffer holds ten FP16 planes: the offsets h_0..h_8 and the reference densities r.  The
+ * population f_i at cell x is stored relative to the reference density of the cell it
+ * streamed from,
+ *     f_i(x) = h_i(x) + Wr_i * r(x - c_i),  Wr = (1824, 456, 456, 456, 456, 114, 114, 114, 114) / 4096
+ * (Wr = (4104/4096) w, proportional to the lattice weights w; Wr_i * r is exact in FP32).  A
+ * time step writes r(x) = fp16(rho(x)) with the populations cell x pushes, so each offset is
+ * the population's departure from its source cell's rest equilibrium.  The rest population
+ * of each cell takes the cell's mass balance and is rounded stochastically (unbiased); the
+ * moving ones are rounded to nearest.  Bytes per cell update: 2 x (9 + 1) x 2 = 40. */
 
 /* Network arithmetic for the correction. */
 #define PL_MLP_F64 0  /* FP64 on CUDA cores                                        */
@@ -70,7 +82,7 @@ extern "C" {
 #define PL_MAX_DROPLETS 4096
 
 /* Lattice parameters.  G, tau, rho0: Sec. II-A / Sec. III-A (the paper's g and tau);
- * rho_ref: reference density of the FP16-offset storage (ignored otherwise);
+ * rho_ref: unused (FP16-offset storage keeps a reference density per cell); must be finite;
  * beta_rho, beta_u: gains of the interface correction; threshold: the
  * |grad rho| threshold of the interface width W (Eq. 9; the paper uses 0.01). */
 typedef struct pl_params {
@@ -80,7 +92,7 @@ typedef struct pl_params {
     double G;         /* interaction strength (< 0 attracts); the paper: -5.5   */
     double tau;       /* BGK relaxation time, > 0.5; the paper: 1.0             */
     double rho0;      /* pseudopotential scale, > 0                             */
-    double rho_ref;   /* FP16-offset reference density                          */
+    double rho_ref;   /* unused, finite (kept for layout compatibility)         */
     double beta_rho;  /* correction gain on density  (default 0.1)              */
     double beta_u;    /* correction gain on momentum (default 0.01)             */
     double threshold; /* Eq. 9 gradient threshold    (default 0.01)             */
@@ -125,7 +137,7 @@ PL_API int pl_last_cuda_error(void);
  * replay counts each of its kernel nodes), for launch accounting. */
 PL_API int pl_kernel_launches(int64_t* out);
 /* Fill p with the defaults: storage F32, mlp BF16, G=-5.5, tau=1, rho0=1,
- * rho_ref=1.075, beta_rho=0.1, beta_u=0.01, threshold=0.01, size nx x ny. */
+ * rho_ref=1 (unused), beta_rho=0.1, beta_u=0.01, threshold=0.01, size nx x ny. */
 PL_API int pl_params_default(pl_params* p, int32_t nx, int32_t ny);
 
 /* Bytes of caller device memory one lattice with these parameters needs. */
@@ -195,7 +207,9 @@ PL_API int pl_get_mlp_field(pl_lattice* lat, double* host_out3);
 
 /* Checkpoint: the current populations in the exchange format (9*nx*ny FP64) and
  * the step count.  pl_get_state synchronises; pl_set_state encodes into the
- * lattice's storage type (rounding for F32/F16) and sets the step count. */
+ * lattice's storage type (rounding to nearest for F32; for FP16-offset storage the
+ * references r = fp16(rho) with rho summed over i = 0..8 in order in FP64, then
+ * h_i = fp16(f_i - Wr_i r(x - c_i)) computed in FP64) and sets the step count. */
 PL_API int pl_get_state(pl_lattice* lat, double* host_f, int64_t* step);
 PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
 
@@ -208,7 +222,8 @@ PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
  * sum_g, sum_g2 and count (threshold: the gradient threshold that W and count use), the
  * same quantities pl_metrics returns, of populations that the caller passes at dev_pops
  * (device memory, element type given by `storage`, 9 planes of ny rows of `pitch` >= nx
- * elements, x fastest, FP16-offset values h_i = f_i - w_i*rho_ref).  The Laplace fields
+ * elements, x fastest; FP16-offset storage: 10 planes, the offsets h_0..h_8 and the reference
+ * densities, as described at PL_F16_OFFSET; rho_ref is unused).  The Laplace fields
  * and mass0 are NaN, step, status and corrections 0.  The record is written to host memory
  * at `out`.  Its scratch (density field, block partials, record) is a static device array
  * of 8.07 MB that every GPU loading the library keeps until the process exits; the call

@@ -49,7 +49,7 @@ LatLayout lattice_layout(const pl_params* p) {
     size_t o = 0;
     for (int b = 0; b < 2; ++b) {
         L.pops[b] = o;
-        o = align_up(o + 9 * (size_t)L.plane * storage_bytes(p->storage));
+        o = align_up(o + (size_t)planes_of(p->storage) * (size_t)L.plane * storage_bytes(p->storage));
     }
     L.scratch = o;  // rho, jx, jy, g, out3[3]: 7 fields (also >= 8N bytes for FP64 staging)
     o = align_up(o + 7 * N * scratch_elem_bytes(p->storage));
@@ -139,14 +139,17 @@ cudaError_t Table::upload(cudaStream_t s) {
     wp[0] = 0;
     bp[0] = 0;
     tp[0] = 0;
+    int edge = 0;
     for (int j = 0; j < n; ++j) {
         const long long N = (long long)d[j].nx * d[j].ny;
+        edge += f16_edge_lattice(d[j].nx, d[j].plane) ? 1 : 0;
         wp[j + 1] = wp[j] + (long long)d[j].nstrips * d[j].chunks;
         bp[j + 1] = bp[j] + d[j].red_blocks;
         tp[j + 1] = tp[j] + (N + MLP_TILE - 1) / MLP_TILE;
     }
-    TabHeader h;
+    TabHeader h{};
     h.n = n;
+    h.edge_lattices = edge;
     h.total_warps = wp[n];
     h.total_blocks = bp[n];
     h.total_tiles = tp[n];
@@ -257,7 +260,7 @@ int pl_params_default(pl_params* p, int32_t nx, int32_t ny) {
     p->G = -5.5;
     p->tau = 1.0;
     p->rho0 = 1.0;
-    p->rho_ref = 1.075;
+    p->rho_ref = 1.0;
     p->beta_rho = 0.1;
     p->beta_u = 0.01;
     p->threshold = 0.01;
@@ -394,7 +397,7 @@ int pl_init_mlp_weights(pl_lattice* L, uint64_t seed) {
 
 static int do_steps(pl_lattice* L, int n) {
     for (int k = 0; k < n; ++k) {
-        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, L->cur, L->stream));
+        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, L->cur, L->stream, f16_edge_lattice(L->p.nx, L->v.plane)));
         L->cur ^= 1;
     }
     L->step += n;
@@ -419,7 +422,7 @@ int pl_apply_correction(pl_lattice* L) {
 static int enqueue_run(pl_lattice* L, int nsteps, int K, long long step0, int parity) {
     int cur = parity;
     for (int s = 1; s <= nsteps; ++s) {
-        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, cur, L->stream));
+        PL_CUDA(launch_step_tab(L->tab.view, L->p.storage, cur, L->stream, f16_edge_lattice(L->p.nx, L->v.plane)));
         cur ^= 1;
         if (K > 0 && ((step0 + s) % K) == 0)
             PL_CUDA(launch_correction_tab(L->tab.view, L->p.storage, cur, L->p.mlp, L->p.mlp_in, L->w32, L->wbf16, L->stream));
@@ -596,6 +599,17 @@ int pl_set_state(pl_lattice* L, const double* host_f, int64_t step) {
     double* staging = static_cast<double*>(L->v.rho);
     const int fresh = !L->initialised;
     if (fresh) PL_CUDA(cudaMemsetAsync(L->v.rec, 0, sizeof(DevRecord), L->stream));
+    if (L->p.storage == PL_F16_OFFSET) {
+        // the density of the given state (planes summed in order 0..8, FP64) sets the reference
+        // plane the populations are then encoded against; the scratch holds both arrays
+        double* acc = staging + N;
+        for (int i = 0; i < 9; ++i) {
+            PL_CUDA(cudaMemcpyAsync(staging, host_f + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice,
+                                    L->stream));
+            PL_CUDA(launch_state_accumulate(L->v, acc, staging, i == 0, L->stream));
+        }
+        PL_CUDA(launch_state_ref(L->v, L->cur, acc, L->stream));
+    }
     for (int i = 0; i < 9; ++i) {
         PL_CUDA(cudaMemcpyAsync(staging, host_f + (size_t)i * N, N * sizeof(double), cudaMemcpyHostToDevice, L->stream));
         PL_CUDA(launch_state_convert(L->v, L->phys, L->cur, staging, i, 0, L->stream));

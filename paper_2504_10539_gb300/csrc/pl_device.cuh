@@ -41,16 +41,64 @@ template <> struct Traits<PL_F16_OFFSET> {
     using R = float;
 };
 
-// Decode / encode one population.  FP16-offset stores h_i = rn(f_i - w_i rho_ref).
+// Stored value <-> arithmetic value of FP64 / FP32 storage (the identity).  FP16-offset
+// storage decodes with its reference plane (below), never through these.
 template <int MODE>
-__device__ __forceinline__ typename Traits<MODE>::R decode(typename Traits<MODE>::S v, typename Traits<MODE>::R off) {
-    if constexpr (MODE == PL_F16_OFFSET) return __half2float(v) + off;
-    else return v;
+__device__ __forceinline__ typename Traits<MODE>::R decode(typename Traits<MODE>::S v) {
+    static_assert(MODE != PL_F16_OFFSET, "FP16-offset populations decode with their source's reference");
+    return v;
 }
 template <int MODE>
-__device__ __forceinline__ typename Traits<MODE>::S encode(typename Traits<MODE>::R v, typename Traits<MODE>::R off) {
-    if constexpr (MODE == PL_F16_OFFSET) return __float2half_rn(v - off);
-    else return v;
+__device__ __forceinline__ typename Traits<MODE>::S encode(typename Traits<MODE>::R v) {
+    static_assert(MODE != PL_F16_OFFSET, "FP16-offset populations encode against a reference");
+    return v;
+}
+
+// FP16-offset storage (a storage measure of this implementation; the paper states no number
+// format).  A buffer holds ten FP16 planes: h_0..h_8 and the reference densities r.  The
+// population f_i at cell x is stored relative to the reference density of the cell it
+// streamed from:
+//     f_i(x) = h_i(x) + Wr_i r(x - c_i),
+// and a step stores r(x) = fp16(rho(x)) with the populations x pushes, so each offset is the
+// departure of f_i from its source cell's rest equilibrium (velocity and non-equilibrium
+// terms only, a few per cent of f_i).  Wr_i = kappa w_i = (1824, 456 x4, 114 x4) / 4096 with
+// kappa = 4104/4096: proportional to the lattice weights (so the offset folds into the
+// equilibrium's isotropic part) and short binary fractions (so Wr_i r and kappa r are exact
+// in FP32 for an FP16 r).  A cell's decoded populations carry sum h_i + kappa r(x).
+constexpr int F16_PLANES = 10;   // h_0..h_8, r
+constexpr int REF_PLANE = 9;
+constexpr float REF_KAPPA = 4104.0f / 4096.0f;
+__host__ __device__ constexpr float wref(int i) {
+    return i == 0 ? 1824.0f / 4096.0f : (i <= 4 ? 456.0f / 4096.0f : 114.0f / 4096.0f);
+}
+__host__ __device__ constexpr int planes_of(int storage) { return storage == PL_F16_OFFSET ? F16_PLANES : 9; }
+
+// One FP16-offset cell (x, y) of a buffer f (ten planes of `plane` elements, rows of `pitch`):
+// its offsets h_i and reference terms t_i = Wr_i r(x - c_i) (exact products), so that
+// f_i = h_i + t_i and the cell's mass is A + H with A = sum t_i, H = sum h_i.
+__device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long plane, int pitch, int nx, int ny, int x,
+                                         int y, float (&h)[9], float (&t)[9]) {
+    const long long o = (long long)y * pitch + x;
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const long long rm = (long long)(y == 0 ? ny - 1 : y - 1) * pitch, r0 = (long long)y * pitch,
+                    rp = (long long)(y == ny - 1 ? 0 : y + 1) * pitch;
+    const __half* ref = f + REF_PLANE * plane;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = __half2float(f[i * plane + o]);
+    t[0] = wref(0) * __half2float(ref[r0 + x]);
+    t[1] = wref(1) * __half2float(ref[r0 + xm]);  // c_1 = (1, 0): from x - 1
+    t[2] = wref(2) * __half2float(ref[rm + x]);   // c_2 = (0, 1): from y - 1
+    t[3] = wref(3) * __half2float(ref[r0 + xp]);
+    t[4] = wref(4) * __half2float(ref[rp + x]);
+    t[5] = wref(5) * __half2float(ref[rm + xm]);  // c_5 = (1, 1)
+    t[6] = wref(6) * __half2float(ref[rm + xp]);  // c_6 = (-1, 1)
+    t[7] = wref(7) * __half2float(ref[rp + xp]);  // c_7 = (-1, -1)
+    t[8] = wref(8) * __half2float(ref[rp + xm]);  // c_8 = (1, -1)
+}
+// Sums of nine terms in the walker's order.
+template <typename R>
+__device__ __forceinline__ R sum9(const R (&v)[9]) {
+    return (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
 }
 
 __device__ __forceinline__ float psi_of(float rho, float rho0, float inv_rho0) {
@@ -88,19 +136,27 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     return h;
 }
 
-// Stochastic rounding of two FP32 values to FP16, packed (a -> low half, b -> high half):
-// 13 dither bits are added below the FP16 mantissa's last bit and the result is truncated,
-// so E[rounded] = value for values in the normal FP16 range (|v| >= 2^-14).  Bits 0-12 of
-// rnd dither a, bits 16-28 dither b.
-__device__ __forceinline__ __half2 sr_pack_half2(float a, float b, uint32_t rnd) {
-    const float da = __uint_as_float(__float_as_uint(a) + (rnd & 0x1FFFu));
-    const float db = __uint_as_float(__float_as_uint(b) + ((rnd >> 16) & 0x1FFFu));
+// Stochastic rounding of FP32 values to FP16 (a -> low half, b -> high half of the packed
+// result).  Uniform dither bits are added to the magnitude below the bit of the FP32 value
+// that is the FP16 result's last place, and the sum is truncated toward zero, so that
+// E[rounded] = value.  That place is 13 bits up from the FP32 last place for FP16 normals
+// (|v| >= 2^-14) and 2^-24, higher up, for FP16 subnormals; values below 2^-22 use 22
+// dither bits (a bias below 2^-24 for them).  A carry out of the mantissa moves to the next
+// binade, which truncation handles as well.
+__device__ __forceinline__ uint32_t sr_dither(float v, uint32_t rnd) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFFu) - 127;
+    const int p = min(max(-1 - e, 13), 22);
+    return b + (rnd & ((1u << p) - 1u));
+}
+__device__ __forceinline__ __half2 sr_pack_half2(float a, float b, uint32_t ra, uint32_t rb) {
     uint32_t r;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(db), "f"(da));
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(sr_dither(b, rb))),
+        "f"(__uint_as_float(sr_dither(a, ra))));
     return *reinterpret_cast<__half2*>(&r);
 }
 __device__ __forceinline__ __half sr_half(float a, uint32_t rnd) {
-    return __float2half_rz(__uint_as_float(__float_as_uint(a) + (rnd & 0x1FFFu)));
+    return __float2half_rz(__uint_as_float(sr_dither(a, rnd)));
 }
 
 // Per-lattice device record: reductions land here, later kernels read them,
@@ -115,7 +171,6 @@ struct DevRecord {
     double mass0;        // M0
     double sum_m, sum_dr, sum_jx, sum_jy, mass_now;
     double proj, mjx, mjy;  // per-lattice constants of the apply pass (formed once, in FP64)
-    long long fix_n;        // FP16 mass restoration: signed number of rest populations shifted by one unit
     int status;          // sticky PL_ERR_* detected on the device
     int reject;          // set by the correction check pass, cleared per correction
     int applied;         // corrections applied

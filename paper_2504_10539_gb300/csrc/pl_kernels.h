@@ -67,6 +67,9 @@ struct TabHeader {
     int total_blocks;       // sum of red_blocks
     long long total_warps;  // sum of nstrips * chunks
     long long total_tiles;  // sum of ceil(nx*ny / 128)
+    int edge_lattices;      // lattices whose FP16 step has strips off the vector path (odd nx,
+                            // or ten planes beyond 32-bit element offsets)
+    int pad;
 };
 
 // Device arrays of a table (capacity cap lattices; prefix arrays have cap+1 entries).
@@ -98,11 +101,21 @@ cudaError_t launch_init_droplets(const LatticeView& v, const PhysParams& p, int 
 cudaError_t launch_init_from_rho(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho,
                                  cudaStream_t s);
 // Convert population plane `plane` of buffer `cur` to (to_f64=1) or from (0) the FP64 array d_buf[nx*ny].
+// FP16-offset storage encodes against the buffer's reference plane, which launch_state_ref sets
+// from the density of the state first.
 cudaError_t launch_state_convert(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int plane,
                                  int to_f64, cudaStream_t s);
+// d_acc = d_buf (first) or d_acc + d_buf (the density of a state uploaded plane by plane).
+cudaError_t launch_state_accumulate(const LatticeView& v, double* d_acc, const double* d_buf, int first, cudaStream_t s);
+// FP16-offset storage: the reference plane of buffer `cur` from the FP64 density d_rho (no-op otherwise).
+cudaError_t launch_state_ref(const LatticeView& v, int cur, const double* d_rho, cudaStream_t s);
 
-// Table kernels (all lattices of a table share `storage`).
-cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s);
+// Table kernels (all lattices of a table share `storage`).  FP16-offset storage runs the strips
+// off the vector path in a second kernel when `edge` is set (set it when the table may hold
+// a lattice with odd nx: always for a batch, whose table changes under a captured graph).
+cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s, bool edge = true);
+// Whether a lattice's FP16 step can have strips off the vector path.
+__host__ __device__ inline bool f16_edge_lattice(int nx, long long plane) { return (nx & 1) || 10ll * plane > 0xFFFFFFFFll; }
 // Metrics of every lattice: moments, Eq. 16 gradient, Eqs. 9-15 sums (+ Laplace where defined).
 cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
                                cudaStream_t s);

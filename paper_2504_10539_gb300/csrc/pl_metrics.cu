@@ -286,7 +286,6 @@ __global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity)
         R* rho = static_cast<R*>(d.rho);
         R* jx = static_cast<R*>(d.jx);
         R* jy = static_cast<R*>(d.jy);
-        const R rho_ref = R(d.rho_ref);
         const long long N = (long long)d.nx * d.ny;
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
@@ -294,18 +293,17 @@ __global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity)
             const long long o = it.pop_offset(d.pitch);
             R P[9];
             if constexpr (MODE == PL_F16_OFFSET) {
-                // sum the stored offsets (exact to 2^-24 here) and add rho_ref once: decoding
-                // each population first would add nine roundings per cell, the same in every
-                // cell of a uniform phase, i.e. a bias of ~1e-7 in the lattice mass
+                // f_i = h_i + t_i; the mass as the sum of the two exact-where-possible parts
+                float h[9], tt[9];
+                f16_cell(f, d.plane, d.pitch, d.nx, d.ny, it.x, it.y, h, tt);
+                rho[c] = sum9(tt) + sum9(h);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) P[i] = __half2float(f[i * d.plane + o]);
-                rho[c] = ((((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7]))) + P[8]) + rho_ref;
+                for (int i = 0; i < 9; ++i) P[i] = h[i] + tt[i];
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o], wq<R>(i) * rho_ref);
+                for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o]);
                 rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
             }
-            // sum_i c_i f_i: the offsets w_i rho_ref have no first moment
             jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
             jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
         }
@@ -703,19 +701,11 @@ __device__ __forceinline__ void feq9(R rho, R ux, R uy, R (&fe)[9]) {
     }
 }
 
-// FP16 mass restoration (below): one FP16 unit of the binade [1/4, 1/2), and the rest
-// populations that can move by exactly one unit without leaving it.
-constexpr float FIX_U = 1.0f / 4096.0f;
-
-__device__ __forceinline__ bool fix_candidate(__half h) {
-    const float a = fabsf(__half2float(h));
-    return a >= 0.25f + FIX_U && a <= 0.5f - FIX_U;
-}
-
-// FP16-offset lattices also accumulate, per block, the stored mass of the corrected state
-// (per cell in FP32 - nine FP16 offsets below 2 in magnitude sum there to within 2^-24 - then
-// error-free pair sums over cells) and the number of restoration candidates, into partial
-// slots 0 and 1, for the mass restoration that follows.
+// The correction changes the populations of a corrected cell by f_i^eq(rho', u') - f_i^eq(rho, u).
+// FP16-offset storage applies it to the stored offsets directly (the references, and with
+// them the decoding, stay as they are): the moving offsets are rounded to nearest, the rest
+// offset takes the cell's corrected mass minus their rounded values and is rounded
+// stochastically, so small changes are realised on average instead of being rounded away.
 template <int MODE>
 __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_corr_apply(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
@@ -736,8 +726,6 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
         S* f = static_cast<S*>(d.pops[d.phase ^ parity]);
         const R sjx = R(rec->mjx), sjy = R(rec->mjy);
         const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u);
-        SumAcc<float> stored;  // FP16 only: stored mass after the correction, and candidates
-        unsigned cand = 0;
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
             const long long c = it.c;
@@ -747,16 +735,7 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
             S fs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) fs[i] = f[i * d.plane + o];
-            if (!(in.g > R(0))) {
-                if constexpr (MODE == PL_F16_OFFSET) {
-                    float sc = 0.0f;
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) sc += __half2float(fs[i]);
-                    stored.add(sc);
-                    cand += fix_candidate(fs[0]) ? 1u : 0u;
-                }
-                continue;
-            }
+            if (!(in.g > R(0))) continue;
             const CellCorr<R> q = cell_corr(in, k);
             const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
             const R r = in.r, jxc = in.jx, jyc = in.jy;
@@ -764,130 +743,22 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
             feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
             feq9<R>(r, jxc / r, jyc / r, fo);
             if constexpr (MODE == PL_F16_OFFSET) {
-                // stored offsets h_i + (f_i^eq' - f_i^eq): the moving populations rounded to
-                // nearest, the rest population taking the cell's corrected stored mass minus their
-                // rounded values and rounded stochastically, so that small per-cell changes
-                // (below half an FP16 step) are realised on average instead of being rounded away
                 float hn[9];
-                float res = 0.0f, sq = 0.0f;
+                float res = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hn[i] = __half2float(fs[i]) + (fn[i] - fo[i]);
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const __half qh = __float2half_rn(hn[i]);
-                    const float qf = __half2float(qh);
-                    res += qf - hn[i];
-                    sq += qf;
+                    res += __half2float(qh) - hn[i];
                     f[i * d.plane + o] = qh;
                 }
                 const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u) ^
                                             ((seq - d.seq0) * 0x27D4EB2Fu));
-                const __half h0 = sr_half(hn[0] - res, rnd);
-                f[o] = h0;
-                stored.add(sq + __half2float(h0));
-                cand += fix_candidate(h0) ? 1u : 0u;
+                f[o] = sr_half(hn[0] - res, rnd);
             } else {
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const R off = R(wq<double>(i) * d.rho_ref);
-                    const R fi = decode<MODE>(fs[i], off);
-                    f[i * d.plane + o] = encode<MODE>(fi + (fn[i] - fo[i]), off);
-                }
-            }
-        }
-        if constexpr (MODE == PL_F16_OFFSET) {
-            __shared__ double sm[2 * 32];
-            const int op[2] = {0, 0};
-            double v[2] = {stored.value(), (double)cand};
-            block_reduce<2>(v, op, sm);
-            if (threadIdx.x == 0) {
-                d.partials[m.lb * PARTIAL_STRIDE + 0] = v[0];
-                d.partials[m.lb * PARTIAL_STRIDE + 1] = v[1];
-            }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// FP16-offset storage: mass restoration after a correction (a storage measure of this
-// implementation; the paper has no reduced-precision storage).  The projection returns the
-// mass to M0 in exact arithmetic, but the apply pass stores each corrected rest population
-// with one stochastic rounding, which leaves the stored mass off by a zero-mean sum of about
-// ulp * sqrt(cells).  Shifting the stored rest population h_0 of n cells by one FP16 unit
-// u = 2^-12 is exact when 1/4 + u <= |h_0| <= 1/2 - u (the value stays in the binade
-// [1/4, 1/2], whose spacing is u), so n = round((M - M0) / u) such shifts restore the mass to
-// within u/2.  The n cells are the first candidates in a fixed order: by reduction block,
-// within a block by thread, within a thread by loop index; the result is deterministic and
-// the same for a lattice alone or in a batch.
-
-
-__device__ __forceinline__ bool fix_active(const DevRecord* rec) { return !rec->reject && rec->sum_m > 0.0; }
-
-// One thread per lattice (after the apply pass has left the stored sum and the candidates
-// of each block in partial slots 0 and 1): stored mass M = sum h + N rho_ref, n = round((M - M0)/u)
-// (limited by the candidates available), and each block's first candidate index.
-__global__ void k_fix_final(TableView t) {
-    const int n = t.hdr->n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const LatDesc& d = t.d[j];
-        DevRecord* rec = d.rec;
-        rec->fix_n = 0;
-        if (!fix_active(rec)) continue;
-        double sum_h = 0.0, cand = 0.0;
-        for (int b = 0; b < d.red_blocks; ++b) {
-            sum_h += d.partials[b * PARTIAL_STRIDE + 0];
-            d.partials[b * PARTIAL_STRIDE + 2] = cand;  // candidates before block b
-            cand += d.partials[b * PARTIAL_STRIDE + 1];
-        }
-        // the offsets are relative to the FP32 reference density the kernels use
-        const double M = sum_h + (double)d.nx * (double)d.ny * (double)(float)d.rho_ref;
-        long long k = llrint((M - rec->mass0) / (double)FIX_U);
-        const long long c = (long long)cand;
-        if (k > c) k = c;
-        if (k < -c) k = -c;
-        rec->fix_n = k;
-    }
-}
-
-// Shift the chosen rest populations by -sign(n) u.
-__global__ void __launch_bounds__(RB_THREADS) k_fix_apply(TableView t, int parity) {
-    __shared__ unsigned scan[RB_THREADS];
-    const int n = t.hdr->n, total = t.hdr->total_blocks;
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
-        const BlkMap m = map_blk(t, n, vb);
-        const LatDesc& d = t.d[m.j];
-        const long long k = d.rec->fix_n;
-        if (k == 0 || !fix_active(d.rec)) continue;
-        const long long kk = k < 0 ? -k : k;
-        const long long before = (long long)d.partials[m.lb * PARTIAL_STRIDE + 2];
-        const long long mine = (long long)d.partials[m.lb * PARTIAL_STRIDE + 1];
-        long long quota = kk - before;
-        if (quota <= 0) continue;                   // uniform over the block
-        if (quota > mine) quota = mine;
-        __half* f = static_cast<__half*>(d.pops[d.phase ^ parity]);
-        const long long N = (long long)d.nx * d.ny;
-        const long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x, stride = (long long)d.red_blocks * RB_THREADS;
-        unsigned cnt = 0;
-        for (CellIt it(c0, stride, d.nx); it.c < N; it.next(d.nx)) cnt += fix_candidate(f[it.pop_offset(d.pitch)]) ? 1u : 0u;
-        // exclusive scan of the per-thread counts (Hillis-Steele in shared memory)
-        scan[threadIdx.x] = cnt;
-        __syncthreads();
-        for (int off = 1; off < RB_THREADS; off <<= 1) {
-            const unsigned add = threadIdx.x >= off ? scan[threadIdx.x - off] : 0u;
-            __syncthreads();
-            scan[threadIdx.x] += add;
-            __syncthreads();
-        }
-        const long long first = (long long)scan[threadIdx.x] - cnt;   // candidates of lower threads
-        __syncthreads();
-        long long take = quota - first;
-        if (take > (long long)cnt) take = cnt;
-        const float du = k > 0 ? -FIX_U : FIX_U;
-        for (CellIt it(c0, stride, d.nx); it.c < N && take > 0; it.next(d.nx)) {
-            __half* h0 = f + it.pop_offset(d.pitch);
-            if (fix_candidate(*h0)) {
-                *h0 = __float2half_rn(__half2float(*h0) + du);
-                --take;
+                for (int i = 0; i < 9; ++i) f[i * d.plane + o] = encode<MODE>(decode<MODE>(fs[i]) + (fn[i] - fo[i]));
             }
         }
     }
@@ -908,11 +779,6 @@ static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, in
     k_corr_final2<<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_corr_apply<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
     note_launches(8);
-    if constexpr (MODE == PL_F16_OFFSET) {
-        k_fix_final<<<(RED_GRID + 127) / 128, 128, 0, s>>>(t);
-        k_fix_apply<<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
-        note_launches(2);
-    }
     return cudaGetLastError();
 }
 
@@ -977,27 +843,27 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 // Density of every cell from populations in the library's layout, into a dense array.
 template <int MODE>
 __global__ void k_density_noalloc(const typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch,
-                                  long long plane, typename Traits<MODE>::R rho_ref,
-                                  typename Traits<MODE>::R* __restrict__ rho) {
+                                  long long plane, typename Traits<MODE>::R* __restrict__ rho) {
     using R = typename Traits<MODE>::R;
     const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const long long o = (c / nx) * pitch + c % nx;
-        R P[9];
-        if constexpr (MODE == PL_F16_OFFSET) {  // offsets summed first, rho_ref added once
-#pragma unroll
-            for (int i = 0; i < 9; ++i) P[i] = __half2float(f[i * plane + o]);
-            rho[c] = ((((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7]))) + P[8]) + rho_ref;
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        if constexpr (MODE == PL_F16_OFFSET) {
+            float h[9], tt[9];
+            f16_cell(f, plane, pitch, nx, ny, x, y, h, tt);
+            rho[c] = sum9(tt) + sum9(h);
         } else {
+            const long long o = (long long)y * pitch + x;
+            R P[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o], wq<R>(i) * rho_ref);
+            for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * plane + o]);
             rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
         }
     }
 }
 
 template <int MODE>
-static void metrics_noalloc_t(const void* pops, int nx, int ny, int pitch, double rho_ref, double threshold,
+static void metrics_noalloc_t(const void* pops, int nx, int ny, int pitch, double threshold,
                               unsigned char* scratch, DevRecord* rec, cudaStream_t s) {
     using S = typename Traits<MODE>::S;
     using R = typename Traits<MODE>::R;
@@ -1007,7 +873,7 @@ static void metrics_noalloc_t(const void* pops, int nx, int ny, int pitch, doubl
     R* rho = reinterpret_cast<R*>(scratch);
     double* partials = reinterpret_cast<double*>(scratch + NOALLOC_RHO_BYTES);
     k_density_noalloc<MODE><<<(int)nb, RB_THREADS, 0, s>>>(static_cast<const S*>(pops), nx, ny, pitch,
-                                                           (long long)pitch * ny, R(rho_ref), rho);
+                                                           (long long)pitch * ny, rho);
     k_grad_reduce<R><<<(int)nb, RB_THREADS, 0, s>>>(rho, nx, ny, nullptr, threshold, partials);
     k_final_metrics<<<1, RB_THREADS, 0, s>>>(partials, (int)nb, rec, 0);
     note_launches(3);
@@ -1044,9 +910,9 @@ extern "C" PL_API int pl_metrics_noalloc(const void* dev_pops, int32_t nx, int32
     e = cudaMemsetAsync(rec, 0, sizeof(DevRecord), s);  // the record starts at zero on every call
     if (e == cudaSuccess) {
         switch (storage) {
-            case PL_F64: metrics_noalloc_t<PL_F64>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
-            case PL_F32: metrics_noalloc_t<PL_F32>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
-            default: metrics_noalloc_t<PL_F16_OFFSET>(dev_pops, nx, ny, pitch, rho_ref, threshold, scratch, rec, s); break;
+            case PL_F64: metrics_noalloc_t<PL_F64>(dev_pops, nx, ny, pitch, threshold, scratch, rec, s); break;
+            case PL_F32: metrics_noalloc_t<PL_F32>(dev_pops, nx, ny, pitch, threshold, scratch, rec, s); break;
+            default: metrics_noalloc_t<PL_F16_OFFSET>(dev_pops, nx, ny, pitch, threshold, scratch, rec, s); break;
         }
         e = cudaGetLastError();
     }

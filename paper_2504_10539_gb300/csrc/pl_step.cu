@@ -2,17 +2,14 @@
 // of the initial state (Sec. III-A).
 //
 // Storage: structure of arrays, 9 planes of ny rows of `pitch` populations
-// (x fastest, pitch = nx rounded up to 8), two buffers: a step reads the
-// post-streaming state of buffer src and writes the next post-streaming state
-// into buffer 1-src ("push").  Reads never alias writes, so neighbouring strips
-// may recompute each other's densities without racing.
+// (x fastest, pitch = nx rounded up to 8; FP16-offset storage adds a tenth plane of
+// reference densities), two buffers: a step reads the post-streaming state of buffer src
+// and writes the next post-streaming state into buffer 1-src ("push").  Reads never alias
+// writes, so neighbouring strips may recompute each other's densities without racing.
 //
-// FP16-offset storage keeps h_i = f_i - w_i rho_ref.  The step works on the
-// offsets directly: rho = sum h_i + rho_ref (the weights sum to one), the
-// momentum is sum c_i h_i (the offsets cancel), and the relaxation
-// h_i* = h_i + omega (f_i^eq - w_i rho_ref - h_i) needs the equilibrium minus the
-// same offset, which folds into its isotropic part.  FP32/FP64 storage is the
-// same code with rho_ref = 0.
+// FP16-offset storage (pl_device.cuh) keeps each population as an FP16 offset from the rest
+// equilibrium of the cell it streamed from; the FP16 walker (walk_f16) decodes against those
+// references, relaxes in FP32 and encodes against the relaxed cell's own new reference.
 //
 // Fused step kernel ("strip walker"), one pass over HBM per step:
 //   - a warp owns a strip of 60 columns; lane l holds the column pair
@@ -40,9 +37,12 @@ namespace pl {
 // FP32/FP64: blocks of four warps, 4 (FP32) or 2 (FP64) of them per SM, the occupancy their
 // register counts give anyway (FP32 is bound by HBM; one-warp blocks were slower there).
 template <int MODE>
+#ifndef PL_F16_MIN_BLOCKS
+#define PL_F16_MIN_BLOCKS 17
+#endif
 struct StepCfg {
     static constexpr int threads = MODE == PL_F16_OFFSET ? 32 : 128;
-    static constexpr int min_blocks = MODE == PL_F16_OFFSET ? 17 : (MODE == PL_F32 ? 4 : 2);
+    static constexpr int min_blocks = MODE == PL_F16_OFFSET ? PL_F16_MIN_BLOCKS : (MODE == PL_F32 ? 4 : 2);
 };
 
 template <int MODE> struct Pair;
@@ -99,10 +99,10 @@ __device__ __forceinline__ typename Traits<MODE>::R recip(typename Traits<MODE>:
 
 template <typename R>
 struct StepK {
-    R G, tau, omega, rho0, inv_rho0, rho_ref;
+    R G, tau, omega, rho0, inv_rho0;
 };
 
-// One cell: populations h[9] (offset space), density rho, force (fx, fy) -> o[9].
+// One cell: populations h[9], density rho, force (fx, fy) -> o[9].
 template <int MODE>
 __device__ __forceinline__ void collide_cell(const typename Traits<MODE>::R (&h)[9], typename Traits<MODE>::R rho,
                                              typename Traits<MODE>::R fx, typename Traits<MODE>::R fy,
@@ -114,7 +114,7 @@ __device__ __forceinline__ void collide_cell(const typename Traits<MODE>::R (&h)
     const R inv = recip<MODE>(rho);
     const R ux = (jx + k.tau * fx) * inv;  // u + tau F / rho
     const R uy = (jy + k.tau * fy) * inv;
-    const R Ap = rho * (R(1) - R(1.5) * (ux * ux + uy * uy)) - k.rho_ref;
+    const R Ap = rho * (R(1) - R(1.5) * (ux * ux + uy * uy));
     const R t3 = R(3) * rho, t45 = R(4.5) * rho;
     const R w0 = R(4.0 / 9.0), w1 = R(1.0 / 9.0), w2 = R(1.0 / 36.0);
     const R pp = ux + uy, pm = ux - uy;
@@ -200,7 +200,7 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
     PT Nx[9];
     load_row<MODE>(a, wrapi(r0 - 1, ny), cA, cB, vec, Nx);
     R hp[2][9];           // previous row (to be relaxed), decoded
-    R rho_p0 = 0, rho_p1 = 0, sh_p0 = 0, sh_p1 = 0;
+    R rho_p0 = 0, rho_p1 = 0;
     PsiRow<R> A{}, B{}, C{};
     const int nrows = r1 - r0;
     for (int k = 0; k <= nrows + 1; ++k) {
@@ -215,13 +215,11 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
         R hc[2][9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) Pair<MODE>::split(Cur[i], hc[0][i], hc[1][i]);
-        // stored (offset-space) sums of the two cells, and their densities
-        const R sh0c = (((hc[0][0] + hc[0][1]) + (hc[0][2] + hc[0][3])) + ((hc[0][4] + hc[0][5]) + (hc[0][6] + hc[0][7])) +
-                        hc[0][8]);
-        const R sh1c = (((hc[1][0] + hc[1][1]) + (hc[1][2] + hc[1][3])) + ((hc[1][4] + hc[1][5]) + (hc[1][6] + hc[1][7])) +
-                        hc[1][8]);
-        const R rho0c = sh0c + a.k.rho_ref;
-        const R rho1c = sh1c + a.k.rho_ref;
+        // densities of the two cells
+        const R rho0c = (((hc[0][0] + hc[0][1]) + (hc[0][2] + hc[0][3])) + ((hc[0][4] + hc[0][5]) + (hc[0][6] + hc[0][7])) +
+                         hc[0][8]);
+        const R rho1c = (((hc[1][0] + hc[1][1]) + (hc[1][2] + hc[1][3])) + ((hc[1][4] + hc[1][5]) + (hc[1][6] + hc[1][7])) +
+                         hc[1][8]);
         A = B;
         B = C;
         C.a = psi_step<MODE>(rho0c, a.k.rho0, a.k.inv_rho0);
@@ -245,43 +243,9 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
                 const R g = -a.k.G * B.b;
                 collide_cell<MODE>(hp[1], rho_p1, g * sx, g * sy, a.k, o[1]);
             }
-            if constexpr (MODE == PL_F32) {
-                // BGK conserves mass; take the rest population from that balance so the
-                // FP32 weights (which do not sum to one exactly) leave no systematic drift.
-                o[0][0] = sh_p0 - ((((o[0][1] + o[0][2]) + (o[0][3] + o[0][4])) + ((o[0][5] + o[0][6]) + (o[0][7] + o[0][8]))));
-                o[1][0] = sh_p1 - ((((o[1][1] + o[1][2]) + (o[1][3] + o[1][4])) + ((o[1][5] + o[1][6]) + (o[1][7] + o[1][8]))));
-            }
-            __half2 rest16;
-            if constexpr (MODE == PL_F16_OFFSET) {
-                // Mass-conserving FP16 storage: the 8 moving populations are rounded to
-                // nearest; the rest population takes the cell's stored mass minus their
-                // rounded values, and is rounded stochastically (unbiased), so the stored
-                // mass changes by one zero-mean rounding per cell and step.
-                float q0 = 0.0f, q1 = 0.0f;
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    const float2 q = __half22float2(__floats2half2_rn(o[0][i], o[1][i]));
-                    q0 += q.x;
-                    q1 += q.y;
-                }
-                const uint32_t rnd = fmix32(__float_as_uint(hp[0][0]) ^ (__float_as_uint(hp[1][1]) * 0x9E3779B1u) ^
-                                            ((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^
-                                            (a.seq * 0x27D4EB2Fu));
-                rest16 = sr_pack_half2(sh_p0 - q0, sh_p1 - q1, rnd);
-            }
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             // c_x = 0 planes: own pair
-            if constexpr (MODE == PL_F16_OFFSET) {
-                __half* p = a.fout + (long long)y * a.pitch + ua;
-                if (svec) {
-                    *reinterpret_cast<__half2*>(p) = rest16;
-                } else {
-                    if (own0) p[0] = __low2half(rest16);
-                    if (own1) p[1] = __high2half(rest16);
-                }
-            } else {
-                store_pair<MODE>(a, 0, y, ua, svec, own0, own1, o[0][0], o[1][0]);
-            }
+            store_pair<MODE>(a, 0, y, ua, svec, own0, own1, o[0][0], o[1][0]);
             store_pair<MODE>(a, 2, yp, ua, svec, own0, own1, o[0][2], o[1][2]);
             store_pair<MODE>(a, 4, ym, ua, svec, own0, own1, o[0][4], o[1][4]);
             // c_x = +1 planes: (left lane's second cell, own first cell)
@@ -310,8 +274,6 @@ __device__ void walk_segment(const WalkArgs<MODE>& a, int strip, int r0, int r1,
         }
         rho_p0 = rho0c;
         rho_p1 = rho1c;
-        sh_p0 = sh0c;
-        sh_p1 = sh1c;
     }
 }
 
@@ -371,17 +333,20 @@ __device__ __forceinline__ float2 psi2(float2 rho, const StepK<float>& k) {
     }
 }
 
-// Both cells of a pair: populations h[9] (offset space), density rho, force (fx, fy) -> o[9].
-template <int MODE>
+// Both cells of a pair: populations h[9], density rho, force (fx, fy) -> o[9].
+// `shift` (FP16-offset storage: kappa r of the relaxed cell over omega) is subtracted from the
+// equilibrium's isotropic part, so that o_i = f_i* - omega w_i shift for every i.
+template <int MODE, bool SHIFT = false>
 __device__ __forceinline__ void collide_pair(const float2 (&h)[9], float2 rho, float2 fx, float2 fy,
-                                             const StepK<float>& k, float2 (&o)[9]) {
+                                             const StepK<float>& k, float2 (&o)[9], float2 shift = float2{0.0f, 0.0f}) {
     const float2 jx = ((h[1] - h[3]) + (h[5] - h[6])) + (h[8] - h[7]);
     const float2 jy = ((h[2] - h[4]) + (h[5] + h[6])) - (h[7] + h[8]);
     const float2 inv = make_float2(recip<MODE>(rho.x), recip<MODE>(rho.y));
     const float2 ux = fma2(bc2(k.tau), fx, jx) * inv;  // u + tau F / rho
     const float2 uy = fma2(bc2(k.tau), fy, jy) * inv;
     const float2 usq = fma2(ux, ux, uy * uy);
-    const float2 Ap = fma2(rho, fma2(bc2(-1.5f), usq, bc2(1.0f)), bc2(-k.rho_ref));
+    float2 Ap = rho * fma2(bc2(-1.5f), usq, bc2(1.0f));
+    if constexpr (SHIFT) Ap = Ap - shift;
     // o_i = h_i + omega (f_i^eq - h_i) = (1 - omega) h_i + omega f_i^eq, with omega w_i folded
     // into the equilibrium's parts: omega f_i^eq = a_i (Ap + 4.5 rho (c_i.u)^2) +- 3 a_i rho (c_i.u),
     // a_i = omega w_i, so each population costs one add and one FMA
@@ -473,7 +438,7 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
 #pragma unroll
         for (int i = 0; i < 9; ++i) hc[i] = decode2<MODE>(Cur[i]);
         const float2 shc = (((hc[0] + hc[1]) + (hc[2] + hc[3])) + ((hc[4] + hc[5]) + (hc[6] + hc[7]))) + hc[8];
-        const float2 rhoc = shc + bc2(a.k.rho_ref);
+        const float2 rhoc = shc;
         A = B;
         B = C;
         const float2 ps = psi2<MODE>(rhoc, a.k);
@@ -492,35 +457,12 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
             const float g0 = -a.k.G * B.a, g1 = -a.k.G * B.b;
             float2 o[9];
             collide_pair<MODE>(hp, rho_p, make_float2(g0 * sx0, g1 * sx1), make_float2(g0 * sy0, g1 * sy1), a.k, o);
+            // BGK conserves mass; take the rest population from that balance so the FP32
+            // weights (which do not sum to one exactly) leave no systematic drift.
+            o[0] = sh_p - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
             PT out[9];
-            if constexpr (MODE == PL_F32) {
-                // BGK conserves mass; take the rest population from that balance so the
-                // FP32 weights (which do not sum to one exactly) leave no systematic drift.
-                o[0] = sh_p - (((o[1] + o[2]) + (o[3] + o[4])) + ((o[5] + o[6]) + (o[7] + o[8])));
 #pragma unroll
-                for (int i = 0; i < 9; ++i) out[i] = o[i];
-            } else {
-                // Mass-conserving FP16 storage: the 8 moving populations are rounded to
-                // nearest; the rest population takes the cell's stored mass minus their
-                // rounded values, and is rounded stochastically (unbiased), so the stored
-                // mass changes by one zero-mean rounding per cell and step.
-                // sum of the rounded values, each half added to an FP32 accumulator directly
-                // (sm_100 mixed-precision add: no separate conversion)
-                float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    out[i] = __floats2half2_rn(o[i].x, o[i].y);
-                    unsigned short lo, hi;
-                    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(*reinterpret_cast<const uint32_t*>(&out[i])));
-                    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s0) : "h"(lo));
-                    asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s1) : "h"(hi));
-                }
-                const float2 rest = sh_p - make_float2(s0, s1);
-                // dither: a hash of the cell pair's position and the lattice's step count
-                const uint32_t rnd =
-                    fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
-                out[0] = sr_pack_half2(rest.x, rest.y, rnd);
-            }
+            for (int i = 0; i < 9; ++i) out[i] = o[i];
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             auto dst = [&](int i, int row) -> S* {
                 if constexpr (FAST) return a.fout + ((uint32_t)row * pitchU + (uint32_t)ua + (uint32_t)i * planeU);
@@ -532,26 +474,7 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
             store_pair2<MODE>(dst(4, ym), split, own0, own1, out[4]);
             // c_x = +1 planes: (left lane's second cell, own first cell);
             // c_x = -1 planes: (own second cell, right lane's first cell)
-            if constexpr (MODE == PL_F16_OFFSET) {
-                const uint32_t u1 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[1]), 1);
-                const uint32_t u5 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[5]), 1);
-                const uint32_t u8 = __shfl_up_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[8]), 1);
-                const uint32_t d3 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[3]), 1);
-                const uint32_t d6 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[6]), 1);
-                const uint32_t d7 = __shfl_down_sync(0xffffffffu, *reinterpret_cast<const uint32_t*>(&out[7]), 1);
-                // (high half of the left lane's pair, low half of ours) and
-                // (high half of ours, low half of the right lane's pair)
-                auto join = [](uint32_t lo_src, uint32_t hi_src) {
-                    const uint32_t v = __byte_perm(lo_src, hi_src, 0x5432);
-                    return *reinterpret_cast<const __half2*>(&v);
-                };
-                store_pair2<MODE>(dst(1, y), split, own0, own1, join(u1, *reinterpret_cast<const uint32_t*>(&out[1])));
-                store_pair2<MODE>(dst(5, yp), split, own0, own1, join(u5, *reinterpret_cast<const uint32_t*>(&out[5])));
-                store_pair2<MODE>(dst(8, ym), split, own0, own1, join(u8, *reinterpret_cast<const uint32_t*>(&out[8])));
-                store_pair2<MODE>(dst(3, y), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[3]), d3));
-                store_pair2<MODE>(dst(6, yp), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[6]), d6));
-                store_pair2<MODE>(dst(7, ym), split, own0, own1, join(*reinterpret_cast<const uint32_t*>(&out[7]), d7));
-            } else {
+            {
                 const float l1 = __shfl_up_sync(0xffffffffu, o[1].y, 1);
                 const float l5 = __shfl_up_sync(0xffffffffu, o[5].y, 1);
                 const float l8 = __shfl_up_sync(0xffffffffu, o[8].y, 1);
@@ -573,16 +496,229 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// FP16-offset walker: the strip walk of walk_impl2 on packed FP32 pairs, with the storage of
+// pl_device.cuh.  A population arriving at cell x is decoded against the reference density of
+// the cell it streamed from, f_i = h_i + Wr_i r(x - c_i); the relaxed pair stores its new
+// reference r(x) = fp16(rho(x)) in plane 9 and pushes h_i = f_i* - Wr_i r(x).  The reference
+// rows y-1, y, y+1 are held as packed FP16 pairs: the lane's own pair and, in a second word,
+// its left and right neighbours (the adjacent lanes' values by shuffle; lanes 0 and 31 read
+// their one outer column from memory), loaded one row ahead of the populations.
+//
+// Mass: with Wr summing to exactly one and every product Wr_i r exact in FP32, the mass a
+// cell receives is A + H, A = sum Wr_i r(x - c_i) (exact where the references agree in
+// their binade) and H = sum h_i (exact: FP16 offsets).  The pushed populations carry
+// r(x) + sum_{i>0} h_i* + h_0*, and the rest population takes (A - r(x)) + H - sum_{i>0} h_i*,
+// rounded stochastically: the stored mass changes by one zero-mean rounding of a small
+// offset per cell and step.
+__device__ __forceinline__ uint32_t h2u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ __half2 u2h(uint32_t v) { return *reinterpret_cast<__half2*>(&v); }
+
+// A reference row in FP32: the lane's own pair M = (r(a), r(b)) and its outer neighbours
+// L = r(a - 1), R = r(b + 1).
+struct RefRow {
+    float2 M;
+    float L, R;
+};
+
+template <bool FAST>
+__device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int strip, int r0, int r1, int lane) {
+    const int nx = a.nx, ny = a.ny;
+    const int ua = strip * STRIP - 2 + 2 * lane;
+    const int cA = wrapi(ua, nx), cB = wrapi(ua + 1, nx);
+    const bool vec = FAST || ((cB == cA + 1) && ((cA & 1) == 0));
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
+    const bool split = !FAST && !(vec && own0 == own1);
+    const bool halo = lane == 0 || lane == 31;
+    const int cX = lane == 0 ? wrapi(ua - 1, nx) : wrapi(ua + 2, nx);  // a halo lane's outer column
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    const float W0 = wref(0), W1 = wref(1), W2 = wref(5);
+    const uint32_t planeU = (uint32_t)a.plane, pitchU = (uint32_t)a.pitch;
+    // element offset of column 0 of row r of plane i (FAST strips: 32 bits, checked by the caller)
+    auto row_off = [&](int i, int r) -> long long {
+        if constexpr (FAST) return (long long)((uint32_t)r * pitchU + (uint32_t)i * planeU);
+        else return (long long)i * a.plane + (long long)r * a.pitch;
+    };
+    auto ld_pair = [&](const __half* row) -> uint32_t {
+        if (vec) return *reinterpret_cast<const uint32_t*>(row + cA);
+        return (uint32_t)__half_as_ushort(row[cA]) | ((uint32_t)__half_as_ushort(row[cB]) << 16);
+    };
+    auto load_pops = [&](int r, uint32_t (&P)[9]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = ld_pair(a.fin + row_off(i, r));
+    };
+    auto load_ref = [&](int r, uint32_t& own, uint32_t& ext) {
+        const __half* row = a.fin + row_off(REF_PLANE, r);
+        own = ld_pair(row);
+        ext = halo ? (uint32_t)__half_as_ushort(row[cX]) : 0u;
+    };
+    auto ref_row = [&](uint32_t own, uint32_t ext) -> RefRow {
+        const uint32_t up = __shfl_up_sync(0xffffffffu, own, 1);    // left lane's pair
+        const uint32_t dn = __shfl_down_sync(0xffffffffu, own, 1);  // right lane's pair
+        uint32_t sd = __byte_perm(up, dn, 0x5432);                  // (its b, right lane's a)
+        if (lane == 0) sd = (sd & 0xFFFF0000u) | ext;
+        if (lane == 31) sd = (sd & 0x0000FFFFu) | (ext << 16);
+        const float2 s2 = __half22float2(u2h(sd));
+        return RefRow{__half22float2(u2h(own)), s2.x, s2.y};
+    };
+    auto store = [&](__half* p, uint32_t v) {
+        if (!split) {
+            if (own0) *reinterpret_cast<uint32_t*>(p) = v;
+        } else {
+            if (own0) p[0] = __ushort_as_half((unsigned short)(v & 0xFFFFu));
+            if (own1) p[1] = __ushort_as_half((unsigned short)(v >> 16));
+        }
+    };
+
+    // populations of row r0-1 (decoded first), references of rows r0-2, r0-1, r0 (its
+    // neighbourhood) and r0+1 (pending)
+    uint32_t Nx[9];
+    load_pops(wrapi(r0 - 1, ny), Nx);
+    RefRow rm, rc, rp;
+    uint32_t pend_own, pend_ext;
+    {
+        uint32_t o, e;
+        load_ref(wrapi(r0 - 2, ny), o, e);
+        rm = ref_row(o, e);
+        load_ref(wrapi(r0 - 1, ny), o, e);
+        rc = ref_row(o, e);
+        load_ref(wrapi(r0, ny), o, e);
+        rp = ref_row(o, e);
+        load_ref(wrapi(r0 + 1, ny), pend_own, pend_ext);
+    }
+    float2 fp[9];  // previous row (to be relaxed), decoded
+    float2 rho_p = make_float2(0.0f, 0.0f);
+    // pseudopotential of rows y-1, y, y+1 (the pair's own cells; the neighbours come by
+    // shuffle when the force is formed, so that fewer values stay live across rows)
+    float2 PA = make_float2(0.0f, 0.0f), PB = PA, PC = PA;
+    const int nrows = r1 - r0;
+    for (int k = 0; k <= nrows + 1; ++k) {
+        uint32_t Cur[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Cur[i] = Nx[i];
+        if (k <= nrows) {
+            int rn = r0 + k;
+            if (rn >= ny) rn -= ny;
+            load_pops(rn, Nx);                       // prefetch the next row
+        }
+        // decode row r0+k-1 against the references of rows r0+k-2 (rm), r0+k-1 (rc), r0+k (rp):
+        // f_i = h_i + Wr_i r(x - c_i), one FMA each (the shifted views per half)
+        float2 fc[9];
+        {
+            float2 h[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) h[i] = __half22float2(u2h(Cur[i]));
+            fc[0] = fma2(bc2(W0), rc.M, h[0]);
+            fc[1] = make_float2(fmaf(W1, rc.L, h[1].x), fmaf(W1, rc.M.x, h[1].y));   // c_1 = (1, 0): from x - 1
+            fc[3] = make_float2(fmaf(W1, rc.M.y, h[3].x), fmaf(W1, rc.R, h[3].y));
+            fc[2] = fma2(bc2(W1), rm.M, h[2]);                                        // c_y = +1: from row y - 1
+            fc[5] = make_float2(fmaf(W2, rm.L, h[5].x), fmaf(W2, rm.M.x, h[5].y));
+            fc[6] = make_float2(fmaf(W2, rm.M.y, h[6].x), fmaf(W2, rm.R, h[6].y));
+            fc[4] = fma2(bc2(W1), rp.M, h[4]);                                        // c_y = -1: from row y + 1
+            fc[8] = make_float2(fmaf(W2, rp.L, h[8].x), fmaf(W2, rp.M.x, h[8].y));
+            fc[7] = make_float2(fmaf(W2, rp.M.y, h[7].x), fmaf(W2, rp.R, h[7].y));
+        }
+        // slide the reference window: the pending row is complete now
+        rm = rc;
+        rc = rp;
+        rp = ref_row(pend_own, pend_ext);
+        if (k < nrows) load_ref(wrapi(r0 + k + 2, ny), pend_own, pend_ext);  // decoded two iterations on
+        const float2 rhoc = (((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7]))) + fc[8];
+        PA = PB;
+        PB = PC;
+        PC = psi2<PL_F16_OFFSET>(rhoc, a.k);
+        if (k >= 2) {
+            int y = r0 + k - 2;
+            if (y >= ny) y -= ny;
+            PsiRow<float> A, B, C;
+            A.a = PA.x, A.b = PA.y, B.a = PB.x, B.b = PB.y, C.a = PC.x, C.b = PC.y;
+            A.L = __shfl_up_sync(0xffffffffu, A.b, 1);
+            A.Rr = __shfl_down_sync(0xffffffffu, A.a, 1);
+            B.L = __shfl_up_sync(0xffffffffu, B.b, 1);
+            B.Rr = __shfl_down_sync(0xffffffffu, B.a, 1);
+            C.L = __shfl_up_sync(0xffffffffu, C.b, 1);
+            C.Rr = __shfl_down_sync(0xffffffffu, C.a, 1);
+            const float sx0 = w1 * (B.b - B.L) + w2 * ((C.b - C.L) + (A.b - A.L));
+            const float sy0 = w1 * (C.a - A.a) + w2 * ((C.b + C.L) - (A.b + A.L));
+            const float sx1 = w1 * (B.Rr - B.a) + w2 * ((C.Rr - C.a) + (A.Rr - A.a));
+            const float sy1 = w1 * (C.b - A.b) + w2 * ((C.Rr + C.a) - (A.Rr + A.a));
+            const float g0 = -a.k.G * B.a, g1 = -a.k.G * B.b;
+            // the pair's new reference; the relaxation then gives the offsets directly
+            // (o_i = f_i* - Wr_i r, the shift kappa r / omega taken off the isotropic part)
+            uint32_t rq;
+            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(rq) : "f"(rho_p.y), "f"(rho_p.x));
+            const float2 rqf = __half22float2(u2h(rq));
+            float2 o[9];
+            collide_pair<PL_F16_OFFSET, true>(fp, rho_p, make_float2(g0 * sx0, g1 * sx1), make_float2(g0 * sy0, g1 * sy1),
+                                              a.k, o, bc2(REF_KAPPA * a.k.tau) * rqf);
+            uint32_t out[9];
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(out[i]) : "f"(o[i].y), "f"(o[i].x));
+                unsigned short lo, hi;
+                asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(out[i]));
+                asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s0) : "h"(lo));
+                asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s1) : "h"(hi));
+            }
+            // rest offset: the cell's mass minus what the pushed populations carry
+            const float2 rest = (rho_p - bc2(REF_KAPPA) * rqf) - make_float2(s0, s1);
+            const uint32_t rnd =
+                fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
+            out[0] = h2u(sr_pack_half2(rest.x, rest.y, rnd, __funnelshift_l(rnd, rnd, 16)));
+            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+            auto dst = [&](int i, int row) -> __half* { return a.fout + row_off(i, row) + ua; };
+            // c_x = 0 planes and the reference: own pair
+            store(dst(0, y), out[0]);
+            store(dst(REF_PLANE, y), rq);
+            store(dst(2, yp), out[2]);
+            store(dst(4, ym), out[4]);
+            // c_x = +1 planes: (high half of the left lane's pair, low half of ours);
+            // c_x = -1 planes: (high half of ours, low half of the right lane's pair)
+            const uint32_t u1 = __shfl_up_sync(0xffffffffu, out[1], 1);
+            const uint32_t u5 = __shfl_up_sync(0xffffffffu, out[5], 1);
+            const uint32_t u8 = __shfl_up_sync(0xffffffffu, out[8], 1);
+            const uint32_t d3 = __shfl_down_sync(0xffffffffu, out[3], 1);
+            const uint32_t d6 = __shfl_down_sync(0xffffffffu, out[6], 1);
+            const uint32_t d7 = __shfl_down_sync(0xffffffffu, out[7], 1);
+            store(dst(1, y), __byte_perm(u1, out[1], 0x5432));
+            store(dst(5, yp), __byte_perm(u5, out[5], 0x5432));
+            store(dst(8, ym), __byte_perm(u8, out[8], 0x5432));
+            store(dst(3, y), __byte_perm(out[3], d3, 0x5432));
+            store(dst(6, yp), __byte_perm(out[6], d6, 0x5432));
+            store(dst(7, ym), __byte_perm(out[7], d7, 0x5432));
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fp[i] = fc[i];
+        rho_p = rhoc;
+    }
+}
+
+// Whether strip `strip` of a lattice takes the FP16 vector path: every pair of the strip is an
+// aligned vector that owns both of its cells or neither (lanes past the lattice's last column
+// read wrapped columns, needed only for the psi of their neighbours, and store nothing) and
+// ten planes fit 32-bit element offsets.  True for every strip of a lattice with even nx (and
+// planes below 2^32 / 10 elements); warp-uniform.
+__device__ __forceinline__ bool f16_fast_strip(int nx, long long plane, int strip, int lane) {
+    const int ua = strip * STRIP - 2 + 2 * lane;
+    const int cA = wrapi(ua, nx), cB = wrapi(ua + 1, nx);
+    const bool mid = lane >= 1 && lane <= 30;
+    const bool own0 = mid && ua < nx, own1 = mid && ua + 1 < nx;
+    const bool fast = (cB == cA + 1) && ((cA & 1) == 0) && own0 == own1 && (long long)F16_PLANES * plane <= 0xFFFFFFFFll;
+    return __all_sync(0xffffffffu, fast);
+}
+
 template <int MODE>
 __device__ void walk_segment2(const WalkArgs<MODE>& a, int strip, int r0, int r1, int lane) {
-    const int ua = strip * STRIP - 2 + 2 * lane;
-    const int cA = wrapi(ua, a.nx), cB = wrapi(ua + 1, a.nx);
-    const bool mid = lane >= 1 && lane <= 30;
-    const bool fast = (cB == cA + 1) && ((cA & 1) == 0) && (!mid || ua + 1 < a.nx) && 9ll * a.plane <= 0xFFFFFFFFll;
     // (FP32 storage is bound by HBM, not by issue: it keeps one copy of the walk and its
     // register count, and with it four blocks per SM)
-    if (MODE == PL_F16_OFFSET && __all_sync(0xffffffffu, fast)) walk_impl2<MODE, true>(a, strip, r0, r1, lane);
-    else walk_impl2<MODE, false>(a, strip, r0, r1, lane);
+    if constexpr (MODE == PL_F16_OFFSET) {
+        // the vector path only: the other strips are k_step_edge's
+        if (f16_fast_strip(a.nx, a.plane, strip, lane)) walk_f16<true>(a, strip, r0, r1, lane);
+    } else {
+        walk_impl2<MODE, false>(a, strip, r0, r1, lane);
+    }
 }
 
 // Persistent table kernel: physical warp w processes virtual warps w, w+P, w+2P, ...
@@ -633,11 +769,48 @@ __global__ void __launch_bounds__(StepCfg<MODE>::threads, StepCfg<MODE>::min_blo
         a.nstrips = d.nstrips;
         a.chunks = d.chunks;
         a.plane = d.plane;
-        a.k = StepK<R>{R(d.G), R(d.tau), R(1.0 / d.tau), R(d.rho0), R(1.0 / d.rho0),
-                       MODE == PL_F16_OFFSET ? R(d.rho_ref) : R(0)};
+        a.k = StepK<R>{R(d.G), R(d.tau), R(1.0 / d.tau), R(d.rho0), R(1.0 / d.rho0)};
         a.seq = seq - d.seq0;  // the lattice's own step count: the same alone or in a batch
         if constexpr (MODE == PL_F64) walk_segment<MODE>(a, strip, r0, r1, lane);
         else walk_segment2<MODE>(a, strip, r0, r1, lane);
+    }
+}
+
+// FP16-offset strips off the vector path (ragged or wrapping pairs of odd-nx lattices, planes
+// beyond 32-bit offsets), element by element.  A kernel of its own, so that its register needs
+// do not spill the vector path's; it walks only the lattices the header counts and returns at
+// once when there are none.
+__global__ void __launch_bounds__(128) k_step_edge(TableView t, int parity) {
+    if (t.hdr->edge_lattices == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long P = (long long)gridDim.x * (blockDim.x / 32);
+    const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n = t.hdr->n;
+    const uint32_t seq = t.seq[parity];
+    for (int j = 0; j < n; ++j) {
+        const LatDesc& d = t.d[j];
+        if (!f16_edge_lattice(d.nx, d.plane)) continue;
+        const long long nvw = (long long)d.nstrips * d.chunks;
+        for (long long local = w0; local < nvw; local += P) {
+            const int strip = (int)(local % d.nstrips);
+            const long long chunk = local / d.nstrips;
+            const int r0 = (int)(chunk * d.ny / d.chunks);
+            const int r1 = (int)((chunk + 1) * d.ny / d.chunks);
+            if (r1 <= r0 || f16_fast_strip(d.nx, d.plane, strip, lane)) continue;
+            WalkArgs<PL_F16_OFFSET> a;
+            const int src = d.phase ^ parity;
+            a.fin = static_cast<const __half*>(d.pops[src]);
+            a.fout = static_cast<__half*>(d.pops[1 - src]);
+            a.nx = d.nx;
+            a.ny = d.ny;
+            a.pitch = d.pitch;
+            a.nstrips = d.nstrips;
+            a.chunks = d.chunks;
+            a.plane = d.plane;
+            a.k = StepK<float>{float(d.G), float(d.tau), float(1.0 / d.tau), float(d.rho0), float(1.0 / d.rho0)};
+            a.seq = seq - d.seq0;
+            walk_f16<false>(a, strip, r0, r1, lane);
+        }
     }
 }
 
@@ -672,11 +845,24 @@ static cudaError_t launch_step_t(const TableView& t, int parity, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s) {
+cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStream_t s, bool edge) {
     switch (storage) {
         case PL_F64: return launch_step_t<PL_F64>(t, parity, s);
         case PL_F32: return launch_step_t<PL_F32>(t, parity, s);
-        case PL_F16_OFFSET: return launch_step_t<PL_F16_OFFSET>(t, parity, s);
+        case PL_F16_OFFSET: {
+            cudaError_t e = launch_step_t<PL_F16_OFFSET>(t, parity, s);
+            if (e != cudaSuccess || !edge) return e;
+            static int sms = 0;
+            if (!sms) {
+                int dev = 0;
+                cudaGetDevice(&dev);
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+                if (sms < 1) sms = 1;
+            }
+            k_step_edge<<<sms, 128, 0, s>>>(t, parity);
+            note_launches(1);
+            return cudaGetLastError();
+        }
     }
     return cudaErrorInvalidValue;
 }
@@ -689,11 +875,9 @@ __device__ __forceinline__ double min_image(double d, double n) {
     return a > 0.5 * n ? n - a : a;
 }
 
-template <int MODE>
-__global__ void k_init_droplets(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
-                                const pl_droplet* __restrict__ d, int n, double rho_in, double rho_out, double width,
-                                double noise_amp, uint64_t seed, double rho_ref) {
-    using R = typename Traits<MODE>::R;
+// Density of the initial droplet state, rho[y*nx + x] in FP64.
+__global__ void k_droplet_rho(int nx, int ny, const pl_droplet* __restrict__ d, int n, double rho_in, double rho_out,
+                              double width, double noise_amp, uint64_t seed, double* __restrict__ rho) {
     const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx), y = (int)(c / nx);
@@ -707,37 +891,83 @@ __global__ void k_init_droplets(typename Traits<MODE>::S* __restrict__ f, int nx
             const double phi = 0.5 * (1.0 - tanh((sqrt(d2) - d[k].r) / width));
             best = phi > best ? phi : best;
         }
-        const double rho = rho_out + (rho_in - rho_out) * best + noise_amp * (2.0 * uniform01_at(seed, (uint64_t)c) - 1.0);
-        const long long o = (long long)y * pitch + x;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i * plane + o] = encode<MODE>(R(wq<double>(i) * rho), R(wq<double>(i) * rho_ref));
+        rho[c] = rho_out + (rho_in - rho_out) * best + noise_amp * (2.0 * uniform01_at(seed, (uint64_t)c) - 1.0);
     }
 }
 
+// Fluid at rest, f_i = w_i rho (FP64 / FP32 storage).
 template <int MODE>
 __global__ void k_init_from_rho(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
-                                const double* __restrict__ rho, double rho_ref) {
+                                const double* __restrict__ rho) {
     using R = typename Traits<MODE>::R;
     const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const long long o = (c / nx) * pitch + c % nx;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i * plane + o] = encode<MODE>(R(wq<double>(i) * rho[c]), R(wq<double>(i) * rho_ref));
+        for (int i = 0; i < 9; ++i) f[i * plane + o] = encode<MODE>(R(wq<double>(i) * rho[c]));
     }
 }
 
-// FP64 dense exchange array <-> one pitched storage plane (plane index `i`).
-template <int MODE>
-__global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
-                                int i, double* __restrict__ buf, int to_f64, double rho_ref) {
-    using R = typename Traits<MODE>::R;
-    const R off = R(wq<double>(i) * rho_ref);
+// FP16-offset storage: reference plane r = fp16(rho) of a density field given in FP64.
+__global__ void k_ref_from_rho(__half* __restrict__ ref, int nx, int ny, int pitch, const double* __restrict__ rho) {
+    const long long N = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        ref[(c / nx) * pitch + c % nx] = __double2half(rho[c]);
+}
+
+// Reference term Wr_i r(x - c_i) of population i at cell (x, y), exact in FP64.
+__device__ __forceinline__ double ref_term(const __half* __restrict__ ref, int nx, int ny, int pitch, int x, int y, int i) {
+    const int xs = wrapi(x - cx(i), nx), ys = wrapi(y - cy(i), ny);
+    return (double)wref(i) * (double)__half2float(ref[(long long)ys * pitch + xs]);
+}
+
+// FP16-offset storage of a fluid at rest, f_i = w_i rho, against the reference plane: each
+// moving population rounded to nearest, the rest population taking the cell's density minus
+// what the others carry (so the stored mass of a cell is rho within one rounding of h_0).
+__global__ void k_f16_encode_rest(__half* __restrict__ f, int nx, int ny, int pitch, long long plane,
+                                  const double* __restrict__ rho) {
+    const __half* ref = f + REF_PLANE * plane;
     const long long N = (long long)nx * ny;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
-        const long long o = i * plane + (c / nx) * pitch + c % nx;
-        if (to_f64) buf[c] = (double)decode<MODE>(f[o], off);
-        else f[o] = encode<MODE>(R(buf[c]), off);
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        const long long o = (long long)y * pitch + x;
+        double carried = ref_term(ref, nx, ny, pitch, x, y, 0);
+        for (int i = 1; i < 9; ++i) {
+            const double t = ref_term(ref, nx, ny, pitch, x, y, i);
+            const __half h = __double2half(wq<double>(i) * rho[c] - t);
+            f[i * plane + o] = h;
+            carried += (double)__half2float(h) + t;
+        }
+        f[o] = __double2half(rho[c] - carried);
     }
+}
+
+// FP64 dense exchange array <-> one pitched storage plane (plane index `i`).  FP16-offset
+// storage decodes f_i = h_i + Wr_i r(x - c_i) and encodes h_i = fp16(f_i - Wr_i r(x - c_i)) (to
+// nearest, in FP64) against the reference plane, which k_ref_from_rho has set first.
+template <int MODE>
+__global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
+                                int i, double* __restrict__ buf, int to_f64) {
+    using R = typename Traits<MODE>::R;
+    const long long N = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % nx), y = (int)(c / nx);
+        const long long o = i * plane + (long long)y * pitch + x;
+        if constexpr (MODE == PL_F16_OFFSET) {
+            const double t = ref_term(f + REF_PLANE * plane, nx, ny, pitch, x, y, i);
+            if (to_f64) buf[c] = (double)__half2float(f[o]) + t;
+            else f[o] = __double2half(buf[c] - t);
+        } else {
+            if (to_f64) buf[c] = (double)decode<MODE>(f[o]);
+            else f[o] = encode<MODE>(R(buf[c]));
+        }
+    }
+}
+
+// acc = buf (first) or acc + buf: the density of a state uploaded one plane at a time.
+__global__ void k_accumulate(double* __restrict__ acc, const double* __restrict__ buf, long long N, int first) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x)
+        acc[c] = first ? buf[c] : acc[c] + buf[c];
 }
 
 static int grid_for(long long N) {
@@ -745,62 +975,75 @@ static int grid_for(long long N) {
     return (int)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
 }
 
-template <int MODE>
-static void init_droplets_t(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in, double rho_out,
-                            double width, double noise_amp, uint64_t seed, cudaStream_t s) {
-    using S = typename Traits<MODE>::S;
-    k_init_droplets<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(
-        static_cast<S*>(v.pops[cur]), v.nx, v.ny, v.pitch, v.plane, v.droplets, n, rho_in, rho_out, width, noise_amp,
-        seed, p.rho_ref);
-}
-
-cudaError_t launch_init_droplets(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in,
-                                 double rho_out, double width, double noise_amp, uint64_t seed, cudaStream_t s) {
-    switch (v.storage) {
-        case PL_F64: init_droplets_t<PL_F64>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
-        case PL_F32: init_droplets_t<PL_F32>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
-        case PL_F16_OFFSET: init_droplets_t<PL_F16_OFFSET>(v, p, cur, n, rho_in, rho_out, width, noise_amp, seed, s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    note_launches(1);
-    return cudaGetLastError();
-}
-
-template <int MODE>
-static void init_rho_t(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho, cudaStream_t s) {
-    using S = typename Traits<MODE>::S;
-    k_init_from_rho<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.ny,
-                                                                           v.pitch, v.plane, d_rho, p.rho_ref);
-}
-
 cudaError_t launch_init_from_rho(const LatticeView& v, const PhysParams& p, int cur, const double* d_rho,
                                  cudaStream_t s) {
+    (void)p;
+    const int g = grid_for((long long)v.nx * v.ny);
     switch (v.storage) {
-        case PL_F64: init_rho_t<PL_F64>(v, p, cur, d_rho, s); break;
-        case PL_F32: init_rho_t<PL_F32>(v, p, cur, d_rho, s); break;
-        case PL_F16_OFFSET: init_rho_t<PL_F16_OFFSET>(v, p, cur, d_rho, s); break;
+        case PL_F64:
+            k_init_from_rho<PL_F64><<<g, 256, 0, s>>>(static_cast<double*>(v.pops[cur]), v.nx, v.ny, v.pitch, v.plane, d_rho);
+            note_launches(1);
+            break;
+        case PL_F32:
+            k_init_from_rho<PL_F32><<<g, 256, 0, s>>>(static_cast<float*>(v.pops[cur]), v.nx, v.ny, v.pitch, v.plane, d_rho);
+            note_launches(1);
+            break;
+        case PL_F16_OFFSET: {
+            __half* f = static_cast<__half*>(v.pops[cur]);
+            k_ref_from_rho<<<g, 256, 0, s>>>(f + REF_PLANE * v.plane, v.nx, v.ny, v.pitch, d_rho);
+            k_f16_encode_rest<<<g, 256, 0, s>>>(f, v.nx, v.ny, v.pitch, v.plane, d_rho);
+            note_launches(2);
+            break;
+        }
         default: return cudaErrorInvalidValue;
     }
-    note_launches(1);
     return cudaGetLastError();
 }
 
+// The droplet density goes through the lattice's scratch (>= 8 N bytes) as FP64.
+cudaError_t launch_init_droplets(const LatticeView& v, const PhysParams& p, int cur, int n, double rho_in,
+                                 double rho_out, double width, double noise_amp, uint64_t seed, cudaStream_t s) {
+    double* rho = static_cast<double*>(v.rho);
+    k_droplet_rho<<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(v.nx, v.ny, v.droplets, n, rho_in, rho_out, width,
+                                                                   noise_amp, seed, rho);
+    note_launches(1);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_init_from_rho(v, p, cur, rho, s);
+}
+
 template <int MODE>
-static void convert_t(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int i, int to_f64,
-                      cudaStream_t s) {
+static void convert_t(const LatticeView& v, int cur, double* d_buf, int i, int to_f64, cudaStream_t s) {
     using S = typename Traits<MODE>::S;
     k_plane_convert<MODE><<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(static_cast<S*>(v.pops[cur]), v.nx, v.ny,
-                                                                           v.pitch, v.plane, i, d_buf, to_f64, p.rho_ref);
+                                                                           v.pitch, v.plane, i, d_buf, to_f64);
 }
 
 cudaError_t launch_state_convert(const LatticeView& v, const PhysParams& p, int cur, double* d_buf, int i, int to_f64,
                                  cudaStream_t s) {
+    (void)p;
     switch (v.storage) {
-        case PL_F64: convert_t<PL_F64>(v, p, cur, d_buf, i, to_f64, s); break;
-        case PL_F32: convert_t<PL_F32>(v, p, cur, d_buf, i, to_f64, s); break;
-        case PL_F16_OFFSET: convert_t<PL_F16_OFFSET>(v, p, cur, d_buf, i, to_f64, s); break;
+        case PL_F64: convert_t<PL_F64>(v, cur, d_buf, i, to_f64, s); break;
+        case PL_F32: convert_t<PL_F32>(v, cur, d_buf, i, to_f64, s); break;
+        case PL_F16_OFFSET: convert_t<PL_F16_OFFSET>(v, cur, d_buf, i, to_f64, s); break;
         default: return cudaErrorInvalidValue;
     }
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_accumulate(const LatticeView& v, double* d_acc, const double* d_buf, int first,
+                                    cudaStream_t s) {
+    const long long N = (long long)v.nx * v.ny;
+    k_accumulate<<<grid_for(N), 256, 0, s>>>(d_acc, d_buf, N, first);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_ref(const LatticeView& v, int cur, const double* d_rho, cudaStream_t s) {
+    if (v.storage != PL_F16_OFFSET) return cudaSuccess;
+    __half* f = static_cast<__half*>(v.pops[cur]);
+    k_ref_from_rho<<<grid_for((long long)v.nx * v.ny), 256, 0, s>>>(f + REF_PLANE * v.plane, v.nx, v.ny, v.pitch, d_rho);
     note_launches(1);
     return cudaGetLastError();
 }

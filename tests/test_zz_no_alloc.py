@@ -10,7 +10,7 @@ to be collected last, so a run that stops at the first failure has run everythin
 import numpy as np
 import pytest
 
-import oracle as O
+import seeded_states as S
 from paper_2504_10539_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -19,22 +19,21 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-RHO_REF = 1.075
 FIELDS = ("mass", "W", "G_max", "delta_rho", "W_eff", "E_int", "rho_max", "rho_min", "sum_g", "sum_g2")
 
 
 def populations_on_device(f, storage, pitch):
-    """The documented layout: 9 planes of ny rows of `pitch` elements (x fastest)."""
+    """The documented layout: 9 planes (FP16-offset: 10, the offsets and the reference
+    densities) of ny rows of `pitch` elements, x fastest."""
     _, ny, nx = f.shape
     if storage == B.PL_F64:
         dt, vals = torch.float64, torch.from_numpy(f)
     elif storage == B.PL_F32:
         dt, vals = torch.float32, torch.from_numpy(f).float()
     else:
-        _, _, w = O.lattice_tables()
-        off = torch.from_numpy((w * RHO_REF).astype(np.float32))[:, None, None]
-        dt, vals = torch.float16, (torch.from_numpy(f).float() - off).half()
-    buf = torch.zeros((9, ny, pitch), dtype=dt, device="cuda")
+        h, r = S.encode_f16(f)
+        dt, vals = torch.float16, torch.from_numpy(np.concatenate([h, r[None]]))
+    buf = torch.zeros((vals.shape[0], ny, pitch), dtype=dt, device="cuda")
     buf[:, :, :nx] = vals.to("cuda")
     return buf
 
@@ -43,18 +42,18 @@ def populations_on_device(f, storage, pitch):
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (300, 33)])
 def test_noalloc_metrics_match_pl_metrics(storage, nx, ny):
     mlp = B.PL_MLP_F64 if storage == B.PL_F64 else B.PL_MLP_F32
-    lat = B.Lattice(B.pl_params_default(nx, ny, storage=storage, mlp=mlp, rho_ref=RHO_REF))
-    lat.init_droplets([(nx / 2, ny / 2, min(nx, ny) / 4)], 2.0, 0.15, 2.0, 0.01, 11)
-    lat.step(30)
+    lat = B.Lattice(B.pl_params_default(nx, ny, storage=storage, mlp=mlp))
+    # a state the lattice holds exactly, so the caller's buffer below holds the same values
+    f = S.stored(S.oracle_droplet_state(nx, ny, [(nx / 2, ny / 2, min(nx, ny) / 4)], steps=30, seed=11), storage)
+    lat.set_state(f, 30)
     ref = lat.metrics()
-    f, _ = lat.state()
     pitch = (nx + 7) // 8 * 8 + 8          # any pitch >= nx is accepted
     buf = populations_on_device(f, storage, pitch)
     stream = torch.cuda.Stream()
     stream.wait_stream(torch.cuda.current_stream())
     tol = 1e-12 if storage == B.PL_F64 else 1e-6
     for _ in range(2):                     # two calls in a row share the static scratch
-        got = B.pl_metrics_noalloc(buf.data_ptr(), nx, ny, pitch, storage, RHO_REF, 0.01, stream.cuda_stream)
+        got = B.pl_metrics_noalloc(buf.data_ptr(), nx, ny, pitch, storage, 0.0, 0.01, stream.cuda_stream)
         assert got["count"] == ref["count"]
         for k in FIELDS:
             assert abs(got[k] - ref[k]) <= tol * max(abs(ref[k]), 1.0), k
