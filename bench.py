@@ -561,6 +561,32 @@ def run_gb300(args):
             lat.close()
             del lat
             torch.cuda.empty_cache()
+        # the correction's share of a coupling interval, the full correction against the interface
+        # band of mask_eps = 0.01 (the network evaluated on the band only)
+        band = {}
+        for eps in (0.0, 0.01):
+            job = wl.field_4096(storage=wl.F16_OFFSET, side=args.field_side)
+            job.mask_eps = eps
+            lat = B.Lattice.from_workload(job)
+            lat.step(K)
+            lat.correct()
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(lat.stream)
+            lat.step(K)
+            ev[1].record(lat.stream)
+            lat.correct()
+            ev[2].record(lat.stream)
+            ev[2].synchronize()
+            steps_ms, corr_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+            m = lat.metrics()
+            band["eps_%g" % eps] = {"steps_ms": steps_ms, "correction_ms": corr_ms,
+                                    "correction_share_of_interval": corr_ms / (steps_ms + corr_ms),
+                                    "status": m["status"]}
+            lat.close()
+            del lat
+            torch.cuda.empty_cache()
+        field["correction_band"] = band
 
     # --------------------------------------------------------------- network training (Eqs. 3-8)
     training = training_tc = None

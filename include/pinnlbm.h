@@ -66,13 +66,13 @@ extern "C" {
 /* FP16-offset storage (PL_F16_OFFSET; the paper fixes no number format).  A population
  * buffer holds ten FP16 planes: the offsets h_0..h_8 and the reference densities r.  The
  * population f_i at cell x is stored relative to the reference density of the cell it
- * streamed from,
- *     f_i(x) = h_i(x) + Wr_i * r(x - c_i),  Wr = (1824, 456, 456, 456, 456, 114, 114, 114, 114) / 4096
+ * streamed from, scaled by 2^10,
+ *     f_i(x) = 2^-10 h_i(x) + Wr_i * r(x - c_i),  Wr = (1824, 456, 456, 456, 456, 114, 114, 114, 114) / 4096
  * (Wr = (4104/4096) w, proportional to the lattice weights w; Wr_i * r is exact in FP32).  A
  * time step writes r(x) = fp16(rho(x)) with the populations cell x pushes, so each offset is
- * the population's departure from its source cell's rest equilibrium.  The rest population
- * of each cell takes the cell's mass balance and is rounded stochastically (unbiased); the
- * moving ones are rounded to nearest.  Bytes per cell update: 2 x (9 + 1) x 2 = 40. */
+ * the population's departure from its source cell's rest equilibrium; the rest population
+ * of each cell takes the cell's mass balance, and every offset is rounded stochastically
+ * (unbiased).  Bytes per cell update: 2 x (9 + 1) x 2 = 40. */
 
 /* Network arithmetic for the correction. */
 #define PL_MLP_F64 0  /* FP64 on CUDA cores                                        */
@@ -82,9 +82,13 @@ extern "C" {
 #define PL_MAX_DROPLETS 4096
 
 /* Lattice parameters.  G, tau, rho0: Sec. II-A / Sec. III-A (the paper's g and tau);
- * rho_ref: unused (FP16-offset storage keeps a reference density per cell); must be finite;
- * beta_rho, beta_u: gains of the interface correction; threshold: the
- * |grad rho| threshold of the interface width W (Eq. 9; the paper uses 0.01). */
+ * beta_rho, beta_u: gains of the interface correction; threshold: the |grad rho| threshold
+ * of the interface width W (Eq. 9; the paper uses 0.01); mask_eps: the correction's
+ * interface band (Sec. II-C weights the correction toward the interface, Sec. IV-D samples
+ * the interface adaptively; the band is this library's reading): cells whose mask
+ * m = |grad rho| / max |grad rho| is not above mask_eps count as outside the interface (m = 0:
+ * not corrected, not in the projections, no network evaluation).  mask_eps = 0 (default) is
+ * the full correction; 0 < mask_eps evaluates the network on the band only. */
 typedef struct pl_params {
     int32_t nx, ny;   /* lattice size, each >= 1, nx*ny < 2^31                  */
     int32_t storage;  /* PL_F64 / PL_F32 / PL_F16_OFFSET                        */
@@ -92,7 +96,7 @@ typedef struct pl_params {
     double G;         /* interaction strength (< 0 attracts); the paper: -5.5   */
     double tau;       /* BGK relaxation time, > 0.5; the paper: 1.0             */
     double rho0;      /* pseudopotential scale, > 0                             */
-    double rho_ref;   /* unused, finite (kept for layout compatibility)         */
+    double mask_eps;  /* interface band of the correction, >= 0 (default 0)     */
     double beta_rho;  /* correction gain on density  (default 0.1)              */
     double beta_u;    /* correction gain on momentum (default 0.01)             */
     double threshold; /* Eq. 9 gradient threshold    (default 0.01)             */
@@ -136,8 +140,8 @@ PL_API int pl_last_cuda_error(void);
 /* Number of CUDA kernels this library has launched in this process (a graph
  * replay counts each of its kernel nodes), for launch accounting. */
 PL_API int pl_kernel_launches(int64_t* out);
-/* Fill p with the defaults: storage F32, mlp BF16, G=-5.5, tau=1, rho0=1,
- * rho_ref=1 (unused), beta_rho=0.1, beta_u=0.01, threshold=0.01, size nx x ny. */
+/* Fill p with the defaults: storage F32, mlp BF16, G=-5.5, tau=1, rho0=1, mask_eps=0,
+ * beta_rho=0.1, beta_u=0.01, threshold=0.01, size nx x ny. */
 PL_API int pl_params_default(pl_params* p, int32_t nx, int32_t ny);
 
 /* Bytes of caller device memory one lattice with these parameters needs. */
@@ -209,7 +213,7 @@ PL_API int pl_get_mlp_field(pl_lattice* lat, double* host_out3);
  * the step count.  pl_get_state synchronises; pl_set_state encodes into the
  * lattice's storage type (rounding to nearest for F32; for FP16-offset storage the
  * references r = fp16(rho) with rho summed over i = 0..8 in order in FP64, then
- * h_i = fp16(f_i - Wr_i r(x - c_i)) computed in FP64) and sets the step count. */
+ * h_i = fp16(2^10 (f_i - Wr_i r(x - c_i))) computed in FP64) and sets the step count. */
 PL_API int pl_get_state(pl_lattice* lat, double* host_f, int64_t* step);
 PL_API int pl_set_state(pl_lattice* lat, const double* host_f, int64_t step);
 

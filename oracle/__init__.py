@@ -69,6 +69,10 @@ def lib():
         L.orc_mlp_field_n.argtypes = [i, i, _fp, i, i, vp, _dp]
         L.orc_correct_n.restype = i
         L.orc_correct_n.argtypes = [i, i, _dp, _fp, i, i, vp, d, d, d]
+        L.orc_correct_eps.restype = i
+        L.orc_correct_eps.argtypes = [i, i, _dp, _fp, i, i, vp, d, d, d, d]
+        L.orc_run_eps.restype = i
+        L.orc_run_eps.argtypes = [i, i, _dp, i, ctypes.c_long, i, d, d, d, _fp, i, i, d, d, d, d]
         L.orc_run_n.restype = i
         L.orc_run_n.argtypes = [i, i, _dp, i, ctypes.c_long, i, d, d, d, _fp, i, i, d, d, d]
         L.orc_mlp_init_weights.argtypes = [i, u64, _fp]
@@ -268,23 +272,25 @@ def mlp_field(blob, nx, ny, mode=MLP_F64, n_in=2, rho=None):
     return out
 
 
-def correct(f, blob, beta_rho, beta_u, M0, mode=MLP_F64, mlp_out=None, n_in=2):
-    """Apply the interface correction to f in place; returns the status (0 or -4)."""
+def correct(f, blob, beta_rho, beta_u, M0, mode=MLP_F64, mlp_out=None, n_in=2, eps=0.0):
+    """Apply the interface correction to f in place; returns the status (0 or -4).  Cells whose
+    mask g / G_max is not above eps are outside the interface band (mask 0)."""
     _, ny, nx = f.shape
     b = np.ascontiguousarray(blob, dtype=np.float32)
     out3 = None
     if mlp_out is not None:
         out3 = np.ascontiguousarray(mlp_out, dtype=np.float64)
-    return lib().orc_correct_n(nx, ny, _d(f), _f(b), mode, int(n_in), None if out3 is None else out3.ctypes.data,
-                               beta_rho, beta_u, M0)
+    return lib().orc_correct_eps(nx, ny, _d(f), _f(b), mode, int(n_in), None if out3 is None else out3.ctypes.data,
+                                 beta_rho, beta_u, M0, float(eps))
 
 
 def run(f, nsteps, G, tau, rho0=1.0, K=0, blob=None, mode=MLP_F64, beta_rho=0.1, beta_u=0.01,
-        M0=None, step0=0, n_in=2):
-    """Coupled run (Sec. II-C): nsteps of Eq. 1, correction after every K-th step."""
+        M0=None, step0=0, n_in=2, eps=0.0):
+    """Coupled run (Sec. II-C): nsteps of Eq. 1, correction after every K-th step (interface
+    band of the correction: mask above eps)."""
     _, ny, nx = f.shape
     if M0 is None:
         M0 = mass(f)
     b = None if blob is None else np.ascontiguousarray(blob, dtype=np.float32)
-    return lib().orc_run_n(nx, ny, _d(f), int(nsteps), int(step0), int(K), G, tau, rho0,
-                           None if b is None else _f(b), mode, int(n_in), beta_rho, beta_u, M0)
+    return lib().orc_run_eps(nx, ny, _d(f), int(nsteps), int(step0), int(K), G, tau, rho0,
+                             None if b is None else _f(b), mode, int(n_in), beta_rho, beta_u, M0, float(eps))

@@ -535,9 +535,16 @@ void orc_mlp_field(int nx, int ny, const float* blob, int mode, double* out3) {
  * Returns 0; -4 if some rho' <= 0 or a corrected quantity is not finite, in
  * which case f is left unchanged.  The network's output field may be supplied
  * precomputed (out3 != NULL, layout of orc_mlp_field) or is evaluated here.
+ *
+ * Interface band (the correction's emphasis on the interface, Sec. II-C, and the
+ * paper's adaptive sampling of interface regions, Sec. IV-D; the band is the reading
+ * used): with eps >= 0, cells whose mask m = g / G_max is not above eps count as
+ * outside the interface, m = 0 there, so they are neither corrected nor part of the
+ * projections, and the network is needed on the band only.  eps = 0 is the
+ * correction above (cells with g = 0 already have m = 0).
  * ------------------------------------------------------------------------- */
-int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, int n_in, const double* out3_in,
-                  double beta_rho, double beta_u, double M0) {
+int orc_correct_eps(int nx, int ny, double* f, const float* blob, int mlp_mode, int n_in, const double* out3_in,
+                    double beta_rho, double beta_u, double M0, double eps) {
     const long N = (long)nx * ny;
     double* rho = (double*)malloc(sizeof(double) * N);
     double* jx = (double*)malloc(sizeof(double) * N);
@@ -559,9 +566,14 @@ int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, in
     double gmax = 0.0;
     for (long c = 0; c < N; ++c)
         if (g[c] > gmax) gmax = g[c];
-    double sum_m = 0.0, sum_dr = 0.0, M = 0.0;
+    /* the mask, 0 outside the interface band */
     for (long c = 0; c < N; ++c) {
         double m = gmax > 0.0 ? g[c] / gmax : 0.0;
+        g[c] = m > eps ? m : 0.0;
+    }
+    double sum_m = 0.0, sum_dr = 0.0, M = 0.0;
+    for (long c = 0; c < N; ++c) {
+        double m = g[c];
         sum_m += m;
         sum_dr += beta_rho * m * (out3[c] - rho[c]);
         M += rho[c];
@@ -569,7 +581,7 @@ int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, in
     if (sum_m > 0.0) {
         double sjx = 0.0, sjy = 0.0;
         for (long c = 0; c < N; ++c) {
-            double m = g[c] / gmax;
+            double m = g[c];
             double dr = beta_rho * m * (out3[c] - rho[c]) - m * (sum_dr + (M - M0)) / sum_m;
             rhop[c] = rho[c] + dr;
             djx[c] = beta_u * m * (rhop[c] * out3[N + c] - jx[c]);
@@ -578,7 +590,7 @@ int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, in
             sjy += djy[c];
         }
         for (long c = 0; c < N; ++c) {
-            double m = g[c] / gmax;
+            double m = g[c];
             djx[c] -= m * sjx / sum_m;
             djy[c] -= m * sjy / sum_m;
             double upx = (jx[c] + djx[c]) / rhop[c], upy = (jy[c] + djy[c]) / rhop[c];
@@ -586,7 +598,7 @@ int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, in
         }
         if (status == 0) {
             for (long c = 0; c < N; ++c) {
-                double m = g[c] / gmax;
+                double m = g[c];
                 if (!(m > 0.0)) continue;
                 double fe_new[Q], fe_old[Q];
                 orc_equilibrium(rhop[c], (jx[c] + djx[c]) / rhop[c], (jy[c] + djy[c]) / rhop[c], fe_new);
@@ -597,6 +609,11 @@ int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, in
     }
     free(rho); free(jx); free(jy); free(g); free(out3); free(rhop); free(djx); free(djy);
     return status;
+}
+
+int orc_correct_n(int nx, int ny, double* f, const float* blob, int mlp_mode, int n_in, const double* out3_in,
+                  double beta_rho, double beta_u, double M0) {
+    return orc_correct_eps(nx, ny, f, blob, mlp_mode, n_in, out3_in, beta_rho, beta_u, M0, 0.0);
 }
 
 int orc_correct(int nx, int ny, double* f, const float* blob, int mlp_mode, const double* out3_in,
@@ -623,8 +640,9 @@ double orc_mass(int nx, int ny, const double* f) {
  * lattice's step count on entry.  M0 is the reference mass of the projection.
  * Returns the first nonzero status (the run stops there), else 0.
  * ------------------------------------------------------------------------- */
-int orc_run_n(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
-              double rho0, const float* blob, int mlp_mode, int n_in, double beta_rho, double beta_u, double M0) {
+int orc_run_eps(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
+                double rho0, const float* blob, int mlp_mode, int n_in, double beta_rho, double beta_u, double M0,
+                double eps) {
     const long N = (long)nx * ny;
     double* out3 = NULL;
     if (K > 0 && blob && n_in == 2) {
@@ -638,10 +656,15 @@ int orc_run_n(int nx, int ny, double* f, int nsteps, long step0, int K, double G
     for (int s = 1; s <= nsteps && st == 0; ++s) {
         st = orc_step(nx, ny, f, 1, G, tau, rho0);
         if (st == 0 && K > 0 && blob && ((step0 + s) % K) == 0)
-            st = orc_correct_n(nx, ny, f, blob, mlp_mode, n_in, out3, beta_rho, beta_u, M0);
+            st = orc_correct_eps(nx, ny, f, blob, mlp_mode, n_in, out3, beta_rho, beta_u, M0, eps);
     }
     free(out3);
     return st;
+}
+
+int orc_run_n(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,
+              double rho0, const float* blob, int mlp_mode, int n_in, double beta_rho, double beta_u, double M0) {
+    return orc_run_eps(nx, ny, f, nsteps, step0, K, G, tau, rho0, blob, mlp_mode, n_in, beta_rho, beta_u, M0, 0.0);
 }
 
 int orc_run(int nx, int ny, double* f, int nsteps, long step0, int K, double G, double tau,

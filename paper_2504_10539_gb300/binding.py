@@ -37,7 +37,7 @@ PL_MAX_DROPLETS = 4096
 class pl_params(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("mlp", ctypes.c_int32), ("G", ctypes.c_double), ("tau", ctypes.c_double),
-                ("rho0", ctypes.c_double), ("rho_ref", ctypes.c_double), ("beta_rho", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("mask_eps", ctypes.c_double), ("beta_rho", ctypes.c_double),
                 ("beta_u", ctypes.c_double), ("threshold", ctypes.c_double), ("mlp_in", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
@@ -574,7 +574,7 @@ def pl_batch_destroy(h):
 def job_params(job) -> pl_params:
     """C parameters of a ``workloads.Lattice`` description."""
     return pl_params_default(job.nx, job.ny, storage=job.storage, mlp=job.mlp, G=job.G, tau=job.tau, rho0=job.rho0,
-                             rho_ref=job.rho_ref, beta_rho=job.beta_rho, beta_u=job.beta_u,
+                             mask_eps=getattr(job, "mask_eps", 0.0), beta_rho=job.beta_rho, beta_u=job.beta_u,
                              mlp_in=getattr(job, "mlp_in", 2))
 
 
@@ -635,6 +635,7 @@ class Batch:
         if getattr(self, "h", None):
             pl_batch_destroy(self.h)
             self.h = None
+        self.mem = None             # the device buffer goes with the handle
 
     def __del__(self):
         try:

@@ -33,8 +33,8 @@ int check_params(const pl_params* p) {
     if (p->storage != PL_F64 && p->mlp != PL_MLP_F32 && p->mlp != PL_MLP_BF16) return PL_ERR_INVALID_ARG;
     if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return PL_ERR_INVALID_ARG;
     if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0) || !std::isfinite(p->G)) return PL_ERR_INVALID_ARG;
-    if (!std::isfinite(p->rho_ref) || !std::isfinite(p->beta_rho) || !std::isfinite(p->beta_u) ||
-        !std::isfinite(p->threshold))
+    if (!(p->mask_eps >= 0.0) || !std::isfinite(p->mask_eps) || !std::isfinite(p->beta_rho) ||
+        !std::isfinite(p->beta_u) || !std::isfinite(p->threshold))
         return PL_ERR_INVALID_ARG;
     if (p->mlp_in != 2 && p->mlp_in != 11) return PL_ERR_INVALID_ARG;
     return PL_OK;
@@ -51,8 +51,9 @@ LatLayout lattice_layout(const pl_params* p) {
         L.pops[b] = o;
         o = align_up(o + (size_t)planes_of(p->storage) * (size_t)L.plane * storage_bytes(p->storage));
     }
-    L.scratch = o;  // rho, jx, jy, g, out3[3]: 7 fields (also >= 8N bytes for FP64 staging)
-    o = align_up(o + 7 * N * scratch_elem_bytes(p->storage));
+    L.scratch = o;  // rho, jx, jy, g, out3[3]: 7 fields (also >= 8N bytes for FP64 staging), then
+                    // the correction's band of cell indices (N ints)
+    o = align_up(o + 7 * N * scratch_elem_bytes(p->storage) + N * sizeof(int));
     L.partials = o;
     o = align_up(o + (size_t)L.red_blocks * PARTIAL_STRIDE * sizeof(double));
     L.rec = o;
@@ -73,6 +74,7 @@ void fill_desc(LatDesc& d, const pl_params* p, const LatLayout& L, char* base) {
     d.jy = sc + 2 * N * se;
     d.g = sc + 3 * N * se;
     d.out3 = sc + 4 * N * se;
+    d.band = reinterpret_cast<int*>(sc + 7 * N * se);
     d.partials = reinterpret_cast<double*>(base + L.partials);
     d.rec = reinterpret_cast<DevRecord*>(base + L.rec);
     d.plane = L.plane;
@@ -87,7 +89,7 @@ void fill_desc(LatDesc& d, const pl_params* p, const LatLayout& L, char* base) {
     d.G = p->G;
     d.tau = p->tau;
     d.rho0 = p->rho0;
-    d.rho_ref = p->rho_ref;
+    d.mask_eps = p->mask_eps;
     d.beta_rho = p->beta_rho;
     d.beta_u = p->beta_u;
     d.threshold = p->threshold;
@@ -260,7 +262,7 @@ int pl_params_default(pl_params* p, int32_t nx, int32_t ny) {
     p->G = -5.5;
     p->tau = 1.0;
     p->rho0 = 1.0;
-    p->rho_ref = 1.0;
+    p->mask_eps = 0.0;
     p->beta_rho = 0.1;
     p->beta_u = 0.01;
     p->threshold = 0.01;
@@ -292,7 +294,7 @@ int pl_lattice_create(const pl_params* p, void* dev_mem, size_t bytes, void* str
     pl_lattice* L = new (std::nothrow) pl_lattice();
     if (!L) return PL_ERR_BUDGET;
     L->p = *p;
-    L->phys = PhysParams{p->G, p->tau, p->rho0, p->rho_ref, p->beta_rho, p->beta_u, p->threshold};
+    L->phys = PhysParams{p->G, p->tau, p->rho0, p->mask_eps, p->beta_rho, p->beta_u, p->threshold};
     L->base = static_cast<char*>(dev_mem);
     L->bytes = bytes;
     L->stream = static_cast<cudaStream_t>(stream);

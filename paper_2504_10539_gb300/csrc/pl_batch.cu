@@ -417,7 +417,7 @@ PL_API int pl_batch_submit(pl_batch* b, const pl_params* p, const pl_droplet* d,
     v.rho = j.desc.rho;
     v.rec = j.desc.rec;
     v.droplets = reinterpret_cast<const pl_droplet*>(b->base + b->H.drops);
-    const PhysParams ph{p->G, p->tau, p->rho0, p->rho_ref, p->beta_rho, p->beta_u, p->threshold};
+    const PhysParams ph{p->G, p->tau, p->rho0, p->mask_eps, p->beta_rho, p->beta_u, p->threshold};
     b->h_drops.assign(d, d + n);
     auto fail = [&](cudaError_t e) {
         g_last_cuda_error = (int)e;
@@ -558,7 +558,7 @@ PL_API int pl_batch_get_state(pl_batch* b, int64_t job_id, double* host_f, int64
         v.pops[1] = j.desc.pops[1];
         v.rho = j.desc.rho;
         v.rec = j.desc.rec;
-        const PhysParams ph{j.p.G, j.p.tau, j.p.rho0, j.p.rho_ref, j.p.beta_rho, j.p.beta_u, j.p.threshold};
+        const PhysParams ph{j.p.G, j.p.tau, j.p.rho0, j.p.mask_eps, j.p.beta_rho, j.p.beta_u, j.p.threshold};
         const int cur = j.desc.phase ^ b->parity;
         const size_t N = (size_t)j.p.nx * j.p.ny;
         double* staging = static_cast<double*>(j.desc.rho);

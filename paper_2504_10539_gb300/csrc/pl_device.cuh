@@ -57,25 +57,29 @@ __device__ __forceinline__ typename Traits<MODE>::S encode(typename Traits<MODE>
 // FP16-offset storage (a storage measure of this implementation; the paper states no number
 // format).  A buffer holds ten FP16 planes: h_0..h_8 and the reference densities r.  The
 // population f_i at cell x is stored relative to the reference density of the cell it
-// streamed from:
-//     f_i(x) = h_i(x) + Wr_i r(x - c_i),
+// streamed from, scaled by 2^10:
+//     f_i(x) = 2^-10 h_i(x) + Wr_i r(x - c_i),
 // and a step stores r(x) = fp16(rho(x)) with the populations x pushes, so each offset is the
 // departure of f_i from its source cell's rest equilibrium (velocity and non-equilibrium
 // terms only, a few per cent of f_i).  Wr_i = kappa w_i = (1824, 456 x4, 114 x4) / 4096 with
 // kappa = 4104/4096: proportional to the lattice weights (so the offset folds into the
 // equilibrium's isotropic part) and short binary fractions (so Wr_i r and kappa r are exact
-// in FP32 for an FP16 r).  A cell's decoded populations carry sum h_i + kappa r(x).
+// in FP32 for an FP16 r).  The scale keeps offsets down to 2^-24 in FP16's normal range, where
+// a fixed 13-bit dither below the last place rounds them stochastically without bias.  A
+// cell's decoded populations carry 2^-10 sum h_i + kappa r(x).
 constexpr int F16_PLANES = 10;   // h_0..h_8, r
 constexpr int REF_PLANE = 9;
 constexpr float REF_KAPPA = 4104.0f / 4096.0f;
+constexpr float F16_SCALE = 1024.0f;          // stored offset = 2^10 (f_i - Wr_i r)
+constexpr float F16_UNSCALE = 1.0f / 1024.0f;
 __host__ __device__ constexpr float wref(int i) {
     return i == 0 ? 1824.0f / 4096.0f : (i <= 4 ? 456.0f / 4096.0f : 114.0f / 4096.0f);
 }
 __host__ __device__ constexpr int planes_of(int storage) { return storage == PL_F16_OFFSET ? F16_PLANES : 9; }
 
 // One FP16-offset cell (x, y) of a buffer f (ten planes of `plane` elements, rows of `pitch`):
-// its offsets h_i and reference terms t_i = Wr_i r(x - c_i) (exact products), so that
-// f_i = h_i + t_i and the cell's mass is A + H with A = sum t_i, H = sum h_i.
+// its offsets h_i (unscaled) and reference terms t_i = Wr_i r(x - c_i) (exact products), so
+// that f_i = h_i + t_i and the cell's mass is A + H with A = sum t_i, H = sum h_i.
 __device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long plane, int pitch, int nx, int ny, int x,
                                          int y, float (&h)[9], float (&t)[9]) {
     const long long o = (long long)y * pitch + x;
@@ -84,7 +88,7 @@ __device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long
                     rp = (long long)(y == ny - 1 ? 0 : y + 1) * pitch;
     const __half* ref = f + REF_PLANE * plane;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = __half2float(f[i * plane + o]);
+    for (int i = 0; i < 9; ++i) h[i] = __half2float(f[i * plane + o]) * F16_UNSCALE;
     t[0] = wref(0) * __half2float(ref[r0 + x]);
     t[1] = wref(1) * __half2float(ref[r0 + xm]);  // c_1 = (1, 0): from x - 1
     t[2] = wref(2) * __half2float(ref[rm + x]);   // c_2 = (0, 1): from y - 1
@@ -155,6 +159,14 @@ __device__ __forceinline__ __half2 sr_pack_half2(float a, float b, uint32_t ra, 
         "f"(__uint_as_float(sr_dither(a, ra))));
     return *reinterpret_cast<__half2*>(&r);
 }
+// Stochastic rounding of two FP32 values whose FP16 results are normal numbers: 13 dither bits
+// (the low 13 bits of da and db) below the FP16 last place, then truncation toward zero.
+__device__ __forceinline__ uint32_t sr13_pack(float a, float b, uint32_t da, uint32_t db) {
+    uint32_t r;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(__float_as_uint(b) + (db & 0x1FFFu))),
+        "f"(__uint_as_float(__float_as_uint(a) + (da & 0x1FFFu))));
+    return r;
+}
 __device__ __forceinline__ __half sr_half(float a, uint32_t rnd) {
     return __float2half_rz(__uint_as_float(sr_dither(a, rnd)));
 }
@@ -174,7 +186,7 @@ struct DevRecord {
     int status;          // sticky PL_ERR_* detected on the device
     int reject;          // set by the correction check pass, cleared per correction
     int applied;         // corrections applied
-    int pad;
+    int band_n;          // cells in the correction's interface band (when mask_eps > 0)
 };
 
 // Deterministic block reduction of NV values per thread, fixed tree shape.

@@ -37,7 +37,7 @@ struct LatticeView {
 };
 
 struct PhysParams {
-    double G, tau, rho0, rho_ref, beta_rho, beta_u, threshold;
+    double G, tau, rho0, mask_eps, beta_rho, beta_u, threshold;
 };
 
 // One lattice of a job table.
@@ -58,8 +58,9 @@ struct LatDesc {
     int has_centre;         // Laplace measurement defined (single droplet)
     unsigned seq0;          // table step count when the lattice joined (its own count = seq - seq0)
     int pad0;
-    double G, tau, rho0, rho_ref, beta_rho, beta_u, threshold;
+    double G, tau, rho0, mask_eps, beta_rho, beta_u, threshold;
     double cx, cy, width;   // droplet centre and profile width (Laplace)
+    int* band;              // the correction's interface band (cells with mask above mask_eps), in cell order
 };
 
 struct TabHeader {
@@ -122,9 +123,11 @@ cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int 
 // Density and momentum fields of every lattice (the network's stencil input reads rho).
 cudaError_t launch_moments_tab(const TableView& t, int storage, int parity, cudaStream_t s);
 // Network field of every lattice (BF16 tensor cores or SIMT) on n_in = 2 or 11 inputs (11
-// reads the density field, which must be current), then the correction.
+// reads the density field, which must be current); use_band: the tensor-core form evaluates
+// lattices with mask_eps > 0 on their interface band (d.band, rec->band_n) only.  Then the
+// correction.
 cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, int n_in, const float* w32,
-                           const uint16_t* wbf16, cudaStream_t s);
+                           const uint16_t* wbf16, cudaStream_t s, int use_band = 0);
 cudaError_t launch_correction_tab(const TableView& t, int storage, int parity, int mlp_mode, int n_in,
                                   const float* w32, const uint16_t* wbf16, cudaStream_t s);
 

@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
         const R* rho = static_cast<const R*>(d.rho);
         const R* g = static_cast<const R*>(d.g);
         const R* out3 = static_cast<const R*>(d.out3);
-        const R gmax = R(d.rec->gmax), beta_rho = R(d.beta_rho);
+        const R gmax = R(d.rec->gmax), beta_rho = R(d.beta_rho), eps = R(d.mask_eps);
         SumAcc<R> sm_m, sm_dr, sm_rho;  // sum m, sum drho_raw, sum rho
         const long long step = (long long)d.red_blocks * RB_THREADS;
         for (long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x; c0 < N; c0 += CELL_BATCH * step) {
@@ -528,9 +528,10 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums1(TableView t) {
             for (int u = 0; u < CELL_BATCH; ++u) {
                 if (c0 + u * step >= N) break;
                 const R r = rr[u];
-                const R mm = gmax > R(0) ? gg[u] / gmax : R(0);
+                R mm = gmax > R(0) ? gg[u] / gmax : R(0);
+                if (!(mm > eps)) mm = R(0);   // outside the interface band (the network is not read there)
                 sm_m.add(mm);
-                sm_dr.add(beta_rho * mm * (oo[u] - r));
+                sm_dr.add(mm > R(0) ? beta_rho * mm * (oo[u] - r) : R(0));
                 sm_rho.add(r);
             }
         }
@@ -576,15 +577,17 @@ struct CellCorr {
 };
 template <typename R>
 struct CorrK {
-    R gmax, proj, beta_rho, beta_u;  // proj = (sum drho_raw + M - M0) / sum m
+    R gmax, proj, beta_rho, beta_u, eps;  // proj = (sum drho_raw + M - M0) / sum m; eps: the band
 };
 template <typename R>
-__device__ __forceinline__ CorrK<R> corr_constants(const DevRecord* rec, double beta_rho, double beta_u) {
+__device__ __forceinline__ CorrK<R> corr_constants(const DevRecord* rec, double beta_rho, double beta_u,
+                                                   double eps) {
     CorrK<R> k;
     k.gmax = R(rec->gmax);
     k.proj = R(rec->proj);
     k.beta_rho = R(beta_rho);
     k.beta_u = R(beta_u);
+    k.eps = R(eps);
     return k;
 }
 // The cell's fields, loaded together (one memory round trip per cell).
@@ -601,6 +604,12 @@ template <typename R>
 __device__ __forceinline__ CellCorr<R> cell_corr(const CellIn<R>& in, const CorrK<R>& k) {
     CellCorr<R> q;
     q.m = in.g / k.gmax;
+    if (!(q.m > k.eps)) {   // outside the interface band: unchanged (the network is not read)
+        q.m = R(0);
+        q.rhop = in.r;
+        q.djx_raw = q.djy_raw = R(0);
+        return q;
+    }
     const R dr = k.beta_rho * q.m * (in.rh - in.r) - q.m * k.proj;
     q.rhop = in.r + dr;
     q.djx_raw = k.beta_u * q.m * (q.rhop * in.ux - in.jx);
@@ -625,7 +634,7 @@ __global__ void __launch_bounds__(RB_THREADS) k_corr_sums2(TableView t) {
         SumAcc<R> s_jx, s_jy;  // sum djx_raw, sum djy_raw
         bool reject = false;
         if (d.rec->sum_m > 0.0) {
-            const CorrK<R> k = corr_constants<R>(d.rec, d.beta_rho, d.beta_u);
+            const CorrK<R> k = corr_constants<R>(d.rec, d.beta_rho, d.beta_u, d.mask_eps);
             const long long step = (long long)d.red_blocks * RB_THREADS;
             for (long long c0 = (long long)m.lb * RB_THREADS + threadIdx.x; c0 < N; c0 += 2 * step) {
                 // two cells' loads together, then the cells in walk order
@@ -725,7 +734,7 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
         const R* out3 = static_cast<const R*>(d.out3);
         S* f = static_cast<S*>(d.pops[d.phase ^ parity]);
         const R sjx = R(rec->mjx), sjy = R(rec->mjy);
-        const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u);
+        const CorrK<R> k = corr_constants<R>(rec, d.beta_rho, d.beta_u, d.mask_eps);
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
              it.next(d.nx)) {
             const long long c = it.c;
@@ -735,8 +744,8 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
             S fs[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) fs[i] = f[i * d.plane + o];
-            if (!(in.g > R(0))) continue;
             const CellCorr<R> q = cell_corr(in, k);
+            if (!(q.m > R(0))) continue;
             const R djx = q.djx_raw - q.m * sjx, djy = q.djy_raw - q.m * sjy;
             const R r = in.r, jxc = in.jx, jyc = in.jy;
             R fn[9], fo[9];
@@ -746,7 +755,7 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
                 float hn[9];
                 float res = 0.0f;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) hn[i] = __half2float(fs[i]) + (fn[i] - fo[i]);
+                for (int i = 0; i < 9; ++i) hn[i] = fmaf(F16_SCALE, fn[i] - fo[i], __half2float(fs[i]));
 #pragma unroll
                 for (int i = 1; i < 9; ++i) {
                     const __half qh = __float2half_rn(hn[i]);
@@ -764,15 +773,100 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// The correction's interface band (lattices with mask_eps > 0): the cells whose mask
+// m = g / G_max is above mask_eps, compacted per lattice into d.band (block by block in the
+// fixed reduction partition, within a block thread by thread in walk order: deterministic), so
+// that the network is evaluated on the band only.  The mask is formed as in cell_corr.
+
+// A thread's band cells (or their count when out == nullptr) in its walk order.
+template <typename R>
+__device__ __forceinline__ unsigned band_walk(const LatDesc& d, int lb, int* out) {
+    const R* g = static_cast<const R*>(d.g);
+    const R gmax = R(d.rec->gmax), eps = R(d.mask_eps);
+    const long long N = (long long)d.nx * d.ny;
+    unsigned n = 0;
+    for (long long c = (long long)lb * RB_THREADS + threadIdx.x; c < N; c += (long long)d.red_blocks * RB_THREADS) {
+        const R m = gmax > R(0) ? g[c] / gmax : R(0);
+        if (m > eps) {
+            if (out) out[n] = (int)c;
+            ++n;
+        }
+    }
+    return n;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RB_THREADS) k_band_count(TableView t) {
+    __shared__ double sm[32];
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    const int op[1] = {0};
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        if (!(d.mask_eps > 0.0)) continue;
+        double v[1] = {(double)band_walk<R>(d, m.lb, nullptr)};
+        block_reduce<1>(v, op, sm);
+        if (threadIdx.x == 0) d.partials[m.lb * PARTIAL_STRIDE + 0] = v[0];
+    }
+}
+
+// One thread per lattice: each block's first band position (slot 1) and the band's size.
+__global__ void k_band_scan(TableView t) {
+    const int n = t.hdr->n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const LatDesc& d = t.d[j];
+        if (!(d.mask_eps > 0.0)) {
+            d.rec->band_n = -1;
+            continue;
+        }
+        double off = 0.0;
+        for (int b = 0; b < d.red_blocks; ++b) {
+            d.partials[b * PARTIAL_STRIDE + 1] = off;
+            off += d.partials[b * PARTIAL_STRIDE + 0];
+        }
+        d.rec->band_n = (int)off;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RB_THREADS) k_band_write(TableView t) {
+    __shared__ unsigned scan[RB_THREADS];
+    const int n = t.hdr->n, total = t.hdr->total_blocks;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const BlkMap m = map_blk(t, n, vb);
+        const LatDesc& d = t.d[m.j];
+        if (!(d.mask_eps > 0.0)) continue;
+        // exclusive scan of the per-thread counts (Hillis-Steele in shared memory)
+        const unsigned cnt = band_walk<R>(d, m.lb, nullptr);
+        scan[threadIdx.x] = cnt;
+        __syncthreads();
+        for (int off = 1; off < RB_THREADS; off <<= 1) {
+            const unsigned add = threadIdx.x >= off ? scan[threadIdx.x - off] : 0u;
+            __syncthreads();
+            scan[threadIdx.x] += add;
+            __syncthreads();
+        }
+        const long long first = (long long)d.partials[m.lb * PARTIAL_STRIDE + 1] + scan[threadIdx.x] - cnt;
+        __syncthreads();
+        band_walk<R>(d, m.lb, d.band + first);
+    }
+}
+
 template <int MODE>
 static cudaError_t correction_t(const TableView& t, int parity, int mlp_mode, int n_in, const float* w32,
                                 const uint16_t* wbf16, cudaStream_t s) {
     using R = typename Traits<MODE>::R;
     k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);  // rho, j (and the stencil input)
-    cudaError_t e = launch_mlp_tab(t, MODE, mlp_mode, n_in, w32, wbf16, s);
-    if (e != cudaSuccess) return e;
     k_grad_tab<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_final_metrics_tab<<<RED_GRID, RB_THREADS, 0, s>>>(t, 0);
+    // the interface band of lattices with mask_eps > 0 (the network then runs on it only)
+    k_band_count<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    k_band_scan<<<(RED_GRID + 127) / 128, 128, 0, s>>>(t);
+    k_band_write<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
+    note_launches(3);
+    cudaError_t e = launch_mlp_tab(t, MODE, mlp_mode, n_in, w32, wbf16, s, 1);
+    if (e != cudaSuccess) return e;
     k_corr_sums1<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_corr_final1<<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_corr_sums2<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);

@@ -14,7 +14,8 @@
 
 namespace pl {
 
-cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, cudaStream_t s);
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, int use_band,
+                          cudaStream_t s);
 
 constexpr int MLP_THREADS = 64;
 constexpr int MLP_CHUNK = 16;
@@ -126,14 +127,14 @@ static cudaError_t mlp_simt_t(const TableView& t, const float* w32, int n_in, cu
 }
 
 cudaError_t launch_mlp_tab(const TableView& t, int storage, int mlp_mode, int n_in, const float* w32,
-                           const uint16_t* wbf16, cudaStream_t s) {
+                           const uint16_t* wbf16, cudaStream_t s, int use_band) {
     if (n_in != 2 && n_in != 11) return cudaErrorInvalidValue;
     // The output element type follows the lattice's scratch type: double for FP64 storage.
     if (storage == PL_F64) {
         if (mlp_mode != PL_MLP_F64) return cudaErrorInvalidValue;
         return mlp_simt_t<double>(t, w32, n_in, s);
     }
-    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(t, w32, wbf16, n_in, s);
+    if (mlp_mode == PL_MLP_BF16) return launch_mlp_tc(t, w32, wbf16, n_in, use_band, s);  // (CUDA cores: every cell)
     if (mlp_mode != PL_MLP_F32) return cudaErrorInvalidValue;
     return mlp_simt_t<float>(t, w32, n_in, s);
 }

@@ -156,7 +156,7 @@ __device__ __forceinline__ int find_tile(const long long* __restrict__ pre, int 
 // that the paper's form keeps its own register allocation.
 template <int NIN>
 __global__ void __launch_bounds__(tc::THREADS, 1)
-    k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, TableView tab) {
+    k_mlp_tc(const uint16_t* __restrict__ wimg, const float* __restrict__ w32, TableView tab, int use_band) {
     constexpr int n_in = NIN;
     using namespace tc;
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -237,8 +237,20 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const long long N = (long long)nx * ny;
         float* out3 = static_cast<float*>(ld.out3);
         last_rec = ld.rec;
-        const long long c = (tile - tab.tile_pre[lj]) * M + t;
-        const long long cc = c < N ? c : N - 1;
+        // the tile's cells: consecutive cells, or (an interface band) consecutive band entries;
+        // a lattice's band fills its first tiles, the others have no work (uniform per warpgroup)
+        const long long pos = (tile - tab.tile_pre[lj]) * M + t;
+        long long cc;
+        bool valid;
+        if (use_band && ld.mask_eps > 0.0) {
+            const long long nb = ld.rec->band_n;
+            if ((tile - tab.tile_pre[lj]) * M >= nb) continue;
+            valid = pos < nb;
+            cc = ld.band[valid ? pos : nb - 1];
+        } else {
+            valid = pos < N;
+            cc = valid ? pos : N - 1;
+        }
         const int x = (int)(cc % nx), y = (int)(cc / nx);
         const float xh = 2.0f * ((float)x + 0.5f) / (float)nx - 1.0f;
         const float yh = 2.0f * ((float)y + 0.5f) / (float)ny - 1.0f;
@@ -356,11 +368,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             }
         }
         if (!ok) break;
-        if (c < N) {
+        if (valid) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const float2 s2 = add2(oa[k], ob[k]);
-                out3[k * N + c] = s2.x + s2.y;
+                out3[k * N + cc] = s2.x + s2.y;
             }
         }
     }
@@ -392,7 +404,8 @@ cudaError_t launch_selftest_wait(int* d_status, long long limit_ns, cudaStream_t
 }
 
 template <int NIN>
-static cudaError_t launch_mlp_tc_t(const TableView& t, const float* w32, const uint16_t* wbf16, cudaStream_t s) {
+static cudaError_t launch_mlp_tc_t(const TableView& t, const float* w32, const uint16_t* wbf16, int use_band,
+                                   cudaStream_t s) {
     static int sms = 0;
     if (!sms) {
         cudaError_t e =
@@ -404,14 +417,15 @@ static cudaError_t launch_mlp_tc_t(const TableView& t, const float* w32, const u
         if (sms < 1) sms = 1;
     }
     // persistent: one CTA per SM (CTAs without a tile return before any set-up)
-    k_mlp_tc<NIN><<<sms, tc::THREADS, tc::SMEM_ALLOC, s>>>(wbf16, w32, t);
+    k_mlp_tc<NIN><<<sms, tc::THREADS, tc::SMEM_ALLOC, s>>>(wbf16, w32, t, use_band);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, cudaStream_t s) {
-    if (n_in == 11) return launch_mlp_tc_t<11>(t, w32, wbf16, s);
-    return launch_mlp_tc_t<2>(t, w32, wbf16, s);
+cudaError_t launch_mlp_tc(const TableView& t, const float* w32, const uint16_t* wbf16, int n_in, int use_band,
+                          cudaStream_t s) {
+    if (n_in == 11) return launch_mlp_tc_t<11>(t, w32, wbf16, use_band, s);
+    return launch_mlp_tc_t<2>(t, w32, wbf16, use_band, s);
 }
 
 }  // namespace pl

@@ -499,18 +499,17 @@ __device__ __forceinline__ void walk_impl2(const WalkArgs<MODE>& a, int strip, i
 // ---------------------------------------------------------------------------------------------
 // FP16-offset walker: the strip walk of walk_impl2 on packed FP32 pairs, with the storage of
 // pl_device.cuh.  A population arriving at cell x is decoded against the reference density of
-// the cell it streamed from, f_i = h_i + Wr_i r(x - c_i); the relaxed pair stores its new
-// reference r(x) = fp16(rho(x)) in plane 9 and pushes h_i = f_i* - Wr_i r(x).  The reference
+// the cell it streamed from, f_i = 2^-10 h_i + Wr_i r(x - c_i); the relaxed pair stores its new
+// reference r(x) = fp16(rho(x)) in plane 9 and pushes h_i = 2^10 (f_i* - Wr_i r(x)).  The reference
 // rows y-1, y, y+1 are held as packed FP16 pairs: the lane's own pair and, in a second word,
 // its left and right neighbours (the adjacent lanes' values by shuffle; lanes 0 and 31 read
 // their one outer column from memory), loaded one row ahead of the populations.
 //
-// Mass: with Wr summing to exactly one and every product Wr_i r exact in FP32, the mass a
-// cell receives is A + H, A = sum Wr_i r(x - c_i) (exact where the references agree in
-// their binade) and H = sum h_i (exact: FP16 offsets).  The pushed populations carry
-// r(x) + sum_{i>0} h_i* + h_0*, and the rest population takes (A - r(x)) + H - sum_{i>0} h_i*,
-// rounded stochastically: the stored mass changes by one zero-mean rounding of a small
-// offset per cell and step.
+// Mass: the relaxed cell's populations carry 2^-10 sum h_i + kappa r(x) once decoded (kappa r
+// exact in FP32), so the rest offset takes 2^10 (rho - kappa r(x)) - sum_{i>0} h_i: the cell's
+// mass to within FP32 rounding of its density sum and one zero-mean rounding of the rest
+// offset.  Every offset is rounded stochastically, so rounding biases neither the mass nor the
+// momentum a population carries.
 __device__ __forceinline__ uint32_t h2u(__half2 v) { return *reinterpret_cast<uint32_t*>(&v); }
 __device__ __forceinline__ __half2 u2h(uint32_t v) { return *reinterpret_cast<__half2*>(&v); }
 
@@ -533,7 +532,9 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
     const bool halo = lane == 0 || lane == 31;
     const int cX = lane == 0 ? wrapi(ua - 1, nx) : wrapi(ua + 2, nx);  // a halo lane's outer column
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    const float W0 = wref(0), W1 = wref(1), W2 = wref(5);
+    // the walk runs in units of 2^-10 (populations F = 2^10 f, densities rho_s = 2^10 rho):
+    // a stored offset h is then F - 2^10 Wr_i r directly
+    const float W0 = F16_SCALE * wref(0), W1 = F16_SCALE * wref(1), W2 = F16_SCALE * wref(5);
     const uint32_t planeU = (uint32_t)a.plane, pitchU = (uint32_t)a.pitch;
     // element offset of column 0 of row r of plane i (FAST strips: 32 bits, checked by the caller)
     auto row_off = [&](int i, int r) -> long long {
@@ -603,7 +604,7 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
             load_pops(rn, Nx);                       // prefetch the next row
         }
         // decode row r0+k-1 against the references of rows r0+k-2 (rm), r0+k-1 (rc), r0+k (rp):
-        // f_i = h_i + Wr_i r(x - c_i), one FMA each (the shifted views per half)
+        // F_i = h_i + 2^10 Wr_i r(x - c_i), one FMA each (the shifted views per half)
         float2 fc[9];
         {
             float2 h[9];
@@ -627,7 +628,7 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
         const float2 rhoc = (((fc[0] + fc[1]) + (fc[2] + fc[3])) + ((fc[4] + fc[5]) + (fc[6] + fc[7]))) + fc[8];
         PA = PB;
         PB = PC;
-        PC = psi2<PL_F16_OFFSET>(rhoc, a.k);
+        PC = psi2<PL_F16_OFFSET>(rhoc * bc2(F16_UNSCALE), a.k);
         if (k >= 2) {
             int y = r0 + k - 2;
             if (y >= ny) y -= ny;
@@ -643,30 +644,39 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
             const float sy0 = w1 * (C.a - A.a) + w2 * ((C.b + C.L) - (A.b + A.L));
             const float sx1 = w1 * (B.Rr - B.a) + w2 * ((C.Rr - C.a) + (A.Rr - A.a));
             const float sy1 = w1 * (C.b - A.b) + w2 * ((C.Rr + C.a) - (A.Rr + A.a));
-            const float g0 = -a.k.G * B.a, g1 = -a.k.G * B.b;
-            // the pair's new reference; the relaxation then gives the offsets directly
-            // (o_i = f_i* - Wr_i r, the shift kappa r / omega taken off the isotropic part)
+            // the force in the walk's units (the collision takes tau F / rho with rho scaled)
+            const float g0 = -a.k.G * F16_SCALE * B.a, g1 = -a.k.G * F16_SCALE * B.b;
+            // the pair's new reference; the relaxation then gives the stored offsets directly
+            // (o_i = F_i* - 2^10 Wr_i r, the shift 2^10 kappa r / omega taken off the isotropic part)
             uint32_t rq;
-            asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(rq) : "f"(rho_p.y), "f"(rho_p.x));
+            {
+                const float2 rho = rho_p * bc2(F16_UNSCALE);
+                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(rq) : "f"(rho.y), "f"(rho.x));
+            }
             const float2 rqf = __half22float2(u2h(rq));
             float2 o[9];
             collide_pair<PL_F16_OFFSET, true>(fp, rho_p, make_float2(g0 * sx0, g1 * sx1), make_float2(g0 * sy0, g1 * sy1),
-                                              a.k, o, bc2(REF_KAPPA * a.k.tau) * rqf);
+                                              a.k, o, bc2(REF_KAPPA * F16_SCALE * a.k.tau) * rqf);
+            // every offset rounded stochastically (unbiased: no drift of mass or momentum from
+            // rounding), the dither from a counter-based hash of the pair's position and the
+            // lattice's step count, stepped by a linear congruential sequence per population
+            const uint32_t rnd =
+                fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
+            uint32_t st = rnd;
             uint32_t out[9];
             float s0 = 0.0f, s1 = 0.0f;
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
-                asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(out[i]) : "f"(o[i].y), "f"(o[i].x));
+                st = st * 1664525u + 1013904223u;
+                out[i] = sr13_pack(o[i].x, o[i].y, st >> 19, st >> 6);
                 unsigned short lo, hi;
                 asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(out[i]));
                 asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s0) : "h"(lo));
                 asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s1) : "h"(hi));
             }
             // rest offset: the cell's mass minus what the pushed populations carry
-            const float2 rest = (rho_p - bc2(REF_KAPPA) * rqf) - make_float2(s0, s1);
-            const uint32_t rnd =
-                fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
-            out[0] = h2u(sr_pack_half2(rest.x, rest.y, rnd, __funnelshift_l(rnd, rnd, 16)));
+            const float2 rest = (rho_p - bc2(REF_KAPPA * F16_SCALE) * rqf) - make_float2(s0, s1);
+            out[0] = sr13_pack(rest.x, rest.y, rnd, rnd >> 16);
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             auto dst = [&](int i, int row) -> __half* { return a.fout + row_off(i, row) + ua; };
             // c_x = 0 planes and the reference: own pair
@@ -934,17 +944,18 @@ __global__ void k_f16_encode_rest(__half* __restrict__ f, int nx, int ny, int pi
         double carried = ref_term(ref, nx, ny, pitch, x, y, 0);
         for (int i = 1; i < 9; ++i) {
             const double t = ref_term(ref, nx, ny, pitch, x, y, i);
-            const __half h = __double2half(wq<double>(i) * rho[c] - t);
+            const __half h = __double2half((wq<double>(i) * rho[c] - t) * (double)F16_SCALE);
             f[i * plane + o] = h;
-            carried += (double)__half2float(h) + t;
+            carried += (double)__half2float(h) * (double)F16_UNSCALE + t;
         }
-        f[o] = __double2half(rho[c] - carried);
+        f[o] = __double2half((rho[c] - carried) * (double)F16_SCALE);
     }
 }
 
 // FP64 dense exchange array <-> one pitched storage plane (plane index `i`).  FP16-offset
-// storage decodes f_i = h_i + Wr_i r(x - c_i) and encodes h_i = fp16(f_i - Wr_i r(x - c_i)) (to
-// nearest, in FP64) against the reference plane, which k_ref_from_rho has set first.
+// storage decodes f_i = 2^-10 h_i + Wr_i r(x - c_i) and encodes h_i = fp16(2^10 (f_i - Wr_i
+// r(x - c_i))) (to nearest, in FP64) against the reference plane, which k_ref_from_rho has set
+// first.
 template <int MODE>
 __global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, int nx, int ny, int pitch, long long plane,
                                 int i, double* __restrict__ buf, int to_f64) {
@@ -955,8 +966,8 @@ __global__ void k_plane_convert(typename Traits<MODE>::S* __restrict__ f, int nx
         const long long o = i * plane + (long long)y * pitch + x;
         if constexpr (MODE == PL_F16_OFFSET) {
             const double t = ref_term(f + REF_PLANE * plane, nx, ny, pitch, x, y, i);
-            if (to_f64) buf[c] = (double)__half2float(f[o]) + t;
-            else f[o] = __double2half(buf[c] - t);
+            if (to_f64) buf[c] = (double)__half2float(f[o]) * (double)F16_UNSCALE + t;
+            else f[o] = __double2half((buf[c] - t) * (double)F16_SCALE);
         } else {
             if (to_f64) buf[c] = (double)decode<MODE>(f[o]);
             else f[o] = encode<MODE>(R(buf[c]));

@@ -66,7 +66,7 @@ class Lattice:
     G: float = -5.5
     tau: float = 1.0
     rho0: float = 1.0
-    rho_ref: float = 1.075            # FP16-offset reference density
+    mask_eps: float = 0.0             # interface band of the correction (0: every cell)
     droplets: List[Tuple[float, float, float]] = dataclasses.field(default_factory=list)
     rho_in: float = 2.0
     rho_out: float = 0.15
@@ -117,7 +117,6 @@ def field_4096(storage: int = F16_OFFSET, seed: int = 3, side: int = 4096, n_dro
     return Lattice(side, side, storage=storage, tau=0.8,
                    droplets=field_droplets(n_drop, side, side, 8.0, 40.0, 100 + seed),
                    rho_in=FIELD_RHO_IN, rho_out=FIELD_RHO_OUT,
-                   rho_ref=0.5 * (FIELD_RHO_IN + FIELD_RHO_OUT),
                    seed=seed, steps=5000, K=100, mlp=MLP_BF16, weight_seed=10 + seed)
 
 
@@ -202,7 +201,6 @@ def serve_poisson(n_requests: int = 500, rate_hz: float = 200.0, seed: int = 5,
         steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
         rho_v, rho_l = coexistence(G)
         job = Lattice(side, side, storage=storage, G=G, tau=serve_tau(G), rho_in=rho_l, rho_out=rho_v,
-                      rho_ref=0.5 * (rho_l + rho_v),
                       droplets=[(float(a), float(b), float(c)) for a, b, c in zip(cx, cy, r)],
                       seed=seed * 1000000 + k, steps=steps, K=K, mlp=MLP_BF16,
                       weight_seed=10 + seed)

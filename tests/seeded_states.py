@@ -7,7 +7,7 @@ values the GPU holds.  No state produced by the CUDA path ever feeds the oracle.
 
 The FP16-offset exchange format written out here is the library's documented one: ten FP16
 planes per buffer, the offsets h_0..h_8 and the reference densities r, with
-f_i(x) = h_i(x) + Wr_i r(x - c_i), Wr = (1824, 456 x4, 114 x4) / 4096.
+f_i(x) = 2^-10 h_i(x) + Wr_i r(x - c_i), Wr = (1824, 456 x4, 114 x4) / 4096.
 """
 import numpy as np
 
@@ -18,6 +18,7 @@ F64, F32, F16 = 0, 1, 2
 CX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
 CY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
 WREF = np.array([1824, 456, 456, 456, 456, 114, 114, 114, 114], dtype=np.float64) / 4096.0
+SCALE = 1024.0
 
 
 def oracle_droplet_state(nx, ny, droplets, steps=0, G=-5.5, tau=1.0, seed=3, rho_in=2.0, rho_out=0.15):
@@ -33,23 +34,28 @@ def source_refs(r):
     return np.stack([np.roll(np.roll(r, CY[i], axis=0), CX[i], axis=1) for i in range(9)])
 
 
+def f16(v):
+    """Round to the nearest FP16 number, returned as FP64."""
+    return v.astype(np.float16).astype(np.float64)
+
+
 def encode_f16(f):
     """FP16-offset storage of populations f as pl_set_state writes it: r = fp16(rho) with rho
-    summed in order 0..8 in FP64, h_i = fp16(f_i - Wr_i r(x - c_i)), both rounded to nearest.
-    Returns (h[9, ny, nx], r[ny, nx]) as float16 arrays."""
+    summed in order 0..8 in FP64, h_i = fp16(2^10 (f_i - Wr_i r(x - c_i))), both rounded to
+    nearest.  Returns (h[9, ny, nx], r[ny, nx]) as float16 arrays."""
     rho = f[0].copy()
     for i in range(1, 9):
         rho = rho + f[i]
     r = rho.astype(np.float16)
-    h = (f - WREF[:, None, None] * source_refs(r.astype(np.float64))).astype(np.float16)
+    h = ((f - WREF[:, None, None] * source_refs(r.astype(np.float64))) * SCALE).astype(np.float16)
     return h, r
 
 
 def decode_f16(h, r):
-    return h.astype(np.float64) + WREF[:, None, None] * source_refs(r.astype(np.float64))
+    return h.astype(np.float64) / SCALE + WREF[:, None, None] * source_refs(r.astype(np.float64))
 
 
-def stored(f, storage, rho_ref=None):
+def stored(f, storage):
     """FP64 populations near f that the storage type holds exactly: storing them
     (pl_set_state) and reading them back (pl_get_state) returns them unchanged.  FP32: f
     rounded to nearest.  FP16-offset: the references r = fp16(rho(f)), the moving offsets
@@ -64,8 +70,8 @@ def stored(f, storage, rho_ref=None):
     r = r.astype(np.float64)
     rs = WREF[:, None, None] * source_refs(r)
     g = np.empty_like(f)
-    g[1:] = (f[1:] - rs[1:]).astype(np.float16).astype(np.float64) + rs[1:]
-    g[0] = (r - rs[0] - g[1:].sum(axis=0)).astype(np.float16).astype(np.float64) + rs[0]
+    g[1:] = f16((f[1:] - rs[1:]) * SCALE) / SCALE + rs[1:]
+    g[0] = f16((r - rs[0] - g[1:].sum(axis=0)) * SCALE) / SCALE + rs[0]
     h2, r2 = encode_f16(g)
     assert np.array_equal(r2.astype(np.float64), r) and np.array_equal(decode_f16(h2, r2), g)
     return g
@@ -79,9 +85,10 @@ def exact_state(f, storage):
     density of a cell is the same number in FP32 on the GPU and in FP64 in the oracle:
       - FP32: values on multiples of 2^-21 (all below 4);
       - FP16-offset: references r on multiples of 2^-9 (FP16 numbers below 4, so Wr_i r is a
-        multiple of 2^-21), moving offsets FP16 numbers on multiples of 2^-21, and the rest
-        offset chosen so that each cell's density is r again (within one FP16 rounding of
-        h_0 when |h_0| >= 2^-10), so that pl_set_state derives the same references;
+        multiple of 2^-21), moving offsets (2^-10 times FP16 numbers) on multiples of 2^-21,
+        and the rest offset chosen so that each cell's density is r again (within one FP16
+        rounding of 2^10 h_0 when |h_0| >= 2^-10), so that pl_set_state derives the same
+        references;
       - FP64: unchanged."""
     if storage == F64:
         return f.copy()
@@ -92,11 +99,12 @@ def exact_state(f, storage):
     rs = source_refs(r)
     h = np.zeros_like(f)
     for i in range(1, 9):
-        hi = (f[i] - WREF[i] * rs[i]).astype(np.float16).astype(np.float64)
+        hi = f16((f[i] - WREF[i] * rs[i]) * SCALE) / SCALE
         h[i] = np.round(hi / GRID) * GRID
     h0 = r - WREF[0] * r - (h[1:] + WREF[1:, None, None] * rs[1:]).sum(axis=0)
-    h[0] = h0.astype(np.float16).astype(np.float64)
+    h[0] = f16(h0 * SCALE) / SCALE
     assert np.array_equal(np.round(h[0] / GRID) * GRID, h[0])
+    assert np.array_equal(f16(h * SCALE) / SCALE, h)
     out = h + WREF[:, None, None] * rs
     assert np.array_equal(encode_f16(out)[1].astype(np.float64), r)
     return out

@@ -21,8 +21,8 @@ storage, and relative mass drift (from the lattice's own M0) at most 1e-6.
   2000 steps of the batch, FP16-offset and FP32 storage.  Lattice 102 (G = -6.0, a droplet of
   0.32 of the side started far below its coexistence density) is chaotic: FP32 storage leaves
   the oracle's trajectory too (3.5e-2), so the bounds cannot hold for it in any format short
-  of FP64; lattice 31 (1024^2, G = -5.68) amplifies rounding strongly (FP32 8.8e-5, FP16 2.2e-2
-  measured).  Both are recorded, not asserted; the FP16 bound is asserted on the other four.
+  of FP64; it is recorded, not asserted.  The bounds are asserted on the other five (lattice
+  31, 1024^2 at G = -5.68, amplifies rounding most: FP32 8.8e-5, FP16 2.9e-3 measured).
 Every measured number is written to the JSON file named by PL_ACCURACY_OUT, if set.
 """
 import json
@@ -161,7 +161,7 @@ def test_c3_field_fp32_5000_steps(c3_oracle):
 # ----------------------------------------------------------------------------- C4
 
 C4_PICK = (1, 12, 31, 46, 90, 102)      # largest, smallest, extreme tau and G of the batch
-C4_RECORDED_ONLY = {31, 102}
+C4_RECORDED_ONLY = {102}
 
 
 @pytest.fixture(scope="module")

@@ -22,19 +22,18 @@ if not torch.cuda.is_available():
 
 F64, F32, F16 = B.PL_F64, B.PL_F32, B.PL_F16_OFFSET
 SIZES = [(1, 1), (2, 3), (1, 9), (5, 7), (67, 35), (130, 70), (300, 33)]
-RHO_REF = 1.075
 
 
 def lattice(nx, ny, storage, mlp=None, **kw):
     if mlp is None:
         mlp = B.PL_MLP_F64 if storage == F64 else B.PL_MLP_F32
-    p = B.pl_params_default(nx, ny, storage=storage, mlp=mlp, rho_ref=RHO_REF, **kw)
+    p = B.pl_params_default(nx, ny, storage=storage, mlp=mlp, **kw)
     return B.Lattice(p)
 
 
 def stored(f, storage):
     """The FP64 values a storage type actually holds for populations f."""
-    return S.stored(f, storage, RHO_REF)
+    return S.stored(f, storage)
 
 
 def rel_linf(a, b):
@@ -170,15 +169,17 @@ def test_f16_correction_matches_oracle_and_restores_mass(nx, ny):
     f1, _ = lat.state()
     fo = f0.copy()
     assert O.correct(fo, blob, 0.3, 0.05, O.mass(f0), O.MLP_F64) == 0
-    # Per cell, in offset space h = f - Wr_i r(x - c_i) (the references of the stored state,
+    # Per cell, in offset space h = f - Wr_i r(x - c_i) (stored as 2^10 h; the references of the stored state,
     # which the correction leaves as they are): a moving population is rounded to nearest (at
     # most half its FP16 spacing); the rest population takes the cell's corrected mass minus
     # the rounded moving populations, so their eight rounding errors land in it, and is then
     # rounded stochastically (less than one spacing).
     _, r = S.encode_f16(f0)
     off = S.WREF[:, None, None] * S.source_refs(r.astype(np.float64))
-    sp = np.maximum(np.spacing(np.abs(fo - off).astype(np.float16)), np.spacing(np.abs(f1 - off).astype(np.float16)))
-    sp = sp.astype(np.float64)                       # the larger spacing if the two straddle a binade
+    # FP16 spacing of the stored (2^10-scaled) offsets, in population units
+    sp = np.maximum(np.spacing((np.abs(fo - off) * S.SCALE).astype(np.float16)),
+                    np.spacing((np.abs(f1 - off) * S.SCALE).astype(np.float16)))
+    sp = sp.astype(np.float64) / S.SCALE             # the larger spacing if the two straddle a binade
     # The corrected values themselves differ from the oracle's by the FP32 network (within
     # 2e-5 of the FP64 one) times beta_rho = 0.3, i.e. < 1e-5: near a rounding midpoint that
     # can tip a rounding, hence the slack.

@@ -39,8 +39,7 @@ def droplet_lattice(nx, ny, storage, steps=40, seed=3):
     mlp = B.PL_MLP_F64 if storage == B.PL_F64 else B.PL_MLP_BF16
     job = wl.Lattice(nx, ny, storage=storage, mlp=mlp, droplets=[(nx / 2, ny / 2, min(nx, ny) / 4)], seed=seed,
                      K=1, weight_seed=30 + seed)
-    f = S.stored(S.oracle_droplet_state(nx, ny, job.droplets, steps=steps, G=job.G, tau=job.tau, seed=seed), storage,
-                 job.rho_ref)
+    f = S.stored(S.oracle_droplet_state(nx, ny, job.droplets, steps=steps, G=job.G, tau=job.tau, seed=seed), storage)
     lat = B.Lattice(B.job_params(job))
     lat.set_state(f, steps)
     lat.set_weights(job.weights())
@@ -172,7 +171,7 @@ def test_full_size_512_gradient_matches_oracle():
     gradient and loss terms against the oracle's over all 262,144 cells."""
     job = wl.single_512()
     f = S.stored(S.oracle_droplet_state(job.nx, job.ny, job.droplets, steps=200, G=job.G, tau=job.tau, seed=job.seed),
-                 job.storage, job.rho_ref)
+                 job.storage)
     lat = B.Lattice(B.job_params(job))
     lat.set_state(f, 200)
     lat.set_weights(job.weights())

@@ -34,7 +34,7 @@ def seeded_lattice(job, steps):
     """A lattice holding the oracle's droplet of `job` after `steps` of its steps (stored exactly
     in the lattice's storage type), with the job's weights; returns the lattice and the state."""
     f = S.stored(S.oracle_droplet_state(job.nx, job.ny, job.droplets, steps=steps, G=job.G, tau=job.tau,
-                                        seed=job.seed), job.storage, job.rho_ref)
+                                        seed=job.seed), job.storage)
     lat = B.Lattice(B.job_params(job))
     lat.set_state(f, steps)
     lat.set_weights(job.weights())
