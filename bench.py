@@ -147,10 +147,15 @@ def measured_peaks_bf16():
 
 
 def step_kernel_hash():
-    h = hashlib.sha1()
-    for f in ("pl_step.cu", "pl_device.cuh", "pl_kernels.h"):
-        h.update(open(os.path.join(ROOT, "paper_2504_10539_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
+    """Source hash of the step kernel (what the recorded DRAM traffic depends on)."""
+    from paper_2504_10539_gb300 import build as PB
+    return PB.source_hash(("pl_step.cu", "pl_device.cuh", "pl_kernels.h"))
+
+
+def library_hash():
+    """Source hash of the whole library (what the recorded accuracy depends on)."""
+    from paper_2504_10539_gb300 import build as PB
+    return PB.source_hash()
 
 
 def profiled_traffic(key, units):
@@ -199,12 +204,12 @@ def cpu_sample(jobs, budget_s):
 def accuracy_record():
     """The full-length accuracy results (rho rel L-inf, W, mass drift against the FP64 oracle)
     as recorded by tests/test_gpu_accuracy.py on a GB300 (profiles/accuracy_full_length.json),
-    marked stale if the step kernel's source changed since."""
+    marked stale if the library's source changed since."""
     p = os.path.join(ROOT, "profiles", "accuracy_full_length.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p))
-    rec["stale"] = rec.get("kernel_sha1") != step_kernel_hash()
+    rec["stale"] = rec.get("source_sha1") != library_hash()
     return rec
 
 

@@ -6,6 +6,7 @@ compiled in parallel, linked with -shared.  Output:
 """
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -37,6 +38,17 @@ def _sources():
 def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(INCLUDE, "*.h"))
+
+
+def source_hash(names=None):
+    """Short SHA-1 of the library's sources (or of the named files of csrc/ only): recorded
+    measurements carry it, so that a later source change marks them stale."""
+    h = hashlib.sha1()
+    paths = [os.path.join(CSRC, n) for n in names] if names else sorted(_deps())
+    for p in paths:
+        h.update(os.path.basename(p).encode())
+        h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
 
 
 def up_to_date():

@@ -158,6 +158,7 @@ cudaError_t Table::upload(cudaStream_t s) {
     total_warps = wp[n];
     total_blocks = bp[n];
     total_tiles = tp[n];
+    edge_lattices = edge;
     std::memcpy(staging.data(), &h, sizeof(h));
     if (n) std::memcpy(staging.data() + tab_off_desc(cap), d.data(), (size_t)n * sizeof(LatDesc));
     return cudaMemcpyAsync(dev, staging.data(), staging.size(), cudaMemcpyHostToDevice, s);

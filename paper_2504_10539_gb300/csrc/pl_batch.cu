@@ -139,7 +139,7 @@ struct pl_batch {
     int mass0_pending;
     int rows_per_chunk;
     std::map<std::pair<int, int>, int> tune_cache;
-    std::map<int, GraphEntry> graphs;   // by parity at the start of an interval
+    std::map<int, GraphEntry> graphs;   // by parity at the start of an interval | 2 if edge lattices
     // results of retired jobs: device records copied into pinned host slots
     DevRecord* h_records;       // pinned, max_jobs slots
     std::vector<int> free_slots;
@@ -215,7 +215,8 @@ static int autotune(pl_batch* b, int force) {
     const int nc = (int)(sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0]));
     float t_best[sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0])];
     for (int c = 0; c < nc; ++c) t_best[c] = 1e30f;
-    for (int k = 0; k < 20; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));
+    const bool edge = b->tab.edge_lattices > 0;
+    for (int k = 0; k < 20; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream, edge));
     for (int pass = 0; pass < 2; ++pass) {
         for (int q = 0; q < nc; ++q) {
             const int c = pass == 0 ? q : nc - 1 - q;
@@ -223,9 +224,10 @@ static int autotune(pl_batch* b, int force) {
             rebuild_table(b);
             int st = upload_table(b);
             if (st) return st;
-            PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));  // warm-up
+            const bool ed = b->tab.edge_lattices > 0;
+            PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream, ed));  // warm-up
             PL_CUDA(cudaEventRecord(e0, b->stream));
-            for (int k = 0; k < 3; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream));
+            for (int k = 0; k < 3; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream, ed));
             PL_CUDA(cudaEventRecord(e1, b->stream));
             PL_CUDA(cudaEventSynchronize(e1));
             float ms = 0.0f;
@@ -249,13 +251,16 @@ static int autotune(pl_batch* b, int force) {
 }
 
 // One interval: K steps, correction, metrics.  Events around the K step launches (graph
-// event-record nodes when captured) time the step kernels of every interval.
+// event-record nodes when captured) time the step kernels of every interval.  The FP16
+// edge-path step kernel is launched only while some lattice of the table needs it (a graph
+// is captured for each case).
 static int enqueue_interval(pl_batch* b, int parity, bool captured) {
     int cur = parity;
+    const bool edge = b->tab.edge_lattices > 0;
     const unsigned flags = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
     PL_CUDA(cudaEventRecordWithFlags(b->ev[0], b->stream, flags));
     for (int s = 0; s < b->K; ++s) {
-        PL_CUDA(launch_step_tab(b->tab.view, b->storage, cur, b->stream));
+        PL_CUDA(launch_step_tab(b->tab.view, b->storage, cur, b->stream, edge));
         cur ^= 1;
     }
     PL_CUDA(cudaEventRecordWithFlags(b->ev[1], b->stream, flags));
@@ -462,7 +467,8 @@ PL_API int pl_batch_advance(pl_batch* b, int32_t intervals) {
             st = enqueue_interval(b, b->parity, false);
             if (st) return st;
         } else {
-            auto g = b->graphs.find(b->parity);
+            const int gkey = b->parity | (b->tab.edge_lattices > 0 ? 2 : 0);
+            auto g = b->graphs.find(gkey);
             if (g == b->graphs.end()) {
                 cudaGraph_t graph;
                 PL_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -477,7 +483,7 @@ PL_API int pl_batch_advance(pl_batch* b, int32_t intervals) {
                 cudaError_t ie = cudaGraphInstantiate(&ge, graph, 0);
                 cudaGraphDestroy(graph);
                 PL_CUDA(ie);
-                g = b->graphs.emplace(b->parity, GraphEntry{ge, captured}).first;
+                g = b->graphs.emplace(gkey, GraphEntry{ge, captured}).first;
             }
             PL_CUDA(cudaGraphLaunch(g->second.exec, b->stream));
             note_launches(g->second.kernels);

@@ -140,35 +140,17 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     return h;
 }
 
-// Stochastic rounding of FP32 values to FP16 (a -> low half, b -> high half of the packed
-// result).  Uniform dither bits are added to the magnitude below the bit of the FP32 value
-// that is the FP16 result's last place, and the sum is truncated toward zero, so that
-// E[rounded] = value.  That place is 13 bits up from the FP32 last place for FP16 normals
-// (|v| >= 2^-14) and 2^-24, higher up, for FP16 subnormals; values below 2^-22 use 22
-// dither bits (a bias below 2^-24 for them).  A carry out of the mantissa moves to the next
-// binade, which truncation handles as well.
-__device__ __forceinline__ uint32_t sr_dither(float v, uint32_t rnd) {
-    const uint32_t b = __float_as_uint(v);
-    const int e = (int)((b >> 23) & 0xFFu) - 127;
-    const int p = min(max(-1 - e, 13), 22);
-    return b + (rnd & ((1u << p) - 1u));
-}
-__device__ __forceinline__ __half2 sr_pack_half2(float a, float b, uint32_t ra, uint32_t rb) {
+// Stochastic rounding of two FP32 values to FP16 by the sm_100-family conversion with random
+// bits (cvt.rs): a goes to the low half, b to the high half of the result.  The low half takes
+// its random bits from rbits[15:0], the high half from rbits[31:16]; for an FP16 normal result
+// the low 13 of those 16 bits are added below the result's last place before truncation (a
+// probe of every 16-bit pattern on GB300 matched that rule exactly), and FP16 subnormal results
+// round up with probability equal to the discarded fraction as well.  Uniform rbits make each
+// result an unbiased rounding.
+__device__ __forceinline__ uint32_t rs_pack(float a, float b, uint32_t rbits) {
     uint32_t r;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(sr_dither(b, rb))),
-        "f"(__uint_as_float(sr_dither(a, ra))));
-    return *reinterpret_cast<__half2*>(&r);
-}
-// Stochastic rounding of two FP32 values whose FP16 results are normal numbers: 13 dither bits
-// (the low 13 bits of da and db) below the FP16 last place, then truncation toward zero.
-__device__ __forceinline__ uint32_t sr13_pack(float a, float b, uint32_t da, uint32_t db) {
-    uint32_t r;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(__float_as_uint(b) + (db & 0x1FFFu))),
-        "f"(__uint_as_float(__float_as_uint(a) + (da & 0x1FFFu))));
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(b), "f"(a), "r"(rbits));
     return r;
-}
-__device__ __forceinline__ __half sr_half(float a, uint32_t rnd) {
-    return __float2half_rz(__uint_as_float(sr_dither(a, rnd)));
 }
 
 // Per-lattice device record: reductions land here, later kernels read them,

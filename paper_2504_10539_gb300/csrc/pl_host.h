@@ -67,6 +67,7 @@ struct Table {
     std::vector<char> staging;  // host image of the device region
     long long total_warps = 0, total_tiles = 0;
     int total_blocks = 0;
+    int edge_lattices = 0;      // FP16 lattices off the step's vector path (k_step_edge's work)
 
     static size_t bytes(int cap);
     void carve(char* base, int capacity);

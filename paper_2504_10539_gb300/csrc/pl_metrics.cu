@@ -712,9 +712,10 @@ __device__ __forceinline__ void feq9(R rho, R ux, R uy, R (&fe)[9]) {
 
 // The correction changes the populations of a corrected cell by f_i^eq(rho', u') - f_i^eq(rho, u).
 // FP16-offset storage applies it to the stored offsets directly (the references, and with
-// them the decoding, stay as they are): the moving offsets are rounded to nearest, the rest
-// offset takes the cell's corrected mass minus their rounded values and is rounded
-// stochastically, so small changes are realised on average instead of being rounded away.
+// them the decoding, stay as they are): every offset is rounded stochastically (the
+// conversion with random bits), the rest offset taking the cell's corrected mass minus the
+// rounded moving offsets, so small changes are realised on average instead of being rounded
+// away and rounding adds no bias to the mass or the momentum.
 template <int MODE>
 __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_corr_apply(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
@@ -756,15 +757,20 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
                 float res = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hn[i] = fmaf(F16_SCALE, fn[i] - fo[i], __half2float(fs[i]));
+                uint32_t st = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u) ^
+                                     ((seq - d.seq0) * 0x27D4EB2Fu));
 #pragma unroll
-                for (int i = 1; i < 9; ++i) {
-                    const __half qh = __float2half_rn(hn[i]);
-                    res += __half2float(qh) - hn[i];
-                    f[i * d.plane + o] = qh;
+                for (int i = 1; i < 9; i += 2) {
+                    st = st * 1664525u + 1013904223u;
+                    const uint32_t q2 = rs_pack(hn[i], hn[i + 1], st);
+                    const __half qa = __ushort_as_half((unsigned short)(q2 & 0xFFFFu));
+                    const __half qb = __ushort_as_half((unsigned short)(q2 >> 16));
+                    res += (__half2float(qa) - hn[i]) + (__half2float(qb) - hn[i + 1]);
+                    f[i * d.plane + o] = qa;
+                    f[(i + 1) * d.plane + o] = qb;
                 }
-                const uint32_t rnd = fmix32(__float_as_uint(hn[0]) ^ ((uint32_t)c * 0x9E3779B1u) ^
-                                            ((seq - d.seq0) * 0x27D4EB2Fu));
-                f[o] = sr_half(hn[0] - res, rnd);
+                st = st * 1664525u + 1013904223u;
+                f[o] = __ushort_as_half((unsigned short)(rs_pack(hn[0] - res, 0.0f, st) & 0xFFFFu));
             } else {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i * d.plane + o] = encode<MODE>(decode<MODE>(fs[i]) + (fn[i] - fo[i]));

@@ -658,8 +658,9 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
             collide_pair<PL_F16_OFFSET, true>(fp, rho_p, make_float2(g0 * sx0, g1 * sx1), make_float2(g0 * sy0, g1 * sy1),
                                               a.k, o, bc2(REF_KAPPA * F16_SCALE * a.k.tau) * rqf);
             // every offset rounded stochastically (unbiased: no drift of mass or momentum from
-            // rounding), the dither from a counter-based hash of the pair's position and the
-            // lattice's step count, stepped by a linear congruential sequence per population
+            // rounding) by the conversion with random bits, one 32-bit word per pair and
+            // population: a counter-based hash of the pair's position and the lattice's step
+            // count, stepped by a linear congruential sequence per population
             const uint32_t rnd =
                 fmix32(((uint32_t)ua * 0x85EBCA77u) ^ ((uint32_t)y * 0xC2B2AE3Du) ^ (a.seq * 0x27D4EB2Fu));
             uint32_t st = rnd;
@@ -668,7 +669,7 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 st = st * 1664525u + 1013904223u;
-                out[i] = sr13_pack(o[i].x, o[i].y, st >> 19, st >> 6);
+                out[i] = rs_pack(o[i].x, o[i].y, st);
                 unsigned short lo, hi;
                 asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(out[i]));
                 asm("add.rn.f32.f16 %0, %1, %0;" : "+f"(s0) : "h"(lo));
@@ -676,7 +677,7 @@ __device__ __forceinline__ void walk_f16(const WalkArgs<PL_F16_OFFSET>& a, int s
             }
             // rest offset: the cell's mass minus what the pushed populations carry
             const float2 rest = (rho_p - bc2(REF_KAPPA * F16_SCALE) * rqf) - make_float2(s0, s1);
-            out[0] = sr13_pack(rest.x, rest.y, rnd, rnd >> 16);
+            out[0] = rs_pack(rest.x, rest.y, rnd);
             const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
             auto dst = [&](int i, int row) -> __half* { return a.fout + row_off(i, row) + ua; };
             // c_x = 0 planes and the reference: own pair

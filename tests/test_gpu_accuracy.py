@@ -33,6 +33,7 @@ import pytest
 
 import oracle as O
 from paper_2504_10539_gb300 import binding as B
+from paper_2504_10539_gb300 import build as PB
 from paper_2504_10539_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
@@ -47,6 +48,7 @@ RESULTS = {}
 
 def record(key, value):
     RESULTS[key] = value
+    RESULTS["source_sha1"] = PB.source_hash()
     path = os.environ.get("PL_ACCURACY_OUT")
     if path:
         with open(path, "w") as fh:

@@ -53,7 +53,7 @@ def test_stencil_network_field_matches_oracle(storage, mlp, mode, tol, nx, ny):
     blob = wl.mlp_weights(71, dims=DIMS)
     lat = B.Lattice(B.pl_params_default(nx, ny, storage=storage, mlp=mlp, mlp_in=11))
     drops = [(nx / 2, ny / 2, min(nx, ny) / 4), (0.2 * nx, 0.7 * ny, 3.0)]
-    f = S.stored(S.oracle_droplet_state(nx, ny, drops, steps=20, seed=4), storage, 1.075)
+    f = S.stored(S.oracle_droplet_state(nx, ny, drops, steps=20, seed=4), storage)
     lat.set_state(f, 20)
     lat.set_weights(blob)
     out = lat.mlp_field()

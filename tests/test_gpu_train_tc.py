@@ -54,6 +54,10 @@ def oracle_gradient(f, job, hp, iface=None):
                            T.TrainParams(**hp))
 
 
+# relative to the largest component of the FP64 oracle's gradient (of the block, per layer)
+GRAD_TOL = 5 * 2.0 ** -9
+
+
 @pytest.mark.parametrize("which", sorted(HP))
 @pytest.mark.parametrize("nx,ny", [(64, 64), (67, 35), (41, 7)])
 def test_tc_gradient_matches_oracle(nx, ny, which):
@@ -63,7 +67,9 @@ def test_tc_gradient_matches_oracle(nx, ny, which):
     L, terms, go = oracle_gradient(f, job, HP[which])
     assert np.isfinite(g).all()
     err = np.abs(g - go).max() / np.abs(go).max()
-    assert err <= 2e-2, err
+    # BF16 operands (2^-9 relative each); the longest chain of rounded operands on the way to a
+    # weight gradient is five (forward 2-4, reverse 4-3), 5 x 2^-9 ~ 1e-2 (measured up to 4.7e-3)
+    assert err <= GRAD_TOL, err
     assert loss[0] == pytest.approx(L, rel=1e-2)
 
 
@@ -80,7 +86,7 @@ def test_tc_gradient_per_layer_blocks():
     for shp in sizes:
         n = int(np.prod(shp))
         blk, ref = g[o:o + n], go[o:o + n]
-        assert np.abs(blk - ref).max() <= 3e-2 * np.abs(ref).max() + 1e-12, (shp, o)
+        assert np.abs(blk - ref).max() <= GRAD_TOL * np.abs(ref).max() + 1e-12, (shp, o)
         o += n
     assert o == g.size
 
@@ -99,7 +105,7 @@ def test_tc_training_follows_oracle_and_full_size():
     tr2 = B.Trainer(lat2, max_epochs=1, mode=B.PL_TRAIN_TC)
     g, loss = tr2.gradient()
     L, _, go = oracle_gradient(f2, big, {})
-    assert np.abs(g - go).max() <= 2e-2 * np.abs(go).max()
+    assert np.abs(g - go).max() <= GRAD_TOL * np.abs(go).max()
     assert loss[0] == pytest.approx(L, rel=1e-2)
 
 
