@@ -267,7 +267,7 @@ static int enqueue_interval(pl_batch* b, int parity, bool captured) {
     PL_CUDA(launch_correction_tab(b->tab.view, b->storage, cur, b->mlp, b->mlp_in,
                                   reinterpret_cast<const float*>(b->base + b->H.w32),
                                   reinterpret_cast<const uint16_t*>(b->base + b->H.wbf16), b->stream));
-    PL_CUDA(launch_metrics_tab(b->tab.view, b->storage, cur, 0, 1, b->stream));
+    PL_CUDA(launch_metrics_tab(b->tab.view, b->storage, cur, 0, 1, b->stream, 1));  // moments kept by the apply pass
     PL_CUDA(cudaEventRecordWithFlags(b->ev[2], b->stream, flags));
     return PL_OK;
 }

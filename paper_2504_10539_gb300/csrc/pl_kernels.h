@@ -118,8 +118,11 @@ cudaError_t launch_step_tab(const TableView& t, int storage, int parity, cudaStr
 // Whether a lattice's FP16 step can have strips off the vector path.
 __host__ __device__ inline bool f16_edge_lattice(int nx, long long plane) { return (nx & 1) || 10ll * plane > 0xFFFFFFFFll; }
 // Metrics of every lattice: moments, Eq. 16 gradient, Eqs. 9-15 sums (+ Laplace where defined).
+// moments_current: the moment fields already hold the state's density and momentum (right
+// after a correction of the same state, whose apply pass keeps them current), so the moments
+// pass is skipped.
 cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
-                               cudaStream_t s);
+                               cudaStream_t s, int moments_current = 0);
 // Density and momentum fields of every lattice (the network's stencil input reads rho).
 cudaError_t launch_moments_tab(const TableView& t, int storage, int parity, cudaStream_t s);
 // Network field of every lattice (BF16 tensor cores or SIMT) on n_in = 2 or 11 inputs (11

@@ -274,39 +274,46 @@ __global__ void __launch_bounds__(RB_THREADS) k_final_metrics(const double* __re
 // Table kernels: metrics.
 
 // rho = sum_i f_i and j = sum_i f_i c_i per cell, from the decoded stored state.
+// Density and momentum of one cell from the stored populations, into the moment fields (the
+// moments pass, and the correction's apply pass for the cells it changed: the same arithmetic,
+// so the fields hold the same values either way).
+template <int MODE>
+__device__ __forceinline__ void cell_moments(const typename Traits<MODE>::S* f, const LatDesc& d, const CellIt& it) {
+    using R = typename Traits<MODE>::R;
+    R* rho = static_cast<R*>(d.rho);
+    R* jx = static_cast<R*>(d.jx);
+    R* jy = static_cast<R*>(d.jy);
+    const long long c = it.c;
+    R P[9];
+    if constexpr (MODE == PL_F16_OFFSET) {
+        // f_i = h_i + t_i; the mass as the sum of the two exact-where-possible parts
+        float h[9], tt[9];
+        f16_cell(f, d.plane, d.pitch, d.nx, d.ny, it.x, it.y, h, tt);
+        rho[c] = sum9(tt) + sum9(h);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = h[i] + tt[i];
+    } else {
+        const long long o = it.pop_offset(d.pitch);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o]);
+        rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+    }
+    jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
+    jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(RB_THREADS) k_moments(TableView t, int parity) {
     using S = typename Traits<MODE>::S;
-    using R = typename Traits<MODE>::R;
     const int n = t.hdr->n, total = t.hdr->total_blocks;
     for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
         const BlkMap m = map_blk(t, n, vb);
         const LatDesc& d = t.d[m.j];
         const S* f = static_cast<const S*>(d.pops[d.phase ^ parity]);
-        R* rho = static_cast<R*>(d.rho);
-        R* jx = static_cast<R*>(d.jx);
-        R* jy = static_cast<R*>(d.jy);
         const long long N = (long long)d.nx * d.ny;
         for (CellIt it((long long)m.lb * RB_THREADS + threadIdx.x, (long long)d.red_blocks * RB_THREADS, d.nx); it.c < N;
-             it.next(d.nx)) {
-            const long long c = it.c;
-            const long long o = it.pop_offset(d.pitch);
-            R P[9];
-            if constexpr (MODE == PL_F16_OFFSET) {
-                // f_i = h_i + t_i; the mass as the sum of the two exact-where-possible parts
-                float h[9], tt[9];
-                f16_cell(f, d.plane, d.pitch, d.nx, d.ny, it.x, it.y, h, tt);
-                rho[c] = sum9(tt) + sum9(h);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) P[i] = h[i] + tt[i];
-            } else {
-#pragma unroll
-                for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o]);
-                rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
-            }
-            jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
-            jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
-        }
+             it.next(d.nx))
+            cell_moments<MODE>(f, d, it);
     }
 }
 
@@ -464,12 +471,16 @@ __global__ void __launch_bounds__(RB_THREADS) k_laplace_final(TableView t) {
 }
 
 template <int MODE>
-static cudaError_t metrics_t(const TableView& t, int parity, int set_mass0, int laplace, cudaStream_t s) {
+static cudaError_t metrics_t(const TableView& t, int parity, int set_mass0, int laplace, int moments_current,
+                             cudaStream_t s) {
     using R = typename Traits<MODE>::R;
-    k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+    int launches = 2;
+    if (!moments_current) {
+        k_moments<MODE><<<RED_GRID, RB_THREADS, 0, s>>>(t, parity);
+        ++launches;
+    }
     k_grad_tab<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
     k_final_metrics_tab<<<RED_GRID, RB_THREADS, 0, s>>>(t, set_mass0);
-    int launches = 3;
     if (laplace) {
         for (int it = 0; it < 2; ++it) {
             k_laplace_region<R><<<RED_GRID, RB_THREADS, 0, s>>>(t);
@@ -482,11 +493,11 @@ static cudaError_t metrics_t(const TableView& t, int parity, int set_mass0, int 
 }
 
 cudaError_t launch_metrics_tab(const TableView& t, int storage, int parity, int set_mass0, int laplace,
-                               cudaStream_t s) {
+                               cudaStream_t s, int moments_current) {
     switch (storage) {
-        case PL_F64: return metrics_t<PL_F64>(t, parity, set_mass0, laplace, s);
-        case PL_F32: return metrics_t<PL_F32>(t, parity, set_mass0, laplace, s);
-        case PL_F16_OFFSET: return metrics_t<PL_F16_OFFSET>(t, parity, set_mass0, laplace, s);
+        case PL_F64: return metrics_t<PL_F64>(t, parity, set_mass0, laplace, moments_current, s);
+        case PL_F32: return metrics_t<PL_F32>(t, parity, set_mass0, laplace, moments_current, s);
+        case PL_F16_OFFSET: return metrics_t<PL_F16_OFFSET>(t, parity, set_mass0, laplace, moments_current, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -775,6 +786,9 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i * d.plane + o] = encode<MODE>(decode<MODE>(fs[i]) + (fn[i] - fo[i]));
             }
+            // the moment fields follow the corrected state (the cells left alone keep theirs), so
+            // the metric pass after the correction need not recompute them
+            cell_moments<MODE>(f, d, it);
         }
     }
 }

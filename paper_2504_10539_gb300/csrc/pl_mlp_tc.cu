@@ -345,17 +345,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int nout = layer == 4 ? 64 : 128;
             uint8_t* dst = AX;  // the layer's MMA has completed: its operand buffer is free
 #pragma unroll 1
-            for (int c0 = 0; c0 < nout; c0 += 16) {
-                float v[16];
-                tmem_ld16(my_lane_tmem + c0, v);
+            for (int c0 = 0; c0 < nout; c0 += 32) {
+                float v[32];
+                tmem_ld32(my_lane_tmem + c0, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) v[j] = tanh_fast(v[j]);  // the bias is in the accumulator
+                for (int j = 0; j < 32; ++j) v[j] = tanh_fast(v[j]);  // the bias is in the accumulator
                 if (layer < 4) {
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
+                    for (int q = 0; q < 4; ++q) store8(dst, t, c0 + 8 * q, v + 8 * q);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < 8; ++q) {
                         const float2 va = make_float2(v[4 * q], v[4 * q + 1]), vb = make_float2(v[4 * q + 2], v[4 * q + 3]);
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
