@@ -296,7 +296,7 @@ def batch_config(n_lattices, cells, K, world):
             "storage": "f16_offset", "network": "bf16-tcgen05", "K": K,
             "step": "one coupling interval: K lattice steps + correction + metrics of every lattice "
                     "(one CUDA graph replay)",
-            "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (cells * 18 / 1e9),
+            "l2": "inputs larger than L2 (2 x %.2f GB populations)" % (cells * 20 / 1e9),
             "parallelism": "replicas x%d" % world}
 
 
