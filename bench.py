@@ -264,6 +264,13 @@ def config_runs(B, wl, torch):
                                  % (job.nx, job.ny, STORAGE_NAME[job.storage], job.steps, job.K,
                                     {0: "FP64", 1: "FP32", 2: "BF16 tcgen05"}[job.mlp]),
                      "gpu_mlups": job.cells * steps / (ms / 1e3) / 1e6, "gpu_ms": ms, "status": m["status"]}
+        if name.startswith("C3"):
+            # the configured field breaks down in the FP64 oracle as well (recorded by
+            # tests/golden/make_field_4096_stability.py): a non-physical final status is the
+            # method's at this tau, not the storage's
+            gold = os.path.join(ROOT, "tests", "golden", "field_4096_stability.json")
+            if os.path.exists(gold):
+                out[name]["oracle_plain_lbm_nonphysical_at_step"] = json.load(open(gold))["first_nonphysical_step"]
     return out
 
 

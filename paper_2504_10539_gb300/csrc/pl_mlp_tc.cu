@@ -140,8 +140,9 @@ cudaError_t launch_convert_weights_bf16(const float* w32, uint16_t* wbf16, int n
     return cudaGetLastError();
 }
 
-__device__ __forceinline__ int find_tile(const long long* __restrict__ pre, int n, long long v) {
-    int lo = 0, hi = n;  // pre[lo] <= v < pre[hi]
+// The lattice j with pre[j] <= v < pre[j+1], searched in [lo, n) (pre[lo] <= v).
+__device__ __forceinline__ int find_tile(const long long* __restrict__ pre, int lo, int n, long long v) {
+    int hi = n;  // pre[lo] <= v < pre[hi]
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
         if (pre[mid] <= v) lo = mid;
@@ -230,21 +231,38 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     int pending = 0;  // MMA batches committed but not yet waited for
 
     DevRecord* last_rec = nullptr;
+    // The lattice of the current tile and what the tile loop reads of it.  A warpgroup's tiles
+    // rise, so the lookup is redone only when a tile leaves the current lattice, and then
+    // searched from that lattice on (the search's dependent loads are paid once per lattice).
+    int lj = 0;
+    long long t_lo = 0, t_hi = -1;  // tile_pre[lj], tile_pre[lj + 1]
+    const LatDesc* ldp = nullptr;
+    int nx = 1, ny = 1;
+    long long N = 1, nb = 0;
+    float* out3 = nullptr;
+    bool banded = false;
     for (long long tile = (long long)blockIdx.x * NWG + wg; ok && tile < ntiles; tile += (long long)gridDim.x * NWG) {
-        const int lj = find_tile(tab.tile_pre, nlat, tile);
-        const LatDesc& ld = tab.d[lj];
-        const int nx = ld.nx, ny = ld.ny;
-        const long long N = (long long)nx * ny;
-        float* out3 = static_cast<float*>(ld.out3);
-        last_rec = ld.rec;
+        if (tile >= t_hi) {
+            lj = find_tile(tab.tile_pre, lj, nlat, tile);
+            t_lo = tab.tile_pre[lj];
+            t_hi = tab.tile_pre[lj + 1];
+            ldp = &tab.d[lj];
+            nx = ldp->nx;
+            ny = ldp->ny;
+            N = (long long)nx * ny;
+            out3 = static_cast<float*>(ldp->out3);
+            last_rec = ldp->rec;
+            banded = use_band && ldp->mask_eps > 0.0;
+            nb = banded ? ldp->rec->band_n : 0;
+        }
+        const LatDesc& ld = *ldp;
         // the tile's cells: consecutive cells, or (an interface band) consecutive band entries;
         // a lattice's band fills its first tiles, the others have no work (uniform per warpgroup)
-        const long long pos = (tile - tab.tile_pre[lj]) * M + t;
+        const long long pos = (tile - t_lo) * M + t;
         long long cc;
         bool valid;
-        if (use_band && ld.mask_eps > 0.0) {
-            const long long nb = ld.rec->band_n;
-            if ((tile - tab.tile_pre[lj]) * M >= nb) continue;
+        if (banded) {
+            if ((tile - t_lo) * M >= nb) continue;
             valid = pos < nb;
             cc = ld.band[valid ? pos : nb - 1];
         } else {

@@ -14,7 +14,12 @@ The oracle cannot run the full workloads in a test's time, so these checks sampl
   (step + correction + metrics: the same table kernels and grids the benchmark replays with
   K = 100); the smallest lattices are compared whole against the oracle's own initial state,
   step and correction; every lattice must end with status OK and its mass at M0.
+* the 4096x4096 field as configured, plain LBM: it breaks down (a density through zero) in the
+  same 100-step chunk and region as the FP64 oracle's run of it.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -101,3 +106,38 @@ def test_batch_256_one_interval_sampled_lattices():
         # 2^-14 here), the network in BF16 on both sides (the oracle emulates its rounding)
         assert np.abs(f1 - fo).max() <= 1e-3, (k, j.nx, np.abs(f1 - fo).max())
     bt.close()
+
+
+# ----------------------------------------------------------------------------- breakdown
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "field_4096_stability.json")
+
+
+@pytest.mark.parametrize("storage", [wl.F32, wl.F16_OFFSET])
+def test_field_4096_plain_lbm_breaks_down_where_the_oracle_does(storage):
+    """The configured 4096^2 field is dynamically unstable at tau = 0.8: the FP64 oracle's plain
+    LBM holds a non-finite density after the chunk recorded in tests/golden/ (written by
+    make_field_4096_stability.py, which runs the oracle only).  The GPU run of the same field
+    (as configured, full size, without correction) turns non-physical in the same chunk of 100
+    steps, or one chunk either side, and its first non-physical cells lie in the region where
+    the oracle's did (within 64 cells)."""
+    gold = json.load(open(GOLD))
+    s_bad = gold["first_nonphysical_step"]
+    x0, x1, y0, y1 = gold["chunks"][-1]["bad_box"]
+    chunk = gold["chunk_steps"]
+    job = wl.field_4096(storage=storage)
+    job.K = 0
+    lat = B.Lattice.from_workload(job)
+    first = None
+    for s in range(chunk, s_bad + 2 * chunk + 1, chunk):
+        lat.step(chunk)
+        if lat.metrics()["status"] != 0:
+            first = s
+            break
+    assert first is not None and abs(first - s_bad) <= chunk, (first, s_bad)
+    r = lat.rho()
+    lat.close()
+    ys, xs = np.nonzero(~np.isfinite(r) | (r <= 0.0))
+    assert len(xs) > 0
+    near = (xs >= x0 - 64) & (xs <= x1 + 64) & (ys >= y0 - 64) & (ys <= y1 + 64)
+    assert near.any(), (xs.min(), xs.max(), ys.min(), ys.max(), gold["chunks"][-1]["bad_box"])
