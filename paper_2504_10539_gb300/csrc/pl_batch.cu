@@ -215,6 +215,17 @@ static int autotune(pl_batch* b, int force) {
     const int nc = (int)(sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0]));
     float t_best[sizeof(TUNE_CANDIDATES) / sizeof(TUNE_CANDIDATES[0])];
     for (int c = 0; c < nc; ++c) t_best[c] = 1e30f;
+    // the device table must list the current jobs before any trial launch: after retirements
+    // and admissions the one on the device still names retired jobs, whose arena space may
+    // already hold a new job's state (a trial step would write over it)
+    {
+        const int st = upload_table(b);
+        if (st) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+    }
     const bool edge = b->tab.edge_lattices > 0;
     for (int k = 0; k < 20; ++k) PL_CUDA(launch_step_tab(b->tab.view, b->storage, b->parity, b->stream, edge));
     for (int pass = 0; pass < 2; ++pass) {

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(MLP_THREADS) k_mlp_simt(const float* __restric
         R* out3 = static_cast<R*>(d.out3);
         const long long c = (tile - tab.tile_pre[j]) * MLP_TILE + (vh & 1) * MLP_THREADS + t;
         const long long cc = c < N ? c : N - 1;
-        const int x = (int)(cc % nx), y = (int)(cc / nx);
+        // 32-bit division (a lattice holds fewer than 2^31 cells)
+        const int y = (int)((uint32_t)cc / (uint32_t)nx), x = (int)((uint32_t)cc - (uint32_t)y * (uint32_t)nx);
         bufA[0 * MLP_THREADS + t] = R(2) * (R(x) + R(0.5)) / R(nx) - R(1);
         bufA[1 * MLP_THREADS + t] = R(2) * (R(y) + R(0.5)) / R(ny) - R(1);
         if (n_in == 11) {

@@ -269,7 +269,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             valid = pos < N;
             cc = valid ? pos : N - 1;
         }
-        const int x = (int)(cc % nx), y = (int)(cc / nx);
+        // 32-bit division (a lattice holds fewer than 2^31 cells)
+        const int y = (int)((uint32_t)cc / (uint32_t)nx), x = (int)((uint32_t)cc - (uint32_t)y * (uint32_t)nx);
         const float xh = 2.0f * ((float)x + 0.5f) / (float)nx - 1.0f;
         const float yh = 2.0f * ((float)y + 0.5f) / (float)ny - 1.0f;
 

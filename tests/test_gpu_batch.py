@@ -165,3 +165,53 @@ def test_autotune_picks_a_candidate_and_keeps_results():
     b.advance(2)
     for x, y, j in zip(ids, idb, jobs):
         assert np.array_equal(a.state(x)[0], b.state(y)[0])
+
+
+def test_admission_into_retired_space_with_retune_matches_alone():
+    """A job admitted into the arena space of a job that retired in the interval before, when
+    the batch's total cell count moves to an octave the autotuner has not timed.  The retune's
+    trial launches must run on the current job table: the table on the device still lists the
+    retired 512^2 job, whose second population buffer now holds the new job's record and
+    scratch (the new job, 384 x 256 FP16 cells, takes about 7.1 MB from offset 0, the old job's
+    second buffer spans 5.2-10.5 MB).  The new job ends OK and bit-identical to its run alone."""
+    storage = B.PL_F16_OFFSET
+    big = wl.Lattice(512, 512, storage=storage, G=-5.5, tau=1.0, mlp=wl.MLP_F32,
+                     droplets=[(256.0, 256.0, 80.0)], seed=71, steps=K, K=K)
+    small = wl.Lattice(64, 64, storage=storage, G=-5.5, tau=1.0, mlp=wl.MLP_F32,
+                       droplets=[(32.0, 32.0, 12.0)], seed=72, steps=6 * K, K=K)
+    late = wl.Lattice(384, 256, storage=storage, G=-5.5, tau=1.0, mlp=wl.MLP_F32,
+                      droplets=[(192.0, 128.0, 50.0)], seed=73, steps=3 * K, K=K)
+    # the retired job's second population buffer: ten FP16 planes of 512 x 512 after the first
+    buffer = 10 * 512 * 512 * 2
+    assert buffer < B.pl_batch_job_bytes(B.job_params(late)) < 2 * buffer   # its record lies in it
+    blob = wl.mlp_weights(63)
+    bt = B.Batch(storage, B.PL_MLP_F32, K, budget_for([big, small]))
+    bt.set_weights(blob)
+    ib = bt.submit(big)
+    bt.submit(small)
+    bt.advance(1)
+    assert [r["id"] for r in bt.poll()] == [ib]
+    il = bt.submit(late)                  # first fit: the retired job's space
+    assert il is not None
+    bt.advance(3)
+    done = {r["id"]: r for r in bt.poll()}
+    assert done[il]["status"] == 0 and done[il]["steps"] == 3 * K, done[il]
+    alone = B.Batch(storage, B.PL_MLP_F32, K, budget_for([late]))
+    alone.set_weights(blob)
+    aid = alone.submit(late)
+    alone.advance(2)
+    fa, sa = alone.state(aid)
+    alone.close()
+    bt2 = B.Batch(storage, B.PL_MLP_F32, K, budget_for([big, small]))
+    bt2.set_weights(blob)
+    bt2.submit(big)
+    bt2.submit(small)
+    bt2.advance(1)
+    bt2.poll()
+    il2 = bt2.submit(late)
+    bt2.advance(2)
+    fm, sm = bt2.state(il2)
+    bt2.close()
+    bt.close()
+    assert sa == sm == 2 * K
+    assert np.array_equal(fa, fm)

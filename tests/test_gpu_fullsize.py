@@ -141,3 +141,47 @@ def test_field_4096_plain_lbm_breaks_down_where_the_oracle_does(storage):
     assert len(xs) > 0
     near = (xs >= x0 - 64) & (xs <= x1 + 64) & (ys >= y0 - 64) & (ys <= y1 + 64)
     assert near.any(), (xs.min(), xs.max(), ys.min(), ys.max(), gold["chunks"][-1]["bad_box"])
+
+
+# ----------------------------------------------------------------------------- largest planes
+
+# 20736^2 cells: ten FP16 planes span 4.3e9 elements, past 32-bit element offsets, so the FP16
+# step takes its element-by-element path with 64-bit offsets (the vector path's offsets are 32
+# bits); FP32 storage of the same size always uses 64-bit offsets.  About 31 / 43 GB of device
+# memory and 7 GB of host memory.
+BIG = 20736
+
+
+@pytest.mark.parametrize("storage,tol", [(wl.F16_OFFSET, 2e-4), (wl.F32, 1e-6)])
+def test_planes_beyond_32_bit_element_offsets(storage, tol):
+    """One step of a 20736^2 lattice from rest on a seeded random density field, compared on
+    windows, including the last rows (the largest offsets) and across the periodic edges, with
+    the oracle's step of the same window (interior at distance >= 3 exact, as above).  Bounds:
+    FP32 a few FP32 roundings; FP16-offset the initial encoding (moving offsets up to ~11 in
+    2^-10 units, whose FP16 spacing is 2^-7: 3.8e-6 per population, nine arriving per cell)."""
+    assert 10 * BIG * BIG > 2 ** 32
+    p = B.pl_params_default(BIG, BIG, storage=storage)
+    rng = np.random.default_rng(5)
+    rho = rng.random((BIG, BIG))
+    rho *= 0.1
+    rho += 0.3
+    lat = B.Lattice(p)
+    lat.init_rho(rho)
+    lat.step(1)
+    r1 = lat.rho()
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    corners = [(0, 0), (BIG - WIN, BIG - WIN), (BIG - WIN // 2, BIG - WIN // 2), (BIG // 2, BIG - WIN - 1),
+               (17, BIG - WIN)]
+    worst = 0.0
+    for x0, y0 in corners:
+        ys = (y0 + np.arange(WIN)) % BIG
+        xs = (x0 + np.arange(WIN)) % BIG
+        w0 = O.init_equilibrium(np.ascontiguousarray(rho[ys][:, xs]))
+        O.step(w0, 1, p.G, p.tau)
+        ro = O.density(w0)
+        rg = r1[ys][:, xs]
+        inner = (slice(MARGIN, WIN - MARGIN), slice(MARGIN, WIN - MARGIN))
+        worst = max(worst, float(np.abs(rg[inner] - ro[inner]).max()))
+    assert worst <= tol, worst
