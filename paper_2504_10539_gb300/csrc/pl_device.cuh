@@ -79,16 +79,14 @@ __host__ __device__ constexpr int planes_of(int storage) { return storage == PL_
 
 // One FP16-offset cell (x, y) of a buffer f (ten planes of `plane` elements, rows of `pitch`):
 // its offsets h_i (unscaled) and reference terms t_i = Wr_i r(x - c_i) (exact products), so
-// that f_i = h_i + t_i and the cell's mass is A + H with A = sum t_i, H = sum h_i.
-__device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long plane, int pitch, int nx, int ny, int x,
-                                         int y, float (&h)[9], float (&t)[9]) {
-    const long long o = (long long)y * pitch + x;
+// that f_i = h_i + t_i and the cell's mass is A + H with A = sum t_i, H = sum h_i.  f16_refs
+// gives the reference terms alone.
+__device__ __forceinline__ void f16_refs(const __half* __restrict__ f, long long plane, int pitch, int nx, int ny, int x,
+                                         int y, float (&t)[9]) {
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     const long long rm = (long long)(y == 0 ? ny - 1 : y - 1) * pitch, r0 = (long long)y * pitch,
                     rp = (long long)(y == ny - 1 ? 0 : y + 1) * pitch;
     const __half* ref = f + REF_PLANE * plane;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = __half2float(f[i * plane + o]) * F16_UNSCALE;
     t[0] = wref(0) * __half2float(ref[r0 + x]);
     t[1] = wref(1) * __half2float(ref[r0 + xm]);  // c_1 = (1, 0): from x - 1
     t[2] = wref(2) * __half2float(ref[rm + x]);   // c_2 = (0, 1): from y - 1
@@ -98,6 +96,13 @@ __device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long
     t[6] = wref(6) * __half2float(ref[rm + xp]);  // c_6 = (-1, 1)
     t[7] = wref(7) * __half2float(ref[rp + xp]);  // c_7 = (-1, -1)
     t[8] = wref(8) * __half2float(ref[rp + xm]);  // c_8 = (1, -1)
+}
+__device__ __forceinline__ void f16_cell(const __half* __restrict__ f, long long plane, int pitch, int nx, int ny, int x,
+                                         int y, float (&h)[9], float (&t)[9]) {
+    const long long o = (long long)y * pitch + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = __half2float(f[i * plane + o]) * F16_UNSCALE;
+    f16_refs(f, plane, pitch, nx, ny, x, y, t);
 }
 // Sums of nine terms in the walker's order.
 template <typename R>

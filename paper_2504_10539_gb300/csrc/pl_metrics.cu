@@ -274,32 +274,43 @@ __global__ void __launch_bounds__(RB_THREADS) k_final_metrics(const double* __re
 // Table kernels: metrics.
 
 // rho = sum_i f_i and j = sum_i f_i c_i per cell, from the decoded stored state.
-// Density and momentum of one cell from the stored populations, into the moment fields (the
-// moments pass, and the correction's apply pass for the cells it changed: the same arithmetic,
-// so the fields hold the same values either way).
+// Density and momentum of one cell into the moment fields, from its populations P (FP32 / FP64)
+// or from its FP16 offsets h and reference terms t.  The moments pass and the correction's
+// apply pass (for the cells it changed, from the values it stores) both write through these, so
+// the fields hold the same values either way.
+template <typename R>
+__device__ __forceinline__ void put_moments(const LatDesc& d, long long c, R rho_c, const R (&P)[9]) {
+    static_cast<R*>(d.rho)[c] = rho_c;
+    static_cast<R*>(d.jx)[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
+    static_cast<R*>(d.jy)[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
+}
+__device__ __forceinline__ void put_moments_f16(const LatDesc& d, long long c, const float (&h)[9], const float (&tt)[9]) {
+    // f_i = h_i + t_i; the mass as the sum of the two exact-where-possible parts
+    float P[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P[i] = h[i] + tt[i];
+    put_moments<float>(d, c, sum9(tt) + sum9(h), P);
+}
+template <typename R>
+__device__ __forceinline__ void put_moments_p(const LatDesc& d, long long c, const R (&P)[9]) {
+    put_moments<R>(d, c, ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8], P);
+}
+
+// The same from the stored populations.
 template <int MODE>
 __device__ __forceinline__ void cell_moments(const typename Traits<MODE>::S* f, const LatDesc& d, const CellIt& it) {
     using R = typename Traits<MODE>::R;
-    R* rho = static_cast<R*>(d.rho);
-    R* jx = static_cast<R*>(d.jx);
-    R* jy = static_cast<R*>(d.jy);
-    const long long c = it.c;
-    R P[9];
     if constexpr (MODE == PL_F16_OFFSET) {
-        // f_i = h_i + t_i; the mass as the sum of the two exact-where-possible parts
         float h[9], tt[9];
         f16_cell(f, d.plane, d.pitch, d.nx, d.ny, it.x, it.y, h, tt);
-        rho[c] = sum9(tt) + sum9(h);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) P[i] = h[i] + tt[i];
+        put_moments_f16(d, it.c, h, tt);
     } else {
         const long long o = it.pop_offset(d.pitch);
+        R P[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) P[i] = decode<MODE>(f[i * d.plane + o]);
-        rho[c] = ((P[0] + P[1]) + (P[2] + P[3])) + ((P[4] + P[5]) + (P[6] + P[7])) + P[8];
+        put_moments_p<R>(d, it.c, P);
     }
-    jx[c] = (P[1] - P[3]) + (P[5] - P[6]) + (P[8] - P[7]);
-    jy[c] = (P[2] - P[4]) + (P[5] + P[6]) - (P[7] + P[8]);
 }
 
 template <int MODE>
@@ -763,8 +774,11 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
             R fn[9], fo[9];
             feq9<R>(q.rhop, (jxc + djx) / q.rhop, (jyc + djy) / q.rhop, fn);
             feq9<R>(r, jxc / r, jyc / r, fo);
+            // the moment fields follow the corrected state, from the values stored (the cells
+            // left alone keep theirs), so the metric pass after the correction need not
+            // recompute them
             if constexpr (MODE == PL_F16_OFFSET) {
-                float hn[9];
+                float hn[9], hs[9], tt[9];
                 float res = 0.0f;
 #pragma unroll
                 for (int i = 0; i < 9; ++i) hn[i] = fmaf(F16_SCALE, fn[i] - fo[i], __half2float(fs[i]));
@@ -776,19 +790,30 @@ __global__ void __launch_bounds__(RB_THREADS, MODE == PL_F16_OFFSET ? 4 : 1) k_c
                     const uint32_t q2 = rs_pack(hn[i], hn[i + 1], st);
                     const __half qa = __ushort_as_half((unsigned short)(q2 & 0xFFFFu));
                     const __half qb = __ushort_as_half((unsigned short)(q2 >> 16));
-                    res += (__half2float(qa) - hn[i]) + (__half2float(qb) - hn[i + 1]);
+                    hs[i] = __half2float(qa);
+                    hs[i + 1] = __half2float(qb);
+                    res += (hs[i] - hn[i]) + (hs[i + 1] - hn[i + 1]);
                     f[i * d.plane + o] = qa;
                     f[(i + 1) * d.plane + o] = qb;
                 }
                 st = st * 1664525u + 1013904223u;
-                f[o] = __ushort_as_half((unsigned short)(rs_pack(hn[0] - res, 0.0f, st) & 0xFFFFu));
-            } else {
+                const __half q0 = __ushort_as_half((unsigned short)(rs_pack(hn[0] - res, 0.0f, st) & 0xFFFFu));
+                f[o] = q0;
+                hs[0] = __half2float(q0);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i * d.plane + o] = encode<MODE>(decode<MODE>(fs[i]) + (fn[i] - fo[i]));
+                for (int i = 0; i < 9; ++i) hs[i] *= F16_UNSCALE;
+                f16_refs(f, d.plane, d.pitch, d.nx, d.ny, it.x, it.y, tt);
+                put_moments_f16(d, c, hs, tt);
+            } else {
+                R P[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    const S v = encode<MODE>(decode<MODE>(fs[i]) + (fn[i] - fo[i]));
+                    f[i * d.plane + o] = v;
+                    P[i] = decode<MODE>(v);
+                }
+                put_moments_p<R>(d, c, P);
             }
-            // the moment fields follow the corrected state (the cells left alone keep theirs), so
-            // the metric pass after the correction need not recompute them
-            cell_moments<MODE>(f, d, it);
         }
     }
 }

@@ -215,3 +215,28 @@ def test_admission_into_retired_space_with_retune_matches_alone():
     bt.close()
     assert sa == sm == 2 * K
     assert np.array_equal(fa, fm)
+
+
+@pytest.mark.parametrize("storage", [B.PL_F32, B.PL_F16_OFFSET])
+def test_interval_metrics_equal_a_fresh_metric_pass(storage):
+    """A batch interval's metric pass reads the moment fields that the correction's apply pass
+    leaves current (it skips its own moments pass).  Its records equal, bit for bit, those of a
+    fresh metric pass of the same state (the single-lattice API, which recomputes the moments
+    from the stored populations)."""
+    job = jobs_mix(storage)[3]
+    blob = wl.mlp_weights(65)
+    bt = B.Batch(storage, B.PL_MLP_F32, K, budget_for([job]))
+    bt.set_weights(blob)
+    jid = bt.submit(job)
+    bt.advance(4)
+    live = {r["id"]: r for r in B.pl_batch_metrics(bt.h)}[jid]["metrics"]
+    lat = B.Lattice(B.job_params(job))
+    lat.init_droplets(job.droplets, job.rho_in, job.rho_out, job.width, job.noise_amp, job.seed)
+    lat.set_weights(blob)
+    lat.run(4 * K, K)
+    assert np.array_equal(bt.state(jid)[0], lat.state()[0])
+    fresh = lat.metrics()
+    bt.close()
+    for key in ("mass", "W", "G_max", "delta_rho", "W_eff", "E_int", "rho_max", "rho_min", "sum_g", "sum_g2",
+                "count", "R_eq", "rho_in", "rho_out", "p_in", "p_out", "dP"):
+        assert live[key] == fresh[key] or (np.isnan(live[key]) and np.isnan(fresh[key])), (key, live[key], fresh[key])
