@@ -255,6 +255,67 @@ def test_laplace_pressure_jump_linear_in_inverse_radius():
     assert abs(b) < 0.1 * y.min()
 
 
+def test_laplace_top_hat_closed_form():
+    """A top-hat droplet (rho = a on the cells within R0 of the centre, b elsewhere; the centre
+    off the grid and near a corner, so the disk wraps across both periodic edges): the
+    equimolar radius is sqrt(n_disk / pi) exactly (the excess mass is n_disk (a - b)), and the
+    inner and outer regions hold a and b alone, so rho_in = a, rho_out = b, p_in = p(a),
+    p_out = p(b) exactly, on both iterations."""
+    nx, ny, a, b, R0, G = 53, 47, 2.1, 0.12, 9.3, -5.5
+    cx, cy = 50.6, 3.2
+    dx = np.abs(np.arange(nx) - cx)
+    dx = np.minimum(dx, nx - dx)
+    dy = np.abs(np.arange(ny) - cy)
+    dy = np.minimum(dy, ny - dy)
+    d = np.hypot(dx[None, :], dy[:, None])
+    rho = np.where(d < R0, a, b)
+    L = O.laplace(rho, cx, cy, 1.0, G)
+    assert L["R_eq"] == pytest.approx(np.sqrt((d < R0).sum() / np.pi), rel=1e-14)
+    assert L["rho_in"] == pytest.approx(a, rel=1e-15) and L["rho_out"] == pytest.approx(b, rel=1e-15)
+    assert L["p_in"] == pytest.approx(O.pressure(a, G), rel=1e-14)
+    assert L["p_out"] == pytest.approx(O.pressure(b, G), rel=1e-14)
+
+
+def test_laplace_regions_by_brute_force():
+    """A radially varying droplet on a small non-square lattice, centred across the periodic
+    corner: the estimator's two iterations recomputed cell by cell (pure-Python loops over the
+    minimum-image distance, inner region d < R_eq / 2, outer region d > R_eq + 4 width, starting
+    from rho_in = max rho, rho_out = min rho) give the oracle's six numbers.  A region radius or
+    boundary off by a cell, a missed periodic image or one iteration fewer fails this."""
+    nx, ny, G, width = 29, 23, -5.3, 1.5
+    cx, cy = 27.4, 1.8
+    rng = np.random.default_rng(3)
+    rho = np.empty((ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            ddx = min(abs(x - cx), nx - abs(x - cx))
+            ddy = min(abs(y - cy), ny - abs(y - cy))
+            d = (ddx * ddx + ddy * ddy) ** 0.5
+            rho[y, x] = 0.2 + 0.9 * (1.0 - np.tanh((d - 6.0) / width)) + 0.05 * np.cos(d)
+    rho += 0.01 * rng.random((ny, nx))
+    rin, rout = rho.max(), rho.min()
+    for _ in range(2):
+        excess = sum(rho[y, x] - rout for y in range(ny) for x in range(nx))
+        req = (excess / (np.pi * (rin - rout))) ** 0.5
+        inner, outer = [], []
+        for y in range(ny):
+            for x in range(nx):
+                ddx = min(abs(x - cx), nx - abs(x - cx))
+                ddy = min(abs(y - cy), ny - abs(y - cy))
+                d = (ddx * ddx + ddy * ddy) ** 0.5
+                if d < 0.5 * req:
+                    inner.append(rho[y, x])
+                if d > req + 4.0 * width:
+                    outer.append(rho[y, x])
+        rin, rout = sum(inner) / len(inner), sum(outer) / len(outer)
+        pin = sum(O.pressure(r, G) for r in inner) / len(inner)
+        pout = sum(O.pressure(r, G) for r in outer) / len(outer)
+    L = O.laplace(rho, cx, cy, width, G)
+    for key, val in (("R_eq", req), ("rho_in", rin), ("rho_out", rout), ("p_in", pin), ("p_out", pout),
+                     ("dP", pin - pout)):
+        assert L[key] == pytest.approx(val, rel=1e-12, abs=1e-14), key
+
+
 def test_centred_droplet_keeps_d4_symmetry():
     n = 64
     f = O.init_equilibrium(O.init_rho(n, n, [(32.0, 32.0, 12.0)], 2.0, 0.15, 2.0, 0.0, 1))
