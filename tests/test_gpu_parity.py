@@ -76,6 +76,48 @@ def test_step_matches_oracle(storage, nx, ny, tau):
     assert np.abs(f - fo).max() <= tol * np.abs(fo).max()
 
 
+# ----------------------------------------------------------------------------- degenerate cases
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_uniform_fluid_at_rest_stays_at_rest(storage):
+    """A uniform density at rest is a fixed point of Eq. 1 (zero force, equilibrium populations),
+    and a stable one below the critical coupling (G = -3 against -4 for this pseudopotential;
+    inside the spinodal, e.g. rho = 0.7 at G = -5.5, rounding noise grows into phase
+    separation, as it must): after 50 steps every cell's density is the initial one and its
+    momentum zero, to the storage's rounding (FP16: offsets of a rest state against per-cell
+    references are a fixed small value, rounded stochastically each step)."""
+    nx, ny, rho0 = 40, 24, 0.7
+    lat = lattice(nx, ny, storage, G=-3.0, tau=0.9)
+    lat.init_rho(np.full((ny, nx), rho0))
+    lat.step(50)
+    f, _ = lat.state()
+    rho = f.sum(axis=0)
+    jx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7])
+    jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8])
+    tol = {F64: 1e-14, F32: 1e-6, F16: 2e-5}[storage]
+    assert np.abs(rho - rho0).max() <= tol * rho0
+    assert max(np.abs(jx).max(), np.abs(jy).max()) <= tol * rho0
+    m = lat.metrics()
+    assert m["status"] == 0 and m["W"] == 0.0
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_no_interaction_droplet_matches_oracle(storage):
+    """G = 0: no Shan-Chen force, the droplet only relaxes and diffuses (no phase separation);
+    20 steps against the oracle.  Tolerances of the three-step test above, the FP16 one scaled
+    by sqrt(20 / 3) for the stochastic rounding of every step accumulating as a random walk."""
+    nx, ny = 48, 40
+    f0 = stored(S.oracle_droplet_state(nx, ny, [(24.0, 20.0, 9.0)], steps=0, seed=5), storage)
+    lat = lattice(nx, ny, storage, G=0.0, tau=1.0)
+    lat.set_state(f0, 0)
+    lat.step(20)
+    f, _ = lat.state()
+    fo = f0.copy()
+    O.step(fo, 20, 0.0, 1.0)
+    tol = {F64: 1e-13, F32: 2e-6, F16: 2e-3 * (20 / 3) ** 0.5}[storage]
+    assert np.abs(f - fo).max() <= tol * np.abs(fo).max()
+
+
 # ----------------------------------------------------------------------------- coupled droplet runs
 
 def test_single_64_fp64_coupled_run_matches_oracle():
