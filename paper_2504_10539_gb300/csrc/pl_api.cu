@@ -104,7 +104,10 @@ void set_chunks(LatDesc& d, int rows_per_chunk) {
 
 void set_chunks_single(LatDesc& d, int storage) {
     long long chunks = (long long)step_capacity_warps(storage) / d.nstrips;
-    const long long max_chunks = d.ny / 8 > 0 ? d.ny / 8 : 1;
+    // chunks of at least 8 rows (each chunk walks two rows more than it relaxes), FP64 of at
+    // least 2: FP64 lattices are bound by the FP64 rate of the SMs their warps occupy
+    const int min_rows = storage == PL_F64 ? 2 : 8;
+    const long long max_chunks = d.ny / min_rows > 0 ? d.ny / min_rows : 1;
     if (chunks > max_chunks) chunks = max_chunks;
     if (chunks < 1) chunks = 1;
     d.chunks = (int)chunks;

@@ -761,7 +761,13 @@ __global__ void __launch_bounds__(StepCfg<MODE>::threads, StepCfg<MODE>::min_blo
     const int n = t.hdr->n;
     const uint32_t seq = t.seq[parity];
     if (blockIdx.x == 0 && threadIdx.x == 0) t.seq[parity ^ 1] = seq + 1u;
-    for (long long vw = ((long long)blockIdx.x * TH + threadIdx.x) >> 5; vw < total; vw += P) {
+    // when the table has fewer virtual warps than the grid has warps, consecutive virtual warps
+    // go to different blocks (SMs), so a small lattice's few warps spread over as many SMs as
+    // they can instead of filling the first blocks; else the warps of a block take
+    // consecutive virtual warps (neighbouring strips, whose shared columns then hit in L1)
+    const long long w = threadIdx.x >> 5;
+    const long long vw0 = total < P ? w * gridDim.x + blockIdx.x : (long long)blockIdx.x * (TH / 32) + w;
+    for (long long vw = vw0; vw < total; vw += P) {
         const int j = find_seg(t.warp_pre, n, vw);
         const LatDesc& d = t.d[j];
         const long long local = vw - t.warp_pre[j];
