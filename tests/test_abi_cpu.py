@@ -116,3 +116,55 @@ def test_train_params_default_and_argument_checks(lib):
     assert lib.pl_trainer_bytes(ctypes.byref(p), 0, ctypes.byref(out)) == B.PL_ERR_INVALID_ARG
     assert lib.pl_train(None, 1) == B.PL_ERR_INVALID_ARG
     assert lib.pl_trainer_destroy(None) == B.PL_ERR_INVALID_ARG
+
+
+def test_batch_sizes_follow_storage_and_job_count(lib):
+    # arena bytes of one job: two population buffers and the per-cell scratch fields (density,
+    # momentum, gradient, network output), without the single-lattice handle's own weights and
+    # table, ordered by storage width like a single lattice's
+    p = B.pl_params_default(128, 96)
+    n32 = B.pl_batch_job_bytes(p)
+    assert 2 * 9 * 128 * 96 * 4 + 7 * 128 * 96 * 4 <= n32 < B.pl_lattice_bytes(p)
+    p.storage = B.PL_F16_OFFSET
+    n16 = B.pl_batch_job_bytes(p)
+    assert 2 * 10 * 128 * 96 * 2 <= n16 < n32
+    p.storage, p.mlp = B.PL_F64, B.PL_MLP_F64
+    assert B.pl_batch_job_bytes(p) > n32 >= 2 * 9 * 128 * 96 * 4
+    # the head grows with the job table and not with anything else
+    heads = [B.pl_batch_overhead_bytes(m) for m in (1, 2, 64, 256, 4096)]
+    assert all(a < b for a, b in zip(heads, heads[1:]))
+    out = ctypes.c_size_t(0)
+    for m in (0, -1, (1 << 20) + 1):
+        assert lib.pl_batch_overhead_bytes(m, ctypes.byref(out)) == B.PL_ERR_INVALID_ARG
+    bad = B.pl_params_default(16, 16)
+    bad.tau = 0.5
+    assert lib.pl_batch_job_bytes(ctypes.byref(bad), ctypes.byref(out)) == B.PL_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("storage,mlp,K,max_jobs,addr,status", [
+    (7, B.PL_MLP_BF16, 100, 8, 0x1000, B.PL_ERR_INVALID_ARG),                  # unknown storage
+    (B.PL_F64, B.PL_MLP_BF16, 100, 8, 0x1000, B.PL_ERR_INVALID_ARG),           # FP64 storage needs the FP64 network
+    (B.PL_F32, B.PL_MLP_F64, 100, 8, 0x1000, B.PL_ERR_INVALID_ARG),            # FP64 network only with FP64 storage
+    (B.PL_F16_OFFSET, B.PL_MLP_BF16, 0, 8, 0x1000, B.PL_ERR_INVALID_ARG),      # K < 1
+    (B.PL_F16_OFFSET, B.PL_MLP_BF16, 100, 0, 0x1000, B.PL_ERR_INVALID_ARG),    # no job slots
+    (B.PL_F16_OFFSET, B.PL_MLP_BF16, 100, 8, 0x1000 + 8, B.PL_ERR_INVALID_ARG),  # misaligned buffer
+    (B.PL_F16_OFFSET, B.PL_MLP_BF16, 100, 8, 0, B.PL_ERR_INVALID_ARG),         # NULL buffer
+])
+def test_batch_create_rejects_bad_arguments_without_touching_the_device(lib, storage, mlp, K, max_jobs, addr,
+                                                                        status):
+    h = ctypes.c_void_p()
+    head = B.pl_batch_overhead_bytes(8)
+    assert lib.pl_batch_create(storage, mlp, K, max_jobs, ctypes.c_void_p(addr), head + (1 << 20), None,
+                               ctypes.byref(h)) == status
+    assert h.value is None
+
+
+def test_batch_create_refuses_a_buffer_below_its_head(lib):
+    h = ctypes.c_void_p()
+    head = B.pl_batch_overhead_bytes(8)
+    assert lib.pl_batch_create(B.PL_F16_OFFSET, B.PL_MLP_BF16, 100, 8, ctypes.c_void_p(0x1000), head - 1, None,
+                               ctypes.byref(h)) == B.PL_ERR_BUDGET
+    assert h.value is None
+    for name in ("pl_batch_advance", "pl_batch_destroy"):
+        fn = getattr(lib, name)
+        assert fn(*([None] + ([1] if name == "pl_batch_advance" else []))) == B.PL_ERR_INVALID_ARG
