@@ -130,6 +130,26 @@ def test_retirement_results_and_budget():
     assert bt.poll()[0]["steps"] == 2 * K
 
 
+def test_empty_batch_and_weights_order():
+    """A batch refuses to advance before it has weights (PL_ERR_STATE); with weights and no job,
+    advancing does nothing; a job submitted afterwards runs and retires as usual."""
+    job = jobs_mix(B.PL_F32)[0]
+    bt = B.Batch(B.PL_F32, B.PL_MLP_F32, K, budget_for([job], max_jobs=8), max_jobs=8)
+    with pytest.raises(B.PLError) as e:
+        bt.advance(1)
+    assert e.value.status == B.PL_ERR_STATE
+    bt.set_weights(job.weights())
+    bt.advance(3)
+    assert bt.poll() == [] and bt.info()["active"] == 0 and bt.info()["arena_used"] == 0
+    jid = bt.submit(job, steps=K)
+    assert jid is not None
+    bt.advance(1)
+    res = bt.poll()
+    assert [r["id"] for r in res] == [jid] and res[0]["status"] == 0 and res[0]["steps"] == K
+    assert res[0]["metrics"]["corrections"] == 1
+    bt.close()
+
+
 def test_fault_in_one_job_leaves_the_others_untouched():
     jobs = jobs_mix(B.PL_F32)[:3]
     bad = wl.Lattice(80, 80, storage=B.PL_F32, mlp=wl.MLP_F32, droplets=[(40.0, 40.0, 15.0)], rho_in=2.0,

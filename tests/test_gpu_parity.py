@@ -102,6 +102,26 @@ def test_uniform_fluid_at_rest_stays_at_rest(storage):
 
 
 @pytest.mark.parametrize("storage", [F64, F32, F16])
+def test_correction_without_an_interface_changes_nothing(storage):
+    """A uniform field has no density gradient: G_max = 0, the mask m is 0 in every cell, and
+    the correction (Sec. II-C, as the oracle reads it) changes no population and reports OK,
+    in the oracle and on the GPU alike."""
+    nx, ny = 40, 24
+    blob = wl.mlp_weights(42)
+    lat = lattice(nx, ny, storage)
+    lat.init_rho(np.full((ny, nx), 0.7))
+    lat.set_weights(blob)
+    f0, step0 = lat.state()
+    lat.correct()
+    f1, step1 = lat.state()
+    assert step1 == step0 and np.array_equal(f1, f0)
+    assert lat.status() == 0
+    fo = f0.copy()
+    assert O.correct(fo, blob, 0.1, 0.01, O.mass(f0), O.MLP_F64) == 0
+    assert np.array_equal(fo, f0)
+
+
+@pytest.mark.parametrize("storage", [F64, F32, F16])
 def test_no_interaction_droplet_matches_oracle(storage):
     """G = 0: no Shan-Chen force, the droplet only relaxes and diffuses (no phase separation);
     20 steps against the oracle.  Tolerances of the three-step test above, the FP16 one scaled
