@@ -89,3 +89,43 @@ def test_identical_requests_keep_their_own_index_and_wait_for_memory():
     # admission in arrival order: the i-th admitted job is request i
     assert [x["request"] for x in sorted(out["results"], key=lambda x: x["id"])] == list(range(6))
     assert max(x["admitted_interval"] for x in out["results"]) > 0
+
+
+class SlowFakeBatch(FakeBatch):
+    """An interval takes `dt` seconds of wall clock, like a device interval would."""
+
+    def __init__(self, arena, K, dt):
+        super().__init__(arena, K)
+        self.dt = dt
+
+    def advance(self, n=1):
+        import time
+        time.sleep(self.dt * n)
+        super().advance(n)
+
+
+@pytest.mark.timeout(60)
+def test_reported_statistics_follow_the_results():
+    """Three requests 50 ms apart, each three intervals of 30 ms (250 steps rounded up to 300):
+    they overlap on the device; every reported figure is the one the per-request results give."""
+    import numpy as np
+    r = [wl.Request(0.05 * k, wl.Lattice(32, 32, steps=250, K=100)) for k in range(3)]
+    srv = S.Server(wl.F16_OFFSET, wl.MLP_BF16, 100, 0, None, batch=SlowFakeBatch(10 * 32 * 32, 100, 0.03))
+    out = srv.run(r)
+    assert out["jobs_done"] == 3 and out["jobs_rejected"] == 0 and out["statuses"] == {0: 3}
+    res = sorted(out["results"], key=lambda x: x["request"])
+    for x, q in zip(res, r):
+        assert x["steps"] == 300
+        assert q.arrival_s <= x["admitted_s"] <= x["done_s"]
+        assert x["done_s"] - x["admitted_s"] >= 3 * 0.03 * 0.9      # three intervals on the device
+        assert x["done_interval"] - x["admitted_interval"] == 3
+    lat = [x["done_s"] - q.arrival_s for x, q in zip(res, r)]
+    wait = [x["admitted_s"] - q.arrival_s for x, q in zip(res, r)]
+    assert out["p50_latency_s"] == float(np.percentile(lat, 50))
+    assert out["p99_latency_s"] == float(np.percentile(lat, 99))
+    assert out["p50_queue_wait_s"] == float(np.percentile(wait, 50))
+    assert out["peak_active_jobs"] >= 2                               # arrivals while others run
+    work = 3 * 32 * 32 * 300
+    assert out["served_mlups"] == pytest.approx(work / out["elapsed_s"] / 1e6)
+    assert out["offered_mlups"] == pytest.approx(work / 0.1 / 1e6)    # over the arrival span
+    assert out["elapsed_s"] >= 0.1 + 3 * 0.03 * 0.9                   # the last request's own run
