@@ -487,6 +487,69 @@ def test_mlp_single_path_composition():
     assert out[0] == 0.0 and out[2] == 0.0
 
 
+def _bf16_bits(v):
+    """Nearest BF16 value (ties to even) by integer rounding of the FP64 bit pattern: 45 of the
+    52 mantissa bits dropped (BF16 keeps 7), the carry running into the exponent; normal
+    numbers only.  An independent route to the rounding the oracle does with frexp/nearbyint."""
+    import struct
+    b = struct.unpack("<Q", struct.pack("<d", v))[0]
+    drop = 45
+    lower, half = b & ((1 << drop) - 1), 1 << (drop - 1)
+    b >>= drop
+    if lower > half or (lower == half and (b & 1)):
+        b += 1
+    return struct.unpack("<d", struct.pack("<Q", b << drop))[0]
+
+
+def test_mlp_bf16_emulation_single_path_closed_form():
+    """The tensor-core form rounds exactly these values to BF16: the activations h1, h2, h3 that
+    feed the MMA layers 2-4 and the weights of those layers; layer 1, the biases, h4 and
+    layer 5 stay exact.  One non-zero path gives a closed form.  Its biases in layers 1-3 cancel
+    the path's input down to four rounding steps of it, so that one rounding more or less
+    anywhere (an activation, a weight, a bias) changes a later BF16 activation and with it the
+    output by more than 1e-12, while the oracle must match the closed form to the last bit."""
+    dims = wl.MLP_DIMS
+    offs = _offsets()
+    path = [(3, 1), (70, 3), (5, 70), (40, 5), (1, 40)]
+    R = _bf16_bits
+    ws = [float(np.float32(w)) for w in (0.7071, -1.2345, 0.55555, 1.9999, -0.6180)]
+    y = -0.3
+    bs, h = [], y
+    for l in range(3):
+        w = R(ws[l]) if l >= 1 else ws[l]
+        bs.append(float(np.float32(-w * h + 4 * abs(w * h) * 2 ** -9)))
+        h = R(math.tanh(w * h + bs[l]))
+    bs += [float(np.float32(0.0789)), float(np.float32(0.3691))]
+    blob = np.zeros(wl.mlp_blob_size(), dtype=np.float32)
+    for l, ((o, i), w, b) in enumerate(zip(path, ws, bs)):
+        wo, bo = offs[l]
+        blob[wo + o * dims[l] + i] = w
+        blob[bo + o] = b
+
+    def closed_form(round_h=(1, 1, 1, 0), round_w=(0, 1, 1, 1, 0), round_b=False):
+        h = y
+        for l in range(4):
+            w = R(ws[l]) if round_w[l] else ws[l]
+            b = R(bs[l]) if round_b else bs[l]
+            h = math.tanh(w * h + b)
+            if round_h[l]:
+                h = R(h)
+        w5 = R(ws[4]) if round_w[4] else ws[4]
+        return w5 * h + bs[4]
+
+    expect = closed_form()
+    out = O.mlp_forward(blob, 0.9, y, O.MLP_BF16)
+    assert out[1] == expect
+    assert out[0] == 0.0 and out[2] == 0.0
+    # the pin's power: every other reading of what is rounded gives a visibly different output
+    alternatives = [closed_form(round_h=(0, 1, 1, 0)), closed_form(round_h=(1, 0, 1, 0)),
+                    closed_form(round_h=(1, 1, 0, 0)), closed_form(round_h=(1, 1, 1, 1)),
+                    closed_form(round_w=(1, 1, 1, 1, 0)), closed_form(round_w=(0, 0, 1, 1, 0)),
+                    closed_form(round_w=(0, 1, 0, 1, 0)), closed_form(round_w=(0, 1, 1, 0, 0)),
+                    closed_form(round_w=(0, 1, 1, 1, 1)), closed_form(round_b=True)]
+    assert min(abs(a - expect) for a in alternatives) > 1e-12
+
+
 # ----------------------------------------------------------------------------- stencil-input network
 # A variant that is not in the paper: the network also reads the density of the cell and its
 # 8 neighbours (inputs 2..10, velocity order c_0..c_8, periodic).
