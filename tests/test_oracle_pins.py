@@ -406,6 +406,22 @@ def test_metrics_bruteforce_4x4():
     assert abs(m["delta_rho"] - (rho.max() - rho.min())) < 1e-15
 
 
+def test_metrics_threshold_is_strict():
+    """Eq. 9 counts the cells whose gradient magnitude is above the threshold: a triangular
+    density wave of step 1/4 (exact in binary) has |grad rho| = 1/4 exactly in 6 of every 8
+    columns and 0 in the other 2, so a threshold of 1/4 counts none of them and one just below
+    counts all six; G_max, W_eff and E_int follow exactly."""
+    row = np.array([1.0, 1.25, 1.5, 1.75, 2.0, 1.75, 1.5, 1.25])
+    ny = 3
+    rho = np.tile(row, (ny, 1))
+    at = O.metrics_rho(rho, threshold=0.25)
+    below = O.metrics_rho(rho, threshold=0.25 - 2 ** -20)
+    assert at["count"] == 0 and at["W"] == 0.0
+    assert below["count"] == 6 * ny and below["W"] == 0.75
+    assert at["G_max"] == 0.25 and at["W_eff"] == 0.75 and at["E_int"] == 6 * ny * 0.0625
+    assert at["delta_rho"] == 1.0 and at["mass"] == ny * row.sum()
+
+
 def test_metrics_uniform_field_has_no_interface():
     m = O.metrics_rho(np.full((5, 6), 1.3))
     assert m["G_max"] == 0.0 and m["W_eff"] == 0.0 and m["E_int"] == 0.0 and m["W"] == 0.0
