@@ -700,6 +700,38 @@ def test_correction_moves_interface_density_toward_network():
     assert after < before
 
 
+def test_correction_closed_form_on_a_sine_field_at_rest():
+    """A density wave rho = a + b sin(theta), theta = 2 pi x / nx, at rest, with a network whose
+    output is its bias (rho^, u^) everywhere.  Eq. 16 gives g = |b cos(theta) sin(2 pi / nx)|,
+    so the mask m = g / G_max is |cos(theta)|; the sums of m sin(theta) and m^2 sin(theta) over
+    a period vanish, so the m-weighted projections remove exactly (rho^ - a) and a u^:
+    rho' = rho - beta_rho m b sin(theta) (whatever rho^ is), j' = beta_u m u^ (rho' - a), and every
+    cell ends at the equilibrium of (rho', j' / rho').  A mask not normalised by G_max, a
+    projection weighted otherwise, or a dropped gain fails it."""
+    nx, ny, a, b = 16, 4, 1.0, 0.3
+    f = O.init_equilibrium(wl.sine_rho(nx, ny, a, b))
+    f0 = f.copy()
+    blob = np.zeros(wl.mlp_blob_size(), dtype=np.float32)
+    blob[-3:] = [0.9, 0.05, -0.03]
+    rh, ux, uy = (float(v) for v in blob[-3:])
+    beta, beta_u = 0.3, 0.2
+    assert O.correct(f, blob, beta, beta_u, O.mass(f0), O.MLP_F64) == 0
+    th = 2 * np.pi * np.arange(nx) / nx
+    m = np.abs(np.cos(th))
+    rp = a + b * np.sin(th) - beta * m * b * np.sin(th)
+    for x in range(nx):
+        fe = O.equilibrium(rp[x], beta_u * m[x] * ux * (rp[x] - a) / rp[x],
+                           beta_u * m[x] * uy * (rp[x] - a) / rp[x])
+        for y in range(ny):
+            assert np.abs(f[:, y, x] - fe).max() < 1e-15, (x, y)
+    # the closed form is not the identity, and rho^ does not enter it
+    assert np.abs(f - f0).max() > 1e-3
+    blob[-3] = 1.7
+    f2 = f0.copy()
+    assert O.correct(f2, blob, beta, beta_u, O.mass(f0), O.MLP_F64) == 0
+    assert np.abs(f2 - f).max() < 1e-15
+
+
 def test_correction_rejects_nonphysical_result():
     f = _droplet_state()
     f0 = f.copy()
