@@ -18,8 +18,8 @@ single-lattice API ("fp32_plain"); a served Poisson request stream (continuous
 batching, p50/p99 latency, offered vs served MLUPS); the single 4096x4096 droplet
 field with FP16 and FP32 storage (step-kernel HBM fractions); the FP64 CPU oracle on
 a bounded sample (cpu_baseline).  --impl reference times that oracle alone.
-Multi-GPU (torchrun): every rank runs an independent replica (weak scaling, no
-collective on the data path).
+Multi-GPU (torchrun): every rank runs an independent replica of the same batch (weak
+scaling, no collective on the data path).
 """
 import argparse
 import ctypes
@@ -443,7 +443,9 @@ def run_gb300(args):
     K = 100
     n_e2e = 0 if args.no_e2e else min(args.steps, 5)
     n_int = args.warmup + args.steps + n_e2e + 2     # no job retires before the last timed interval
-    jobs = wl.batch_256(n=args.lattices, seed=4 + rank, steps=n_int * K, K=K)
+    # every rank runs the same batch (replicas: the per-GPU work is fixed as N grows, so the
+    # updates of all ranks are the per-rank updates times N)
+    jobs = wl.batch_256(n=args.lattices, seed=4, steps=n_int * K, K=K)
     blob = np.ascontiguousarray(jobs[0].weights())
     cells = sum(j.cells for j in jobs)
     budget = B.pl_batch_overhead_bytes(len(jobs) + 1) + sum(B.pl_batch_job_bytes(B.job_params(j)) for j in jobs)
