@@ -504,7 +504,7 @@ def run_gb300(args):
 
     # --------------------------------------------------------------- plain per-lattice FP32
     fp32 = None
-    if not args.no_fp32:
+    if not args.no_fp32 and world == 1:     # a per-GPU comparison: one GPU only
         lats = []
         t_plain = 0.0
         n_plain = 2
