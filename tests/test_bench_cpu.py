@@ -66,3 +66,22 @@ def test_step_kernel_hash_covers_only_the_step_sources():
     from paper_2504_10539_gb300 import build as PB
     assert bench.step_kernel_hash() == PB.source_hash(("pl_step.cu", "pl_device.cuh", "pl_kernels.h"))
     assert bench.library_hash() == PB.source_hash() != bench.step_kernel_hash()
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` times the oracle on host cores and prints one JSON line with
+    the benchmark's metric, its own CPU-baseline description and an end-to-end figure without
+    device copies."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--lattices", "8"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "MLUPS" and d["unit"] == "MLUPS"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 0
+    assert d["config"]["workload"] == "batch_8" and d["dtype"] == "f64"
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
