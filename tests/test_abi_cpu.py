@@ -168,3 +168,47 @@ def test_batch_create_refuses_a_buffer_below_its_head(lib):
     for name in ("pl_batch_advance", "pl_batch_destroy"):
         fn = getattr(lib, name)
         assert fn(*([None] + ([1] if name == "pl_batch_advance" else []))) == B.PL_ERR_INVALID_ARG
+
+
+def _c_layout():
+    """sizeof / offsetof of every ABI struct and the value of every #define constant, as the C
+    compiler sees include/pinnlbm.h."""
+    import shutil
+    import subprocess
+    import tempfile
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"pl_params": B.pl_params, "pl_droplet": B.pl_droplet, "pl_metric_record": B.pl_metric_record,
+               "pl_job_result": B.pl_job_result, "pl_train_params": B.pl_train_params}
+    consts = sorted(n for n in dir(B) if re.fullmatch(r"PL_[A-Z0-9_]+", n))
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pinnlbm.h"', "int main(void) {"]
+    for s, cls in structs.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    for c in consts:
+        lines.append('printf("%s %%ld\\n", (long)(%s));' % (c, c))
+    lines += ["return 0;", "}"]
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    vals = {}
+    for ln in out.splitlines():
+        parts = ln.split()
+        vals[" ".join(parts[:-1])] = int(parts[-1])
+    return structs, consts, vals
+
+
+def test_binding_structs_and_constants_match_the_header():
+    structs, consts, c = _c_layout()
+    for s, cls in structs.items():
+        assert c["%s size" % s] == ctypes.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert c["%s.%s" % (s, f)] == getattr(cls, f).offset, (s, f)
+    for name in consts:
+        assert c[name] == getattr(B, name), name
+    # the Python-side codes of the input generators are the header's
+    assert (wl.F64, wl.F32, wl.F16_OFFSET) == (c["PL_F64"], c["PL_F32"], c["PL_F16_OFFSET"])
+    assert (wl.MLP_F64, wl.MLP_F32, wl.MLP_BF16) == (c["PL_MLP_F64"], c["PL_MLP_F32"], c["PL_MLP_BF16"])
